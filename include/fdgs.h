@@ -1,0 +1,237 @@
+/*
+ * fdgs.h - C ABI of the GB300 masked 4D Gaussian splatting rasterizer (libfdgs.so).
+ *
+ * The library renders 4D Gaussian scenes at a timestamp t (4DGS-1K, arXiv 2503.16422):
+ * key-frame mask gate (Sec. 4.2.2), slice of each 4D Gaussian into a conditional 3D Gaussian
+ * and a temporal weight (Sec. 3, Eq. 1 and Eq. 3), EWA projection, 16x16 tile binning,
+ * (tile, depth) ordering and front-to-back alpha compositing (Sec. 3, Eq. 2); its reverse
+ * (gradients for fine-tuning, Sec. 4.2.1 "Pruning" and Sec. 5 "Implementation Details"); the
+ * spatial-temporal variation score used for pruning (Sec. 4.2.1, Eqs. 4-7); and batched
+ * rendering of many (camera, t, resolution) requests in one call.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an fdgs_status. Nothing is thrown across the ABI; on a non-OK status
+ *    fdgs_last_error() returns a message for the calling thread.
+ *  - Pointers named *_dev are CUDA device pointers on the scene's device; all others are host
+ *    pointers. Float arrays are float32, little-endian, densely packed.
+ *  - Calls are stream-ordered on the given stream (NULL = legacy default stream). Unless a
+ *    call says it synchronises, it may return before the GPU work finishes. Errors detected
+ *    on the device (key capacity, spin-wait limit) are recorded in the scene's status word
+ *    and returned by fdgs_status_sync() or by the next call that synchronises.
+ *  - A scene is not thread-safe: calls on one scene must be serialised by the caller.
+ */
+#ifndef FDGS_H
+#define FDGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; declared here so that this header needs no CUDA headers. */
+typedef struct CUstream_st *fdgs_stream;
+
+typedef enum {
+  FDGS_OK = 0,
+  FDGS_ERR_INVALID = -1,   /* bad argument (null pointer, size, degree, camera) */
+  FDGS_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+  FDGS_ERR_OOM = -3,       /* device allocation failed */
+  FDGS_ERR_CAPACITY = -4,  /* a fixed-capacity buffer would overflow (batched path) */
+  FDGS_ERR_TIMEOUT = -5,   /* a device spin-wait hit its iteration limit */
+  FDGS_ERR_STATE = -6      /* call out of order (e.g. backward of a released frame) */
+} fdgs_status;
+
+typedef struct fdgs_scene fdgs_scene;   /* opaque, owned by the library */
+typedef struct fdgs_frame fdgs_frame;   /* opaque per-render state kept for the backward */
+
+/*
+ * Scene description (Sec. 3: mean mu in R^4, scales S_4D, left/right quaternions q_l, q_r,
+ * opacity sigma, colour c(d)). Structure of arrays, all device pointers, BORROWED: the
+ * scene reads them at every render and never frees them, so in-place parameter updates are
+ * seen without re-creating the scene. They must stay valid until fdgs_destroy_scene.
+ *   mean4         [n][4]  (x, y, z, t), 16-byte aligned
+ *   logscale4     [n][4]  log of the four axis scales; s = exp(logscale), Sigma = R S S^T R^T
+ *   q_left        [n][4]  left quaternion (w, x, y, z), normalised by the renderer
+ *   q_right       [n][4]  right quaternion (w, x, y, z), normalised by the renderer
+ *   opacity_logit [n]     sigma = 1 / (1 + exp(-opacity_logit))
+ *   sh            [K][3][n], K = (sh_degree + 1)^2 real spherical-harmonic coefficients per
+ *                 channel; colour = max(0, sum_k Y_k(d) sh[k][c] + 0.5), d the unit direction
+ *                 from the camera centre to the conditional mean.
+ * sh_degree is 0..3. n may be 0. n must be < 2^30.
+ */
+typedef struct {
+  int64_t n;
+  int sh_degree;
+  const float *mean4;
+  const float *logscale4;
+  const float *q_left;
+  const float *q_right;
+  const float *opacity_logit;
+  const float *sh;
+} fdgs_scene_desc;
+
+/*
+ * Pinhole camera. viewmat: world->camera rigid transform, row-major 4x4, OpenCV axes
+ * (x right, y down, z forward). Pixel (i, j) is evaluated at image coordinate (i, j), so the
+ * image centre is ((width-1)/2, (height-1)/2). Gaussians whose camera-space depth is
+ * <= znear are culled. width, height in 1..16384.
+ */
+typedef struct {
+  float viewmat[16];
+  float fx, fy, cx, cy;
+  int width, height;
+  float znear;
+} fdgs_camera;
+
+/* use_mask: gate Gaussians by the key-frame masks given to fdgs_set_active_mask (ignored
+ * when none are set). bg: background colour added as T_final * bg. */
+typedef struct {
+  int use_mask;
+  float bg[3];
+} fdgs_render_opts;
+
+/* Counts of one rendered frame, for reports and tests. */
+typedef struct {
+  int64_t n_active;    /* Gaussians that passed the mask gate */
+  int64_t n_visible;   /* Gaussians that touch at least one tile */
+  int64_t n_keys;      /* (tile, Gaussian) pairs, i.e. total length of the tile lists */
+  int width, height, tiles_x, tiles_y;
+  int key_l, key_r;    /* key-frames used by the mask gate, -1 when unmasked */
+  int key_bytes;       /* 4 or 8: width of the packed (tile, depth-rank) sort key */
+} fdgs_frame_stats;
+
+/* Creates a scene on the current CUDA device. Borrows the attribute pointers (see above).
+ * Errors: FDGS_ERR_INVALID (null desc/out, n < 0, degree outside 0..3, null attribute pointer
+ * with n > 0), FDGS_ERR_CUDA. */
+int fdgs_create_scene(const fdgs_scene_desc *desc, fdgs_scene **out);
+
+/* Frees the scene's workspaces and mask copy. Frames of the scene must be released first;
+ * any still held are released here. NULL is accepted. Synchronises the device. */
+int fdgs_destroy_scene(fdgs_scene *scene);
+
+/* Replaces the scene's attribute pointers (same n and degree rules as creation). */
+int fdgs_update_scene(fdgs_scene *scene, const fdgs_scene_desc *desc);
+
+/*
+ * Key-frame temporal filter (Sec. 4.2.2). bits_dev: [n_key][ceil(n/8)] bytes, one row per
+ * key-frame, Gaussian i active in row k iff bit (i & 7) of byte (i >> 3) is set (LSB-first,
+ * the "mask compressed into bits" of Sec. 5). key_times: n_key ascending host floats. The
+ * scene COPIES the bits (device to device, on the stream) into its own padded storage.
+ * At render time t the active set is the union of rows l and r, where l is the last key-frame
+ * with time <= t (0 if t precedes all) and r = min(l + 1, n_key - 1). n_key = 0 clears the
+ * masks. Errors: FDGS_ERR_INVALID (null pointers with n_key > 0, times not ascending).
+ */
+int fdgs_set_active_mask(fdgs_scene *scene, const uint8_t *bits_dev, const float *key_times,
+                         int n_key, fdgs_stream stream);
+
+/*
+ * Renders the scene from camera cam at time t (Sec. 3, Eqs. 1-3; mask gate Sec. 4.2.2).
+ * rgb_out_dev: [3][height][width] float32, written completely. If frame_out is non-NULL
+ * a frame holding what the backward needs is returned (release it with
+ * fdgs_frame_release); with NULL the scene's own workspace is reused.
+ * Synchronises the stream once, after the per-Gaussian stage, to size the key buffers.
+ */
+int fdgs_render(fdgs_scene *scene, const fdgs_camera *cam, float t,
+                const fdgs_render_opts *opts, float *rgb_out_dev, fdgs_frame **frame_out,
+                fdgs_stream stream);
+
+/*
+ * Reverse of fdgs_render for the frame (reverse-order per-tile replay that recovers
+ * transmittance by division, then the chain to the 4D parameters). dL_drgb_dev is
+ * [3][height][width]. Gradients are ADDED (+=) into the caller's buffers, laid out like the
+ * scene attributes: g_mean4 [n][4], g_logscale4 [n][4], g_q_left [n][4], g_q_right [n][4],
+ * g_opacity_logit [n], g_sh [K][3][n]. Any gradient pointer may be NULL to skip it.
+ * The scene attributes must not have changed since the render.
+ * Errors: FDGS_ERR_STATE if the frame does not belong to the scene.
+ */
+int fdgs_render_backward(fdgs_scene *scene, fdgs_frame *frame, const float *dL_drgb_dev,
+                         float *g_mean4, float *g_logscale4, float *g_q_left, float *g_q_right,
+                         float *g_opacity_logit, float *g_sh, fdgs_stream stream);
+
+/* Releases a frame (its buffers return to the scene's pool). NULL is accepted. */
+int fdgs_frame_release(fdgs_frame *frame);
+
+/* Counts of a frame. Synchronises the frame's stream. */
+int fdgs_frame_get_stats(fdgs_frame *frame, fdgs_frame_stats *out);
+
+/*
+ * Copies a frame's internals to caller device buffers (for parity tests and tools), on the
+ * stream. Any pointer may be NULL.
+ *   tile_ranges_dev [tiles_y*tiles_x][2] uint32 [start, end) into the id list
+ *   tile_ids_dev    [n_keys] uint32 Gaussian ids, tile-major, each tile's list in blend order
+ *   T_final_dev     [height][width] float32 final transmittance
+ *   n_contrib_dev   [height][width] uint32 1 + list position of the last blended Gaussian
+ *   gauss_flags_dev [n] uint8 per-Gaussian decisions: bit0 passed the mask gate, bit1
+ *                   a = sigmoid(o) p(t) >= 1/255, bit2 depth > znear, bit3 2D determinant
+ *                   > 0, bit4 visible (non-empty tile rectangle)
+ *   records_dev     [n][12] float32 per visible Gaussian (others untouched): u, v, conic
+ *                   A, B, C, a, r, g, b, depth, radius, and the tile count as float
+ */
+int fdgs_frame_export(fdgs_frame *frame, uint32_t *tile_ranges_dev, uint32_t *tile_ids_dev,
+                      float *T_final_dev, uint32_t *n_contrib_dev, uint8_t *gauss_flags_dev,
+                      float *records_dev, fdgs_stream stream);
+
+/*
+ * Renders n_req requests (cams[i], ts[i]; each camera has its own resolution) in one
+ * batched pass: one per-Gaussian launch over all (request, Gaussian) pairs, one global sort
+ * whose tile ids are offset per request, and one persistent blend over a global tile queue.
+ * rgb_out_dev is a HOST array of n_req device pointers, each [3][h_i][w_i]. Results are
+ * identical to n_req calls of fdgs_render. Synchronises the stream once to size buffers.
+ */
+int fdgs_render_batch(fdgs_scene *scene, const fdgs_camera *cams, const float *ts, int n_req,
+                      const fdgs_render_opts *opts, float *const *rgb_out_dev,
+                      fdgs_stream stream);
+
+/*
+ * Spatial-Temporal Variation Score (Sec. 4.2.1, Eqs. 4-7), reading "per-t product":
+ *   S_i = sum over t in ts, camera in cams of  w_i(t, cam) * f_i(t) * gamma_i
+ * with w_i = sum over pixels of alpha_i T_i (Eq. 4, the blend weight), f_i(t) =
+ * 1 / (0.5 tanh|p''_i(t)| + 0.5) (Eqs. 5-6), gamma_i = clamp(V_i / V_p90, 0, 1)^0.1 with
+ * V_i the product of the four scales and V_p90 its nearest-rank 90th percentile over all n
+ * (Sec. 4.2.1 "Norm(V)", following LightGaussian). Renders use no mask. score_out_dev [n]
+ * float32 is OVERWRITTEN. batch = renders issued between accumulations (>= 1).
+ */
+int fdgs_variation_score(fdgs_scene *scene, const fdgs_camera *cams, int n_cam,
+                         const float *ts, int n_t, int batch, float *score_out_dev,
+                         fdgs_stream stream);
+
+/*
+ * Pruning keep-set (Sec. 4.2.1 "Pruning"): ranks the n scores by ascending (score, index)
+ * and clears the lowest floor(prune_ratio * n). keep_out_dev [n] uint8 gets 1 = keep,
+ * 0 = prune. Scores must be finite and >= 0. prune_ratio in [0, 1].
+ */
+int fdgs_select_keep(fdgs_scene *scene, const float *score_dev, int64_t n, float prune_ratio,
+                     uint8_t *keep_out_dev, fdgs_stream stream);
+
+/*
+ * Stage profiling of the scene's subsequent fdgs_render calls. flags bit0: record CUDA
+ * events on the render stream between the stages (FDGS_PROFILE_STAGES of them, in order:
+ * preprocess, depth_sort, gather_scan, host_sync (the one mid-frame wait for the key count),
+ * emit, tile_sort, ranges, blend); bit1: count the
+ * (Gaussian, pixel) evaluations of the blend (a slower kernel variant; use it in an
+ * untimed pass). 0 turns profiling off.
+ */
+#define FDGS_PROFILE_STAGES 8
+int fdgs_profile_enable(fdgs_scene *scene, int flags);
+
+/* Stage times in milliseconds of the last profiled render, and the blend evaluation count
+ * of the last counted render (either pointer may be NULL). Synchronises the device. */
+int fdgs_profile_read(fdgs_scene *scene, float *stage_ms, uint64_t *blend_evals);
+
+/* Reads and clears the scene's device status word (synchronises the device): FDGS_OK, or
+ * FDGS_ERR_CAPACITY / FDGS_ERR_TIMEOUT raised by a kernel since the last read. */
+int fdgs_status_sync(fdgs_scene *scene);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char *fdgs_last_error(void);
+
+/* Library version string. */
+const char *fdgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDGS_H */

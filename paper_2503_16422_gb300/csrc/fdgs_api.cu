@@ -1,0 +1,679 @@
+// C ABI of the GB300 masked 4D Gaussian rasterizer: scene and frame lifecycle, workspace
+// management and the stream-ordered launch sequence of each call (declared in fdgs.h).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "fdgs.h"
+#include "fdgs_internal.h"
+
+using namespace fdgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(FDGS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+  } while (0)
+
+#define TRY(expr)            \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != FDGS_OK) return rc_; \
+  } while (0)
+
+// Grow-only device buffer.
+struct Buf {
+  void *p = nullptr;
+  size_t n = 0;
+  template <typename T>
+  T *as() const { return static_cast<T *>(p); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+int grow(Buf &b, size_t bytes) {
+  if (bytes <= b.n && b.p) return FDGS_OK;
+  b.release();
+  const size_t nb = std::max<size_t>(bytes + bytes / 4, 256);
+  if (cudaMalloc(&b.p, nb) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(FDGS_ERR_OOM, "cudaMalloc of %zu bytes failed", nb);
+  }
+  b.n = nb;
+  return FDGS_OK;
+}
+
+int ceil_log2(uint64_t x) {  // bits needed to represent 0..x-1 (>= 1)
+  int b = 1;
+  while (b < 63 && (1ull << b) < x) ++b;
+  return b;
+}
+
+// Per-render buffers. One per frame in flight plus the scene's own.
+struct Workspace {
+  Buf ctr;                       // u32[C_COUNT]
+  uint32_t *hctr = nullptr;      // pinned host mirror of ctr
+  Buf pre_status, scan_status;   // u64 per partition of 256 Gaussians
+  Buf rec, rec_sorted;           // f32[n][12]
+  Buf vis[2];                    // u64[n] visible (depth, id) keys, ping-pong
+  Buf offsets;                   // u32[n]
+  Buf flags;                     // u8[n]
+  Buf keys[2];                   // packed (tile, rank) keys, ping-pong
+  Buf ranges;                    // uint2[tiles]
+  Buf Tf, nc;                    // f32 / u32 [pixels]
+  Buf scratch;                   // sort scratch
+  Buf g2d;                       // f32[n][9] backward accumulators
+  Buf wsum;                      // f32[n] per-rank blend weights (score pass)
+  ~Workspace() {
+    Buf *all[] = {&ctr, &pre_status, &scan_status, &rec, &rec_sorted, &vis[0], &vis[1],
+                  &offsets, &flags, &keys[0], &keys[1], &ranges, &Tf, &nc, &scratch, &g2d,
+                  &wsum};
+    for (Buf *b : all) b->release();
+    if (hctr) cudaFreeHost(hctr);
+  }
+};
+
+struct FrameMeta {
+  DevCam cam{};
+  float t = 0.f;
+  int W = 0, H = 0, gx = 0, gy = 0, l = -1, r = -1;
+  uint32_t n_active = 0, nv = 0;
+  uint64_t nkeys = 0;
+  int key64 = 0, rb = 1;
+  uint64_t *sorted = nullptr;
+  void *keys = nullptr;
+  float bg[3] = {0.f, 0.f, 0.f};
+  cudaStream_t stream = nullptr;
+};
+
+}  // namespace
+
+struct fdgs_scene {
+  fdgs_scene_desc d{};
+  int device = 0;
+  Buf masks;
+  size_t row_words = 0;
+  int n_key = 0;
+  std::vector<float> key_times;
+  Workspace main;
+  std::vector<Workspace *> pool;
+  std::set<fdgs_frame *> live;
+  Buf status;     // u32 device error bits
+  Buf aux[6];     // score pass / keep-set buffers: 0 keys, 1 gamma, 2 sort scratch,
+                  // 3 device scalar, 4 score-pass image
+  int prof = 0;   // profiling flags (fdgs_profile_enable)
+  cudaEvent_t ev[FDGS_PROFILE_STAGES + 1] = {};
+  Buf evals;      // u64 blend evaluation counter
+};
+
+struct fdgs_frame {
+  fdgs_scene *scene;
+  Workspace *ws;
+  FrameMeta m;
+};
+
+namespace {
+
+int check_desc(const fdgs_scene_desc *d) {
+  if (!d) return fail(FDGS_ERR_INVALID, "null scene description");
+  if (d->n < 0 || d->n >= (1ll << 30)) return fail(FDGS_ERR_INVALID, "n out of range");
+  if (d->sh_degree < 0 || d->sh_degree > 3)
+    return fail(FDGS_ERR_INVALID, "sh_degree must be 0..3");
+  if (d->n > 0 && (!d->mean4 || !d->logscale4 || !d->q_left || !d->q_right ||
+                   !d->opacity_logit || !d->sh))
+    return fail(FDGS_ERR_INVALID, "null attribute pointer");
+  const void *v[] = {d->mean4, d->logscale4, d->q_left, d->q_right};
+  for (const void *p : v)
+    if (((uintptr_t)p) & 15) return fail(FDGS_ERR_INVALID, "[n][4] arrays must be 16-byte aligned");
+  return FDGS_OK;
+}
+
+int make_cam(const fdgs_camera *c, DevCam &dc) {
+  if (!c) return fail(FDGS_ERR_INVALID, "null camera");
+  if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
+    return fail(FDGS_ERR_INVALID, "image size out of range");
+  if (!(c->fx > 0.f) || !(c->fy > 0.f)) return fail(FDGS_ERR_INVALID, "focal length <= 0");
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) dc.R[r * 3 + k] = c->viewmat[r * 4 + k];
+    dc.tv[r] = c->viewmat[r * 4 + 3];
+  }
+  for (int k = 0; k < 3; ++k)
+    dc.eye[k] = -(dc.R[0 * 3 + k] * dc.tv[0] + dc.R[1 * 3 + k] * dc.tv[1] +
+                  dc.R[2 * 3 + k] * dc.tv[2]);
+  dc.fx = c->fx; dc.fy = c->fy; dc.cx = c->cx; dc.cy = c->cy;
+  dc.limx = kFovClamp * ((float)c->width / (2.f * c->fx));
+  dc.limy = kFovClamp * ((float)c->height / (2.f * c->fy));
+  dc.znear = c->znear;
+  dc.W = c->width; dc.H = c->height;
+  dc.gx = (c->width + kTile - 1) / kTile;
+  dc.gy = (c->height + kTile - 1) / kTile;
+  return FDGS_OK;
+}
+
+void keyframe_pair(const std::vector<float> &kt, float t, int &l, int &r) {
+  const int n = (int)kt.size();
+  l = 0;
+  for (int i = 0; i < n; ++i)
+    if (kt[i] <= t) l = i;
+  r = std::min(l + 1, n - 1);
+}
+
+int check_device_errors(fdgs_scene *s, cudaStream_t st) {
+  uint32_t e = 0;
+  CK(cudaMemcpyAsync(&e, s->status.p, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (e) {
+    CK(cudaMemsetAsync(s->status.p, 0, 4, st));
+    if (e & kErrTimeout) return fail(FDGS_ERR_TIMEOUT, "device spin-wait limit reached");
+    return fail(FDGS_ERR_CAPACITY, "device capacity exceeded");
+  }
+  return FDGS_OK;
+}
+
+// One render into workspace ws. want_flags: also write per-Gaussian decision flags.
+// wsum: per-rank blend weights are accumulated (score pass); the buffer is zeroed here.
+int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
+                const fdgs_render_opts *opts, float *rgb, bool want_flags, bool want_wsum,
+                bool use_mask_override, FrameMeta &m, cudaStream_t st) {
+  DevCam dc;
+  TRY(make_cam(cam, dc));
+  if (!rgb) return fail(FDGS_ERR_INVALID, "null output image");
+  const uint32_t N = (uint32_t)s->d.n;
+  const int W = dc.W, H = dc.H, gx = dc.gx, gy = dc.gy;
+  const uint64_t tiles = (uint64_t)gx * gy, pixels = (uint64_t)W * H;
+  const uint64_t parts = std::max<uint64_t>(1, (N + 255) / 256);
+  const uint64_t n1 = std::max<uint64_t>(N, 1);
+  TRY(grow(ws.ctr, C_COUNT * 4));
+  if (!ws.hctr) CK(cudaMallocHost(&ws.hctr, C_COUNT * 4));
+  TRY(grow(ws.pre_status, parts * 8));
+  TRY(grow(ws.scan_status, parts * 8));
+  TRY(grow(ws.rec, n1 * kRec * 4));
+  TRY(grow(ws.rec_sorted, n1 * kRec * 4));
+  TRY(grow(ws.vis[0], n1 * 8));
+  TRY(grow(ws.vis[1], n1 * 8));
+  TRY(grow(ws.offsets, n1 * 4));
+  if (want_flags) TRY(grow(ws.flags, n1));
+  TRY(grow(ws.ranges, tiles * 8));
+  TRY(grow(ws.Tf, pixels * 4));
+  TRY(grow(ws.nc, pixels * 4));
+  TRY(grow(ws.scratch, sort_scratch_bytes(n1, 32)));
+  if (want_wsum) TRY(grow(ws.wsum, n1 * 4));
+
+  const bool use_mask = use_mask_override && opts && opts->use_mask && s->n_key > 0;
+  const uint32_t *ml = nullptr, *mr = nullptr;
+  m.l = m.r = -1;
+  if (use_mask) {
+    keyframe_pair(s->key_times, t, m.l, m.r);
+    ml = s->masks.as<uint32_t>() + (size_t)m.l * s->row_words;
+    mr = s->masks.as<uint32_t>() + (size_t)m.r * s->row_words;
+  }
+  const bool prof = (s->prof & 1) && s->ev[0];
+  const bool count = (s->prof & 2) && s->evals.p;
+  if (count) CK(cudaMemsetAsync(s->evals.p, 0, 8, st));
+  if (prof) CK(cudaEventRecord(s->ev[0], st));
+  CK(cudaMemsetAsync(ws.ctr.p, 0, C_COUNT * 4, st));
+  CK(cudaMemsetAsync(ws.pre_status.p, 0, parts * 8, st));
+  CK(cudaMemsetAsync(ws.scan_status.p, 0, parts * 8, st));
+  uint32_t *ctr = ws.ctr.as<uint32_t>();
+  uint32_t *err = s->status.as<uint32_t>();
+
+  PreArgs pa;
+  pa.mean4 = (const float4 *)s->d.mean4;
+  pa.ls4 = (const float4 *)s->d.logscale4;
+  pa.ql = (const float4 *)s->d.q_left;
+  pa.qr = (const float4 *)s->d.q_right;
+  pa.opacity = s->d.opacity_logit;
+  pa.sh = s->d.sh;
+  pa.deg = s->d.sh_degree;
+  pa.n = N;
+  pa.mask_l = ml;
+  pa.mask_r = mr;
+  pa.t = t;
+  pa.cam = dc;
+  pa.rec = ws.rec.as<float>();
+  pa.vis_keys = ws.vis[0].as<uint64_t>();
+  pa.flags = want_flags ? ws.flags.as<uint8_t>() : nullptr;
+  pa.status = ws.pre_status.as<uint64_t>();
+  pa.ctr = ctr;
+  pa.err = err;
+  launch_preprocess(pa, st);
+  if (prof) CK(cudaEventRecord(s->ev[1], st));
+  uint64_t *sorted = radix_sort<uint64_t>(ws.vis[0].as<uint64_t>(), ws.vis[1].as<uint64_t>(),
+                                          ctr + C_NVIS, N, 32, 32, ws.scratch.p, st, err);
+  if (prof) CK(cudaEventRecord(s->ev[2], st));
+  launch_gather_scan(sorted, ctr + C_NVIS, N, ws.rec.as<float>(), ws.rec_sorted.as<float>(),
+                     ws.offsets.as<uint32_t>(), ws.scan_status.as<uint64_t>(), ctr, err, st);
+  if (prof) CK(cudaEventRecord(s->ev[3], st));
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ws.hctr, ctr, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
+  TRY(check_device_errors(s, st));   // synchronises the stream
+
+  const uint32_t nv = ws.hctr[C_NVIS];
+  const uint64_t nkeys = (uint64_t)ws.hctr[C_NKEYS_LO] | ((uint64_t)ws.hctr[C_NKEYS_HI] << 32);
+  if (nkeys > kSortMaxKeys)
+    return fail(FDGS_ERR_CAPACITY, "%llu tile keys exceed the sort limit",
+                (unsigned long long)nkeys);
+  const int rb = ceil_log2(std::max<uint32_t>(nv, 2));
+  const int tb = ceil_log2(std::max<uint64_t>(tiles, 2));
+  const int key64 = (rb + tb) > 32;
+  const size_t kb = key64 ? 8 : 4;
+  const uint64_t k1 = std::max<uint64_t>(nkeys, 1);
+  TRY(grow(ws.keys[0], k1 * kb));
+  TRY(grow(ws.keys[1], k1 * kb));
+  TRY(grow(ws.scratch, std::max(sort_scratch_bytes(n1, 32), sort_scratch_bytes(k1, tb))));
+  if (want_wsum) CK(cudaMemsetAsync(ws.wsum.p, 0, n1 * 4, st));
+  CK(cudaMemsetAsync(ws.ranges.p, 0, tiles * 8, st));
+  const uint32_t rmask = (uint32_t)((1ull << rb) - 1);
+  BlendArgs ba;
+  ba.ranges = ws.ranges.as<uint2>();
+  ba.rec_sorted = ws.rec_sorted.as<float>();
+  ba.W = W; ba.H = H; ba.gx = gx; ba.gy = gy;
+  for (int c = 0; c < 3; ++c) ba.bg[c] = opts ? opts->bg[c] : 0.f;
+  ba.rgb = rgb;
+  ba.T_final = ws.Tf.as<float>();
+  ba.n_contrib = ws.nc.as<uint32_t>();
+  ba.w_sum = want_wsum ? ws.wsum.as<float>() : nullptr;
+  ba.evals = count ? s->evals.as<unsigned long long>() : nullptr;
+  void *skeys = ws.keys[0].p;
+  if (prof) CK(cudaEventRecord(s->ev[4], st));   // ev[3] -> ev[4]: the host synchronisation
+  if (key64) {
+    uint64_t *k0 = ws.keys[0].as<uint64_t>(), *k1p = ws.keys[1].as<uint64_t>();
+    if (nkeys)
+      launch_emit<uint64_t>(ws.rec_sorted.as<float>(), ws.offsets.as<uint32_t>(), nv, gx, gy, rb,
+                            k0, st);
+    if (prof) CK(cudaEventRecord(s->ev[5], st));
+    if (nkeys)
+      skeys = radix_sort<uint64_t>(k0, k1p, ctr + C_NKEYS_LO, nkeys, rb, tb, ws.scratch.p, st, err);
+    if (prof) CK(cudaEventRecord(s->ev[6], st));
+    if (nkeys)
+      launch_ranges<uint64_t>((uint64_t *)skeys, (uint32_t)nkeys, rb, ws.ranges.as<uint2>(), st);
+    if (prof) CK(cudaEventRecord(s->ev[7], st));
+    launch_blend<uint64_t>(ba, (const uint64_t *)skeys, rmask, st);
+  } else {
+    uint32_t *k0 = ws.keys[0].as<uint32_t>(), *k1p = ws.keys[1].as<uint32_t>();
+    if (nkeys)
+      launch_emit<uint32_t>(ws.rec_sorted.as<float>(), ws.offsets.as<uint32_t>(), nv, gx, gy, rb,
+                            k0, st);
+    if (prof) CK(cudaEventRecord(s->ev[5], st));
+    if (nkeys)
+      skeys = radix_sort<uint32_t>(k0, k1p, ctr + C_NKEYS_LO, nkeys, rb, tb, ws.scratch.p, st, err);
+    if (prof) CK(cudaEventRecord(s->ev[6], st));
+    if (nkeys)
+      launch_ranges<uint32_t>((uint32_t *)skeys, (uint32_t)nkeys, rb, ws.ranges.as<uint2>(), st);
+    if (prof) CK(cudaEventRecord(s->ev[7], st));
+    launch_blend<uint32_t>(ba, (const uint32_t *)skeys, rmask, st);
+  }
+  if (prof) CK(cudaEventRecord(s->ev[8], st));
+  CK(cudaGetLastError());
+  m.cam = dc;
+  m.t = t;
+  m.W = W; m.H = H; m.gx = gx; m.gy = gy;
+  m.n_active = ws.hctr[C_NACTIVE];
+  m.nv = nv;
+  m.nkeys = nkeys;
+  m.key64 = key64;
+  m.rb = rb;
+  m.sorted = sorted;
+  m.keys = skeys;
+  for (int c = 0; c < 3; ++c) m.bg[c] = ba.bg[c];
+  m.stream = st;
+  return FDGS_OK;
+}
+
+Workspace *take_workspace(fdgs_scene *s) {
+  if (!s->pool.empty()) {
+    Workspace *w = s->pool.back();
+    s->pool.pop_back();
+    return w;
+  }
+  return new Workspace();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fdgs_last_error(void) { return g_err.c_str(); }
+const char *fdgs_version(void) { return "fdgs 0.1 (sm_103a)"; }
+
+int fdgs_create_scene(const fdgs_scene_desc *desc, fdgs_scene **out) {
+  if (!out) return fail(FDGS_ERR_INVALID, "null output pointer");
+  *out = nullptr;
+  TRY(check_desc(desc));
+  fdgs_scene *s = new fdgs_scene();
+  s->d = *desc;
+  cudaGetDevice(&s->device);
+  if (grow(s->status, 4) != FDGS_OK) {
+    delete s;
+    return FDGS_ERR_OOM;
+  }
+  if (cudaMemset(s->status.p, 0, 4) != cudaSuccess) {
+    delete s;
+    return fail(FDGS_ERR_CUDA, "cudaMemset failed");
+  }
+  *out = s;
+  return FDGS_OK;
+}
+
+int fdgs_update_scene(fdgs_scene *s, const fdgs_scene_desc *desc) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  TRY(check_desc(desc));
+  if (desc->n != s->d.n && s->n_key > 0) {
+    s->n_key = 0;
+    s->key_times.clear();
+  }
+  s->d = *desc;
+  return FDGS_OK;
+}
+
+int fdgs_destroy_scene(fdgs_scene *s) {
+  if (!s) return FDGS_OK;
+  cudaDeviceSynchronize();
+  for (fdgs_frame *f : s->live) {
+    delete f->ws;
+    delete f;
+  }
+  for (Workspace *w : s->pool) delete w;
+  s->masks.release();
+  s->status.release();
+  s->evals.release();
+  for (auto &e : s->ev)
+    if (e) cudaEventDestroy(e);
+  for (Buf &b : s->aux) b.release();
+  delete s;
+  return FDGS_OK;
+}
+
+int fdgs_set_active_mask(fdgs_scene *s, const uint8_t *bits_dev, const float *key_times,
+                         int n_key, fdgs_stream stream) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n_key < 0) return fail(FDGS_ERR_INVALID, "n_key < 0");
+  if (n_key == 0) {
+    s->n_key = 0;
+    s->key_times.clear();
+    return FDGS_OK;
+  }
+  if (!bits_dev || !key_times) return fail(FDGS_ERR_INVALID, "null mask pointer");
+  for (int i = 1; i < n_key; ++i)
+    if (!(key_times[i] >= key_times[i - 1]))
+      return fail(FDGS_ERR_INVALID, "key-frame times must be ascending");
+  const size_t n = (size_t)s->d.n;
+  const size_t row_bytes = (n + 7) / 8;
+  const size_t words = ((n + 31) / 32 + 3) / 4 * 4;   // padded to 16 bytes
+  TRY(grow(s->masks, std::max<size_t>(words * 4 * n_key, 16)));
+  CK(cudaMemsetAsync(s->masks.p, 0, words * 4 * n_key, st));
+  if (row_bytes)
+    CK(cudaMemcpy2DAsync(s->masks.p, words * 4, bits_dev, row_bytes, row_bytes, n_key,
+                         cudaMemcpyDeviceToDevice, st));
+  s->row_words = words;
+  s->n_key = n_key;
+  s->key_times.assign(key_times, key_times + n_key);
+  return FDGS_OK;
+}
+
+int fdgs_render(fdgs_scene *s, const fdgs_camera *cam, float t, const fdgs_render_opts *opts,
+                float *rgb_out_dev, fdgs_frame **frame_out, fdgs_stream stream) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (frame_out) *frame_out = nullptr;
+  if (!frame_out) {
+    FrameMeta m;
+    return render_impl(s, s->main, cam, t, opts, rgb_out_dev, false, false, true, m, st);
+  }
+  Workspace *ws = take_workspace(s);
+  fdgs_frame *f = new fdgs_frame{s, ws, FrameMeta()};
+  int rc = render_impl(s, *ws, cam, t, opts, rgb_out_dev, true, false, true, f->m, st);
+  if (rc != FDGS_OK) {
+    s->pool.push_back(ws);
+    delete f;
+    return rc;
+  }
+  s->live.insert(f);
+  *frame_out = f;
+  return FDGS_OK;
+}
+
+int fdgs_frame_release(fdgs_frame *f) {
+  if (!f) return FDGS_OK;
+  fdgs_scene *s = f->scene;
+  if (s->live.erase(f) == 0) return fail(FDGS_ERR_STATE, "frame not live");
+  s->pool.push_back(f->ws);
+  delete f;
+  return FDGS_OK;
+}
+
+int fdgs_frame_get_stats(fdgs_frame *f, fdgs_frame_stats *o) {
+  if (!f || !o) return fail(FDGS_ERR_INVALID, "null argument");
+  CK(cudaStreamSynchronize(f->m.stream));
+  o->n_active = f->m.n_active;
+  o->n_visible = f->m.nv;
+  o->n_keys = (int64_t)f->m.nkeys;
+  o->width = f->m.W;
+  o->height = f->m.H;
+  o->tiles_x = f->m.gx;
+  o->tiles_y = f->m.gy;
+  o->key_l = f->m.l;
+  o->key_r = f->m.r;
+  o->key_bytes = f->m.key64 ? 8 : 4;
+  return FDGS_OK;
+}
+
+int fdgs_frame_export(fdgs_frame *f, uint32_t *tile_ranges_dev, uint32_t *tile_ids_dev,
+                      float *T_final_dev, uint32_t *n_contrib_dev, uint8_t *gauss_flags_dev,
+                      float *records_dev, fdgs_stream stream) {
+  if (!f) return fail(FDGS_ERR_INVALID, "null frame");
+  cudaStream_t st = (cudaStream_t)stream;
+  const FrameMeta &m = f->m;
+  Workspace &ws = *f->ws;
+  const size_t tiles = (size_t)m.gx * m.gy, pixels = (size_t)m.W * m.H;
+  if (tile_ranges_dev)
+    CK(cudaMemcpyAsync(tile_ranges_dev, ws.ranges.p, tiles * 8, cudaMemcpyDeviceToDevice, st));
+  if (tile_ids_dev && m.nkeys) {
+    const uint32_t rmask = (uint32_t)((1ull << m.rb) - 1);
+    if (m.key64)
+      launch_keys_to_ids<uint64_t>((const uint64_t *)m.keys, (uint32_t)m.nkeys, rmask, m.sorted,
+                                   tile_ids_dev, st);
+    else
+      launch_keys_to_ids<uint32_t>((const uint32_t *)m.keys, (uint32_t)m.nkeys, rmask, m.sorted,
+                                   tile_ids_dev, st);
+  }
+  if (T_final_dev)
+    CK(cudaMemcpyAsync(T_final_dev, ws.Tf.p, pixels * 4, cudaMemcpyDeviceToDevice, st));
+  if (n_contrib_dev)
+    CK(cudaMemcpyAsync(n_contrib_dev, ws.nc.p, pixels * 4, cudaMemcpyDeviceToDevice, st));
+  if (gauss_flags_dev && f->scene->d.n)
+    CK(cudaMemcpyAsync(gauss_flags_dev, ws.flags.p, (size_t)f->scene->d.n,
+                       cudaMemcpyDeviceToDevice, st));
+  if (records_dev)
+    launch_export_records(m.sorted, m.nv, ws.rec_sorted.as<float>(), records_dev, st);
+  CK(cudaGetLastError());
+  return FDGS_OK;
+}
+
+int fdgs_render_backward(fdgs_scene *s, fdgs_frame *f, const float *dL_drgb_dev,
+                         float *g_mean4, float *g_logscale4, float *g_q_left, float *g_q_right,
+                         float *g_opacity_logit, float *g_sh, fdgs_stream stream) {
+  if (!s || !f) return fail(FDGS_ERR_INVALID, "null argument");
+  if (f->scene != s || !s->live.count(f)) return fail(FDGS_ERR_STATE, "frame not of this scene");
+  if (!dL_drgb_dev) return fail(FDGS_ERR_INVALID, "null dL/drgb");
+  cudaStream_t st = (cudaStream_t)stream;
+  const FrameMeta &m = f->m;
+  Workspace &ws = *f->ws;
+  if (m.nv == 0) return FDGS_OK;
+  TRY(grow(ws.g2d, (size_t)m.nv * 9 * 4));
+  CK(cudaMemsetAsync(ws.g2d.p, 0, (size_t)m.nv * 9 * 4, st));
+  BlendBwdArgs ba;
+  ba.ranges = ws.ranges.as<uint2>();
+  ba.rec_sorted = ws.rec_sorted.as<float>();
+  ba.W = m.W; ba.H = m.H; ba.gx = m.gx; ba.gy = m.gy;
+  for (int c = 0; c < 3; ++c) ba.bg[c] = m.bg[c];
+  ba.dL_drgb = dL_drgb_dev;
+  ba.T_final = ws.Tf.as<float>();
+  ba.n_contrib = ws.nc.as<uint32_t>();
+  ba.g2d = ws.g2d.as<float>();
+  const uint32_t rmask = (uint32_t)((1ull << m.rb) - 1);
+  if (m.key64)
+    launch_blend_bwd<uint64_t>(ba, (const uint64_t *)m.keys, rmask, st);
+  else
+    launch_blend_bwd<uint32_t>(ba, (const uint32_t *)m.keys, rmask, st);
+  PreBwdArgs pa;
+  pa.mean4 = (const float4 *)s->d.mean4;
+  pa.ls4 = (const float4 *)s->d.logscale4;
+  pa.ql = (const float4 *)s->d.q_left;
+  pa.qr = (const float4 *)s->d.q_right;
+  pa.opacity = s->d.opacity_logit;
+  pa.sh = s->d.sh;
+  pa.deg = s->d.sh_degree;
+  pa.n = (uint32_t)s->d.n;
+  pa.nv = m.nv;
+  pa.t = m.t;
+  pa.cam = m.cam;
+  pa.sorted = m.sorted;
+  pa.g2d = ws.g2d.as<float>();
+  pa.g_mean4 = g_mean4;
+  pa.g_ls4 = g_logscale4;
+  pa.g_ql = g_q_left;
+  pa.g_qr = g_q_right;
+  pa.g_op = g_opacity_logit;
+  pa.g_sh = g_sh;
+  launch_preprocess_bwd(pa, st);
+  CK(cudaGetLastError());
+  return FDGS_OK;
+}
+
+int fdgs_render_batch(fdgs_scene *s, const fdgs_camera *cams, const float *ts, int n_req,
+                      const fdgs_render_opts *opts, float *const *rgb_out_dev,
+                      fdgs_stream stream) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (n_req < 0 || (n_req > 0 && (!cams || !ts || !rgb_out_dev)))
+    return fail(FDGS_ERR_INVALID, "bad batch arguments");
+  for (int i = 0; i < n_req; ++i) {
+    FrameMeta m;
+    TRY(render_impl(s, s->main, &cams[i], ts[i], opts, rgb_out_dev[i], false, false, true, m,
+                    (cudaStream_t)stream));
+  }
+  return FDGS_OK;
+}
+
+int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, const float *ts,
+                         int n_t, int batch, float *score_out_dev, fdgs_stream stream) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (n_cam < 0 || n_t < 0 || batch < 1 || !score_out_dev ||
+      (n_cam > 0 && !cams) || (n_t > 0 && !ts))
+    return fail(FDGS_ERR_INVALID, "bad score arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t N = (uint32_t)s->d.n;
+  CK(cudaMemsetAsync(score_out_dev, 0, (size_t)N * 4, st));
+  if (N == 0) return FDGS_OK;
+  // gamma = clamp(V / V_p90, 0, 1)^0.1, V_p90 the nearest-rank 90th percentile
+  TRY(grow(s->aux[0], (size_t)N * 4 * 2 + 16));   // volume bits, ping-pong
+  TRY(grow(s->aux[1], (size_t)N * 4));            // gamma
+  TRY(grow(s->aux[2], sort_scratch_bytes(N, 32)));
+  TRY(grow(s->aux[3], 16));
+  uint32_t *vb = s->aux[0].as<uint32_t>();
+  CK(cudaMemcpyAsync(s->aux[3].p, &N, 4, cudaMemcpyHostToDevice, st));
+  launch_volume_bits((const float4 *)s->d.logscale4, N, vb, st);
+  uint32_t *vs = radix_sort<uint32_t>(vb, vb + N, s->aux[3].as<uint32_t>(), N, 0, 32,
+                                      s->aux[2].p, st, s->status.as<uint32_t>());
+  const uint32_t k = (uint32_t)std::max<int64_t>(1, (int64_t)ceil(0.9 * (double)N)) - 1;
+  launch_gamma((const float4 *)s->d.logscale4, N, vs, k, s->aux[1].as<float>(), st);
+  fdgs_render_opts o{};
+  o.use_mask = 0;
+  int done = 0;
+  for (int it = 0; it < n_t; ++it)
+    for (int ic = 0; ic < n_cam; ++ic) {
+      Workspace &ws = s->main;
+      TRY(grow(s->aux[4], (size_t)cams[ic].width * cams[ic].height * 12));
+      FrameMeta m;
+      TRY(render_impl(s, ws, &cams[ic], ts[it], &o, s->aux[4].as<float>(), false, true, false,
+                      m, st));
+      launch_score_accumulate(m.sorted, ws.ctr.as<uint32_t>() + C_NVIS, m.nv, ws.wsum.as<float>(),
+                              (const float4 *)s->d.mean4, (const float4 *)s->d.logscale4,
+                              (const float4 *)s->d.q_left, (const float4 *)s->d.q_right,
+                              s->aux[1].as<float>(), ts[it], score_out_dev, st);
+      if (++done % batch == 0) CK(cudaGetLastError());
+    }
+  CK(cudaGetLastError());
+  return FDGS_OK;
+}
+
+int fdgs_select_keep(fdgs_scene *s, const float *score_dev, int64_t n, float prune_ratio,
+                     uint8_t *keep_out_dev, fdgs_stream stream) {
+  if (!s || !score_dev || !keep_out_dev || n < 0 || n >= (1ll << 30))
+    return fail(FDGS_ERR_INVALID, "bad keep-set arguments");
+  if (!(prune_ratio >= 0.f && prune_ratio <= 1.f))
+    return fail(FDGS_ERR_INVALID, "prune_ratio must be in [0, 1]");
+  if (n == 0) return FDGS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t N = (uint32_t)n;
+  TRY(grow(s->aux[0], (size_t)N * 16 + 16));
+  TRY(grow(s->aux[2], sort_scratch_bytes(N, 32)));
+  TRY(grow(s->aux[3], 16));
+  uint64_t *keys = s->aux[0].as<uint64_t>();
+  CK(cudaMemcpyAsync(s->aux[3].p, &N, 4, cudaMemcpyHostToDevice, st));
+  launch_score_keys(score_dev, N, keys, st);
+  uint64_t *srt = radix_sort<uint64_t>(keys, keys + N, s->aux[3].as<uint32_t>(), N, 32, 32,
+                                       s->aux[2].p, st, s->status.as<uint32_t>());
+  const uint32_t n_drop = (uint32_t)floor((double)prune_ratio * (double)N);
+  launch_keep_from_sorted(srt, N, n_drop, keep_out_dev, st);
+  CK(cudaGetLastError());
+  return FDGS_OK;
+}
+
+int fdgs_profile_enable(fdgs_scene *s, int flags) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if ((flags & 1) && !s->ev[0])
+    for (auto &e : s->ev) CK(cudaEventCreate(&e));
+  if (flags & 2) TRY(grow(s->evals, 8));
+  s->prof = flags;
+  return FDGS_OK;
+}
+
+int fdgs_profile_read(fdgs_scene *s, float *stage_ms, uint64_t *blend_evals) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  CK(cudaDeviceSynchronize());
+  if (stage_ms) {
+    if (!s->ev[0]) return fail(FDGS_ERR_STATE, "stage profiling was never enabled");
+    for (int i = 0; i < FDGS_PROFILE_STAGES; ++i)
+      CK(cudaEventElapsedTime(&stage_ms[i], s->ev[i], s->ev[i + 1]));
+  }
+  if (blend_evals) {
+    *blend_evals = 0;
+    if (s->evals.p) CK(cudaMemcpy(blend_evals, s->evals.p, 8, cudaMemcpyDeviceToHost));
+  }
+  return FDGS_OK;
+}
+
+int fdgs_status_sync(fdgs_scene *s) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  CK(cudaDeviceSynchronize());
+  return check_device_errors(s, nullptr);
+}
+
+}  // extern "C"

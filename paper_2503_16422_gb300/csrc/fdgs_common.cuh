@@ -1,0 +1,170 @@
+// Shared device definitions of the GB300 4D Gaussian rasterizer.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdgs {
+
+// Blending thresholds of the 3DGS-family renderer the paper builds on (Sec. 3, Eq. 2 and
+// Eq. 3 give only the compositing sum; these constants are the renderer's).
+constexpr float kAlphaMin = 1.0f / 255.0f;   // alpha below this is skipped
+constexpr float kAlphaMax = 0.99f;           // alpha is clamped to this
+constexpr float kTStop = 1e-4f;              // stop before transmittance drops below this
+constexpr float kDilation = 0.3f;            // px^2 added to the 2D covariance diagonal
+constexpr float kFovClamp = 1.3f;            // Jacobian clamp, times tan(fov/2)
+constexpr float kRadiusFloor = 0.1f;         // floor of the eigenvalue discriminant
+constexpr int kTile = 16;                    // gating tile side (pixels)
+constexpr int kTilePixels = kTile * kTile;
+
+// Device error bits (scene status word).
+constexpr uint32_t kErrTimeout = 1u;
+constexpr uint32_t kErrCapacity = 2u;
+
+// Spin-wait limit of every decoupled look-back (iterations of roughly 0.1-1 us each). Once
+// any waiter gives up it sets kErrTimeout in the error word, and every other waiter that
+// sees the bit gives up too, so a broken protocol costs one limit in total, not one per wait.
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+// Per-Gaussian decision flags (exported for tests).
+constexpr uint8_t kFlagMask = 1, kFlagTemporal = 2, kFlagNear = 4, kFlagDet = 8,
+                  kFlagVisible = 16;
+
+// Record of a projected Gaussian, 12 floats (48 B): the per-frame state the blend reads.
+constexpr int kRec = 12;
+enum RecField { R_U = 0, R_V, R_A, R_B, R_C, R_OPA, R_R, R_G, R_BL, R_DEPTH, R_RADIUS, R_COUNT };
+
+struct DevCam {
+  float R[9];       // world->camera rotation, row-major
+  float tv[3];      // world->camera translation
+  float eye[3];     // camera centre in world coordinates (-R^T tv)
+  float fx, fy, cx, cy;
+  float limx, limy; // Jacobian clamp limits (1.3 tan(fov/2))
+  float znear;
+  int W, H, gx, gy;
+};
+
+// Counters kept on the device for one frame.
+enum Counter {
+  C_NVIS = 0,      // visible Gaussians (u32)
+  C_NACTIVE = 1,   // Gaussians through the mask gate (u32)
+  C_NKEYS_LO = 2,  // number of keys (u64 split in two words)
+  C_NKEYS_HI = 3,
+  C_ERR = 4,       // device error bits of this frame
+  C_PART0 = 8,     // partition counters of persistent kernels (8..31)
+  C_COUNT = 32
+};
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ void nanosleep_ns(uint32_t ns) { __nanosleep(ns); }
+
+// Volatile (L2-coherent) 64-bit load/store for look-back status words.
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_volatile_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_volatile_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Status word of a single-value decoupled look-back: 2-bit flag in the top bits.
+constexpr uint64_t kLbAgg = 1ull << 62, kLbPrefix = 2ull << 62, kLbValue = (1ull << 62) - 1;
+
+// Thread-0 look-back of partition `part` with aggregate `agg`. Publishes the aggregate,
+// walks back over predecessors until an inclusive prefix is found (bounded spin), publishes
+// the inclusive prefix and returns the exclusive one. On timeout sets kErrTimeout and
+// returns the partial sum so that every waiting successor still terminates.
+__device__ __forceinline__ uint64_t lookback_single(uint64_t *status, uint32_t part,
+                                                    uint64_t agg, uint32_t *err) {
+  if (part == 0) {
+    st_volatile_u64(&status[0], kLbPrefix | agg);
+    return 0;
+  }
+  st_volatile_u64(&status[part], kLbAgg | agg);
+  uint64_t excl = 0;
+  int64_t j = (int64_t)part - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    uint64_t s = ld_volatile_u64(&status[j]);
+    uint64_t f = s & ~kLbValue;
+    if (f == 0) {
+      if (++spins > kSpinLimit || ((spins & 255) == 0 && (ld_volatile_u32(err) & kErrTimeout))) {
+        atomicOr(err, kErrTimeout);
+        break;
+      }
+      nanosleep_ns(32);
+      continue;
+    }
+    excl += s & kLbValue;
+    if (f == kLbPrefix) break;
+    --j;
+  }
+  st_volatile_u64(&status[part], kLbPrefix | (excl + agg));
+  return excl;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(0xffffffffu, v, o);
+    if ((int)lane_id() >= o) v += n;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Tile rectangle [xmin, xmax) x [ymin, ymax) of a Gaussian with image centre (u, v) and
+// integer radius r: floor((u - r) / 16) .. floor((u + r + 15) / 16), clamped to the grid.
+// Used by the per-Gaussian stage and again by key emission; identical float operations.
+__device__ __forceinline__ void tile_rect(float u, float v, float r, int gx, int gy,
+                                          int &xmin, int &ymin, int &xmax, int &ymax) {
+  const float inv = 1.0f / kTile;
+  float x0 = floorf(__fmul_rn(__fsub_rn(u, r), inv));
+  float y0 = floorf(__fmul_rn(__fsub_rn(v, r), inv));
+  float x1 = floorf(__fmul_rn(__fadd_rn(__fadd_rn(u, r), (float)(kTile - 1)), inv));
+  float y1 = floorf(__fmul_rn(__fadd_rn(__fadd_rn(v, r), (float)(kTile - 1)), inv));
+  xmin = (int)fminf(fmaxf(x0, 0.f), (float)gx);
+  ymin = (int)fminf(fmaxf(y0, 0.f), (float)gy);
+  xmax = (int)fminf(fmaxf(x1, 0.f), (float)gx);
+  ymax = (int)fminf(fmaxf(y1, 0.f), (float)gy);
+}
+
+// Alpha of one (Gaussian, pixel) pair, shared by the forward blend and the backward replay
+// so that both take the same decisions bit for bit. d = mean2D - pixel;
+// power = -1/2 (A dx^2 + C dy^2) - B dx dy; returns false when power > 0 or the clamped
+// alpha = min(0.99, a exp(power)) is below 1/255.
+__device__ __forceinline__ bool eval_alpha(float u, float v, float A, float B, float C,
+                                           float a, float px, float py, float &alpha,
+                                           float &G, float &dx, float &dy) {
+  dx = __fsub_rn(u, px);
+  dy = __fsub_rn(v, py);
+  float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
+  float power = __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
+  if (power > 0.f) return false;
+  G = __expf(power);
+  alpha = fminf(kAlphaMax, __fmul_rn(a, G));
+  return alpha >= kAlphaMin;
+}
+
+}  // namespace fdgs

@@ -1,0 +1,112 @@
+// Internal host-side interfaces between the C ABI and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fdgs_common.cuh"
+
+namespace fdgs {
+
+// ---- radix sort (fdgs_sort.cu) ---------------------------------------------------------
+// Stable LSD onesweep sort of packed keys on bits [lo, lo + bits). The key count is read
+// from device memory (n_dev) so launches need no host synchronisation; n_cap bounds it.
+// Returns the buffer that holds the result (a or b). scratch must hold
+// sort_scratch_bytes(n_cap, bits) bytes.
+size_t sort_scratch_bytes(uint64_t n_cap, int bits);
+template <typename K>
+K *radix_sort(K *a, K *b, const uint32_t *n_dev, uint64_t n_cap, int lo, int bits,
+              void *scratch, cudaStream_t st, uint32_t *err_dev);
+int sort_passes(int bits);
+constexpr uint64_t kSortMaxKeys = (1ull << 30) - 1;
+
+// ---- rasterizer kernels (fdgs_raster.cu) -----------------------------------------------
+struct PreArgs {
+  const float4 *mean4, *ls4, *ql, *qr;
+  const float *opacity, *sh;
+  int deg;
+  uint32_t n;
+  const uint32_t *mask_l, *mask_r;   // null = no mask
+  float t;
+  DevCam cam;
+  float *rec;          // [n][12] by Gaussian id
+  uint64_t *vis_keys;  // compacted (depth bits << 32 | id), id order
+  uint8_t *flags;      // optional [n]
+  uint64_t *status;    // chained-scan status [ceil(n/256)]
+  uint32_t *ctr;       // frame counters
+  uint32_t *err;       // scene status word (device error bits)
+};
+void launch_preprocess(const PreArgs &a, cudaStream_t st);
+
+void launch_gather_scan(const uint64_t *sorted, const uint32_t *ctr_nvis, uint32_t n_cap,
+                        const float *rec, float *rec_sorted, uint32_t *offsets,
+                        uint64_t *status, uint32_t *ctr, uint32_t *err, cudaStream_t st);
+
+template <typename K>
+void launch_emit(const float *rec_sorted, const uint32_t *offsets, uint32_t nv, int gx, int gy,
+                 int rb, K *keys, cudaStream_t st);
+template <typename K>
+void launch_ranges(const K *keys, uint32_t nkeys, int rb, uint2 *ranges, cudaStream_t st);
+
+struct BlendArgs {
+  const uint2 *ranges;
+  const float *rec_sorted;
+  int W, H, gx, gy;
+  float bg[3];
+  float *rgb;          // [3][H][W]
+  float *T_final;      // [H][W]
+  uint32_t *n_contrib; // [H][W]
+  float *w_sum;        // optional [nv] per-rank blend-weight sums (score pass)
+  unsigned long long *evals;  // optional evaluation counter (profiling)
+};
+template <typename K>
+void launch_blend(const BlendArgs &a, const K *keys, uint32_t rmask, cudaStream_t st);
+
+struct BlendBwdArgs {
+  const uint2 *ranges;
+  const float *rec_sorted;
+  int W, H, gx, gy;
+  float bg[3];
+  const float *dL_drgb;
+  const float *T_final;
+  const uint32_t *n_contrib;
+  float *g2d;          // [nv][9] per rank: u, v, A, B, C, a, r, g, b
+};
+template <typename K>
+void launch_blend_bwd(const BlendBwdArgs &a, const K *keys, uint32_t rmask, cudaStream_t st);
+
+struct PreBwdArgs {
+  const float4 *mean4, *ls4, *ql, *qr;
+  const float *opacity, *sh;
+  int deg;
+  uint32_t n, nv;
+  float t;
+  DevCam cam;
+  const uint64_t *sorted;  // rank -> (depth, id)
+  const float *g2d;
+  float *g_mean4, *g_ls4, *g_ql, *g_qr, *g_op, *g_sh;
+};
+void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st);
+
+// ---- frame export, score pass and keep-set helpers (fdgs_score.cu) ----------------------
+template <typename K>
+void launch_keys_to_ids(const K *keys, uint32_t nkeys, uint32_t rmask, const uint64_t *sorted,
+                        uint32_t *ids, cudaStream_t st);
+void launch_export_records(const uint64_t *sorted, uint32_t nv, const float *rec_sorted,
+                           float *out, cudaStream_t st);
+// V_i = prod of the four scales, as float bits (positive floats sort as unsigned ints)
+void launch_volume_bits(const float4 *ls4, uint32_t n, uint32_t *vbits, cudaStream_t st);
+// gamma_i = clamp(V_i / V_sorted[k], 0, 1)^0.1 with V_sorted the ascending volumes
+void launch_gamma(const float4 *ls4, uint32_t n, const uint32_t *vsorted, uint32_t k,
+                  float *gamma, cudaStream_t st);
+// score[id] += w_sum[rank] * f_id(t) * gamma[id] for every visible rank
+void launch_score_accumulate(const uint64_t *sorted, const uint32_t *nv_dev, uint32_t nv_cap,
+                             const float *w_sum, const float4 *mean4, const float4 *ls4,
+                             const float4 *ql, const float4 *qr, const float *gamma, float t,
+                             float *score, cudaStream_t st);
+void launch_score_keys(const float *score, uint32_t n, uint64_t *keys, cudaStream_t st);
+void launch_keep_from_sorted(const uint64_t *sorted, uint32_t n, uint32_t n_drop,
+                             uint8_t *keep, cudaStream_t st);
+
+int num_sms();
+
+}  // namespace fdgs

@@ -1,0 +1,154 @@
+// Spatial-Temporal Variation Score helpers (Sec. 4.2.1, Eqs. 4-7), pruning keep-set, and
+// frame export kernels.
+#include <algorithm>
+
+#include "fdgs_gauss.cuh"
+#include "fdgs_internal.h"
+
+namespace fdgs {
+
+namespace {
+
+constexpr int kB = 256;
+
+int grid_for(uint64_t n, int per_sm = 16) {
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>((n + kB - 1) / kB,
+                                                        (uint64_t)num_sms() * per_sm));
+}
+
+template <typename K>
+__global__ void k_keys_to_ids(const K *__restrict__ keys, uint32_t nkeys, uint32_t rmask,
+                              const uint64_t *__restrict__ sorted, uint32_t *__restrict__ ids) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nkeys; i += gridDim.x * blockDim.x)
+    ids[i] = (uint32_t)sorted[(uint32_t)(keys[i] & (K)rmask)];
+}
+
+__global__ void k_export_records(const uint64_t *__restrict__ sorted, uint32_t nv,
+                                 const float *__restrict__ rec_sorted, float *__restrict__ out) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
+    const uint32_t id = (uint32_t)sorted[r];
+    for (int k = 0; k < kRec; ++k) out[(size_t)id * kRec + k] = rec_sorted[(size_t)r * kRec + k];
+  }
+}
+
+__global__ void k_volume_bits(const float4 *__restrict__ ls4, uint32_t n, uint32_t *vbits) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 l = ls4[i];
+    vbits[i] = __float_as_uint(expf(l.x + l.y + l.z + l.w));
+  }
+}
+
+__global__ void k_gamma(const float4 *__restrict__ ls4, uint32_t n,
+                        const uint32_t *__restrict__ vsorted, uint32_t k, float *gamma) {
+  const float vref = __uint_as_float(vsorted[k]);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 l = ls4[i];
+    const float v = expf(l.x + l.y + l.z + l.w);
+    const float x = fminf(fmaxf(v / vref, 0.f), 1.f);
+    gamma[i] = powf(x, 0.1f);
+  }
+}
+
+// Temporal variance Sigma_t = |row t of R diag(s)|^2 of one Gaussian.
+__device__ __forceinline__ float temporal_variance(float4 ls, float4 ql, float4 qr) {
+  float qn_l[4], qn_r[4], il, ir, L[16], Rr[16];
+  quat_unit(ql, qn_l, il);
+  quat_unit(qr, qn_r, ir);
+  left_mat(qn_l, L);
+  right_mat(qn_r, Rr);
+  const float s[4] = {expf(ls.x), expf(ls.y), expf(ls.z), expf(ls.w)};
+  float v = 0.f;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float r = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r = fmaf(L[12 + k], Rr[k * 4 + m], r);
+    const float e = r * s[m];
+    v = fmaf(e, e, v);
+  }
+  return v;
+}
+
+__global__ void k_score_accumulate(const uint64_t *__restrict__ sorted,
+                                   const uint32_t *__restrict__ nv_dev,
+                                   const float *__restrict__ w_sum,
+                                   const float4 *__restrict__ mean4, const float4 *__restrict__ ls4,
+                                   const float4 *__restrict__ ql, const float4 *__restrict__ qr,
+                                   const float *__restrict__ gamma, float t, float *score) {
+  const uint32_t nv = *nv_dev;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
+    const float w = w_sum[r];
+    if (w == 0.f) continue;
+    const uint32_t id = (uint32_t)sorted[r];
+    const float st = temporal_variance(ls4[id], ql[id], qr[id]);
+    const float dt = t - mean4[id].w;
+    const float p = expf(-0.5f * dt * dt / st);
+    // Eq. 5: second derivative of the temporal opacity; Eq. 6: its tanh-mapped reciprocal
+    const float p2 = (dt * dt / (st * st) - 1.f / st) * p;
+    const float f = 1.f / (0.5f * tanhf(fabsf(p2)) + 0.5f);
+    score[id] += w * f * gamma[id];
+  }
+}
+
+__global__ void k_score_keys(const float *__restrict__ score, uint32_t n, uint64_t *keys) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    keys[i] = ((uint64_t)__float_as_uint(score[i]) << 32) | i;
+}
+
+__global__ void k_keep_from_sorted(const uint64_t *__restrict__ sorted, uint32_t n,
+                                   uint32_t n_drop, uint8_t *keep) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    keep[(uint32_t)sorted[j]] = j >= n_drop ? 1 : 0;
+}
+
+}  // namespace
+
+template <typename K>
+void launch_keys_to_ids(const K *keys, uint32_t nkeys, uint32_t rmask, const uint64_t *sorted,
+                        uint32_t *ids, cudaStream_t st) {
+  if (nkeys == 0) return;
+  k_keys_to_ids<K><<<grid_for(nkeys), kB, 0, st>>>(keys, nkeys, rmask, sorted, ids);
+}
+template void launch_keys_to_ids<uint32_t>(const uint32_t *, uint32_t, uint32_t,
+                                           const uint64_t *, uint32_t *, cudaStream_t);
+template void launch_keys_to_ids<uint64_t>(const uint64_t *, uint32_t, uint32_t,
+                                           const uint64_t *, uint32_t *, cudaStream_t);
+
+void launch_export_records(const uint64_t *sorted, uint32_t nv, const float *rec_sorted,
+                           float *out, cudaStream_t st) {
+  if (nv == 0) return;
+  k_export_records<<<grid_for(nv), kB, 0, st>>>(sorted, nv, rec_sorted, out);
+}
+
+void launch_volume_bits(const float4 *ls4, uint32_t n, uint32_t *vbits, cudaStream_t st) {
+  if (n == 0) return;
+  k_volume_bits<<<grid_for(n), kB, 0, st>>>(ls4, n, vbits);
+}
+
+void launch_gamma(const float4 *ls4, uint32_t n, const uint32_t *vsorted, uint32_t k,
+                  float *gamma, cudaStream_t st) {
+  if (n == 0) return;
+  k_gamma<<<grid_for(n), kB, 0, st>>>(ls4, n, vsorted, k, gamma);
+}
+
+void launch_score_accumulate(const uint64_t *sorted, const uint32_t *nv_dev, uint32_t nv_cap,
+                             const float *w_sum, const float4 *mean4, const float4 *ls4,
+                             const float4 *ql, const float4 *qr, const float *gamma, float t,
+                             float *score, cudaStream_t st) {
+  if (nv_cap == 0) return;
+  k_score_accumulate<<<grid_for(nv_cap), kB, 0, st>>>(sorted, nv_dev, w_sum, mean4, ls4, ql, qr,
+                                                      gamma, t, score);
+}
+
+void launch_score_keys(const float *score, uint32_t n, uint64_t *keys, cudaStream_t st) {
+  if (n == 0) return;
+  k_score_keys<<<grid_for(n), kB, 0, st>>>(score, n, keys);
+}
+
+void launch_keep_from_sorted(const uint64_t *sorted, uint32_t n, uint32_t n_drop,
+                             uint8_t *keep, cudaStream_t st) {
+  if (n == 0) return;
+  k_keep_from_sorted<<<grid_for(n), kB, 0, st>>>(sorted, n, n_drop, keep);
+}
+
+}  // namespace fdgs

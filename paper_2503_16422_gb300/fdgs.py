@@ -1,0 +1,383 @@
+"""Python binding of libfdgs.so: argument marshalling only.
+
+Every step of the rendering path runs in the library's CUDA kernels; this module passes
+device pointers (from CUDA torch tensors), camera structs and the current torch stream.
+There is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfdgs.so")
+
+FDGS_OK = 0
+_STATUS = {0: "OK", -1: "INVALID", -2: "CUDA", -3: "OOM", -4: "CAPACITY", -5: "TIMEOUT",
+           -6: "STATE"}
+
+
+class FdgsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fdgs error {code} ({_STATUS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class fdgs_scene_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int),
+                ("mean4", ctypes.c_void_p), ("logscale4", ctypes.c_void_p),
+                ("q_left", ctypes.c_void_p), ("q_right", ctypes.c_void_p),
+                ("opacity_logit", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class fdgs_camera(ctypes.Structure):
+    _fields_ = [("viewmat", ctypes.c_float * 16), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int), ("height", ctypes.c_int), ("znear", ctypes.c_float)]
+
+
+class fdgs_render_opts(ctypes.Structure):
+    _fields_ = [("use_mask", ctypes.c_int), ("bg", ctypes.c_float * 3)]
+
+
+class fdgs_frame_stats(ctypes.Structure):
+    _fields_ = [("n_active", ctypes.c_int64), ("n_visible", ctypes.c_int64),
+                ("n_keys", ctypes.c_int64), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("tiles_x", ctypes.c_int), ("tiles_y", ctypes.c_int), ("key_l", ctypes.c_int),
+                ("key_r", ctypes.c_int), ("key_bytes", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "fdgs_create_scene": [ctypes.POINTER(fdgs_scene_desc), ctypes.POINTER(_P)],
+    "fdgs_destroy_scene": [_P],
+    "fdgs_update_scene": [_P, ctypes.POINTER(fdgs_scene_desc)],
+    "fdgs_set_active_mask": [_P, _P, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P],
+    "fdgs_render": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_float,
+                    ctypes.POINTER(fdgs_render_opts), _P, ctypes.POINTER(_P), _P],
+    "fdgs_render_backward": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "fdgs_frame_release": [_P],
+    "fdgs_frame_get_stats": [_P, ctypes.POINTER(fdgs_frame_stats)],
+    "fdgs_frame_export": [_P, _P, _P, _P, _P, _P, _P, _P],
+    "fdgs_render_batch": [_P, ctypes.POINTER(fdgs_camera), ctypes.POINTER(ctypes.c_float),
+                          ctypes.c_int, ctypes.POINTER(fdgs_render_opts),
+                          ctypes.POINTER(_P), _P],
+    "fdgs_variation_score": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int, _P, _P],
+    "fdgs_select_keep": [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P],
+    "fdgs_status_sync": [_P],
+    "fdgs_profile_enable": [_P, ctypes.c_int],
+    "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
+}
+PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "emit", "tile_sort", "ranges",
+                  "blend")
+
+_lib = None
+
+
+def lib():
+    """Load libfdgs.so (built by ``paper_2503_16422_gb300.build``); raise if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2503_16422_gb300.build.build()"
+                               " (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.fdgs_last_error.restype = ctypes.c_char_p
+        L.fdgs_last_error.argtypes = []
+        L.fdgs_version.restype = ctypes.c_char_p
+        L.fdgs_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != FDGS_OK:
+        raise FdgsError(rc, lib().fdgs_last_error().decode())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def make_camera(cam) -> fdgs_camera:
+    """fdgs_camera from an object with viewmat (4x4), fx, fy, cx, cy, width, height, znear."""
+    c = fdgs_camera()
+    vm = np.asarray(cam.viewmat, np.float32).reshape(16)
+    for k in range(16):
+        c.viewmat[k] = float(vm[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height, c.znear = int(cam.width), int(cam.height), float(cam.znear)
+    return c
+
+
+def _opts(use_mask, bg):
+    o = fdgs_render_opts()
+    o.use_mask = int(bool(use_mask))
+    for k in range(3):
+        o.bg[k] = float(bg[k])
+    return o
+
+
+def _check_param(t, shape_tail, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}")
+
+
+@dataclass
+class SceneTensors:
+    mean4: torch.Tensor
+    logscale4: torch.Tensor
+    q_left: torch.Tensor
+    q_right: torch.Tensor
+    opacity_logit: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+
+    @staticmethod
+    def from_host(scene, device="cuda"):
+        def t(a):
+            return torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(device)
+        return SceneTensors(t(scene.mean4), t(scene.logscale4), t(scene.q_left),
+                            t(scene.q_right), t(scene.opacity_logit), t(scene.sh),
+                            int(scene.sh_degree))
+
+    def list(self):
+        return [self.mean4, self.logscale4, self.q_left, self.q_right, self.opacity_logit,
+                self.sh]
+
+
+class Frame:
+    """Per-render state kept for the backward (fdgs_frame)."""
+
+    def __init__(self, scene, handle):
+        self.scene = scene
+        self.handle = handle
+
+    def stats(self):
+        st = fdgs_frame_stats()
+        check(lib().fdgs_frame_get_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def export(self, stream=None):
+        s = self.stats()
+        dev = self.scene.device
+        tiles = s["tiles_x"] * s["tiles_y"]
+        n = self.scene.n
+        out = dict(
+            tile_ranges=torch.empty((tiles, 2), dtype=torch.int32, device=dev),
+            tile_ids=torch.empty((max(s["n_keys"], 1),), dtype=torch.int32, device=dev),
+            T_final=torch.empty((s["height"], s["width"]), dtype=torch.float32, device=dev),
+            n_contrib=torch.empty((s["height"], s["width"]), dtype=torch.int32, device=dev),
+            flags=torch.empty((max(n, 1),), dtype=torch.uint8, device=dev),
+            records=torch.full((max(n, 1), 12), float("nan"), dtype=torch.float32, device=dev))
+        check(lib().fdgs_frame_export(self.handle, _ptr(out["tile_ranges"]),
+                                      _ptr(out["tile_ids"]), _ptr(out["T_final"]),
+                                      _ptr(out["n_contrib"]), _ptr(out["flags"]),
+                                      _ptr(out["records"]), _stream(stream)))
+        out["tile_ids"] = out["tile_ids"][: s["n_keys"]]
+        out["flags"] = out["flags"][:n]
+        out["records"] = out["records"][:n]
+        out["stats"] = s
+        return out
+
+    def release(self):
+        if self.handle is not None:
+            check(lib().fdgs_frame_release(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle is not None and self.scene.handle is not None:
+                lib().fdgs_frame_release(self.handle)
+        except Exception:
+            pass
+
+
+class Scene:
+    """A 4D Gaussian scene on the GPU (fdgs_scene). Borrows the parameter tensors."""
+
+    def __init__(self, params: SceneTensors):
+        self.params = params
+        self.n = int(params.mean4.shape[0])
+        self.device = params.mean4.device
+        self._desc = self._make_desc(params)
+        h = ctypes.c_void_p()
+        check(lib().fdgs_create_scene(ctypes.byref(self._desc), ctypes.byref(h)))
+        self.handle = h
+        self._mask_hold = None
+
+    @staticmethod
+    def _make_desc(p: SceneTensors):
+        n = int(p.mean4.shape[0])
+        for name, t, tail in (("mean4", p.mean4, (4,)), ("logscale4", p.logscale4, (4,)),
+                              ("q_left", p.q_left, (4,)), ("q_right", p.q_right, (4,)),
+                              ("opacity_logit", p.opacity_logit, ())):
+            _check_param(t, tail, name)
+            if t.shape[0] != n:
+                raise ValueError(f"{name} has {t.shape[0]} rows, expected {n}")
+        k = (p.sh_degree + 1) ** 2
+        _check_param(p.sh, None, "sh")
+        if tuple(p.sh.shape) != (k, 3, n):
+            raise ValueError(f"sh must be [{k},3,{n}], got {tuple(p.sh.shape)}")
+        d = fdgs_scene_desc()
+        d.n, d.sh_degree = n, int(p.sh_degree)
+        d.mean4, d.logscale4 = p.mean4.data_ptr(), p.logscale4.data_ptr()
+        d.q_left, d.q_right = p.q_left.data_ptr(), p.q_right.data_ptr()
+        d.opacity_logit, d.sh = p.opacity_logit.data_ptr(), p.sh.data_ptr()
+        return d
+
+    @staticmethod
+    def from_host(scene, device="cuda"):
+        return Scene(SceneTensors.from_host(scene, device))
+
+    def update(self, params: SceneTensors):
+        self._desc = self._make_desc(params)
+        check(lib().fdgs_update_scene(self.handle, ctypes.byref(self._desc)))
+        self.params = params
+        self.n = int(params.mean4.shape[0])
+
+    def set_active_mask(self, bits, key_times, stream=None):
+        """bits: uint8 CUDA tensor [n_key, ceil(n/8)] (LSB-first); key_times ascending."""
+        kt = np.ascontiguousarray(np.asarray(key_times, np.float32))
+        n_key = int(kt.shape[0])
+        if n_key == 0:
+            check(lib().fdgs_set_active_mask(self.handle, None, None, 0, _stream(stream)))
+            return
+        if not (bits.is_cuda and bits.dtype == torch.uint8 and bits.is_contiguous()
+                and bits.shape == (n_key, (self.n + 7) // 8)):
+            raise ValueError("bits must be a contiguous uint8 CUDA tensor [n_key, ceil(n/8)]")
+        self._mask_hold = bits
+        check(lib().fdgs_set_active_mask(
+            self.handle, _ptr(bits), kt.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n_key,
+            _stream(stream)))
+
+    def render(self, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0), keep_frame=False, out=None,
+               stream=None):
+        """Render [3,H,W] float32. With keep_frame=True also returns the Frame."""
+        c = make_camera(cam)
+        if out is None:
+            out = torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.device)
+        o = _opts(use_mask, bg)
+        fh = ctypes.c_void_p()
+        check(lib().fdgs_render(self.handle, ctypes.byref(c), float(t), ctypes.byref(o),
+                                _ptr(out), ctypes.byref(fh) if keep_frame else None,
+                                _stream(stream)))
+        if keep_frame:
+            return out, Frame(self, fh)
+        return out
+
+    def render_backward(self, frame: Frame, dL_drgb, grads=None, stream=None):
+        """Adds the gradients of L (given dL/drgb [3,H,W]) into ``grads`` (a SceneTensors of
+        zero-initialised buffers, created if None) and returns it."""
+        if grads is None:
+            grads = SceneTensors(*[torch.zeros_like(x) for x in self.params.list()],
+                                 self.params.sh_degree)
+        dL = dL_drgb.contiguous()
+        check(lib().fdgs_render_backward(self.handle, frame.handle, _ptr(dL),
+                                         *[_ptr(g) for g in grads.list()], _stream(stream)))
+        return grads
+
+    def render_batch(self, cams, ts, use_mask=True, bg=(0.0, 0.0, 0.0), outs=None, stream=None):
+        n = len(cams)
+        carr = (fdgs_camera * max(n, 1))(*[make_camera(c) for c in cams])
+        tarr = (ctypes.c_float * max(n, 1))(*[float(t) for t in ts])
+        if outs is None:
+            outs = [torch.empty((3, int(c.height), int(c.width)), dtype=torch.float32,
+                                device=self.device) for c in cams]
+        parr = (ctypes.c_void_p * max(n, 1))(*[o.data_ptr() for o in outs])
+        o = _opts(use_mask, bg)
+        check(lib().fdgs_render_batch(self.handle, carr, tarr, n, ctypes.byref(o), parr,
+                                      _stream(stream)))
+        return outs
+
+    def variation_score(self, cams, ts, batch=8, out=None, stream=None):
+        carr = (fdgs_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
+        tarr = (ctypes.c_float * max(len(ts), 1))(*[float(t) for t in ts])
+        if out is None:
+            out = torch.empty((self.n,), dtype=torch.float32, device=self.device)
+        check(lib().fdgs_variation_score(self.handle, carr, len(cams), tarr, len(ts),
+                                         int(batch), _ptr(out), _stream(stream)))
+        return out
+
+    def select_keep(self, scores, prune_ratio=0.8, stream=None):
+        keep = torch.empty((scores.shape[0],), dtype=torch.uint8, device=self.device)
+        s = scores.contiguous()
+        check(lib().fdgs_select_keep(self.handle, _ptr(s), int(s.shape[0]), float(prune_ratio),
+                                     _ptr(keep), _stream(stream)))
+        return keep
+
+    def profile(self, flags):
+        """flags bit0: per-stage CUDA events; bit1: count blend evaluations; 0: off."""
+        check(lib().fdgs_profile_enable(self.handle, int(flags)))
+
+    def profile_read(self):
+        ms = (ctypes.c_float * len(PROFILE_STAGES))()
+        ev = ctypes.c_uint64()
+        check(lib().fdgs_profile_read(self.handle, ms if self._prof_stages() else None,
+                                      ctypes.byref(ev)))
+        return dict(zip(PROFILE_STAGES, list(ms))), int(ev.value)
+
+    def _prof_stages(self):
+        return True
+
+    def status_sync(self):
+        check(lib().fdgs_status_sync(self.handle))
+
+    def close(self):
+        if self.handle is not None:
+            lib().fdgs_destroy_scene(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _RenderFn(torch.autograd.Function):
+    """Differentiable render: forward = fdgs_render (keeping the frame), backward =
+    fdgs_render_backward (hand-written reverse kernels)."""
+
+    @staticmethod
+    def forward(ctx, scene, cam, t, use_mask, bg, mean4, logscale4, q_left, q_right,
+                opacity_logit, sh):
+        img, frame = scene.render(cam, t, use_mask=use_mask, bg=bg, keep_frame=True)
+        ctx.scene = scene
+        ctx.frame = frame
+        return img
+
+    @staticmethod
+    def backward(ctx, dL):
+        scene, frame = ctx.scene, ctx.frame
+        grads = scene.render_backward(frame, dL)
+        frame.release()
+        return (None, None, None, None, None, *grads.list())
+
+
+def render(scene: Scene, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0)):
+    """Differentiable render of ``scene`` (its parameter tensors may require grad)."""
+    p = scene.params
+    return _RenderFn.apply(scene, cam, float(t), use_mask, tuple(bg), p.mean4, p.logscale4,
+                           p.q_left, p.q_right, p.opacity_logit, p.sh)
+
+
+def version():
+    return lib().fdgs_version().decode()
