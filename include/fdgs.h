@@ -206,6 +206,25 @@ int fdgs_select_keep(fdgs_scene *scene, const float *score_dev, int64_t n, float
                      uint8_t *keep_out_dev, fdgs_stream stream);
 
 /*
+ * Same result as fdgs_select_keep, for callers that cannot allocate device memory. (The paper
+ * has no counterpart: this is a deployment variant.) fdgs_select_keep grows buffers with
+ * cudaMalloc/cudaFree, which synchronise the whole device and need free HBM; a caller inside a
+ * real-time render or training loop, or one whose HBM is fully reserved by another allocator,
+ * cannot allow either. This entry point allocates nothing: all of its scratch is one static
+ * 18 MiB device array that every GPU loading the library holds until the process exits.
+ *   - n must be <= 1048576 (2^20); larger n returns FDGS_ERR_CAPACITY. Other argument errors
+ *     return FDGS_ERR_INVALID. No scene is needed.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     and caches it; make that first call before any stream capture on that device.
+ *   - Every call on a device shares the one array and overwrites it (the parts that must start
+ *     at zero are cleared by each call). Calls whose GPU work overlaps (different streams,
+ *     or concurrent host threads) race on the array: serialise them.
+ *   - A device spin-wait timeout inside the sort is not reported by this entry point.
+ */
+int fdgs_select_keep_noalloc(const float *score_dev, int64_t n, float prune_ratio,
+                             uint8_t *keep_out_dev, fdgs_stream stream);
+
+/*
  * Stage profiling of the scene's subsequent fdgs_render calls. flags bit0: record CUDA
  * events on the render stream between the stages (FDGS_PROFILE_STAGES of them, in order:
  * preprocess, depth_sort, gather_scan, host_sync (the one mid-frame wait for the key count),

@@ -356,6 +356,8 @@ Workspace *take_workspace(fdgs_scene *s) {
 
 }  // namespace
 
+void fdgs::set_error_message(const char *msg) { g_err = msg ? msg : ""; }
+
 extern "C" {
 
 const char *fdgs_last_error(void) { return g_err.c_str(); }

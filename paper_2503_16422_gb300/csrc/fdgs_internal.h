@@ -109,4 +109,7 @@ void launch_keep_from_sorted(const uint64_t *sorted, uint32_t n, uint32_t n_drop
 
 int num_sms();
 
+// Sets the message returned by fdgs_last_error() on this thread.
+void set_error_message(const char *msg);
+
 }  // namespace fdgs

@@ -69,6 +69,7 @@ _SIGNATURES = {
     "fdgs_variation_score": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
                              ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int, _P, _P],
     "fdgs_select_keep": [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P],
+    "fdgs_select_keep_noalloc": [_P, ctypes.c_int64, ctypes.c_float, _P, _P],
     "fdgs_status_sync": [_P],
     "fdgs_profile_enable": [_P, ctypes.c_int],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
