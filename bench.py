@@ -179,18 +179,88 @@ def stage_bytes(stats, n, deg, masked):
     return {
         "preprocess": (2 * math.ceil(n / 32) * 4 if masked else 0) + na * 68 + nv * (sh + 48 + 8),
         "depth_sort": nv * 8 + 4 * nv * 16,
-        "gather_scan": nv * (8 + 48 + 48 + 4),
-        "emit": nv * (12 + 4) + K * kb,
-        "tile_sort": K * kb + passes * K * kb * 2,
-        "ranges": K * kb + tiles * 8,
+        "gather_scan": nv * (8 + 48 + 64 + 4 + 16),
+        "emit": nv * (20 + 4) + K * kb,
+        "tile_sort": passes * K * kb * 2,
+        "tile_scan": (stats["tiles_x"] + 1) * (stats["tiles_y"] + 1) * 4 * 3 + tiles * 8,
     }
+
+
+def _timed_steps(sc, cams, times, frames, masked, out, flush, stream):
+    import torch
+    step_ms = []
+    for k in frames:
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    return step_ms
+
+
+def _profile_frames(sc, cams, times, frames, masked, out, flush, scene):
+    """Untimed pass over the same frames: per-stage CUDA-event times, frame counts and the
+    blend evaluation count (the counting kernel variant is not the timed one)."""
+    from paper_2503_16422_gb300 import fdgs
+    sc.profile(1)
+    acc = {s: 0.0 for s in fdgs.PROFILE_STAGES}
+    stats_acc = []
+    for k in frames:
+        flush.fill_(1.0)
+        _, fr = sc.render(cams[k], float(times[k]), use_mask=masked, out=out, keep_frame=True)
+        ms, _ = sc.profile_read()
+        for s_ in acc:
+            acc[s_] += ms[s_]
+        stats_acc.append(fr.stats())
+        fr.release()
+    sc.profile(2)
+    evals = 0
+    for k in frames:
+        sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
+        evals += sc.profile_read()[1]
+    sc.profile(0)
+    nfr = len(frames)
+    stage_ms = {s_: acc[s_] / nfr for s_ in acc}
+    mean_stats = {f: float(np.mean([st[f] for st in stats_acc]))
+                  for f in ("n_active", "n_visible", "n_keys")}
+    sb = [stage_bytes(st, scene.n, scene.sh_degree, masked) for st in stats_acc]
+    bytes_mean = {s_: float(np.mean([b[s_] for b in sb])) for s_ in sb[0]}
+    return stage_ms, mean_stats, bytes_mean, evals / nfr
+
+
+def _roofline(stage_ms, bytes_mean, evals_per_frame):
+    pk = peaks()
+    dom = max((s_ for s_ in stage_ms if s_ != "host_sync"), key=stage_ms.get)
+    if dom == "blend":
+        ach = evals_per_frame * BLEND_FLOP_PER_EVAL / (stage_ms["blend"] / 1e3) / 1e12
+        peak = fp32_peak_tflops(pk["sm_mhz"])
+        return {"bound": "alu", "kernel": "k_blend", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_mhz']:.0f} MHz"}
+    ach = bytes_mean[dom] / (stage_ms[dom] / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
+            "frac": ach / pk["hbm"], "traffic": None, "peak_src": pk["src"]}
+
+
+def _scene_on_gpu(name):
+    import torch
+
+    from paper_2503_16422_gb300 import fdgs
+    scene, masked, kt, masks = make_workload(name)
+    sc = fdgs.Scene.from_host(scene)
+    if masked:
+        sc.set_active_mask(torch.as_tensor(masks).cuda(), kt)
+    return scene, masked, kt, masks, sc
 
 
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2503_16422_gb300 import build, fdgs, scenes
+    from paper_2503_16422_gb300 import build, scenes
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -198,21 +268,15 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    scene, masked, kt, masks = make_workload(args.workload)
-    sc = fdgs.Scene.from_host(scene)
-    if masked:
-        sc.set_active_mask(torch.as_tensor(masks).cuda(), kt)
+    scene, masked, kt, masks, sc = _scene_on_gpu(args.workload)
     times = scenes.frame_times()
     cams = {k: scenes.arc_camera(scenes.frame_theta(k)) for k in range(300)}
     out = torch.empty((3, 1014, 1352), dtype=torch.float32, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def render(k):
-        sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
-
     for k in frame_list(args.warmup, 1000 + rank):
-        render(k)
+        sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
     torch.cuda.synchronize()
     frames = frame_list(args.steps, rank * 37)
     clocks = Clocks(local)
@@ -220,16 +284,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms = []
-    for k in frames:
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        render(k)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+    step_ms = _timed_steps(sc, cams, times, frames, masked, out, flush, stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -241,68 +296,54 @@ def run_ours(args):
         total_ms = float(tt.item())
     value = world * len(frames) / (total_ms / 1e3)
 
-    # end to end: per step the camera/time go host->device as launch arguments and the
-    # rendered image comes back to pinned host memory
+    # end to end through the public API: per step the camera and t go host->device as
+    # launch arguments and the rendered image comes back to pinned host memory
     host = torch.empty((3, 1014, 1352), dtype=torch.float32, pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in frames:
-        render(k)
+        sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
         host.copy_(out, non_blocking=True)
         stream.synchronize()
     e2e_s = time.perf_counter() - t0
     cam_bytes = 16 * 4 + 4 * 4 + 3 * 4 + 4 + 4 + 4   # fdgs_camera + t + opts
     res = {}
     if rank == 0:
-        # per-stage profile and evaluation counts over the same frames (untimed pass)
-        sc.profile(1)
-        acc = {s: 0.0 for s in fdgs.PROFILE_STAGES}
-        stats_acc = []
-        for k in frames:
-            flush.fill_(1.0)
-            _, fr = sc.render(cams[k], float(times[k]), use_mask=masked, out=out,
-                              keep_frame=True)
-            ms, _ = sc.profile_read()
-            for s_ in acc:
-                acc[s_] += ms[s_]
-            stats_acc.append(fr.stats())
-            fr.release()
-        sc.profile(2)
-        evals = 0
-        for k in frames:
-            render(k)
-            evals += sc.profile_read()[1]
-        sc.profile(0)
-        nfr = len(frames)
-        stage_ms = {s_: acc[s_] / nfr for s_ in acc}
-        pk = peaks()
-        mean_stats = {f: float(np.mean([st[f] for st in stats_acc]))
-                      for f in ("n_active", "n_visible", "n_keys")}
-        sb = [stage_bytes(st, scene.n, scene.sh_degree, masked) for st in stats_acc]
-        bytes_mean = {s_: float(np.mean([b[s_] for b in sb])) for s_ in sb[0]}
-        dom = max((s_ for s_ in stage_ms if s_ != "host_sync"), key=stage_ms.get)
-        if dom == "blend":
-            ach = evals / nfr * BLEND_FLOP_PER_EVAL / (stage_ms["blend"] / 1e3) / 1e12
-            peak = fp32_peak_tflops(pk["sm_mhz"])
-            roof = {"bound": "alu", "kernel": "blend", "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                    "peak_src": f"152 SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_mhz']:.0f} MHz"}
-        else:
-            ach = bytes_mean[dom] / (stage_ms[dom] / 1e3) / 1e9
-            roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm"],
-                    "unit": "GB/s", "frac": ach / pk["hbm"], "traffic": None,
-                    "peak_src": pk["src"]}
-        res = dict(stage_ms=stage_ms, mean_counts=mean_stats, evals_per_frame=evals / nfr,
-                   roofline=roof, clocks=clk,
+        stage_ms, mean_stats, bytes_mean, evals = _profile_frames(
+            sc, cams, times, frames, masked, out, flush, scene)
+        res = dict(stage_ms=stage_ms, mean_counts=mean_stats, evals_per_frame=evals,
+                   roofline=_roofline(stage_ms, bytes_mean, evals), clocks=clk,
                    e2e=dict(value=len(frames) / e2e_s, unit="FPS",
                             h2d_bytes_per_step=cam_bytes,
                             d2h_bytes_per_step=3 * 1014 * 1352 * 4),
                    stage_gbs={s_: bytes_mean[s_] / (stage_ms[s_] / 1e3) / 1e9
                               for s_ in bytes_mean if stage_ms[s_] > 0},
-                   blend_tflops=evals / nfr * BLEND_FLOP_PER_EVAL /
-                   max(stage_ms["blend"], 1e-9) / 1e9,
-                   gpu_launches=None)
+                   blend_tflops=evals * BLEND_FLOP_PER_EVAL / max(stage_ms["blend"], 1e-9) / 1e9)
     sc.close()
+    if rank == 0 and not args.no_extra:
+        res["comparisons"] = {}
+        for name in ("pruned_unmasked", "unpruned_masked", "unpruned_unmasked"):
+            if name == args.workload:
+                continue
+            sc2 = None
+            try:
+                scn, msk, _, _, sc2 = _scene_on_gpu(name)
+                fr = frame_list(12, 5)
+                for k in frame_list(2, 900):
+                    sc2.render(cams[k], float(times[k]), use_mask=msk, out=out)
+                ms = _timed_steps(sc2, cams, times, fr, msk, out, flush, stream)
+                st_ms, counts, _, ev = _profile_frames(sc2, cams, times, fr[:4], msk, out,
+                                                       flush, scn)
+                res["comparisons"][name] = dict(
+                    fps=len(fr) / (sum(ms) / 1e3), ms_per_frame=sum(ms) / len(fr),
+                    raster_ms=sum(st_ms[s_] for s_ in ("tile_scan", "emit", "tile_sort", "blend")),
+                    stages_ms=st_ms, counts_per_frame=dict(counts, blend_evals=ev))
+            except Exception as e:   # a comparison must not hide the headline number
+                res["comparisons"][name] = {"error": str(e)[:200]}
+            finally:
+                if sc2 is not None:
+                    sc2.close()
+                torch.cuda.empty_cache()
     return value, total_ms / len(frames), res, scene, masked, kt, masks, world, rank
 
 
@@ -351,6 +392,9 @@ def main():
     line["stage_gbs"] = res["stage_gbs"]
     line["blend_tflops"] = res["blend_tflops"]
     line["counts_per_frame"] = dict(res["mean_counts"], blend_evals=res["evals_per_frame"])
+    line["raster_ms"] = sum(res["stage_ms"][s_] for s_ in ("tile_scan", "emit", "tile_sort", "blend"))
+    if "comparisons" in res:
+        line["comparisons"] = res["comparisons"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_fps(scene, masked, kt, masks)
     print(json.dumps(line))

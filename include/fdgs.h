@@ -100,6 +100,7 @@ typedef struct {
   int width, height, tiles_x, tiles_y;
   int key_l, key_r;    /* key-frames used by the mask gate, -1 when unmasked */
   int key_bytes;       /* 4 or 8: width of the packed (tile, depth-rank) sort key */
+  int list_builder;    /* how the tile lists were built: 1 emit + radix sort, 2 bitmasks */
 } fdgs_frame_stats;
 
 /* Creates a scene on the current CUDA device. Borrows the attribute pointers (see above).
@@ -228,7 +229,7 @@ int fdgs_select_keep_noalloc(const float *score_dev, int64_t n, float prune_rati
  * Stage profiling of the scene's subsequent fdgs_render calls. flags bit0: record CUDA
  * events on the render stream between the stages (FDGS_PROFILE_STAGES of them, in order:
  * preprocess, depth_sort, gather_scan, host_sync (the one mid-frame wait for the key count),
- * emit, tile_sort, ranges, blend); bit1: count the
+ * tile_scan, emit, tile_sort, blend); bit1: count the
  * (Gaussian, pixel) evaluations of the blend (a slower kernel variant; use it in an
  * untimed pass). 0 turns profiling off.
  */
@@ -238,6 +239,19 @@ int fdgs_profile_enable(fdgs_scene *scene, int flags);
 /* Stage times in milliseconds of the last profiled render, and the blend evaluation count
  * of the last counted render (either pointer may be NULL). Synchronises the device. */
 int fdgs_profile_read(fdgs_scene *scene, float *stage_ms, uint64_t *blend_evals);
+
+/* How renders build the per-tile lists, process-wide. 1: emit one (tile, depth-rank) key
+ * per covered tile and radix-sort the keys by tile; 2: AND per-tile-row and per-tile-column
+ * coverage bitmasks over the depth ranks (no sort; wins when Gaussians cover many tiles);
+ * 0 (default): choose per frame by a traffic estimate. The lists, and so every result, are
+ * identical either way. Returns FDGS_ERR_INVALID for other values. */
+int fdgs_set_list_builder(int mode);
+
+/* Launch shape of the forward blend, process-wide: the pixel footprint of one warp inside a
+ * 16x16 tile (0: 16x2, 1: 8x4 (default), 2: 4x8). Each warp culls, by ballot, the Gaussians
+ * that cannot reach alpha >= 1/255 anywhere in its footprint; results do not depend on the
+ * shape. Returns FDGS_ERR_INVALID for other values. */
+int fdgs_set_blend_shape(int footprint);
 
 /* Reads and clears the scene's device status word (synchronises the device): FDGS_OK, or
  * FDGS_ERR_CAPACITY / FDGS_ERR_TIMEOUT raised by a kernel since the last read. */

@@ -89,10 +89,12 @@ struct Workspace {
   Buf scratch;                   // sort scratch
   Buf g2d;                       // f32[n][9] backward accumulators
   Buf wsum;                      // f32[n] per-rank blend weights (score pass)
+  Buf diff;                      // i32[gy + 1][gx + 1] tile-coverage difference array
+  Buf rowmask, colmask;          // u32 coverage bitmasks by depth rank per tile row / column
   ~Workspace() {
     Buf *all[] = {&ctr, &pre_status, &scan_status, &rec, &rec_sorted, &vis[0], &vis[1],
                   &offsets, &flags, &keys[0], &keys[1], &ranges, &Tf, &nc, &scratch, &g2d,
-                  &wsum};
+                  &wsum, &diff, &rowmask, &colmask};
     for (Buf *b : all) b->release();
     if (hctr) cudaFreeHost(hctr);
   }
@@ -104,7 +106,7 @@ struct FrameMeta {
   int W = 0, H = 0, gx = 0, gy = 0, l = -1, r = -1;
   uint32_t n_active = 0, nv = 0;
   uint64_t nkeys = 0;
-  int key64 = 0, rb = 1;
+  int key64 = 0, rb = 1, builder = 1;
   uint64_t *sorted = nullptr;
   void *keys = nullptr;
   float bg[3] = {0.f, 0.f, 0.f};
@@ -195,6 +197,22 @@ int check_device_errors(fdgs_scene *s, cudaStream_t st) {
   return FDGS_OK;
 }
 
+// Key emission in depth-rank order, then the stable sort on the tile bits (the digit
+// offsets were written by the tile scan). Returns the buffer holding the sorted keys.
+template <typename K>
+K *emit_and_sort(Workspace &ws, uint32_t nv, uint64_t nkeys, int gx, int gy, int rb, int tb,
+                 uint32_t *ctr, uint32_t *err, cudaEvent_t *ev, cudaStream_t st) {
+  K *k0 = ws.keys[0].as<K>(), *k1 = ws.keys[1].as<K>();
+  K *out = k0;
+  if (nkeys)
+    launch_emit<K>(ws.rec_sorted.as<float>(), ws.offsets.as<uint32_t>(), nv, gx, gy, rb, k0, st);
+  if (ev) cudaEventRecord(ev[6], st);
+  if (nkeys)
+    out = radix_sort<K>(k0, k1, ctr + C_NKEYS_LO, nkeys, rb, tb, ws.scratch.p, st, err, true);
+  if (ev) cudaEventRecord(ev[7], st);
+  return out;
+}
+
 // One render into workspace ws. want_flags: also write per-Gaussian decision flags.
 // wsum: per-rank blend weights are accumulated (score pass); the buffer is zeroed here.
 int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
@@ -213,7 +231,17 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   TRY(grow(ws.pre_status, parts * 8));
   TRY(grow(ws.scan_status, parts * 8));
   TRY(grow(ws.rec, n1 * kRec * 4));
-  TRY(grow(ws.rec_sorted, n1 * kRec * 4));
+  TRY(grow(ws.rec_sorted, n1 * kRecS * 4));
+  TRY(grow(ws.diff, (uint64_t)(gx + 1) * (gy + 1) * 4));
+  // coverage bitmasks (one bit per depth rank, per tile row and per tile column) are written
+  // by the gather whenever the bitmask list builder may be chosen after the key count is known
+  const uint32_t mask_words = (uint32_t)((N + 255) / 256 * 8);
+  const uint64_t mask_bytes = (uint64_t)(gx + gy) * mask_words * 4;
+  const bool want_masks = g_list_mode != 1 && N > 0 && mask_bytes <= (512ull << 20);
+  if (want_masks) {
+    TRY(grow(ws.rowmask, (uint64_t)gy * mask_words * 4));
+    TRY(grow(ws.colmask, (uint64_t)gx * mask_words * 4));
+  }
   TRY(grow(ws.vis[0], n1 * 8));
   TRY(grow(ws.vis[1], n1 * 8));
   TRY(grow(ws.offsets, n1 * 4));
@@ -239,6 +267,7 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   CK(cudaMemsetAsync(ws.ctr.p, 0, C_COUNT * 4, st));
   CK(cudaMemsetAsync(ws.pre_status.p, 0, parts * 8, st));
   CK(cudaMemsetAsync(ws.scan_status.p, 0, parts * 8, st));
+  CK(cudaMemsetAsync(ws.diff.p, 0, (size_t)(gx + 1) * (gy + 1) * 4, st));
   uint32_t *ctr = ws.ctr.as<uint32_t>();
   uint32_t *err = s->status.as<uint32_t>();
 
@@ -267,7 +296,9 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
                                           ctr + C_NVIS, N, 32, 32, ws.scratch.p, st, err);
   if (prof) CK(cudaEventRecord(s->ev[2], st));
   launch_gather_scan(sorted, ctr + C_NVIS, N, ws.rec.as<float>(), ws.rec_sorted.as<float>(),
-                     ws.offsets.as<uint32_t>(), ws.scan_status.as<uint64_t>(), ctr, err, st);
+                     ws.offsets.as<uint32_t>(), ws.scan_status.as<uint64_t>(), ctr, err, gx, gy,
+                     ws.diff.as<int>(), want_masks ? ws.rowmask.as<uint32_t>() : nullptr,
+                     want_masks ? ws.colmask.as<uint32_t>() : nullptr, mask_words, st);
   if (prof) CK(cudaEventRecord(s->ev[3], st));
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(ws.hctr, ctr, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
@@ -278,16 +309,24 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   if (nkeys > kSortMaxKeys)
     return fail(FDGS_ERR_CAPACITY, "%llu tile keys exceed the sort limit",
                 (unsigned long long)nkeys);
-  const int rb = ceil_log2(std::max<uint32_t>(nv, 2));
   const int tb = ceil_log2(std::max<uint64_t>(tiles, 2));
-  const int key64 = (rb + tb) > 32;
+  // List builder: coverage bitmasks read tiles x ceil(nv/32) word pairs from L2; emit + sort
+  // move the keys through DRAM (1 write + 2 per pass). Bitmasks win when coverage is dense.
+  const uint64_t words = (nv + 31) / 32;
+  const int rb_sort = ceil_log2(std::max<uint32_t>(nv, 2));
+  const uint64_t kb_sort = (rb_sort + tb) > 32 ? 8 : 4;
+  const bool use_masks =
+      want_masks && nkeys > 0 &&
+      (g_list_mode == 2 ||
+       tiles * words * 8 < 2 * nkeys * kb_sort * (1 + 2 * (uint64_t)sort_passes(tb)));
+  const int rb = use_masks ? 32 : rb_sort;
+  const int key64 = use_masks ? 0 : (rb + tb) > 32;
   const size_t kb = key64 ? 8 : 4;
   const uint64_t k1 = std::max<uint64_t>(nkeys, 1);
   TRY(grow(ws.keys[0], k1 * kb));
-  TRY(grow(ws.keys[1], k1 * kb));
+  if (!use_masks) TRY(grow(ws.keys[1], k1 * kb));
   TRY(grow(ws.scratch, std::max(sort_scratch_bytes(n1, 32), sort_scratch_bytes(k1, tb))));
   if (want_wsum) CK(cudaMemsetAsync(ws.wsum.p, 0, n1 * 4, st));
-  CK(cudaMemsetAsync(ws.ranges.p, 0, tiles * 8, st));
   const uint32_t rmask = (uint32_t)((1ull << rb) - 1);
   BlendArgs ba;
   ba.ranges = ws.ranges.as<uint2>();
@@ -299,35 +338,29 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   ba.n_contrib = ws.nc.as<uint32_t>();
   ba.w_sum = want_wsum ? ws.wsum.as<float>() : nullptr;
   ba.evals = count ? s->evals.as<unsigned long long>() : nullptr;
-  void *skeys = ws.keys[0].p;
   if (prof) CK(cudaEventRecord(s->ev[4], st));   // ev[3] -> ev[4]: the host synchronisation
-  if (key64) {
-    uint64_t *k0 = ws.keys[0].as<uint64_t>(), *k1p = ws.keys[1].as<uint64_t>();
-    if (nkeys)
-      launch_emit<uint64_t>(ws.rec_sorted.as<float>(), ws.offsets.as<uint32_t>(), nv, gx, gy, rb,
-                            k0, st);
-    if (prof) CK(cudaEventRecord(s->ev[5], st));
-    if (nkeys)
-      skeys = radix_sort<uint64_t>(k0, k1p, ctr + C_NKEYS_LO, nkeys, rb, tb, ws.scratch.p, st, err);
+  // tile ranges and the tile sort's digit offsets, straight from the coverage counts
+  launch_tile_scan(ws.diff.as<int>(), gx, gy, use_masks ? 0 : sort_passes(tb),
+                   sort_digit_bits(tb), ws.ranges.as<uint2>(), sort_hist(ws.scratch.p), st);
+  if (prof) CK(cudaEventRecord(s->ev[5], st));
+  void *skeys;
+  if (use_masks) {
+    // lists of plain ranks straight in tile-major, depth order (the "emit" stage; no sort)
+    launch_tile_lists(ws.rowmask.as<uint32_t>(), ws.colmask.as<uint32_t>(), mask_words, nv, gx,
+                      gy, ws.ranges.as<uint2>(), ws.keys[0].as<uint32_t>(), st);
     if (prof) CK(cudaEventRecord(s->ev[6], st));
-    if (nkeys)
-      launch_ranges<uint64_t>((uint64_t *)skeys, (uint32_t)nkeys, rb, ws.ranges.as<uint2>(), st);
     if (prof) CK(cudaEventRecord(s->ev[7], st));
-    launch_blend<uint64_t>(ba, (const uint64_t *)skeys, rmask, st);
+    skeys = ws.keys[0].p;
   } else {
-    uint32_t *k0 = ws.keys[0].as<uint32_t>(), *k1p = ws.keys[1].as<uint32_t>();
-    if (nkeys)
-      launch_emit<uint32_t>(ws.rec_sorted.as<float>(), ws.offsets.as<uint32_t>(), nv, gx, gy, rb,
-                            k0, st);
-    if (prof) CK(cudaEventRecord(s->ev[5], st));
-    if (nkeys)
-      skeys = radix_sort<uint32_t>(k0, k1p, ctr + C_NKEYS_LO, nkeys, rb, tb, ws.scratch.p, st, err);
-    if (prof) CK(cudaEventRecord(s->ev[6], st));
-    if (nkeys)
-      launch_ranges<uint32_t>((uint32_t *)skeys, (uint32_t)nkeys, rb, ws.ranges.as<uint2>(), st);
-    if (prof) CK(cudaEventRecord(s->ev[7], st));
-    launch_blend<uint32_t>(ba, (const uint32_t *)skeys, rmask, st);
+    skeys = key64 ? (void *)emit_and_sort<uint64_t>(ws, nv, nkeys, gx, gy, rb, tb, ctr, err,
+                                                     prof ? s->ev : nullptr, st)
+                  : (void *)emit_and_sort<uint32_t>(ws, nv, nkeys, gx, gy, rb, tb, ctr, err,
+                                                     prof ? s->ev : nullptr, st);
   }
+  if (key64)
+    launch_blend<uint64_t>(ba, (const uint64_t *)skeys, rmask, st);
+  else
+    launch_blend<uint32_t>(ba, (const uint32_t *)skeys, rmask, st);
   if (prof) CK(cudaEventRecord(s->ev[8], st));
   CK(cudaGetLastError());
   m.cam = dc;
@@ -338,6 +371,7 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   m.nkeys = nkeys;
   m.key64 = key64;
   m.rb = rb;
+  m.builder = use_masks ? 2 : 1;
   m.sorted = sorted;
   m.keys = skeys;
   for (int c = 0; c < 3; ++c) m.bg[c] = ba.bg[c];
@@ -357,6 +391,7 @@ Workspace *take_workspace(fdgs_scene *s) {
 }  // namespace
 
 void fdgs::set_error_message(const char *msg) { g_err = msg ? msg : ""; }
+int fdgs::g_list_mode = 0;
 
 extern "C" {
 
@@ -483,6 +518,7 @@ int fdgs_frame_get_stats(fdgs_frame *f, fdgs_frame_stats *o) {
   o->key_l = f->m.l;
   o->key_r = f->m.r;
   o->key_bytes = f->m.key64 ? 8 : 4;
+  o->list_builder = f->m.builder;
   return FDGS_OK;
 }
 
@@ -513,7 +549,7 @@ int fdgs_frame_export(fdgs_frame *f, uint32_t *tile_ranges_dev, uint32_t *tile_i
     CK(cudaMemcpyAsync(gauss_flags_dev, ws.flags.p, (size_t)f->scene->d.n,
                        cudaMemcpyDeviceToDevice, st));
   if (records_dev)
-    launch_export_records(m.sorted, m.nv, ws.rec_sorted.as<float>(), records_dev, st);
+    launch_export_records(m.sorted, m.nv, ws.rec.as<float>(), records_dev, st);
   CK(cudaGetLastError());
   return FDGS_OK;
 }
@@ -645,6 +681,20 @@ int fdgs_select_keep(fdgs_scene *s, const float *score_dev, int64_t n, float pru
   const uint32_t n_drop = (uint32_t)floor((double)prune_ratio * (double)N);
   launch_keep_from_sorted(srt, N, n_drop, keep_out_dev, st);
   CK(cudaGetLastError());
+  return FDGS_OK;
+}
+
+int fdgs_set_list_builder(int mode) {
+  if (mode < 0 || mode > 2)
+    return fail(FDGS_ERR_INVALID, "mode must be 0 (auto), 1 (sort) or 2 (bitmask)");
+  g_list_mode = mode;
+  return FDGS_OK;
+}
+
+int fdgs_set_blend_shape(int footprint) {
+  if (footprint < 0 || footprint > 2)
+    return fail(FDGS_ERR_INVALID, "footprint must be 0 (16x2), 1 (8x4) or 2 (4x8)");
+  g_blend_shape = footprint;
   return FDGS_OK;
 }
 

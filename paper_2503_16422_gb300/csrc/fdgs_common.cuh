@@ -150,21 +150,70 @@ __device__ __forceinline__ void tile_rect(float u, float v, float r, int gx, int
   ymax = (int)fminf(fmaxf(y1, 0.f), (float)gy);
 }
 
-// Alpha of one (Gaussian, pixel) pair, shared by the forward blend and the backward replay
-// so that both take the same decisions bit for bit. d = mean2D - pixel;
-// power = -1/2 (A dx^2 + C dy^2) - B dx dy; returns false when power > 0 or the clamped
-// alpha = min(0.99, a exp(power)) is below 1/255.
-__device__ __forceinline__ bool eval_alpha(float u, float v, float A, float B, float C,
-                                           float a, float px, float py, float &alpha,
-                                           float &G, float &dx, float &dy) {
+// ---- blend-ready record (depth-rank order), 16 floats = 64 B -----------------------------
+// [0..3]  u, v, a2 = -A/2 log2(e), b2 = -B log2(e)       (image centre, scaled conic)
+// [4..7]  c2 = -C/2 log2(e), lga = log2(a), r, g        (a = sigmoid(o) p(t))
+// [8..11] b, kx = -b2 / (2 a2), ky = -b2 / (2 c2), radius
+// [12..15] A, B, C, a                                   (raw conic and opacity, backward)
+constexpr int kRecS = 16;
+constexpr int kRecSRadius = 11;
+// Footprint culling margin (log2 units): a Gaussian is culled for a pixel footprint only if
+// its largest exponent over the footprint rectangle is below log2(1/255) by more than this,
+// far beyond float32 rounding of the per-pixel exponent, so per-pixel decisions never change.
+constexpr float kCullMargin = 0.01f;
+
+// Largest value of q(d) = a2 dx^2 + b2 dx dy + c2 dy^2 (a concave quadratic) over the
+// rectangle of offsets d in [dxl, dxh] x [dyl, dyh]: 0 if the rectangle holds d = 0, else
+// the best of its four edges (on each edge the 1D maximiser, kx*Y or ky*X, clamped).
+__device__ __forceinline__ float quad_max_rect(float a2, float b2, float c2, float kx, float ky,
+                                               float dxl, float dxh, float dyl, float dyh) {
+  if (dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f) return 0.f;
+  float best = -INFINITY;
+  {
+    const float dy = fminf(fmaxf(ky * dxl, dyl), dyh);
+    best = fmaxf(best, dxl * (a2 * dxl + b2 * dy) + c2 * dy * dy);
+  }
+  {
+    const float dy = fminf(fmaxf(ky * dxh, dyl), dyh);
+    best = fmaxf(best, dxh * (a2 * dxh + b2 * dy) + c2 * dy * dy);
+  }
+  {
+    const float dx = fminf(fmaxf(kx * dyl, dxl), dxh);
+    best = fmaxf(best, dx * (a2 * dx + b2 * dyl) + c2 * dyl * dyl);
+  }
+  {
+    const float dx = fminf(fmaxf(kx * dyh, dxl), dxh);
+    best = fmaxf(best, dx * (a2 * dx + b2 * dyh) + c2 * dyh * dyh);
+  }
+  return best;
+}
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLog2AlphaMin = -7.9943534368588578f;   // log2(1/255)
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Alpha of one (Gaussian, pixel) pair from the blend-ready record, shared by the forward
+// blend and the backward replay so both take the same decisions bit for bit.
+// d = mean2D - pixel; q = log2(e) * power with power = -1/2 (A dx^2 + 2 B dx dy + C dy^2);
+// skipped when power > 0 or when the exponent e = q + log2(a) puts a * exp(power) below
+// 1/255; otherwise alpha = min(0.99, 2^e) and raw = 2^e (before the clamp).
+__device__ __forceinline__ bool splat_alpha(float u, float v, float a2, float b2, float c2,
+                                            float lga, float px, float py, float &alpha,
+                                            float &raw, float &dx, float &dy) {
   dx = __fsub_rn(u, px);
   dy = __fsub_rn(v, py);
-  float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
-  float power = __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
-  if (power > 0.f) return false;
-  G = __expf(power);
-  alpha = fminf(kAlphaMax, __fmul_rn(a, G));
-  return alpha >= kAlphaMin;
+  const float q = __fmaf_rn(dx, __fmaf_rn(a2, dx, __fmul_rn(b2, dy)),
+                            __fmul_rn(__fmul_rn(c2, dy), dy));
+  if (q > 0.f) return false;
+  const float e = __fadd_rn(q, lga);
+  if (e < kLog2AlphaMin) return false;
+  raw = ex2_approx(e);
+  alpha = fminf(kAlphaMax, raw);
+  return true;
 }
 
 }  // namespace fdgs

@@ -13,10 +13,14 @@ namespace fdgs {
 // Returns the buffer that holds the result (a or b). scratch must hold
 // sort_scratch_bytes(n_cap, bits) bytes.
 size_t sort_scratch_bytes(uint64_t n_cap, int bits);
+// With hist_ready the caller has already written each pass's exclusive digit offsets into
+// sort_hist(scratch) (256 words per pass) and the histogram kernels are skipped.
 template <typename K>
 K *radix_sort(K *a, K *b, const uint32_t *n_dev, uint64_t n_cap, int lo, int bits,
-              void *scratch, cudaStream_t st, uint32_t *err_dev);
+              void *scratch, cudaStream_t st, uint32_t *err_dev, bool hist_ready = false);
 int sort_passes(int bits);
+int sort_digit_bits(int bits);
+inline uint32_t *sort_hist(void *scratch) { return static_cast<uint32_t *>(scratch); }
 constexpr uint64_t kSortMaxKeys = (1ull << 30) - 1;
 
 // ---- rasterizer kernels (fdgs_raster.cu) -----------------------------------------------
@@ -37,15 +41,27 @@ struct PreArgs {
 };
 void launch_preprocess(const PreArgs &a, cudaStream_t st);
 
+// rec_sorted is the blend-ready record [nv][16] (see fdgs_common.cuh); diff is the
+// [gy + 1][gx + 1] tile-coverage difference array (zeroed by the caller).
 void launch_gather_scan(const uint64_t *sorted, const uint32_t *ctr_nvis, uint32_t n_cap,
                         const float *rec, float *rec_sorted, uint32_t *offsets,
-                        uint64_t *status, uint32_t *ctr, uint32_t *err, cudaStream_t st);
+                        uint64_t *status, uint32_t *ctr, uint32_t *err, int gx, int gy,
+                        int *diff, uint32_t *rowmask, uint32_t *colmask, uint32_t mask_words,
+                        cudaStream_t st);
+// Tile lists by coverage bitmasks (rowmask/colmask written by the gather when non-null,
+// [gy or gx][mask_words] words): lists[ranges[t].x ..] = ranks covering tile t, ascending.
+void launch_tile_lists(const uint32_t *rowmask, const uint32_t *colmask, uint32_t mask_words,
+                       uint32_t nv, int gx, int gy, const uint2 *ranges, uint32_t *lists,
+                       cudaStream_t st);
+// Tile-list builder: 0 auto (cost model), 1 emit + radix sort, 2 coverage bitmasks.
+extern int g_list_mode;
+// Integrates diff into per-tile counts; writes tile ranges and the tile sort's digit offsets.
+void launch_tile_scan(int *diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
+                      uint32_t *hist, cudaStream_t st);
 
 template <typename K>
 void launch_emit(const float *rec_sorted, const uint32_t *offsets, uint32_t nv, int gx, int gy,
                  int rb, K *keys, cudaStream_t st);
-template <typename K>
-void launch_ranges(const K *keys, uint32_t nkeys, int rb, uint2 *ranges, cudaStream_t st);
 
 struct BlendArgs {
   const uint2 *ranges;
@@ -91,7 +107,7 @@ void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st);
 template <typename K>
 void launch_keys_to_ids(const K *keys, uint32_t nkeys, uint32_t rmask, const uint64_t *sorted,
                         uint32_t *ids, cudaStream_t st);
-void launch_export_records(const uint64_t *sorted, uint32_t nv, const float *rec_sorted,
+void launch_export_records(const uint64_t *sorted, uint32_t nv, const float *rec,
                            float *out, cudaStream_t st);
 // V_i = prod of the four scales, as float bits (positive floats sort as unsigned ints)
 void launch_volume_bits(const float4 *ls4, uint32_t n, uint32_t *vbits, cudaStream_t st);
@@ -108,6 +124,7 @@ void launch_keep_from_sorted(const uint64_t *sorted, uint32_t n, uint32_t n_drop
                              uint8_t *keep, cudaStream_t st);
 
 int num_sms();
+extern int g_blend_shape;   // warp footprint of the forward blend: 0 16x2, 1 8x4, 2 4x8
 
 // Sets the message returned by fdgs_last_error() on this thread.
 void set_error_message(const char *msg);

@@ -122,12 +122,16 @@ __global__ void __launch_bounds__(kBlock) k_preprocess(PreArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Records into depth-rank order + exclusive scan of the per-Gaussian tile counts.
+// Records into depth-rank order (blend-ready form) + exclusive scan of the per-Gaussian
+// tile counts (key offsets) + per-tile coverage counts as a 2D difference array (four
+// atomics per Gaussian; k_tile_scan integrates it).
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock)
 k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ nv_dev,
               const float *__restrict__ rec, float *__restrict__ rec_sorted,
-              uint32_t *__restrict__ offsets, uint64_t *status, uint32_t *ctr, uint32_t *err) {
+              uint32_t *__restrict__ offsets, uint64_t *status, uint32_t *ctr, uint32_t *err,
+              int gx, int gy, int *__restrict__ diff, uint32_t *__restrict__ rowmask,
+              uint32_t *__restrict__ colmask, uint32_t mask_words) {
   __shared__ uint32_t s_part;
   __shared__ uint32_t s_wtot[kWarps];
   __shared__ uint64_t s_base;
@@ -141,15 +145,43 @@ k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ 
     if (part >= nparts) break;
     const uint32_t r = part * kBlock + tid;
     uint32_t cnt = 0;
+    if (rowmask) {
+      // coverage bitmasks by depth rank: bit (r & 31) of word r / 32 of tile row y / column x
+      // is set iff the Gaussian of rank r covers that row / column. Each warp owns one word.
+      int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+      if (r < nv) {
+        const float *src = rec + (size_t)((uint32_t)sorted[r]) * kRec;
+        tile_rect(src[R_U], src[R_V], src[R_RADIUS], gx, gy, x0, y0, x1, y1);
+      }
+      const uint32_t word = r >> 5;
+      for (int y = 0; y < gy; ++y) {
+        const uint32_t b = __ballot_sync(0xffffffffu, y >= y0 && y < y1);
+        if (lane == (y & 31)) rowmask[(size_t)y * mask_words + word] = b;
+      }
+      for (int x = 0; x < gx; ++x) {
+        const uint32_t b = __ballot_sync(0xffffffffu, x >= x0 && x < x1);
+        if (lane == (x & 31)) colmask[(size_t)x * mask_words + word] = b;
+      }
+    }
     if (r < nv) {
       const uint32_t id = (uint32_t)sorted[r];
       const float4 *src = reinterpret_cast<const float4 *>(rec + (size_t)id * kRec);
-      float4 *dst = reinterpret_cast<float4 *>(rec_sorted + (size_t)r * kRec);
+      float4 *dst = reinterpret_cast<float4 *>(rec_sorted + (size_t)r * kRecS);
       const float4 a0 = src[0], a1 = src[1], a2 = src[2];
-      dst[0] = a0;
-      dst[1] = a1;
-      dst[2] = a2;
+      // a0 = (u, v, A, B), a1 = (C, a, r, g), a2 = (b, depth, radius, count)
+      const float qa = -0.5f * kLog2e * a0.z, qb = -kLog2e * a0.w, qc = -0.5f * kLog2e * a1.x;
+      dst[0] = make_float4(a0.x, a0.y, qa, qb);
+      dst[1] = make_float4(qc, log2f(a1.y), a1.z, a1.w);
+      dst[2] = make_float4(a2.x, -qb / (2.f * qa), -qb / (2.f * qc), a2.z);
+      dst[3] = make_float4(a0.z, a0.w, a1.x, a1.y);
       cnt = (uint32_t)a2.w;
+      int x0, y0, x1, y1;
+      tile_rect(a0.x, a0.y, a2.z, gx, gy, x0, y0, x1, y1);
+      const int W1 = gx + 1;
+      atomicAdd(&diff[y0 * W1 + x0], 1);
+      atomicAdd(&diff[y0 * W1 + x1], -1);
+      atomicAdd(&diff[y1 * W1 + x0], -1);
+      atomicAdd(&diff[y1 * W1 + x1], 1);
     }
     const uint32_t inc = warp_incl_scan(cnt);
     if (lane == 31) s_wtot[warp] = inc;
@@ -176,236 +208,160 @@ k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------------------
-// Key emission: each warp expands the tile rectangles of 32 consecutive ranks into
-// contiguous, coalesced key writes.
+// Per-tile coverage counts from the difference array -> tile ranges [start, end) and the
+// exclusive digit offsets of each pass of the tile sort (so the sort skips its histogram).
+// One CTA; diff is [gy + 1][gx + 1] and is integrated in place.
+// ---------------------------------------------------------------------------------------
+constexpr int kScanBlock = 1024;
+__global__ void __launch_bounds__(kScanBlock)
+k_tile_scan(int *__restrict__ diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
+            uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_hist[4 * 256];
+  __shared__ uint32_t s_wsum[kScanBlock / 32];
+  __shared__ uint32_t s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int W1 = gx + 1;
+  for (int i = tid; i < 4 * 256; i += kScanBlock) s_hist[i] = 0;
+  // rows: prefix along x (one warp per row)
+  for (int y = warp; y < gy; y += kScanBlock / 32) {
+    int carry = 0;
+    for (int x0 = 0; x0 < gx; x0 += 32) {
+      const int x = x0 + lane;
+      int v = x < gx ? diff[y * W1 + x] : 0;
+      v = warp_incl_scan(v) + carry;
+      if (x < gx) diff[y * W1 + x] = v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+  __syncthreads();
+  // columns: prefix along y (one thread per column)
+  for (int x = tid; x < gx; x += kScanBlock) {
+    int acc = 0;
+    for (int y = 0; y < gy; ++y) {
+      acc += diff[y * W1 + x];
+      diff[y * W1 + x] = acc;
+    }
+  }
+  __syncthreads();
+  // exclusive scan over tiles in id order (ty * gx + tx), chunked by the block
+  const uint32_t tiles = (uint32_t)gx * gy;
+  const uint32_t mask = (1u << dbits) - 1u;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t t0 = 0; t0 < tiles; t0 += kScanBlock) {
+    const uint32_t t = t0 + tid;
+    uint32_t c = 0;
+    if (t < tiles) c = (uint32_t)diff[(t / gx) * W1 + (t % gx)];
+    const uint32_t inc = warp_incl_scan(c);
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = s_wsum[lane];
+      const uint32_t wi = warp_incl_scan(w);
+      s_wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    const uint32_t start = s_carry + s_wsum[warp] + inc - c;
+    if (t < tiles) {
+      ranges[t] = make_uint2(start, start + c);
+      for (int p = 0; p < npass; ++p)
+        if (c) atomicAdd(&s_hist[p * 256 + ((t >> (p * dbits)) & mask)], c);
+    }
+    __syncthreads();
+    if (tid == kScanBlock - 1) s_carry = start + c;
+    __syncthreads();
+  }
+  // exclusive digit offsets per pass (threads 0..255 = warps 0..7 hold the 256 digits)
+  for (int p = 0; p < npass; ++p) {
+    uint32_t v = 0, inc = 0;
+    if (tid < 256) {
+      v = s_hist[p * 256 + tid];
+      inc = warp_incl_scan(v);
+      if (lane == 31) s_wsum[warp] = inc;
+    }
+    __syncthreads();
+    if (tid < 256) {
+      uint32_t wo = 0;
+      for (int w = 0; w < warp; ++w) wo += s_wsum[w];
+      hist[p * 256 + tid] = wo + inc - v;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Key emission: a warp takes 32 consecutive ranks and writes their keys one Gaussian at a
+// time, the 32 lanes walking the tile rectangle in row-major order (consecutive addresses,
+// one integer division per Gaussian and lane).
+// ---------------------------------------------------------------------------------------
+// Tile lists without a sort (dense coverage): the list of tile (tx, ty) is the set bits of
+// rowmask[ty] AND colmask[tx], i.e. the ranks of the Gaussians whose rectangle covers the
+// tile, already in depth order. One warp per tile writes them from ranges[tile].x on.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock)
+k_tile_lists(const uint32_t *__restrict__ rowmask, const uint32_t *__restrict__ colmask,
+             uint32_t mask_words, uint32_t words, int gx, int gy,
+             const uint2 *__restrict__ ranges, uint32_t *__restrict__ lists) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tiles = (uint32_t)gx * gy;
+  for (uint32_t t = blockIdx.x * kWarps + warp; t < tiles; t += gridDim.x * kWarps) {
+    const uint32_t *rows = rowmask + (size_t)(t / gx) * mask_words;
+    const uint32_t *cols = colmask + (size_t)(t % gx) * mask_words;
+    uint32_t off = ranges[t].x;
+    for (uint32_t c0 = 0; c0 < words; c0 += 32) {
+      const uint32_t c = c0 + lane;
+      uint32_t m = c < words ? (__ldg(&rows[c]) & __ldg(&cols[c])) : 0u;
+      const uint32_t pc = __popc(m);
+      const uint32_t inc = warp_incl_scan(pc);
+      uint32_t o = off + inc - pc;
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        lists[o++] = c * 32 + b;
+      }
+      off += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 template <typename K>
 __global__ void __launch_bounds__(kBlock)
 k_emit(const float *__restrict__ rec_sorted, const uint32_t *__restrict__ offsets, uint32_t nv,
        int gx, int gy, int rb, K *__restrict__ keys) {
-  __shared__ uint32_t s_excl[kWarps][32];
-  __shared__ int s_x0[kWarps][32], s_y0[kWarps][32], s_w[kWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t total_warps = gridDim.x * kWarps;
   for (uint32_t chunk = blockIdx.x * kWarps + warp; (uint64_t)chunk * 32 < nv;
        chunk += total_warps) {
     const uint32_t r = chunk * 32 + lane;
-    uint32_t cnt = 0;
     int x0 = 0, y0 = 0, w = 1;
+    uint32_t cnt = 0, off = 0;
     if (r < nv) {
-      const float *rp = rec_sorted + (size_t)r * kRec;
+      const float4 g0 = *reinterpret_cast<const float4 *>(rec_sorted + (size_t)r * kRecS);
+      const float rad = rec_sorted[(size_t)r * kRecS + kRecSRadius];
       int x1, y1;
-      tile_rect(rp[R_U], rp[R_V], rp[R_RADIUS], gx, gy, x0, y0, x1, y1);
+      tile_rect(g0.x, g0.y, rad, gx, gy, x0, y0, x1, y1);
       w = x1 - x0;
       cnt = (uint32_t)(w * (y1 - y0));
+      off = offsets[r];
     }
-    const uint32_t inc = warp_incl_scan(cnt);
-    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-    s_excl[warp][lane] = inc - cnt;
-    s_x0[warp][lane] = x0;
-    s_y0[warp][lane] = y0;
-    s_w[warp][lane] = w;
-    const uint32_t base = __shfl_sync(0xffffffffu, r < nv ? offsets[r] - (inc - cnt) : 0u, 0);
-    __syncwarp();
-    for (uint32_t j = lane; j < total; j += 32) {
-      int lo = 0, hi = 31;
-      while (lo < hi) {
-        const int m = (lo + hi + 1) >> 1;
-        if (s_excl[warp][m] <= j) lo = m; else hi = m - 1;
-      }
-      const uint32_t q = j - s_excl[warp][lo];
-      const uint32_t ww = (uint32_t)s_w[warp][lo];
-      const uint32_t tx = s_x0[warp][lo] + q % ww;
-      const uint32_t ty = s_y0[warp][lo] + q / ww;
-      keys[base + j] = ((K)(ty * (uint32_t)gx + tx) << rb) | (K)(chunk * 32 + lo);
-    }
-    __syncwarp();
-  }
-}
-
-template <typename K>
-__global__ void k_ranges(const K *__restrict__ keys, uint32_t nkeys, int rb,
-                         uint2 *__restrict__ ranges) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nkeys;
-       i += gridDim.x * blockDim.x) {
-    const uint32_t t = (uint32_t)(keys[i] >> rb);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> rb) != t) ranges[t].x = i;
-    if (i == nkeys - 1 || (uint32_t)(keys[i + 1] >> rb) != t) ranges[t].y = i + 1;
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// Forward blend: one CTA per 16x16 tile, one thread per pixel. Records are staged in
-// shared memory 256 at a time; the CTA leaves as soon as every pixel has stopped.
-// ---------------------------------------------------------------------------------------
-template <typename K, bool kWeights, bool kCount>
-__global__ void __launch_bounds__(kBlock) k_blend(BlendArgs a, const K *__restrict__ keys,
-                                                  uint32_t rmask) {
-  __shared__ float2 s_xy[kBlock];
-  __shared__ float4 s_co[kBlock];
-  __shared__ float4 s_rgb[kBlock];
-  const int tile = blockIdx.x;
-  const int tx = tile % a.gx, ty = tile / a.gx;
-  const int tid = threadIdx.x;
-  const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
-  const bool inside = px < a.W && py < a.H;
-  const uint2 range = a.ranges[tile];
-  const float fpx = (float)px, fpy = (float)py;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0, nevals = 0;
-  bool done = !inside;
-  for (uint32_t start = range.x; start < range.y; start += kBlock) {
-    if (__syncthreads_count(done) == kBlock) break;
-    const uint32_t idx = start + tid;
-    if (idx < range.y) {
-      const uint32_t r = (uint32_t)(keys[idx] & (K)rmask);
-      const float4 *rp = reinterpret_cast<const float4 *>(a.rec_sorted + (size_t)r * kRec);
-      const float4 r0 = rp[0], r1 = rp[1];
-      const float r2 = a.rec_sorted[(size_t)r * kRec + 8];
-      s_xy[tid] = make_float2(r0.x, r0.y);
-      s_co[tid] = make_float4(r0.z, r0.w, r1.x, r1.y);
-      s_rgb[tid] = make_float4(r1.z, r1.w, r2, __uint_as_float(r));
-    }
-    __syncthreads();
-    const int nb = (int)min((uint32_t)kBlock, range.y - start);
-    for (int j = 0; j < nb; ++j) {
-      float wgt = 0.f;
-      if (!done) {
-        const float2 xy = s_xy[j];
-        const float4 co = s_co[j];
-        float alpha, G, dx, dy;
-        if (kCount) ++nevals;
-        if (eval_alpha(xy.x, xy.y, co.x, co.y, co.z, co.w, fpx, fpy, alpha, G, dx, dy)) {
-          const float nT = T * (1.f - alpha);
-          if (nT < kTStop) {
-            done = true;
-          } else {
-            const float4 c = s_rgb[j];
-            wgt = alpha * T;
-            C0 = fmaf(c.x, wgt, C0);
-            C1 = fmaf(c.y, wgt, C1);
-            C2 = fmaf(c.z, wgt, C2);
-            T = nT;
-            last = start - range.x + j + 1;
-          }
-        }
-      }
-      if (kWeights) {
-        if (__any_sync(0xffffffffu, wgt != 0.f)) {
-          const float s = warp_sum(wgt);
-          if ((tid & 31) == 0) atomicAdd(&a.w_sum[__float_as_uint(s_rgb[j].w)], s);
-        }
-      } else if (done) {
-        break;
-      }
-    }
-  }
-  if (kCount) {
-    const uint32_t ws = warp_sum(nevals);
-    if ((tid & 31) == 0 && ws) atomicAdd(a.evals, (unsigned long long)ws);
-  }
-  if (inside) {
-    const size_t pix = (size_t)py * a.W + px, hw = (size_t)a.W * a.H;
-    a.rgb[pix] = C0 + T * a.bg[0];
-    a.rgb[hw + pix] = C1 + T * a.bg[1];
-    a.rgb[2 * hw + pix] = C2 + T * a.bg[2];
-    a.T_final[pix] = T;
-    a.n_contrib[pix] = last;
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// Backward blend: reverse replay of each tile list from the largest n_contrib down to 0.
-// Transmittance is recovered as T_i = T_{i+1} / (1 - alpha_i) from T_final.
-// ---------------------------------------------------------------------------------------
-template <typename K>
-__global__ void __launch_bounds__(kBlock) k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys,
-                                                      uint32_t rmask) {
-  __shared__ float2 s_xy[kBlock];
-  __shared__ float4 s_co[kBlock];
-  __shared__ float4 s_rgb[kBlock];
-  __shared__ uint32_t s_max;
-  const int tile = blockIdx.x;
-  const int tx = tile % a.gx, ty = tile / a.gx;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
-  const bool inside = px < a.W && py < a.H;
-  const uint2 range = a.ranges[tile];
-  const size_t pix = (size_t)py * a.W + px, hw = (size_t)a.W * a.H;
-  if (tid == 0) s_max = 0;
-  __syncthreads();
-  uint32_t nc = 0;
-  float T = 1.f, dL0 = 0.f, dL1 = 0.f, dL2 = 0.f;
-  if (inside) {
-    nc = a.n_contrib[pix];
-    T = a.T_final[pix];
-    dL0 = a.dL_drgb[pix];
-    dL1 = a.dL_drgb[hw + pix];
-    dL2 = a.dL_drgb[2 * hw + pix];
-    atomicMax(&s_max, nc);
-  }
-  const float Tf = T;
-  const float bg_dot = a.bg[0] * dL0 + a.bg[1] * dL1 + a.bg[2] * dL2;
-  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, last_a = 0.f, lc0 = 0.f, lc1 = 0.f, lc2 = 0.f;
-  const float fpx = (float)px, fpy = (float)py;
-  __syncthreads();
-  const int maxnc = (int)s_max;
-  for (int bend = maxnc; bend > 0; bend -= kBlock) {
-    const int bstart = max(0, bend - kBlock);
-    __syncthreads();
-    if (bstart + tid < bend) {
-      const uint32_t r = (uint32_t)(keys[range.x + bstart + tid] & (K)rmask);
-      const float4 *rp = reinterpret_cast<const float4 *>(a.rec_sorted + (size_t)r * kRec);
-      const float4 r0 = rp[0], r1 = rp[1];
-      const float r2 = a.rec_sorted[(size_t)r * kRec + 8];
-      s_xy[tid] = make_float2(r0.x, r0.y);
-      s_co[tid] = make_float4(r0.z, r0.w, r1.x, r1.y);
-      s_rgb[tid] = make_float4(r1.z, r1.w, r2, __uint_as_float(r));
-    }
-    __syncthreads();
-    for (int jj = bend - bstart - 1; jj >= 0; --jj) {
-      const int pos = bstart + jj;
-      float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bool contrib = false;
-      if ((uint32_t)pos < nc) {
-        const float2 xy = s_xy[jj];
-        const float4 co = s_co[jj];
-        float alpha, G, dx, dy;
-        if (eval_alpha(xy.x, xy.y, co.x, co.y, co.z, co.w, fpx, fpy, alpha, G, dx, dy)) {
-          contrib = true;
-          const float4 c = s_rgb[jj];
-          const float om = 1.f - alpha;
-          T = T / om;
-          const float wgt = alpha * T;
-          acc0 = last_a * lc0 + (1.f - last_a) * acc0;
-          acc1 = last_a * lc1 + (1.f - last_a) * acc1;
-          acc2 = last_a * lc2 + (1.f - last_a) * acc2;
-          float dLda = (c.x - acc0) * dL0 + (c.y - acc1) * dL1 + (c.z - acc2) * dL2;
-          dLda = dLda * T - Tf / om * bg_dot;
-          g[6] = wgt * dL0;
-          g[7] = wgt * dL1;
-          g[8] = wgt * dL2;
-          last_a = alpha;
-          lc0 = c.x; lc1 = c.y; lc2 = c.z;
-          if (__fmul_rn(co.w, G) < kAlphaMax) {
-            g[5] = G * dLda;
-            const float gp = alpha * dLda;
-            g[0] = gp * (-co.x * dx - co.y * dy);
-            g[1] = gp * (-co.z * dy - co.y * dx);
-            g[2] = gp * (-0.5f * dx * dx);
-            g[3] = gp * (-dx * dy);
-            g[4] = gp * (-0.5f * dy * dy);
-          }
-        }
-      }
-      if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int f = 0; f < 9; ++f) g[f] = warp_sum(g[f]);
-        if (lane == 0) {
-          float *dst = a.g2d + (size_t)__float_as_uint(s_rgb[jj].w) * 9;
-#pragma unroll
-          for (int f = 0; f < 9; ++f)
-            if (g[f] != 0.f) atomicAdd(&dst[f], g[f]);
+    const uint32_t nlanes = min(32u, nv - chunk * 32);
+    for (uint32_t g = 0; g < nlanes; ++g) {
+      const uint32_t gc = __shfl_sync(0xffffffffu, cnt, g);
+      const int gw = __shfl_sync(0xffffffffu, w, g);
+      const int gx0 = __shfl_sync(0xffffffffu, x0, g);
+      const int gy0 = __shfl_sync(0xffffffffu, y0, g);
+      const uint32_t goff = __shfl_sync(0xffffffffu, off, g);
+      const K rank = (K)(chunk * 32 + g);
+      int row = lane / gw, col = lane - row * gw;
+      const int srow = 32 / gw, scol = 32 - srow * gw;
+      for (uint32_t j = lane; j < gc; j += 32) {
+        keys[goff + j] = ((K)((uint32_t)(gy0 + row) * (uint32_t)gx + (uint32_t)(gx0 + col)) << rb) | rank;
+        col += scol;
+        row += srow;
+        if (col >= gw) {
+          col -= gw;
+          ++row;
         }
       }
     }
@@ -465,13 +421,32 @@ void launch_preprocess(const PreArgs &a, cudaStream_t st) {
 
 void launch_gather_scan(const uint64_t *sorted, const uint32_t *ctr_nvis, uint32_t n_cap,
                         const float *rec, float *rec_sorted, uint32_t *offsets,
-                        uint64_t *status, uint32_t *ctr, uint32_t *err, cudaStream_t st) {
+                        uint64_t *status, uint32_t *ctr, uint32_t *err, int gx, int gy,
+                        int *diff, uint32_t *rowmask, uint32_t *colmask, uint32_t mask_words,
+                        cudaStream_t st) {
   if (n_cap == 0) return;
   const uint64_t parts = (n_cap + kBlock - 1) / kBlock;
   static int grid_cap = 0;
   if (!grid_cap) grid_cap = persistent_grid(k_gather_scan, ~0ull);
   k_gather_scan<<<(int)std::min<uint64_t>(parts, grid_cap), kBlock, 0, st>>>(
-      sorted, ctr_nvis, rec, rec_sorted, offsets, status, ctr, err);
+      sorted, ctr_nvis, rec, rec_sorted, offsets, status, ctr, err, gx, gy, diff, rowmask,
+      colmask, mask_words);
+}
+
+void launch_tile_scan(int *diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
+                      uint32_t *hist, cudaStream_t st) {
+  k_tile_scan<<<1, kScanBlock, 0, st>>>(diff, gx, gy, npass, dbits, ranges, hist);
+}
+
+void launch_tile_lists(const uint32_t *rowmask, const uint32_t *colmask, uint32_t mask_words,
+                       uint32_t nv, int gx, int gy, const uint2 *ranges, uint32_t *lists,
+                       cudaStream_t st) {
+  const uint64_t tiles = (uint64_t)gx * gy;
+  if (tiles == 0 || nv == 0) return;
+  const int grid = (int)std::min<uint64_t>((tiles + kWarps - 1) / kWarps,
+                                           (uint64_t)num_sms() * 8);
+  k_tile_lists<<<grid, kBlock, 0, st>>>(rowmask, colmask, mask_words, (nv + 31) / 32, gx, gy,
+                                        ranges, lists);
 }
 
 template <typename K>
@@ -484,47 +459,15 @@ void launch_emit(const float *rec_sorted, const uint32_t *offsets, uint32_t nv, 
   k_emit<K><<<grid, kBlock, 0, st>>>(rec_sorted, offsets, nv, gx, gy, rb, keys);
 }
 
-template <typename K>
-void launch_ranges(const K *keys, uint32_t nkeys, int rb, uint2 *ranges, cudaStream_t st) {
-  if (nkeys == 0) return;
-  const int grid = (int)std::min<uint64_t>((nkeys + kBlock - 1) / kBlock,
-                                           (uint64_t)num_sms() * 16);
-  k_ranges<K><<<grid, kBlock, 0, st>>>(keys, nkeys, rb, ranges);
-}
-
-template <typename K>
-void launch_blend(const BlendArgs &a, const K *keys, uint32_t rmask, cudaStream_t st) {
-  const int tiles = a.gx * a.gy;
-  if (tiles == 0) return;
-  if (a.w_sum)
-    k_blend<K, true, false><<<tiles, kBlock, 0, st>>>(a, keys, rmask);
-  else if (a.evals)
-    k_blend<K, false, true><<<tiles, kBlock, 0, st>>>(a, keys, rmask);
-  else
-    k_blend<K, false, false><<<tiles, kBlock, 0, st>>>(a, keys, rmask);
-}
-
-template <typename K>
-void launch_blend_bwd(const BlendBwdArgs &a, const K *keys, uint32_t rmask, cudaStream_t st) {
-  const int tiles = a.gx * a.gy;
-  if (tiles == 0) return;
-  k_blend_bwd<K><<<tiles, kBlock, 0, st>>>(a, keys, rmask);
-}
-
 void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st) {
   if (a.nv == 0) return;
   const int grid = (int)std::min<uint64_t>((a.nv + 127) / 128, (uint64_t)num_sms() * 8);
   k_preprocess_bwd<<<grid, 128, 0, st>>>(a);
 }
 
-#define FDGS_INST(K)                                                                      \
-  template void launch_emit<K>(const float *, const uint32_t *, uint32_t, int, int, int, K *, \
-                               cudaStream_t);                                             \
-  template void launch_ranges<K>(const K *, uint32_t, int, uint2 *, cudaStream_t);        \
-  template void launch_blend<K>(const BlendArgs &, const K *, uint32_t, cudaStream_t);    \
-  template void launch_blend_bwd<K>(const BlendBwdArgs &, const K *, uint32_t, cudaStream_t);
-FDGS_INST(uint32_t)
-FDGS_INST(uint64_t)
-#undef FDGS_INST
+template void launch_emit<uint32_t>(const float *, const uint32_t *, uint32_t, int, int, int,
+                                    uint32_t *, cudaStream_t);
+template void launch_emit<uint64_t>(const float *, const uint32_t *, uint32_t, int, int, int,
+                                    uint64_t *, cudaStream_t);
 
 }  // namespace fdgs

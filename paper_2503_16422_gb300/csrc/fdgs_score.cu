@@ -24,10 +24,10 @@ __global__ void k_keys_to_ids(const K *__restrict__ keys, uint32_t nkeys, uint32
 }
 
 __global__ void k_export_records(const uint64_t *__restrict__ sorted, uint32_t nv,
-                                 const float *__restrict__ rec_sorted, float *__restrict__ out) {
+                                 const float *__restrict__ rec, float *__restrict__ out) {
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
     const uint32_t id = (uint32_t)sorted[r];
-    for (int k = 0; k < kRec; ++k) out[(size_t)id * kRec + k] = rec_sorted[(size_t)r * kRec + k];
+    for (int k = 0; k < kRec; ++k) out[(size_t)id * kRec + k] = rec[(size_t)id * kRec + k];
   }
 }
 
@@ -114,10 +114,10 @@ template void launch_keys_to_ids<uint32_t>(const uint32_t *, uint32_t, uint32_t,
 template void launch_keys_to_ids<uint64_t>(const uint64_t *, uint32_t, uint32_t,
                                            const uint64_t *, uint32_t *, cudaStream_t);
 
-void launch_export_records(const uint64_t *sorted, uint32_t nv, const float *rec_sorted,
+void launch_export_records(const uint64_t *sorted, uint32_t nv, const float *rec,
                            float *out, cudaStream_t st) {
   if (nv == 0) return;
-  k_export_records<<<grid_for(nv), kB, 0, st>>>(sorted, nv, rec_sorted, out);
+  k_export_records<<<grid_for(nv), kB, 0, st>>>(sorted, nv, rec, out);
 }
 
 void launch_volume_bits(const float4 *ls4, uint32_t n, uint32_t *vbits, cudaStream_t st) {

@@ -187,6 +187,10 @@ size_t status_bytes(uint64_t n_cap) {
 }  // namespace
 
 int sort_passes(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
+int sort_digit_bits(int bits) {
+  const int np = sort_passes(bits);
+  return np ? (bits + np - 1) / np : 0;
+}
 
 size_t sort_scratch_bytes(uint64_t n_cap, int bits) {
   const int np = std::max(1, sort_passes(bits));
@@ -196,7 +200,7 @@ size_t sort_scratch_bytes(uint64_t n_cap, int bits) {
 
 template <typename K>
 K *radix_sort(K *a, K *b, const uint32_t *n_dev, uint64_t n_cap, int lo, int bits,
-              void *scratch, cudaStream_t st, uint32_t *err_dev) {
+              void *scratch, cudaStream_t st, uint32_t *err_dev, bool hist_ready) {
   const int np = sort_passes(bits);
   if (np == 0 || n_cap == 0) return a;
   const int dbits = (bits + np - 1) / np;
@@ -204,10 +208,16 @@ K *radix_sort(K *a, K *b, const uint32_t *n_dev, uint64_t n_cap, int lo, int bit
   uint32_t *ctr = hist + 4 * kRadix;
   uint8_t *status0 = (uint8_t *)scratch + 4 * kRadix * sizeof(uint32_t) + 256;
   const size_t sb = status_bytes(n_cap);
-  cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n_cap, bits), st);
-  const int hgrid = (int)std::min<uint64_t>((n_cap + 4095) / 4096, (uint64_t)num_sms() * 4);
-  k_histogram<K><<<std::max(1, hgrid), kSortBlock, 0, st>>>(a, n_dev, lo, dbits, np, hist);
-  k_hist_scan<<<np, kRadix, 0, st>>>(hist);
+  const size_t hist_bytes = 4 * kRadix * sizeof(uint32_t);
+  if (hist_ready) {
+    cudaMemsetAsync((uint8_t *)scratch + hist_bytes, 0,
+                    sort_scratch_bytes(n_cap, bits) - hist_bytes, st);
+  } else {
+    cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n_cap, bits), st);
+    const int hgrid = (int)std::min<uint64_t>((n_cap + 4095) / 4096, (uint64_t)num_sms() * 4);
+    k_histogram<K><<<std::max(1, hgrid), kSortBlock, 0, st>>>(a, n_dev, lo, dbits, np, hist);
+    k_hist_scan<<<np, kRadix, 0, st>>>(hist);
+  }
   const uint64_t parts = (n_cap + kTileKeys - 1) / kTileKeys;
   const int grid = (int)std::min<uint64_t>(parts, (uint64_t)onesweep_grid<K>());
   K *src = a, *dst = b;
@@ -221,8 +231,8 @@ K *radix_sort(K *a, K *b, const uint32_t *n_dev, uint64_t n_cap, int lo, int bit
 }
 
 template uint32_t *radix_sort<uint32_t>(uint32_t *, uint32_t *, const uint32_t *, uint64_t, int,
-                                        int, void *, cudaStream_t, uint32_t *);
+                                        int, void *, cudaStream_t, uint32_t *, bool);
 template uint64_t *radix_sort<uint64_t>(uint64_t *, uint64_t *, const uint32_t *, uint64_t, int,
-                                        int, void *, cudaStream_t, uint32_t *);
+                                        int, void *, cudaStream_t, uint32_t *, bool);
 
 }  // namespace fdgs

@@ -48,7 +48,8 @@ class fdgs_frame_stats(ctypes.Structure):
     _fields_ = [("n_active", ctypes.c_int64), ("n_visible", ctypes.c_int64),
                 ("n_keys", ctypes.c_int64), ("width", ctypes.c_int), ("height", ctypes.c_int),
                 ("tiles_x", ctypes.c_int), ("tiles_y", ctypes.c_int), ("key_l", ctypes.c_int),
-                ("key_r", ctypes.c_int), ("key_bytes", ctypes.c_int)]
+                ("key_r", ctypes.c_int), ("key_bytes", ctypes.c_int),
+                ("list_builder", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -72,10 +73,12 @@ _SIGNATURES = {
     "fdgs_select_keep_noalloc": [_P, ctypes.c_int64, ctypes.c_float, _P, _P],
     "fdgs_status_sync": [_P],
     "fdgs_profile_enable": [_P, ctypes.c_int],
+    "fdgs_set_blend_shape": [ctypes.c_int],
+    "fdgs_set_list_builder": [ctypes.c_int],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
 }
-PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "emit", "tile_sort", "ranges",
-                  "blend")
+PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "tile_scan", "emit",
+                  "tile_sort", "blend")
 
 _lib = None
 
@@ -382,3 +385,13 @@ def render(scene: Scene, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0)):
 
 def version():
     return lib().fdgs_version().decode()
+
+
+def set_list_builder(mode):
+    """Tile-list builder (0: auto, 1: emit + radix sort, 2: coverage bitmasks), process-wide."""
+    check(lib().fdgs_set_list_builder(int(mode)))
+
+
+def set_blend_shape(footprint):
+    """Forward-blend warp footprint (0: 16x2, 1: 8x4, 2: 4x8 pixels), process-wide."""
+    check(lib().fdgs_set_blend_shape(int(footprint)))

@@ -143,6 +143,27 @@ def test_background_colour(fd):
     sc.close()
 
 
+@pytest.mark.parametrize("builder,shape", [(1, 0), (1, 2), (2, 0), (2, 1), (2, 2)])
+def test_list_builders_and_blend_shapes_give_identical_frames(fd, builder, shape):
+    """Bitmask vs sort tile lists, and the three warp footprints of the blend (with their
+    ballot culling), must all give the same lists and bit-identical images."""
+    s = scenes.make_scene(6000, 17, sh_degree=1, lt_long=(-1.0, 0.5))
+    cam = scenes.arc_camera(4.0, 200, 150)
+    fd.set_list_builder(1)
+    fd.set_blend_shape(1)
+    try:
+        ref = _run(fd, s, cam, 0.4)
+        fd.set_list_builder(builder)
+        fd.set_blend_shape(shape)
+        g = _run(fd, s, cam, 0.4)
+    finally:
+        fd.set_list_builder(0)
+        fd.set_blend_shape(1)
+    assert ref["stats"]["list_builder"] == 1 and g["stats"]["list_builder"] == builder
+    for k in ("image", "T_final", "n_contrib", "tile_ranges", "tile_ids"):
+        assert np.array_equal(g[k], ref[k]), k
+
+
 @pytest.mark.slow
 def test_full_size_pruned_masked_frame_sampled_tiles(fd):
     """The benchmark workload (200k pruned scene, 1352x1014, masked, degree-3 SH): full
