@@ -1,207 +1,60 @@
-// Per-tile front-to-back compositing (Eq. 2 with Eq. 3's alpha) and its reverse replay.
-//
-// One CTA of 256 threads per 16x16 tile; each warp owns an FW x (32/FW) pixel footprint of
-// the tile, one pixel per lane. The tile's records are staged 256 at a time with cp.async
-// into a double buffer (the copy of batch b+1 is in flight while batch b is composited; the
-// keys of batch b+2 are already loading into registers).
-//
-// Warp-ballot culling: the 32 lanes of a warp each test one of 32 staged Gaussians against
-// the warp's footprint rectangle (the largest exponent over the rectangle, exact for the
-// concave quadratic, minus a margin) and __ballot_sync the hits; the warp then evaluates only
-// those Gaussians, one at a time, for its 32 pixels. A culled Gaussian has alpha < 1/255 at
-// every pixel of the footprint, so it would have been skipped pixel by pixel anyway: the
-// result is identical to evaluating every list entry at every pixel. A warp stops when all
-// its pixels have stopped; the CTA stops when all warps have.
+// Blend kernels: the per-tile forward (one CTA per 16x16 tile, body in fdgs_blend.cuh) and the
+// reverse replay used by the backward.
 #include <algorithm>
 
-#include "fdgs_internal.h"
+#include "fdgs_blend.cuh"
 
 namespace fdgs {
 
 namespace {
 
-constexpr int kBatch = 256;
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Pixel of lane `lane` in warp `warp` of tile (tx, ty) for an FW-wide warp footprint.
-template <int FW>
-struct Footprint {
-  static constexpr int FH = 32 / FW;
-  static constexpr int WX = kTile / FW;
-  int x0, y0;       // footprint origin (pixels)
-  int px, py;       // this lane's pixel
-  __device__ __forceinline__ Footprint(int tx, int ty, int warp, int lane) {
-    x0 = tx * kTile + (warp % WX) * FW;
-    y0 = ty * kTile + (warp / WX) * FH;
-    px = x0 + lane % FW;
-    py = y0 + lane / FW;
-  }
-  // Whether the Gaussian can reach alpha >= 1/255 at some pixel of the footprint.
-  __device__ __forceinline__ bool may_hit(float4 g0, float c2, float lga, float kx,
-                                          float ky) const {
-    const float qmax = quad_max_rect(g0.z, g0.w, c2, kx, ky, g0.x - (float)(x0 + FW - 1),
-                                     g0.x - (float)x0, g0.y - (float)(y0 + FH - 1),
-                                     g0.y - (float)y0);
-    return qmax + lga >= kLog2AlphaMin - kCullMargin;
-  }
-};
-
 template <typename K, int FW, bool kWeights, bool kCount>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kBlendThreads)
 k_blend(BlendArgs a, const K *__restrict__ keys, uint32_t rmask) {
-  constexpr int NT = 256;
-  constexpr int E = kBatch / NT;
-  __shared__ __align__(16) float4 s_g0[2][kBatch];   // u, v, a2, b2
-  __shared__ __align__(16) float4 s_g1[2][kBatch];   // c2, lga, r, g
-  __shared__ __align__(16) float4 s_g2[2][kBatch];   // b, kx, ky, radius
-  __shared__ uint32_t s_rk[kWeights ? 2 : 1][kBatch];
-  const int tile = blockIdx.x;
-  const int tx = tile % a.gx, ty = tile / a.gx;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Footprint<FW> fp(tx, ty, warp, lane);
-  const uint2 range = a.ranges[tile];
-  const uint32_t n = range.y - range.x;
-  const int nb = (int)((n + kBatch - 1) / kBatch);
-  const bool inside = fp.px < a.W && fp.py < a.H;
-  const float fpx = (float)fp.px, fpy = (float)fp.py;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0, nevals = 0;
-  bool done = !inside;
-  bool warp_done = __all_sync(0xffffffffu, done);
-
-  K kr[E];
-  auto load_keys = [&](int b) {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const uint32_t i = (uint32_t)b * kBatch + e * NT + tid;
-      kr[e] = i < n ? keys[range.x + i] : (K)0;
-    }
-  };
-  auto issue = [&](int b) {
-    const int st = b & 1;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const uint32_t i = (uint32_t)b * kBatch + e * NT + tid;
-      if (i < n) {
-        const uint32_t r = (uint32_t)(kr[e] & (K)rmask);
-        const float *rp = a.rec_sorted + (size_t)r * kRecS;
-        const int j = e * NT + tid;
-        cp_async16(&s_g0[st][j], rp);
-        cp_async16(&s_g1[st][j], rp + 4);
-        cp_async16(&s_g2[st][j], rp + 8);
-        if (kWeights) s_rk[st][j] = r;
-      }
-    }
-    cp_async_commit();
-  };
-
-  if (nb > 0) {
-    load_keys(0);
-    issue(0);
-    if (nb > 1) load_keys(1);
-  }
-  for (int b = 0; b < nb; ++b) {
-    if (b + 1 < nb) {
-      issue(b + 1);
-      if (b + 2 < nb) load_keys(b + 2);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const int st = b & 1;
-    const int cnt = (int)min((uint32_t)kBatch, n - (uint32_t)b * kBatch);
-    const uint32_t pos0 = (uint32_t)b * kBatch;
-    for (int j0 = 0; j0 < cnt && !warp_done; j0 += 32) {
-      bool hit = false;
-      if (j0 + lane < cnt) {
-        const float4 g0 = s_g0[st][j0 + lane];
-        const float2 g1 = *reinterpret_cast<const float2 *>(&s_g1[st][j0 + lane]);
-        const float4 g2 = s_g2[st][j0 + lane];
-        hit = fp.may_hit(g0, g1.x, g1.y, g2.y, g2.z);
-      }
-      uint32_t m = __ballot_sync(0xffffffffu, hit);
-      while (m) {
-        const int j = j0 + __ffs(m) - 1;
-        m &= m - 1;
-        float w = 0.f;
-        if (!done) {
-          if (kCount) ++nevals;
-          const float4 g0 = s_g0[st][j];
-          const float4 g1 = s_g1[st][j];
-          float alpha, raw, dx, dy;
-          if (splat_alpha(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, fpx, fpy, alpha, raw, dx, dy)) {
-            const float nT = T * (1.f - alpha);
-            if (nT < kTStop) {
-              done = true;
-            } else {
-              w = alpha * T;
-              C0 = fmaf(g1.z, w, C0);
-              C1 = fmaf(g1.w, w, C1);
-              C2 = fmaf(s_g2[st][j].x, w, C2);
-              T = nT;
-              last = pos0 + j + 1;
-            }
-          }
-        }
-        if (kWeights) {
-          if (__any_sync(0xffffffffu, w != 0.f)) {
-            const float s = warp_sum(w);
-            if (lane == 0) atomicAdd(&a.w_sum[s_rk[st][j]], s);
-          }
-        }
-      }
-      warp_done = __all_sync(0xffffffffu, done);
-    }
-    if (__syncthreads_and(warp_done)) {
-      cp_async_wait<0>();
-      break;
-    }
-  }
-  if (kCount) {
-    const uint32_t ws = warp_sum(nevals);
-    if (lane == 0 && ws) atomicAdd(a.evals, (unsigned long long)ws);
-  }
-  if (inside) {
-    const size_t hw = (size_t)a.W * a.H;
-    const size_t pix = (size_t)fp.py * a.W + fp.px;
-    a.rgb[pix] = C0 + T * a.bg[0];
-    a.rgb[hw + pix] = C1 + T * a.bg[1];
-    a.rgb[2 * hw + pix] = C2 + T * a.bg[2];
-    a.T_final[pix] = T;
-    a.n_contrib[pix] = last;
-  }
+  __shared__ BlendSmem sm;
+  BlendTile bt;
+  bt.tx = blockIdx.x % a.gx;
+  bt.ty = blockIdx.x / a.gx;
+  bt.W = a.W;
+  bt.H = a.H;
+  bt.range = a.ranges[blockIdx.x];
+  bt.rec_sorted = a.rec_sorted;
+  bt.rgb = a.rgb;
+  bt.T_final = a.T_final;
+  bt.n_contrib = a.n_contrib;
+  bt.bg0 = a.bg[0];
+  bt.bg1 = a.bg[1];
+  bt.bg2 = a.bg[2];
+  bt.w_sum = a.w_sum;
+  bt.evals = a.evals;
+  blend_tile<K, FW, kWeights, kCount>(bt, keys, rmask, sm);
 }
 
-// Reverse replay of each tile list from the largest n_contrib down to 0, with the same
-// warp-footprint culling (a culled Gaussian was skipped by every pixel of the footprint).
+// Reverse replay of each tile list from the largest n_contrib down to 0, one pixel per
+// lane, with the warp-footprint culling of the forward (a culled Gaussian was skipped by
+// every pixel of the footprint). Transmittance is recovered as T_i = T_{i+1} / (1 - alpha_i).
 template <typename K, int FW>
 __global__ void __launch_bounds__(256)
 k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
-  __shared__ __align__(16) float4 s_g0[kBatch];   // u, v, a2, b2
-  __shared__ __align__(16) float4 s_g1[kBatch];   // c2, lga, r, g
-  __shared__ __align__(16) float4 s_g2[kBatch];   // b, kx, ky, radius
-  __shared__ __align__(16) float4 s_g3[kBatch];   // A, B, C, a
-  __shared__ uint32_t s_rk[kBatch];
+  constexpr int FH = 32 / FW;
+  constexpr int WX = kTile / FW;
+  constexpr int kB = kBlendBatch;
+  __shared__ __align__(16) float4 s_g0[kB];   // u, v, a2, b2
+  __shared__ __align__(16) float4 s_g1[kB];   // c2, lga, r, g
+  __shared__ __align__(16) float4 s_g2[kB];   // b, kx, ky, radius
+  __shared__ __align__(16) float4 s_g3[kB];   // A, B, C, a
+  __shared__ uint32_t s_rk[kB];
   __shared__ uint32_t s_max;
   const int tile = blockIdx.x;
   const int tx = tile % a.gx, ty = tile / a.gx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Footprint<FW> fp(tx, ty, warp, lane);
-  const bool inside = fp.px < a.W && fp.py < a.H;
+  const int fx0 = tx * kTile + (warp % WX) * FW, fy0 = ty * kTile + (warp / WX) * FH;
+  const int px = fx0 + lane % FW, py = fy0 + lane / FW;
+  const float fxl = (float)fx0, fxh = (float)(fx0 + FW - 1);
+  const float fyl = (float)fy0, fyh = (float)(fy0 + FH - 1);
+  const bool inside = px < a.W && py < a.H;
   const uint2 range = a.ranges[tile];
-  const size_t pix = (size_t)fp.py * a.W + fp.px, hw = (size_t)a.W * a.H;
+  const size_t pix = (size_t)py * a.W + px, hw = (size_t)a.W * a.H;
   if (tid == 0) s_max = 0;
   __syncthreads();
   uint32_t nc = 0;
@@ -218,11 +71,11 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
   const float Tf = T;
   const float bg_dot = a.bg[0] * dL0 + a.bg[1] * dL1 + a.bg[2] * dL2;
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, last_a = 0.f, lc0 = 0.f, lc1 = 0.f, lc2 = 0.f;
-  const float fpx = (float)fp.px, fpy = (float)fp.py;
+  const float fpx = (float)px, fpy = (float)py;
   __syncthreads();
   const int maxnc = (int)s_max;
-  for (int bend = maxnc; bend > 0; bend -= kBatch) {
-    const int bstart = max(0, bend - kBatch);
+  for (int bend = maxnc; bend > 0; bend -= kB) {
+    const int bstart = max(0, bend - kB);
     __syncthreads();
     if (bstart + tid < bend) {
       const uint32_t r = (uint32_t)(keys[range.x + bstart + tid] & (K)rmask);
@@ -244,7 +97,7 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
         const float4 g0 = s_g0[jl];
         const float2 g1 = *reinterpret_cast<const float2 *>(&s_g1[jl]);
         const float4 g2 = s_g2[jl];
-        hit = fp.may_hit(g0, g1.x, g1.y, g2.y, g2.z);
+        hit = may_hit_rect(g0, g1.x, g1.y, g2.y, g2.z, fxl, fxh, fyl, fyh);
       }
       uint32_t m = __ballot_sync(0xffffffffu, hit);
       while (m) {
@@ -305,11 +158,11 @@ template <typename K, int FW>
 void blend_fw(const BlendArgs &a, const K *keys, uint32_t rmask, cudaStream_t st) {
   const int tiles = a.gx * a.gy;
   if (a.w_sum)
-    k_blend<K, FW, true, false><<<tiles, 256, 0, st>>>(a, keys, rmask);
+    k_blend<K, FW, true, false><<<tiles, kBlendThreads, 0, st>>>(a, keys, rmask);
   else if (a.evals)
-    k_blend<K, FW, false, true><<<tiles, 256, 0, st>>>(a, keys, rmask);
+    k_blend<K, FW, false, true><<<tiles, kBlendThreads, 0, st>>>(a, keys, rmask);
   else
-    k_blend<K, FW, false, false><<<tiles, 256, 0, st>>>(a, keys, rmask);
+    k_blend<K, FW, false, false><<<tiles, kBlendThreads, 0, st>>>(a, keys, rmask);
 }
 
 }  // namespace

@@ -308,9 +308,18 @@ k_tile_lists(const uint32_t *__restrict__ rowmask, const uint32_t *__restrict__ 
     const uint32_t *rows = rowmask + (size_t)(t / gx) * mask_words;
     const uint32_t *cols = colmask + (size_t)(t % gx) * mask_words;
     uint32_t off = ranges[t].x;
+    // the words of group g+2 are loading while group g is written out
+    uint32_t nr0 = lane < words ? __ldg(&rows[lane]) : 0u;
+    uint32_t nc0 = lane < words ? __ldg(&cols[lane]) : 0u;
+    uint32_t nr1 = lane + 32 < words ? __ldg(&rows[lane + 32]) : 0u;
+    uint32_t nc1 = lane + 32 < words ? __ldg(&cols[lane + 32]) : 0u;
     for (uint32_t c0 = 0; c0 < words; c0 += 32) {
       const uint32_t c = c0 + lane;
-      uint32_t m = c < words ? (__ldg(&rows[c]) & __ldg(&cols[c])) : 0u;
+      uint32_t m = nr0 & nc0;
+      nr0 = nr1;
+      nc0 = nc1;
+      nr1 = c + 64 < words ? __ldg(&rows[c + 64]) : 0u;
+      nc1 = c + 64 < words ? __ldg(&cols[c + 64]) : 0u;
       const uint32_t pc = __popc(m);
       const uint32_t inc = warp_incl_scan(pc);
       uint32_t o = off + inc - pc;
