@@ -1,19 +1,24 @@
 #!/usr/bin/env python
-"""Benchmark: masked 4D Gaussian render FPS at 1352x1014 on one GB300, with per-stage times,
-the roofline fraction of the dominant stage, an end-to-end number and the CPU oracle.
+"""Benchmark: masked, batched 4D Gaussian rendering at 1352x1014 on one GB300.
 
-Workload (default): the pruned 4DGS-1K-like scene (200,000 Gaussians, degree-3 SH, temporal
-log-scales N(-1, 0.5)) rendered with the key-frame temporal filter (masks every 6 frames,
-|t_k - mu_t| < 3 s_t) at 1352x1014, frames k = 0..299 with t_k = k/299 and the camera on a
-20-degree arc; one step = one full render (all stages) of the next frame. Inputs are
-synthetic (seeded), resident in HBM; L2 is flushed (256 MiB write) before every timed step.
+Headline (one step = one batch): the pruned 4DGS-1K-like scene (200,000 Gaussians, degree-3
+SH, temporal log-scales N(-1, 0.5)) with the key-frame temporal filter (masks every 6 frames,
+|t_k - mu_t| < 3 s_t), rendered as a batch of 64 requests at 1352x1014: frames k of the
+300-frame sequence (t_k = k/299, camera on a 20-degree arc) through fdgs_render_batch (one
+device-driven pass replayed from a CUDA graph, one persistent longest-first blend). value =
+frames per second. Inputs are synthetic (seeded), resident in HBM; L2 is flushed (256 MiB
+write) before every timed step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload pruned_masked|unpruned_masked|pruned_unmasked|unpruned_unmasked]
+Beside it: the single-request masked and unmasked renders (fdgs_render), the unpruned 3M
+scene, and the mixed-resolution serving batch (64 requests, resolutions from {512^2, 800^2,
+1014x1352, 1352x1014}) with p50/p99 request latency against 64 sequential renders. Per-kernel
+times come from CUDA events on the render stream in a profiled pass over the same frames.
 
-With --gpus N > 1 (launched under torchrun) every rank renders its own frames of a replica of
-the scene (no collective: the frames are independent), timing is the max over ranks and the
-value is the total frames of all ranks per second.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+
+With --gpus N > 1 (torchrun) every rank renders its own batches of a replica of the scene
+(no collective: frames are independent), timing is the max over ranks and the value is the
+total frames of all ranks per second.
 """
 import argparse
 import json
@@ -32,46 +37,45 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FPS at 1352x1014 (masked 4DGS render, 1 GB300)"
 FLUSH_BYTES = 256 << 20
-BLEND_FLOP_PER_EVAL = 20      # algorithmic FP32 FLOP per (Gaussian, pixel) evaluation
+EVAL_FLOP = 20        # FP32 FLOP per (Gaussian, pixel) evaluation (FMA = 2)
+TEST_FLOP = 36        # FP32 FLOP per footprint culling test (4 edges x 9)
+W_FULL, H_FULL = 1352, 1014
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pruned_masked",
-                    choices=["pruned_masked", "unpruned_masked", "pruned_unmasked",
-                             "unpruned_unmasked"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the comparison workloads")
     return ap.parse_args()
 
 
-def make_workload(name):
+def frame_list(n, offset=0):
+    """Frame indices of n consecutive requests: a stride-7 walk over the 300 frames."""
+    return [((offset + i) * 7) % 300 for i in range(n)]
+
+
+def pruned_masked():
     from paper_2503_16422_gb300 import scenes
-    scene = scenes.pruned_scene() if name.startswith("pruned") else scenes.unpruned_scene()
-    masked = name.endswith("_masked")
+    scene = scenes.pruned_scene()
     kt = scenes.keyframe_times()
-    masks = scenes.keyframe_masks(scene, kt) if masked else None
-    return scene, masked, kt, masks
+    return scene, kt, scenes.keyframe_masks(scene, kt)
 
 
-def frame_list(steps, offset=0):
-    """Frame indices visited by the steps: a stride-7 walk over the 300 frames."""
-    return [((offset + i) * 7) % 300 for i in range(steps)]
+def workload_config(scene, kt, batch):
+    return {"workload": f"pruned scene, {scene.n} Gaussians, degree-{scene.sh_degree} SH, "
+                        f"masked (key-frame masks every 6 of 300 frames, {len(kt)} rows), "
+                        f"batches of {batch} frames at {W_FULL}x{H_FULL} on a 20-degree arc",
+            "n_gaussians": scene.n, "width": W_FULL, "height": H_FULL, "tile": 16,
+            "batch": batch, "masked": True,
+            "l2": "flushed before every timed step (256 MiB write)"}
 
 
-def workload_config(name, scene, masked, kt):
-    return {"workload": f"{name}: {scene.n} Gaussians, degree-{scene.sh_degree} SH, 1352x1014, "
-                        f"300 frames on a 20-degree arc" +
-                        (f", key-frame masks every 6 frames ({len(kt)})" if masked else ", no mask"),
-            "n_gaussians": scene.n, "width": 1352, "height": 1014, "tile": 16,
-            "masked": masked, "l2": "flushed before every timed step (256 MiB write)"}
-
-
-# ---- peaks ---------------------------------------------------------------------------------
+# ---- peaks -----------------------------------------------------------------------------
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -87,7 +91,7 @@ def fp32_peak_tflops(sm_mhz, sms=152):
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-# ---- clocks sampler ------------------------------------------------------------------------
+# ---- clocks sampler --------------------------------------------------------------------
 
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -105,8 +109,7 @@ class Clocks:
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
 
@@ -141,126 +144,129 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# ---- CPU oracle baseline -------------------------------------------------------------------
+# ---- CPU oracle baseline ---------------------------------------------------------------
 
-def cpu_oracle_fps(scene, masked, kt, masks, n_tiles=24, frame=150):
-    """FP64 oracle on a bounded sample of one frame: the whole per-Gaussian stage plus the
-    blend of n_tiles randomly chosen tiles (of 5,440); the tile time is scaled to the frame."""
+def cpu_oracle_frame(scene, kt, masks, frame=150, budget_s=12.0, min_tiles=8):
+    """FP64 oracle on a bounded sample of one masked frame: the whole per-Gaussian stage,
+    then the blend of randomly chosen tiles until ~budget_s of CPU work; the tile time is
+    scaled to all 5,440 tiles. Returns seconds per frame, a description and the threads."""
     import torch
 
     import oracle
     from paper_2503_16422_gb300 import scenes
     cam = scenes.arc_camera(scenes.frame_theta(frame))
     t = float(scenes.frame_times()[frame])
-    active = oracle.active_from_masks(masks, kt, t, scene.n) if masked else None
+    active = oracle.active_from_masks(masks, kt, t, scene.n)
     P = oracle.Params.from_scene(scene)
     t0 = time.perf_counter()
     pre = oracle.preprocess(P, cam, t, active)
     t1 = time.perf_counter()
     gx, gy = pre["grid"]
-    tiles = np.random.default_rng(0).choice(gx * gy, n_tiles, replace=False).tolist()
-    oracle.render(P, cam, t, active, tiles=tiles, pre=pre)
+    order = np.random.default_rng(frame).permutation(gx * gy).tolist()
+    done = 0
+    while done < len(order) and (done < min_tiles or time.perf_counter() - t1 < budget_s):
+        chunk = order[done:done + 8]
+        oracle.render(P, cam, t, active, tiles=chunk, pre=pre)
+        done += len(chunk)
     t2 = time.perf_counter()
-    frame_s = (t1 - t0) + (t2 - t1) * (gx * gy) / n_tiles
-    return dict(value=1.0 / frame_s, unit="FPS", cores=torch.get_num_threads(), kind="oracle",
-                sample=f"1 frame (k={frame}): per-Gaussian stage of all {scene.n} Gaussians "
-                       f"+ blend of {n_tiles}/{gx * gy} random tiles, scaled to the frame "
-                       f"({t2 - t0:.1f} s of CPU work)")
+    frame_s = (t1 - t0) + (t2 - t1) * (gx * gy) / done
+    desc = (f"1 frame (k={frame}): per-Gaussian stage of all {scene.n} Gaussians + blend of "
+            f"{done}/{gx * gy} random tiles scaled to the frame ({t2 - t0:.1f} s of CPU work)")
+    return frame_s, desc, torch.get_num_threads()
 
 
-# ---- our implementation ----------------------------------------------------------------------
+# ---- helpers for our implementation ------------------------------------------------------
 
 def stage_bytes(stats, n, deg, masked):
-    """Algorithmic DRAM bytes of each HBM-bound stage for one frame."""
+    """Algorithmic DRAM bytes of each HBM-bound stage of one single-request frame."""
     na, nv, K, kb = stats["n_active"], stats["n_visible"], stats["n_keys"], stats["key_bytes"]
     sh = (deg + 1) ** 2 * 3 * 4
     tiles = stats["tiles_x"] * stats["tiles_y"]
     passes = math.ceil(math.ceil(math.log2(max(tiles, 2))) / 8)
+    emit = nv * 24 + K * kb if stats["list_builder"] == 1 else K * 4
     return {
         "preprocess": (2 * math.ceil(n / 32) * 4 if masked else 0) + na * 68 + nv * (sh + 48 + 8),
         "depth_sort": nv * 8 + 4 * nv * 16,
         "gather_scan": nv * (8 + 48 + 64 + 4 + 16),
-        "emit": nv * (20 + 4) + K * kb,
-        "tile_sort": passes * K * kb * 2,
         "tile_scan": (stats["tiles_x"] + 1) * (stats["tiles_y"] + 1) * 4 * 3 + tiles * 8,
+        "emit": emit,
+        "tile_sort": passes * K * kb * 2 if stats["list_builder"] == 1 else 0,
     }
 
 
-def _timed_steps(sc, cams, times, frames, masked, out, flush, stream):
-    import torch
-    step_ms = []
-    for k in frames:
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-    return step_ms
+def _flush(buf):
+    buf.fill_(1.0)
 
 
-def _profile_frames(sc, cams, times, frames, masked, out, flush, scene):
-    """Untimed pass over the same frames: per-stage CUDA-event times, frame counts and the
-    blend evaluation count (the counting kernel variant is not the timed one)."""
+def profile_single(sc, cams, times, frames, masked, out, flush, scene):
+    """Per-stage CUDA-event times, frame counts and blend work counts of single renders."""
     from paper_2503_16422_gb300 import fdgs
     sc.profile(1)
     acc = {s: 0.0 for s in fdgs.PROFILE_STAGES}
-    stats_acc = []
+    stats = []
     for k in frames:
-        flush.fill_(1.0)
+        _flush(flush)
         _, fr = sc.render(cams[k], float(times[k]), use_mask=masked, out=out, keep_frame=True)
-        ms, _ = sc.profile_read()
+        ms = sc.profile_read()[0]
         for s_ in acc:
-            acc[s_] += ms[s_]
-        stats_acc.append(fr.stats())
+            acc[s_] += ms[s_] / len(frames)
+        stats.append(fr.stats())
         fr.release()
     sc.profile(2)
-    evals = 0
+    ev = te = 0
     for k in frames:
         sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
-        evals += sc.profile_read()[1]
+        _, e, t = sc.profile_read()
+        ev += e / len(frames)
+        te += t / len(frames)
     sc.profile(0)
-    nfr = len(frames)
-    stage_ms = {s_: acc[s_] / nfr for s_ in acc}
-    mean_stats = {f: float(np.mean([st[f] for st in stats_acc]))
-                  for f in ("n_active", "n_visible", "n_keys")}
-    sb = [stage_bytes(st, scene.n, scene.sh_degree, masked) for st in stats_acc]
+    counts = {f: float(np.mean([st[f] for st in stats])) for f in ("n_active", "n_visible",
+                                                                  "n_keys")}
+    counts["blend_evals"] = ev
+    counts["blend_tests"] = te
+    sb = [stage_bytes(st, scene.n, scene.sh_degree, masked) for st in stats]
     bytes_mean = {s_: float(np.mean([b[s_] for b in sb])) for s_ in sb[0]}
-    return stage_ms, mean_stats, bytes_mean, evals / nfr
+    return acc, counts, bytes_mean
 
 
-def _roofline(stage_ms, bytes_mean, evals_per_frame):
+def roofline(stage_ms, counts, bytes_mean):
     pk = peaks()
     dom = max((s_ for s_ in stage_ms if s_ != "host_sync"), key=stage_ms.get)
     if dom == "blend":
-        ach = evals_per_frame * BLEND_FLOP_PER_EVAL / (stage_ms["blend"] / 1e3) / 1e12
+        flop = counts["blend_evals"] * EVAL_FLOP + counts["blend_tests"] * TEST_FLOP
+        ach = flop / (stage_ms["blend"] / 1e3) / 1e12
         peak = fp32_peak_tflops(pk["sm_mhz"])
         return {"bound": "alu", "kernel": "k_blend", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_mhz']:.0f} MHz"}
+                "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_mhz']:.0f} MHz",
+                "work": "executed evaluations x 20 FLOP + culling tests x 36 FLOP"}
     ach = bytes_mean[dom] / (stage_ms[dom] / 1e3) / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
-            "frac": ach / pk["hbm"], "traffic": None, "peak_src": pk["src"]}
+            "frac": ach / pk["hbm"], "traffic": None, "peak_src": pk["src"] + " copy GB/s"}
 
 
-def _scene_on_gpu(name):
+def timed_batches(sc, cams_list, ts_list, outs_list, masked, flush, stream):
     import torch
-
-    from paper_2503_16422_gb300 import fdgs
-    scene, masked, kt, masks = make_workload(name)
-    sc = fdgs.Scene.from_host(scene)
-    if masked:
-        sc.set_active_mask(torch.as_tensor(masks).cuda(), kt)
-    return scene, masked, kt, masks, sc
+    ms = []
+    lat = []
+    for cams, ts, outs in zip(cams_list, ts_list, outs_list):
+        _flush(flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sc.render_batch(cams, ts, use_mask=masked, outs=outs)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        lat += sc.batch_info(len(cams))["latency_ms"]
+    return ms, lat
 
 
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2503_16422_gb300 import build, scenes
+    from paper_2503_16422_gb300 import build, fdgs, scenes
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -268,23 +274,37 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    scene, masked, kt, masks, sc = _scene_on_gpu(args.workload)
+    scene, kt, masks = pruned_masked()
+    sc = fdgs.Scene.from_host(scene)
+    sc.set_active_mask(torch.as_tensor(masks).cuda(), kt)
     times = scenes.frame_times()
     cams = {k: scenes.arc_camera(scenes.frame_theta(k)) for k in range(300)}
-    out = torch.empty((3, 1014, 1352), dtype=torch.float32, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    B = args.batch
+    outs = [torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device="cuda")
+            for _ in range(B)]
 
-    for k in frame_list(args.warmup, 1000 + rank):
-        sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
+    def batch_args(step, base):
+        fr = frame_list(B, base + step * B)
+        return [cams[k] for k in fr], [float(times[k]) for k in fr]
+
+    # autotune the batch launch shape once (untimed), then warm up (graph replays)
+    c0, t0 = batch_args(0, 5000 + rank)
+    sc.batch_autotune(c0, t0, outs=outs)
+    shape = sc.batch_info(B)
+    for w in range(args.warmup):
+        c_, t_ = batch_args(w, 6000 + rank)
+        sc.render_batch(c_, t_, outs=outs)
     torch.cuda.synchronize()
-    frames = frame_list(args.steps, rank * 37)
+    steps = [batch_args(s, rank * 1000) for s in range(args.steps)]
     clocks = Clocks(local)
     clocks.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms = _timed_steps(sc, cams, times, frames, masked, out, flush, stream)
+    step_ms, lat = timed_batches(sc, [a for a, _ in steps], [b for _, b in steps],
+                                 [outs] * len(steps), True, flush, stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -294,109 +314,159 @@ def run_ours(args):
         tt = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
-    value = world * len(frames) / (total_ms / 1e3)
+    frames_done = B * len(steps)
+    value = world * frames_done / (total_ms / 1e3)
+    res = dict(clocks=clk, batch_shape=shape, lat=lat)
 
-    # end to end through the public API: per step the camera and t go host->device as
-    # launch arguments and the rendered image comes back to pinned host memory
-    host = torch.empty((3, 1014, 1352), dtype=torch.float32, pin_memory=True)
+    # end to end through the public API: per step the cameras and times go host->device (the
+    # request descriptors) and all B rendered images come back to pinned host memory
+    host = [torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, pin_memory=True)
+            for _ in range(B)]
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in frames:
-        sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
-        host.copy_(out, non_blocking=True)
+    te = time.perf_counter()
+    for c_, t_ in steps:
+        sc.render_batch(c_, t_, outs=outs)
+        for h, o in zip(host, outs):
+            h.copy_(o, non_blocking=True)
         stream.synchronize()
-    e2e_s = time.perf_counter() - t0
-    cam_bytes = 16 * 4 + 4 * 4 + 3 * 4 + 4 + 4 + 4   # fdgs_camera + t + opts
-    res = {}
+    e2e_s = time.perf_counter() - te
+    res["e2e"] = dict(value=world * frames_done / e2e_s, unit="FPS",
+                      h2d_bytes_per_step=B * (16 * 4 + 8 * 4 + 4),
+                      d2h_bytes_per_step=B * 3 * H_FULL * W_FULL * 4)
+
     if rank == 0:
-        stage_ms, mean_stats, bytes_mean, evals = _profile_frames(
-            sc, cams, times, frames, masked, out, flush, scene)
-        res = dict(stage_ms=stage_ms, mean_counts=mean_stats, evals_per_frame=evals,
-                   roofline=_roofline(stage_ms, bytes_mean, evals), clocks=clk,
-                   e2e=dict(value=len(frames) / e2e_s, unit="FPS",
-                            h2d_bytes_per_step=cam_bytes,
-                            d2h_bytes_per_step=3 * 1014 * 1352 * 4),
+        # per-kernel profile on single renders of the same frames
+        out1 = outs[0]
+        fr_prof = frame_list(24, 11)
+        stage_ms, counts, bytes_mean = profile_single(sc, cams, times, fr_prof, True, out1,
+                                                      flush, scene)
+        res.update(stage_ms=stage_ms, counts=counts,
+                   roofline=roofline(stage_ms, counts, bytes_mean),
                    stage_gbs={s_: bytes_mean[s_] / (stage_ms[s_] / 1e3) / 1e9
-                              for s_ in bytes_mean if stage_ms[s_] > 0},
-                   blend_tflops=evals * BLEND_FLOP_PER_EVAL / max(stage_ms["blend"], 1e-9) / 1e9)
+                              for s_ in bytes_mean if stage_ms[s_] > 1e-4})
+        if not args.no_extra:
+            res["comparisons"] = comparisons(sc, cams, times, flush, stream)
     sc.close()
-    if rank == 0 and not args.no_extra:
-        res["comparisons"] = {}
-        for name in ("pruned_unmasked", "unpruned_masked", "unpruned_unmasked"):
-            if name == args.workload:
-                continue
-            sc2 = None
-            try:
-                scn, msk, _, _, sc2 = _scene_on_gpu(name)
-                fr = frame_list(12, 5)
-                for k in frame_list(2, 900):
-                    sc2.render(cams[k], float(times[k]), use_mask=msk, out=out)
-                ms = _timed_steps(sc2, cams, times, fr, msk, out, flush, stream)
-                st_ms, counts, _, ev = _profile_frames(sc2, cams, times, fr[:4], msk, out,
-                                                       flush, scn)
-                res["comparisons"][name] = dict(
-                    fps=len(fr) / (sum(ms) / 1e3), ms_per_frame=sum(ms) / len(fr),
-                    raster_ms=sum(st_ms[s_] for s_ in ("tile_scan", "emit", "tile_sort", "blend")),
-                    stages_ms=st_ms, counts_per_frame=dict(counts, blend_evals=ev))
-            except Exception as e:   # a comparison must not hide the headline number
-                res["comparisons"][name] = {"error": str(e)[:200]}
-            finally:
-                if sc2 is not None:
-                    sc2.close()
-                torch.cuda.empty_cache()
-    return value, total_ms / len(frames), res, scene, masked, kt, masks, world, rank
+    return value, total_ms / len(steps), res, scene, kt, masks, world, rank
 
 
-def launches_per_frame(masked):
-    # memsets are not kernels; per frame: preprocess, depth sort (hist, scan, 4 passes),
-    # gather_scan, emit, tile sort (hist, scan, 2 passes), ranges, blend
-    return 1 + 6 + 1 + 1 + 4 + 1 + 1
+def comparisons(sc, cams, times, flush, stream):
+    import torch
+
+    from paper_2503_16422_gb300 import fdgs, scenes
+    out = torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device="cuda")
+    res = {}
+    fr = frame_list(24, 3)
+
+    def single(scene_obj, masked, frames):
+        for k in frames[:2]:
+            scene_obj.render(cams[k], float(times[k]), use_mask=masked, out=out)
+        ms = []
+        for k in frames:
+            _flush(flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            scene_obj.render(cams[k], float(times[k]), use_mask=masked, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return dict(fps=len(frames) / (sum(ms) / 1e3), ms_per_frame=sum(ms) / len(frames))
+
+    res["single_masked"] = single(sc, True, fr)
+    res["single_unmasked"] = single(sc, False, fr)
+    # serving batch: 64 requests of mixed resolutions vs 64 sequential renders
+    reqs, rts = scenes.random_requests(64, 4)
+    outs = [torch.empty((3, c.height, c.width), dtype=torch.float32, device="cuda")
+            for c in reqs]
+    sc.batch_autotune(reqs, rts, outs=outs)
+    for _ in range(2):
+        sc.render_batch(reqs, rts, outs=outs)
+    ms, lat = timed_batches(sc, [reqs] * 5, [rts] * 5, [outs] * 5, True, flush, stream)
+    seq_lat, seq_ms = [], []
+    for rep in range(3):
+        _flush(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, t, o in zip(reqs, rts, outs):
+            sc.render(c, float(t), out=o)
+            torch.cuda.synchronize()
+            seq_lat.append((time.perf_counter() - t0) * 1e3)
+        seq_ms.append((time.perf_counter() - t0) * 1e3)
+    res["serving_batch_mixed"] = dict(
+        requests=64, resolutions="uniform over 512x512, 800x800, 1014x1352, 1352x1014",
+        fps=64 / (statistics.median(ms) / 1e3), ms_per_batch=statistics.median(ms),
+        p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+        sequential_fps=64 / (statistics.median(seq_ms) / 1e3),
+        sequential_p50_ms=float(np.percentile(seq_lat, 50)),
+        sequential_p99_ms=float(np.percentile(seq_lat, 99)),
+        shape=sc.batch_info(64))
+    # unpruned 3M scene, single requests
+    big = scenes.unpruned_scene()
+    kt = scenes.keyframe_times()
+    sc2 = fdgs.Scene.from_host(big)
+    sc2.set_active_mask(torch.as_tensor(scenes.keyframe_masks(big, kt)).cuda(), kt)
+    res["unpruned_masked"] = dict(single(sc2, True, fr[:12]), n_gaussians=big.n)
+    res["unpruned_unmasked"] = dict(single(sc2, False, fr[:12]), n_gaussians=big.n)
+    sc2.close()
+    del big
+    torch.cuda.empty_cache()
+    return res
+
+
+def launches_per_batch():
+    # start, preprocess, bases, segment compaction, depth sort (histogram, scan, 5 passes),
+    # gather, tile scan, lists, queue sort (histogram, scan, 3 passes), persistent blend
+    return 1 + 1 + 1 + 1 + 7 + 1 + 1 + 1 + 5 + 1
 
 
 def main():
     args = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         if rank != 0:
             return
-        scene, masked, kt, masks = make_workload(args.workload)
-        for _ in range(args.warmup):
-            pass
-        vals = []
+        scene, kt, masks = pruned_masked()
+        for w in range(args.warmup):
+            cpu_oracle_frame(scene, kt, masks, frame=frame_list(1, 200 + w)[0], budget_s=1.0)
+        secs = []
         for i in range(max(args.steps, 1)):
-            r = cpu_oracle_fps(scene, masked, kt, masks, n_tiles=4, frame=frame_list(1, i)[0])
-            vals.append(1.0 / r["value"])
-        fps = len(vals) / sum(vals)
-        cb = dict(r, value=fps)
+            s_, desc, cores = cpu_oracle_frame(scene, kt, masks, frame=frame_list(1, i)[0],
+                                               budget_s=4.0)
+            secs.append(s_)
+        fps = len(secs) / sum(secs)
         line = {"metric": METRIC, "value": fps, "unit": "FPS", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / fps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
-                "config": workload_config(args.workload, scene, masked, kt),
-                "impl": "reference", "cpu_baseline": cb,
+                "config": workload_config(scene, kt, 1), "impl": "reference",
+                "cpu_baseline": {"value": fps, "unit": "FPS", "cores": cores, "kind": "oracle",
+                                 "sample": "per step: " + desc},
                 "e2e": {"value": fps, "unit": "FPS", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
-    value, ms, res, scene, masked, kt, masks, world, rank = run_ours(args)
+    value, ms, res, scene, kt, masks, world, rank = run_ours(args)
     if rank != 0:
         return
+    lat = res["lat"]
     line = {"metric": METRIC, "value": value, "unit": "FPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config(args.workload, scene, masked, kt)}
-    line.update({k: res[k] for k in ("roofline", "clocks", "e2e")})
-    line["gpu_launches"] = launches_per_frame(masked) * args.steps
-    line["stages_ms"] = res["stage_ms"]
-    line["stage_gbs"] = res["stage_gbs"]
-    line["blend_tflops"] = res["blend_tflops"]
-    line["counts_per_frame"] = dict(res["mean_counts"], blend_evals=res["evals_per_frame"])
-    line["raster_ms"] = sum(res["stage_ms"][s_] for s_ in ("tile_scan", "emit", "tile_sort", "blend"))
+            "data": "synthetic", "config": workload_config(scene, kt, args.batch),
+            "roofline": res["roofline"], "clocks": res["clocks"], "e2e": res["e2e"],
+            "gpu_launches": launches_per_batch() * args.steps,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99))},
+            "batch_shape": res["batch_shape"],
+            "single_frame_stages_ms": res["stage_ms"], "stage_gbs": res["stage_gbs"],
+            "counts_per_frame": res["counts"]}
     if "comparisons" in res:
         line["comparisons"] = res["comparisons"]
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_fps(scene, masked, kt, masks)
+        s_, desc, cores = cpu_oracle_frame(scene, kt, masks)
+        line["cpu_baseline"] = {"value": 1.0 / s_, "unit": "FPS", "cores": cores,
+                                "kind": "oracle", "sample": desc}
     print(json.dumps(line))
 
 

@@ -175,15 +175,32 @@ int fdgs_frame_export(fdgs_frame *frame, uint32_t *tile_ranges_dev, uint32_t *ti
                       float *records_dev, fdgs_stream stream);
 
 /*
- * Renders n_req requests (cams[i], ts[i]; each camera has its own resolution) in one
- * batched pass: one per-Gaussian launch over all (request, Gaussian) pairs, one global sort
- * whose tile ids are offset per request, and one persistent blend over a global tile queue.
- * rgb_out_dev is a HOST array of n_req device pointers, each [3][h_i][w_i]. Results are
- * identical to n_req calls of fdgs_render. Synchronises the stream once to size buffers.
+ * Renders n_req requests (cams[i], ts[i]; each camera has its own resolution; 1 <= n_req <=
+ * 128; n < 2^25) in one device-driven pass: one per-Gaussian launch over all (request,
+ * Gaussian) pairs, one global depth sort whose keys carry the request, per-request tile
+ * lists, and ONE persistent blend launch over a queue of all requests' tiles, longest list
+ * first. The first call for a batch geometry (request count, resolutions, mask use, scene
+ * attribute pointers) runs eagerly and captures the sequence in a CUDA graph; later calls
+ * replay it. rgb_out_dev is a HOST array of n_req device pointers, each [3][h_i][w_i].
+ * Results equal n_req calls of fdgs_render. Synchronises the stream once, at the end; if a
+ * list capacity was exceeded it grows the buffers and reruns before returning.
  */
 int fdgs_render_batch(fdgs_scene *scene, const fdgs_camera *cams, const float *ts, int n_req,
                       const fdgs_render_opts *opts, float *const *rgb_out_dev,
                       fdgs_stream stream);
+
+/* Autotuner of the batched path: renders the batch once per candidate launch shape (warp
+ * footprint of the blend x persistent CTAs per SM), keeps the fastest for this batch
+ * geometry, and leaves the outputs of a final render in rgb_out_dev. Synchronises. */
+int fdgs_batch_autotune(fdgs_scene *scene, const fdgs_camera *cams, const float *ts,
+                        int n_req, const fdgs_render_opts *opts, float *const *rgb_out_dev,
+                        fdgs_stream stream);
+
+/* Last batch: per-request latency in ms (%globaltimer, from the start of the batch to the
+ * completion of the request's last tile) for the first n requests, and the launch shape in
+ * use. Any pointer may be NULL. FDGS_ERR_STATE if no batch was rendered. */
+int fdgs_batch_info(fdgs_scene *scene, float *latency_ms, int n, int *footprint,
+                    int *ctas_per_sm);
 
 /*
  * Spatial-Temporal Variation Score (Sec. 4.2.1, Eqs. 4-7), reading "per-t product":
@@ -236,9 +253,10 @@ int fdgs_select_keep_noalloc(const float *score_dev, int64_t n, float prune_rati
 #define FDGS_PROFILE_STAGES 8
 int fdgs_profile_enable(fdgs_scene *scene, int flags);
 
-/* Stage times in milliseconds of the last profiled render, and the blend evaluation count
- * of the last counted render (either pointer may be NULL). Synchronises the device. */
-int fdgs_profile_read(fdgs_scene *scene, float *stage_ms, uint64_t *blend_evals);
+/* Stage times in milliseconds of the last profiled render, and blend_counts[2] of the last
+ * counted render: (Gaussian, pixel) evaluations executed and footprint culling tests
+ * executed (either pointer may be NULL). Synchronises the device. */
+int fdgs_profile_read(fdgs_scene *scene, float *stage_ms, uint64_t *blend_counts);
 
 /* How renders build the per-tile lists, process-wide. 1: emit one (tile, depth-rank) key
  * per covered tile and radix-sort the keys by tile; 2: AND per-tile-row and per-tile-column

@@ -115,9 +115,48 @@ struct FrameMeta {
 
 }  // namespace
 
+namespace {
+
+// Buffers, captured graph and tuning of one batch geometry (request count, resolutions,
+// mask use, scene attribute pointers). Built on the first batch call of that geometry.
+struct BatchPlan {
+  int nreq = 0;
+  std::vector<int> W, H;
+  bool masked = false;
+  fdgs_scene_desc d{};
+  uint32_t ntiles = 0, mask_words = 0;
+  uint64_t npix = 0, key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
+  std::vector<ReqDesc> tmpl;
+  Buf reqs, ctr, pre_status, scan_status, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base,
+      key_base, rec_sorted, diff, masks, ranges, qkeys, qkeys_alt, lists, Tf, nc, done, t0,
+      scratch;
+  ReqDesc *h_reqs = nullptr;
+  uint32_t *h_ctr = nullptr;
+  unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int footprint = 1, ctas = 0;
+  bool tuned = false;
+  std::vector<float> lat_ms;
+  ~BatchPlan() {
+    Buf *all[] = {&reqs, &ctr, &pre_status, &scan_status, &rec, &vis_seg, &vis, &vis_alt,
+                  &nv, &vis_base, &slot_base, &key_base, &rec_sorted, &diff, &masks,
+                  &ranges, &qkeys, &qkeys_alt, &lists, &Tf, &nc, &done, &t0, &scratch};
+    for (Buf *b : all) b->release();
+    if (h_reqs) cudaFreeHost(h_reqs);
+    if (h_ctr) cudaFreeHost(h_ctr);
+    if (h_done) cudaFreeHost(h_done);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+}  // namespace
+
 struct fdgs_scene {
   fdgs_scene_desc d{};
   int device = 0;
+  BatchPlan *plan = nullptr;
   Buf masks;
   size_t row_words = 0;
   int n_key = 0;
@@ -130,7 +169,7 @@ struct fdgs_scene {
                   // 3 device scalar, 4 score-pass image
   int prof = 0;   // profiling flags (fdgs_profile_enable)
   cudaEvent_t ev[FDGS_PROFILE_STAGES + 1] = {};
-  Buf evals;      // u64 blend evaluation counter
+  Buf evals;      // u64[2] blend evaluations and culling tests
 };
 
 struct fdgs_frame {
@@ -262,7 +301,7 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   }
   const bool prof = (s->prof & 1) && s->ev[0];
   const bool count = (s->prof & 2) && s->evals.p;
-  if (count) CK(cudaMemsetAsync(s->evals.p, 0, 8, st));
+  if (count) CK(cudaMemsetAsync(s->evals.p, 0, 16, st));
   if (prof) CK(cudaEventRecord(s->ev[0], st));
   CK(cudaMemsetAsync(ws.ctr.p, 0, C_COUNT * 4, st));
   CK(cudaMemsetAsync(ws.pre_status.p, 0, parts * 8, st));
@@ -388,6 +427,238 @@ Workspace *take_workspace(fdgs_scene *s) {
   return new Workspace();
 }
 
+// ---- batched rendering -------------------------------------------------------------------
+
+bool plan_matches(const BatchPlan *p, const fdgs_scene *s, const fdgs_camera *cams, int n,
+                  bool masked) {
+  if (!p || p->nreq != n || p->masked != masked || memcmp(&p->d, &s->d, sizeof(s->d)) != 0)
+    return false;
+  for (int i = 0; i < n; ++i)
+    if (p->W[i] != cams[i].width || p->H[i] != cams[i].height) return false;
+  return true;
+}
+
+int plan_alloc_lists(BatchPlan &p) {
+  TRY(grow(p.lists, std::max<uint64_t>(p.key_cap, 1) * 4));
+  return FDGS_OK;
+}
+
+int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
+  if (plan_matches(s->plan, s, cams, n, masked)) return FDGS_OK;
+  delete s->plan;
+  s->plan = new BatchPlan();
+  BatchPlan &p = *s->plan;
+  p.nreq = n;
+  p.masked = masked;
+  p.d = s->d;
+  const uint32_t N = (uint32_t)s->d.n;
+  p.mask_words = (N + 255) / 256 * 8;
+  p.tmpl.resize(n);
+  uint64_t tiles = 0, pix = 0, diff = 0, mask = 0;
+  for (int i = 0; i < n; ++i) {
+    DevCam dc;
+    TRY(make_cam(&cams[i], dc));
+    p.W.push_back(dc.W);
+    p.H.push_back(dc.H);
+    ReqDesc &q = p.tmpl[i];
+    memset(&q, 0, sizeof q);
+    q.tile_base = (uint32_t)tiles;
+    q.pix_base = pix;
+    q.diff_base = (uint32_t)diff;
+    q.mask_base = mask;
+    tiles += (uint64_t)dc.gx * dc.gy;
+    pix += (uint64_t)dc.W * dc.H;
+    diff += (uint64_t)(dc.gx + 1) * (dc.gy + 1);
+    mask += (uint64_t)(dc.gx + dc.gy) * p.mask_words;
+  }
+  if (tiles >= (1ull << 32) || diff >= (1ull << 31))
+    return fail(FDGS_ERR_INVALID, "batch too large");
+  p.ntiles = (uint32_t)tiles;
+  p.npix = pix;
+  p.diff_ints = diff;
+  p.mask_total = mask;
+  p.rn = (uint64_t)n * N;
+  p.slot_cap = p.rn + (uint64_t)n * 256;
+  p.key_cap = std::max<uint64_t>(p.rn * 16, 1 << 20);
+  const uint64_t P = (N + 255) / 256;
+  TRY(grow(p.reqs, n * sizeof(ReqDesc)));
+  TRY(grow(p.ctr, BC_COUNT * 4));
+  TRY(grow(p.pre_status, std::max<uint64_t>(P * n, 1) * 8));
+  TRY(grow(p.scan_status, std::max<uint64_t>(p.slot_cap / 256, 1) * 8));
+  TRY(grow(p.rec, std::max<uint64_t>(p.rn, 1) * kRec * 4));
+  TRY(grow(p.vis_seg, std::max<uint64_t>(p.rn, 1) * 8));
+  TRY(grow(p.vis, std::max<uint64_t>(p.rn, 1) * 8));
+  TRY(grow(p.vis_alt, std::max<uint64_t>(p.rn, 1) * 8));
+  TRY(grow(p.nv, n * 4));
+  TRY(grow(p.vis_base, n * 4));
+  TRY(grow(p.slot_base, n * 4));
+  TRY(grow(p.key_base, n * 8));
+  TRY(grow(p.rec_sorted, p.slot_cap * kRecS * 4));
+  TRY(grow(p.diff, diff * 4));
+  TRY(grow(p.masks, std::max<uint64_t>(mask, 1) * 4));
+  TRY(grow(p.ranges, tiles * 8));
+  TRY(grow(p.qkeys, tiles * 8));
+  TRY(grow(p.qkeys_alt, tiles * 8));
+  TRY(grow(p.Tf, pix * 4));
+  TRY(grow(p.nc, pix * 4));
+  TRY(grow(p.done, n * 8));
+  TRY(grow(p.t0, 8));
+  TRY(grow(p.scratch, std::max(sort_scratch_bytes(std::max<uint64_t>(p.rn, 1), 39),
+                               sort_scratch_bytes(tiles, 24))));
+  TRY(plan_alloc_lists(p));
+  CK(cudaMallocHost(&p.h_reqs, n * sizeof(ReqDesc)));
+  CK(cudaMallocHost(&p.h_ctr, BC_COUNT * 4));
+  CK(cudaMallocHost(&p.h_done, (n + 1) * 8));
+  CK(cudaStreamCreateWithFlags(&p.cap, cudaStreamNonBlocking));
+  p.ctas = std::min(4, batch_blend_max_ctas_per_sm());
+  return FDGS_OK;
+}
+
+// Per-call request contents: camera, time, mask rows of the two nearest key-frames, output.
+int plan_fill(fdgs_scene *s, BatchPlan &p, const fdgs_camera *cams, const float *ts,
+              const fdgs_render_opts *opts, float *const *rgb) {
+  for (int i = 0; i < p.nreq; ++i) {
+    ReqDesc q = p.tmpl[i];
+    TRY(make_cam(&cams[i], q.cam));
+    if (!rgb[i]) return fail(FDGS_ERR_INVALID, "null output image for request %d", i);
+    q.t = ts[i];
+    q.rgb = rgb[i];
+    for (int c = 0; c < 3; ++c) q.bg[c] = opts ? opts->bg[c] : 0.f;
+    q.mask_l = q.mask_r = nullptr;
+    if (p.masked) {
+      int l, r;
+      keyframe_pair(s->key_times, ts[i], l, r);
+      q.mask_l = s->masks.as<uint32_t>() + (size_t)l * s->row_words;
+      q.mask_r = s->masks.as<uint32_t>() + (size_t)r * s->row_words;
+    }
+    p.h_reqs[i] = q;
+  }
+  return FDGS_OK;
+}
+
+void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
+  b.reqs = p.reqs.as<ReqDesc>();
+  b.nreq = p.nreq;
+  b.n = (uint32_t)s->d.n;
+  b.ntiles = p.ntiles;
+  b.mask_words = p.mask_words;
+  b.key_cap = p.key_cap;
+  b.mean4 = (const float4 *)s->d.mean4;
+  b.ls4 = (const float4 *)s->d.logscale4;
+  b.ql = (const float4 *)s->d.q_left;
+  b.qr = (const float4 *)s->d.q_right;
+  b.opacity = s->d.opacity_logit;
+  b.sh = s->d.sh;
+  b.deg = s->d.sh_degree;
+  b.ctr = p.ctr.as<uint32_t>();
+  b.err = s->status.as<uint32_t>();
+  b.pre_status = p.pre_status.as<uint64_t>();
+  b.scan_status = p.scan_status.as<uint64_t>();
+  b.rec = p.rec.as<float>();
+  b.vis_seg = p.vis_seg.as<uint64_t>();
+  b.vis = p.vis.as<uint64_t>();
+  b.vis_alt = p.vis_alt.as<uint64_t>();
+  b.vis_sorted = nullptr;
+  b.nv = p.nv.as<uint32_t>();
+  b.vis_base = p.vis_base.as<uint32_t>();
+  b.slot_base = p.slot_base.as<uint32_t>();
+  b.key_base = p.key_base.as<uint64_t>();
+  b.rec_sorted = p.rec_sorted.as<float>();
+  b.diff = p.diff.as<int>();
+  b.masks = p.masks.as<uint32_t>();
+  b.ranges = p.ranges.as<uint2>();
+  b.qkeys = p.qkeys.as<uint64_t>();
+  b.qkeys_alt = p.qkeys_alt.as<uint64_t>();
+  b.queue = nullptr;
+  b.lists = p.lists.as<uint32_t>();
+  b.T_final = p.Tf.as<float>();
+  b.n_contrib = p.nc.as<uint32_t>();
+  b.done_ns = p.done.as<unsigned long long>();
+  b.t0_ns = p.t0.as<unsigned long long>();
+  const uint64_t P = ((uint64_t)s->d.n + 255) / 256;
+  L.pre_status_bytes = std::max<uint64_t>(P * p.nreq, 1) * 8;
+  L.scan_status_bytes = std::max<uint64_t>(p.slot_cap / 256, 1) * 8;
+  L.diff_bytes = p.diff_ints * 4;
+  L.sort_scratch = p.scratch.p;
+  L.footprint = p.footprint;
+  L.blend_ctas_per_sm = p.ctas;
+}
+
+int plan_capture(fdgs_scene *s, BatchPlan &p) {
+  if (p.exec) {
+    cudaGraphExecDestroy(p.exec);
+    p.exec = nullptr;
+  }
+  BatchDev b;
+  BatchLaunch L;
+  plan_dev(s, p, b, L);
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeRelaxed));
+  cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice, p.cap);
+  launch_batch(b, L, p.cap);
+  const cudaError_t e = cudaStreamEndCapture(p.cap, &g);
+  if (e != cudaSuccess) return fail(FDGS_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(&p.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    p.exec = nullptr;
+    return fail(FDGS_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e2));
+  }
+  return FDGS_OK;
+}
+
+// Runs the batch (graph replay when captured, else eagerly), synchronises the stream, grows
+// the list capacity and reruns if it overflowed, records per-request latencies.
+int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if (p.exec) {
+      CK(cudaGraphLaunch(p.exec, st));
+    } else {
+      BatchDev b;
+      BatchLaunch L;
+      plan_dev(s, p, b, L);
+      CK(cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice,
+                         st));
+      launch_batch(b, L, st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(p.h_ctr, p.ctr.p, BC_COUNT * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(p.h_done, p.done.p, p.nreq * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(p.h_done + p.nreq, p.t0.p, 8, cudaMemcpyDeviceToHost, st));
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&e, s->status.p, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (e & kErrTimeout) {
+      CK(cudaMemset(s->status.p, 0, 4));
+      return fail(FDGS_ERR_TIMEOUT, "device spin-wait limit reached");
+    }
+    if (e & kErrCapacity) {
+      CK(cudaMemset(s->status.p, 0, 4));
+      const uint64_t nkeys = (uint64_t)p.h_ctr[BC_NKEYS_LO] | ((uint64_t)p.h_ctr[BC_NKEYS_HI] << 32);
+      if (nkeys >= (1ull << 32)) return fail(FDGS_ERR_CAPACITY, "batch has >= 2^32 tile keys");
+      p.key_cap = nkeys + nkeys / 8 + 1024;
+      TRY(plan_alloc_lists(p));
+      if (p.exec) TRY(plan_capture(s, p));
+      continue;
+    }
+    p.lat_ms.resize(p.nreq);
+    const unsigned long long t0 = p.h_done[p.nreq];
+    for (int i = 0; i < p.nreq; ++i)
+      p.lat_ms[i] = p.h_done[i] > t0 ? (float)((p.h_done[i] - t0) * 1e-6) : 0.f;
+    return FDGS_OK;
+  }
+  return fail(FDGS_ERR_CAPACITY, "batch list capacity kept overflowing");
+}
+
+int batch_args_ok(fdgs_scene *s, const fdgs_camera *cams, const float *ts, int n_req,
+                  float *const *rgb) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (n_req < 0 || n_req > 128 || (n_req > 0 && (!cams || !ts || !rgb)))
+    return fail(FDGS_ERR_INVALID, "bad batch arguments (1..128 requests)");
+  if (s->d.n >= (1ll << 25)) return fail(FDGS_ERR_INVALID, "batched path needs n < 2^25");
+  return FDGS_OK;
+}
+
 }  // namespace
 
 void fdgs::set_error_message(const char *msg) { g_err = msg ? msg : ""; }
@@ -436,6 +707,7 @@ int fdgs_destroy_scene(fdgs_scene *s) {
     delete f;
   }
   for (Workspace *w : s->pool) delete w;
+  delete s->plan;
   s->masks.release();
   s->status.release();
   s->evals.release();
@@ -608,14 +880,87 @@ int fdgs_render_backward(fdgs_scene *s, fdgs_frame *f, const float *dL_drgb_dev,
 int fdgs_render_batch(fdgs_scene *s, const fdgs_camera *cams, const float *ts, int n_req,
                       const fdgs_render_opts *opts, float *const *rgb_out_dev,
                       fdgs_stream stream) {
-  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
-  if (n_req < 0 || (n_req > 0 && (!cams || !ts || !rgb_out_dev)))
-    return fail(FDGS_ERR_INVALID, "bad batch arguments");
-  for (int i = 0; i < n_req; ++i) {
-    FrameMeta m;
-    TRY(render_impl(s, s->main, &cams[i], ts[i], opts, rgb_out_dev[i], false, false, true, m,
-                    (cudaStream_t)stream));
+  TRY(batch_args_ok(s, cams, ts, n_req, rgb_out_dev));
+  if (n_req == 0 || s->d.n == 0) {
+    for (int i = 0; i < n_req; ++i) {   // empty scene: background only
+      FrameMeta m;
+      TRY(render_impl(s, s->main, &cams[i], ts[i], opts, rgb_out_dev[i], false, false, true, m,
+                      (cudaStream_t)stream));
+    }
+    return FDGS_OK;
   }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool masked = opts && opts->use_mask && s->n_key > 0;
+  TRY(plan_prepare(s, cams, n_req, masked));
+  BatchPlan &p = *s->plan;
+  TRY(plan_fill(s, p, cams, ts, opts, rgb_out_dev));
+  const bool first = !p.exec;
+  TRY(plan_run(s, p, st));
+  if (first) TRY(plan_capture(s, p));   // later calls of this geometry replay the graph
+  return FDGS_OK;
+}
+
+int fdgs_batch_autotune(fdgs_scene *s, const fdgs_camera *cams, const float *ts, int n_req,
+                        const fdgs_render_opts *opts, float *const *rgb_out_dev,
+                        fdgs_stream stream) {
+  TRY(batch_args_ok(s, cams, ts, n_req, rgb_out_dev));
+  if (n_req == 0 || s->d.n == 0) return FDGS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool masked = opts && opts->use_mask && s->n_key > 0;
+  TRY(plan_prepare(s, cams, n_req, masked));
+  BatchPlan &p = *s->plan;
+  TRY(plan_fill(s, p, cams, ts, opts, rgb_out_dev));
+  TRY(plan_run(s, p, st));   // sizes the list capacity
+  const int maxc = batch_blend_max_ctas_per_sm();
+  std::vector<int> ctas = {1, 2, 4, maxc};
+  std::sort(ctas.begin(), ctas.end());
+  ctas.erase(std::unique(ctas.begin(), ctas.end()), ctas.end());
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_f = p.footprint, best_c = p.ctas;
+  for (int f = 0; f < 3; ++f)
+    for (int c : ctas) {
+      if (c > maxc) continue;
+      p.footprint = f;
+      p.ctas = c;
+      TRY(plan_capture(s, p));
+      TRY(plan_run(s, p, st));   // warm
+      float tot = 0.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(e0, st));
+        CK(cudaGraphLaunch(p.exec, st));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        tot += ms;
+      }
+      if (tot < best) {
+        best = tot;
+        best_f = f;
+        best_c = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p.footprint = best_f;
+  p.ctas = best_c;
+  p.tuned = true;
+  TRY(plan_capture(s, p));
+  return plan_run(s, p, st);
+}
+
+int fdgs_batch_info(fdgs_scene *s, float *latency_ms, int n, int *footprint,
+                    int *ctas_per_sm) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (!s->plan) return fail(FDGS_ERR_STATE, "no batch has been rendered");
+  BatchPlan &p = *s->plan;
+  if (latency_ms)
+    for (int i = 0; i < std::min(n, (int)p.lat_ms.size()); ++i) latency_ms[i] = p.lat_ms[i];
+  if (footprint) *footprint = p.footprint;
+  if (ctas_per_sm) *ctas_per_sm = p.ctas;
   return FDGS_OK;
 }
 
@@ -702,12 +1047,12 @@ int fdgs_profile_enable(fdgs_scene *s, int flags) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   if ((flags & 1) && !s->ev[0])
     for (auto &e : s->ev) CK(cudaEventCreate(&e));
-  if (flags & 2) TRY(grow(s->evals, 8));
+  if (flags & 2) TRY(grow(s->evals, 16));
   s->prof = flags;
   return FDGS_OK;
 }
 
-int fdgs_profile_read(fdgs_scene *s, float *stage_ms, uint64_t *blend_evals) {
+int fdgs_profile_read(fdgs_scene *s, float *stage_ms, uint64_t *blend_counts) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   CK(cudaDeviceSynchronize());
   if (stage_ms) {
@@ -715,9 +1060,9 @@ int fdgs_profile_read(fdgs_scene *s, float *stage_ms, uint64_t *blend_evals) {
     for (int i = 0; i < FDGS_PROFILE_STAGES; ++i)
       CK(cudaEventElapsedTime(&stage_ms[i], s->ev[i], s->ev[i + 1]));
   }
-  if (blend_evals) {
-    *blend_evals = 0;
-    if (s->evals.p) CK(cudaMemcpy(blend_evals, s->evals.p, 8, cudaMemcpyDeviceToHost));
+  if (blend_counts) {
+    blend_counts[0] = blend_counts[1] = 0;
+    if (s->evals.p) CK(cudaMemcpy(blend_counts, s->evals.p, 16, cudaMemcpyDeviceToHost));
   }
   return FDGS_OK;
 }

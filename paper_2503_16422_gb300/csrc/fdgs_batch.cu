@@ -1,0 +1,436 @@
+// Batched rendering of many (camera, t, resolution) requests in one device-driven pipeline
+// that is captured once in a CUDA graph and replayed:
+//   k_pre_batch      per-Gaussian stage over all (request, partition) items, compaction of
+//                    each request's visible Gaussians with a per-request chained scan
+//   k_batch_bases    per-request visible counts -> contiguous bases and 256-aligned slots
+//   k_seg_compact    request segments -> one contiguous array of (request, depth, id) keys
+//   radix_sort       one global depth sort (request bits on top keep requests apart)
+//   k_gather_batch   blend-ready records per slot, key offsets, coverage difference arrays
+//                    and row/column bitmasks per request
+//   k_tile_scan_batch  per-request tile ranges (capacity-checked) and longest-first queue keys
+//   k_lists_batch    per-tile lists from the bitmasks, for every request's tiles
+//   radix_sort       queue keys by list length (descending)
+//   k_blend_persist  persistent CTAs take tiles from the queue, longest first, and record
+//                    each request's completion time (%globaltimer)
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fdgs_blend.cuh"
+#include "fdgs_gauss.cuh"
+#include "fdgs_internal.h"
+
+namespace fdgs {
+
+namespace {
+
+constexpr int kB = 256;
+constexpr int kW = kB / 32;
+constexpr int kMaxReq = 128;
+constexpr int kIdBits = 25;                  // Gaussian id bits of the depth key
+constexpr uint64_t kIdMask = (1ull << kIdBits) - 1;
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Index of the last base <= x in an ascending array of n bases (n >= 1).
+__device__ __forceinline__ int find_segment(const uint32_t *bases, int n, uint32_t x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int m = (lo + hi + 1) >> 1;
+    if (bases[m] <= x) lo = m; else hi = m - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
+  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_wcnt[kW];
+  __shared__ uint64_t s_base;
+  const uint32_t P = (b.n + kB - 1) / kB;
+  const uint32_t items = P * b.nreq;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(&b.ctr[BC_PRE_ITEM], 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= items) break;
+    const uint32_t r = item / P, part = item % P;
+    const ReqDesc &q = b.reqs[r];
+    const uint32_t i = part * kB + tid;
+    bool active = false, vis = false;
+    uint64_t key = 0;
+    if (i < b.n) {
+      active = true;
+      if (q.mask_l) {
+        const uint32_t w = __ldg(&q.mask_l[i >> 5]) | __ldg(&q.mask_r[i >> 5]);
+        active = (w >> (i & 31)) & 1u;
+      }
+      if (active) {
+        GaussState g;
+        const uint8_t fl = gauss_forward(q.cam, q.t, __ldg(&b.mean4[i]), __ldg(&b.ls4[i]),
+                                         __ldg(&b.ql[i]), __ldg(&b.qr[i]),
+                                         __ldg(&b.opacity[i]), g);
+        if (fl & kFlagDet) {
+          const float half = 0.5f * (g.c00 - g.c11);
+          const float disc = half * half + g.c01 * g.c01;
+          const float mid = 0.5f * (g.c00 + g.c11);
+          const float lam = mid + sqrtf(fmaxf(kRadiusFloor, disc));
+          const float rad = ceilf(3.f * sqrtf(lam));
+          const float u = fmaf(q.cam.fx, g.xr, q.cam.cx);
+          const float v = fmaf(q.cam.fy, g.yr, q.cam.cy);
+          int x0, y0, x1, y1;
+          tile_rect(u, v, rad, q.cam.gx, q.cam.gy, x0, y0, x1, y1);
+          if (x1 > x0 && y1 > y0) {
+            vis = true;
+            float rgb[3];
+            gauss_colour(q.cam, b.sh, b.deg, b.n, i, g, rgb);
+            const float idet = 1.f / g.det;
+            float4 *rp = reinterpret_cast<float4 *>(b.rec + ((size_t)r * b.n + i) * kRec);
+            rp[0] = make_float4(u, v, g.c11 * idet, -g.c01 * idet);
+            rp[1] = make_float4(g.c00 * idet, g.a, rgb[0], rgb[1]);
+            rp[2] = make_float4(rgb[2], g.xc[2], rad, (float)((x1 - x0) * (y1 - y0)));
+            key = ((uint64_t)r << 57) | ((uint64_t)__float_as_uint(g.xc[2]) << kIdBits) |
+                  (uint64_t)i;
+          }
+        }
+      }
+    }
+    const uint32_t vb = __ballot_sync(0xffffffffu, vis);
+    if (lane == 0) s_wcnt[warp] = __popc(vb);
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < kW; ++w) {
+        const uint32_t c = s_wcnt[w];
+        s_wcnt[w] = tot;
+        tot += c;
+      }
+      const uint64_t base = lookback_single(b.pre_status + (size_t)r * P, part, tot, b.err);
+      s_base = base;
+      if (part == P - 1) b.nv[r] = (uint32_t)(base + tot);
+    }
+    __syncthreads();
+    if (vis) b.vis_seg[(size_t)r * b.n + s_base + s_wcnt[warp] + __popc(vb & lanemask_lt())] = key;
+    __syncthreads();
+  }
+}
+
+// Per-request bases (one warp; nreq <= 128): contiguous visible bases and 256-aligned slots.
+__global__ void k_batch_bases(BatchDev b) {
+  const int lane = threadIdx.x;
+  uint32_t vcarry = 0, scarry = 0;
+  for (int r0 = 0; r0 < b.nreq; r0 += 32) {
+    const int r = r0 + lane;
+    const uint32_t nv = r < b.nreq ? b.nv[r] : 0u;
+    const uint32_t ns = (nv + kB - 1) / kB * kB;
+    const uint32_t vi = warp_incl_scan(nv), si = warp_incl_scan(ns);
+    if (r < b.nreq) {
+      b.vis_base[r] = vcarry + vi - nv;
+      b.slot_base[r] = scarry + si - ns;
+    }
+    vcarry += __shfl_sync(0xffffffffu, vi, 31);
+    scarry += __shfl_sync(0xffffffffu, si, 31);
+  }
+  if (lane == 0) {
+    b.ctr[BC_NVIS] = vcarry;
+    b.ctr[BC_NSLOTS] = scarry;
+    b.ctr[BC_NTILES] = b.ntiles;
+  }
+}
+
+__global__ void k_seg_compact(BatchDev b) {
+  const uint64_t total = (uint64_t)b.nreq * b.n;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = (uint32_t)(k / b.n), i = (uint32_t)(k % b.n);
+    if (i < b.nv[r]) b.vis[b.vis_base[r] + i] = b.vis_seg[k];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kB) k_gather_batch(BatchDev b) {
+  __shared__ uint32_t s_part;
+  __shared__ uint32_t s_wtot[kW];
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_slot_base[kMaxReq];
+  for (int r = threadIdx.x; r < b.nreq; r += kB) s_slot_base[r] = b.slot_base[r];
+  __syncthreads();
+  const uint32_t nslots = b.ctr[BC_NSLOTS];
+  const uint32_t nparts = nslots / kB;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (;;) {
+    if (tid == 0) s_part = atomicAdd(&b.ctr[BC_GATHER_PART], 1u);
+    __syncthreads();
+    const uint32_t part = s_part;
+    if (part >= nparts) break;
+    const uint32_t s = part * kB + tid;
+    const int r = find_segment(s_slot_base, b.nreq, part * kB);   // one request per partition
+    const ReqDesc &q = b.reqs[r];
+    const uint32_t l = s - s_slot_base[r];
+    const bool valid = l < b.nv[r];
+    uint32_t cnt = 0;
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    if (valid) {
+      const uint64_t key = b.vis_sorted[b.vis_base[r] + l];
+      const uint32_t id = (uint32_t)(key & kIdMask);
+      const float4 *src = reinterpret_cast<const float4 *>(b.rec + ((size_t)r * b.n + id) * kRec);
+      float4 *dst = reinterpret_cast<float4 *>(b.rec_sorted + (size_t)s * kRecS);
+      const float4 a0 = src[0], a1 = src[1], a2 = src[2];
+      const float qa = -0.5f * kLog2e * a0.z, qb = -kLog2e * a0.w, qc = -0.5f * kLog2e * a1.x;
+      dst[0] = make_float4(a0.x, a0.y, qa, qb);
+      dst[1] = make_float4(qc, log2f(a1.y), a1.z, a1.w);
+      dst[2] = make_float4(a2.x, -qb / (2.f * qa), -qb / (2.f * qc), a2.z);
+      dst[3] = make_float4(a0.z, a0.w, a1.x, a1.y);
+      cnt = (uint32_t)a2.w;
+      tile_rect(a0.x, a0.y, a2.z, q.cam.gx, q.cam.gy, x0, y0, x1, y1);
+      int *diff = b.diff + q.diff_base;
+      const int W1 = q.cam.gx + 1;
+      atomicAdd(&diff[y0 * W1 + x0], 1);
+      atomicAdd(&diff[y0 * W1 + x1], -1);
+      atomicAdd(&diff[y1 * W1 + x0], -1);
+      atomicAdd(&diff[y1 * W1 + x1], 1);
+    }
+    // coverage bitmasks of the request; the warp owns local word l / 32
+    {
+      uint32_t *rows = b.masks + q.mask_base;
+      uint32_t *cols = rows + (size_t)q.cam.gy * b.mask_words;
+      const uint32_t word = l >> 5;
+      for (int y = 0; y < q.cam.gy; ++y) {
+        const uint32_t bb = __ballot_sync(0xffffffffu, y >= y0 && y < y1);
+        if (lane == (y & 31)) rows[(size_t)y * b.mask_words + word] = bb;
+      }
+      for (int x = 0; x < q.cam.gx; ++x) {
+        const uint32_t bb = __ballot_sync(0xffffffffu, x >= x0 && x < x1);
+        if (lane == (x & 31)) cols[(size_t)x * b.mask_words + word] = bb;
+      }
+    }
+    const uint32_t inc = warp_incl_scan(cnt);
+    if (lane == 31) s_wtot[warp] = inc;
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < kW; ++w) {
+        const uint32_t c = s_wtot[w];
+        s_wtot[w] = tot;
+        tot += c;
+      }
+      const uint64_t base = lookback_single(b.scan_status, part, tot, b.err);
+      s_base = base;
+      if (part == nparts - 1) {
+        b.ctr[BC_NKEYS_LO] = (uint32_t)(base + tot);
+        b.ctr[BC_NKEYS_HI] = (uint32_t)((base + tot) >> 32);
+      }
+    }
+    __syncthreads();
+    if (l == 0 && valid) b.key_base[r] = s_base;   // first slot of the request
+    __syncthreads();
+  }
+}
+
+// One CTA per request: coverage counts -> global tile ranges (or empty ranges if the lists
+// would overflow the capacity) and the longest-first queue keys.
+constexpr int kTS = 1024;
+__global__ void __launch_bounds__(kTS) k_tile_scan_batch(BatchDev b) {
+  __shared__ uint32_t s_wsum[kTS / 32];
+  __shared__ uint32_t s_carry;
+  const int r = blockIdx.x;
+  const ReqDesc &q = b.reqs[r];
+  const int gx = q.cam.gx, gy = q.cam.gy, W1 = gx + 1;
+  int *diff = b.diff + q.diff_base;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int y = warp; y < gy; y += kTS / 32) {
+    int carry = 0;
+    for (int x0 = 0; x0 < gx; x0 += 32) {
+      const int x = x0 + lane;
+      int v = x < gx ? diff[y * W1 + x] : 0;
+      v = warp_incl_scan(v) + carry;
+      if (x < gx) diff[y * W1 + x] = v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+  __syncthreads();
+  for (int x = tid; x < gx; x += kTS) {
+    int acc = 0;
+    for (int y = 0; y < gy; ++y) {
+      acc += diff[y * W1 + x];
+      diff[y * W1 + x] = acc;
+    }
+  }
+  __syncthreads();
+  const uint64_t base = b.nv[r] ? b.key_base[r] : 0;
+  const uint64_t nkeys = (uint64_t)b.ctr[BC_NKEYS_LO] | ((uint64_t)b.ctr[BC_NKEYS_HI] << 32);
+  const bool overflow = nkeys > b.key_cap;
+  if (overflow && tid == 0) atomicOr(b.err, kErrCapacity);
+  const uint32_t tiles = (uint32_t)gx * gy;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t t0 = 0; t0 < tiles; t0 += kTS) {
+    const uint32_t t = t0 + tid;
+    uint32_t c = 0;
+    if (t < tiles) c = (uint32_t)diff[(t / gx) * W1 + (t % gx)];
+    const uint32_t inc = warp_incl_scan(c);
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = s_wsum[lane];
+      const uint32_t wi = warp_incl_scan(w);
+      s_wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    const uint32_t start = s_carry + s_wsum[warp] + inc - c;
+    if (t < tiles) {
+      const uint32_t gt = q.tile_base + t;
+      const uint32_t st = (uint32_t)(base + start);
+      b.ranges[gt] = overflow ? make_uint2(0, 0) : make_uint2(st, st + c);
+      const uint32_t len = overflow ? 0u : min(c, 0xFFFFFFu);
+      b.qkeys[gt] = ((uint64_t)(0xFFFFFFu - len) << 32) | gt;
+    }
+    __syncthreads();
+    if (tid == kTS - 1) s_carry = start + c;
+    __syncthreads();
+  }
+}
+
+// Per-tile lists of slot indices from the request's bitmasks (warp per global tile).
+__global__ void __launch_bounds__(kB) k_lists_batch(BatchDev b) {
+  __shared__ uint32_t s_tile_base[kMaxReq];
+  for (int r = threadIdx.x; r < b.nreq; r += kB) s_tile_base[r] = b.reqs[r].tile_base;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (uint32_t gt = blockIdx.x * kW + warp; gt < b.ntiles; gt += gridDim.x * kW) {
+    const int r = find_segment(s_tile_base, b.nreq, gt);
+    const ReqDesc &q = b.reqs[r];
+    const uint32_t t = gt - q.tile_base;
+    const uint2 rg = b.ranges[gt];
+    if (rg.y == rg.x) continue;
+    const uint32_t words = (b.nv[r] + 31) / 32;
+    const uint32_t *rows = b.masks + q.mask_base + (size_t)(t / q.cam.gx) * b.mask_words;
+    const uint32_t *cols = b.masks + q.mask_base + (size_t)q.cam.gy * b.mask_words +
+                           (size_t)(t % q.cam.gx) * b.mask_words;
+    const uint32_t sb = b.slot_base[r];
+    uint32_t off = rg.x;
+    uint32_t nr0 = lane < words ? __ldg(&rows[lane]) : 0u;
+    uint32_t nc0 = lane < words ? __ldg(&cols[lane]) : 0u;
+    uint32_t nr1 = lane + 32 < words ? __ldg(&rows[lane + 32]) : 0u;
+    uint32_t nc1 = lane + 32 < words ? __ldg(&cols[lane + 32]) : 0u;
+    for (uint32_t c0 = 0; c0 < words; c0 += 32) {
+      const uint32_t c = c0 + lane;
+      uint32_t m = nr0 & nc0;
+      nr0 = nr1;
+      nc0 = nc1;
+      nr1 = c + 64 < words ? __ldg(&rows[c + 64]) : 0u;
+      nc1 = c + 64 < words ? __ldg(&cols[c + 64]) : 0u;
+      const uint32_t pc = __popc(m);
+      const uint32_t inc = warp_incl_scan(pc);
+      uint32_t o = off + inc - pc;
+      while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        b.lists[o++] = sb + c * 32 + bit;
+      }
+      off += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
+// Persistent blend over the longest-first queue of all requests' tiles.
+template <int FW>
+__global__ void __launch_bounds__(kBlendThreads) k_blend_persist(BatchDev b) {
+  __shared__ BlendSmem sm;
+  __shared__ uint32_t s_q;
+  __shared__ uint32_t s_tile_base[kMaxReq];
+  for (int r = threadIdx.x; r < b.nreq; r += kBlendThreads) s_tile_base[r] = b.reqs[r].tile_base;
+  for (;;) {
+    if (threadIdx.x == 0) s_q = atomicAdd(&b.ctr[BC_QUEUE], 1u);
+    __syncthreads();
+    const uint32_t qi = s_q;
+    if (qi >= b.ntiles) break;
+    const uint32_t gt = (uint32_t)b.queue[qi];
+    const int r = find_segment(s_tile_base, b.nreq, gt);
+    const ReqDesc &q = b.reqs[r];
+    const uint32_t t = gt - q.tile_base;
+    BlendTile bt;
+    bt.tx = t % q.cam.gx;
+    bt.ty = t / q.cam.gx;
+    bt.W = q.cam.W;
+    bt.H = q.cam.H;
+    bt.range = b.ranges[gt];
+    bt.rec_sorted = b.rec_sorted;
+    bt.rgb = q.rgb;
+    bt.T_final = b.T_final + q.pix_base;
+    bt.n_contrib = b.n_contrib + q.pix_base;
+    bt.bg0 = q.bg[0];
+    bt.bg1 = q.bg[1];
+    bt.bg2 = q.bg[2];
+    bt.w_sum = nullptr;
+    bt.evals = nullptr;
+    blend_tile<uint32_t, FW, false, false>(bt, b.lists, 0xFFFFFFFFu, sm);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(&b.done_ns[r], (unsigned long long)global_timer_ns());
+  }
+}
+
+__global__ void k_batch_start(BatchDev b) {
+  if (threadIdx.x == 0) *b.t0_ns = global_timer_ns();
+}
+
+int grid_of(const void *kernel, int threads, int per_sm_cap) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  per_sm = std::max(1, std::min(per_sm, per_sm_cap));
+  return per_sm * num_sms();
+}
+
+}  // namespace
+
+// Enqueues the whole batch on `st` (capturable: no host synchronisation, grid sizes depend
+// only on the plan). The caller zeroes nothing: the memsets are part of the sequence.
+void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
+  cudaMemsetAsync(b.ctr, 0, BC_COUNT * sizeof(uint32_t), st);
+  cudaMemsetAsync(b.pre_status, 0, L.pre_status_bytes, st);
+  cudaMemsetAsync(b.scan_status, 0, L.scan_status_bytes, st);
+  cudaMemsetAsync(b.diff, 0, L.diff_bytes, st);
+  cudaMemsetAsync(b.done_ns, 0, b.nreq * sizeof(unsigned long long), st);
+  k_batch_start<<<1, 32, 0, st>>>(b);
+  static int g_pre = 0, g_gather = 0;
+  if (!g_pre) g_pre = grid_of((const void *)k_pre_batch, kB, 64);
+  if (!g_gather) g_gather = grid_of((const void *)k_gather_batch, kB, 64);
+  const uint64_t pre_items = (uint64_t)((b.n + kB - 1) / kB) * b.nreq;
+  k_pre_batch<<<(int)std::min<uint64_t>(pre_items, g_pre), kB, 0, st>>>(b);
+  k_batch_bases<<<1, 32, 0, st>>>(b);
+  const uint64_t rn = (uint64_t)b.nreq * b.n;
+  k_seg_compact<<<(int)std::min<uint64_t>((rn + kB - 1) / kB, (uint64_t)num_sms() * 16), kB, 0,
+                  st>>>(b);
+  uint64_t *srt = radix_sort<uint64_t>(b.vis, b.vis_alt, b.ctr + BC_NVIS, rn, kIdBits,
+                                       64 - kIdBits, L.sort_scratch, st, b.err);
+  BatchDev b2 = b;
+  b2.vis_sorted = srt;
+  const uint64_t slot_parts = (rn + (uint64_t)b.nreq * kB) / kB;
+  k_gather_batch<<<(int)std::min<uint64_t>(slot_parts, g_gather), kB, 0, st>>>(b2);
+  k_tile_scan_batch<<<b.nreq, kTS, 0, st>>>(b2);
+  k_lists_batch<<<(int)std::min<uint64_t>((b.ntiles + kW - 1) / kW, (uint64_t)num_sms() * 8),
+                  kB, 0, st>>>(b2);
+  uint64_t *qs = radix_sort<uint64_t>(b.qkeys, b.qkeys_alt, b.ctr + BC_NTILES, b.ntiles, 32, 24,
+                                      L.sort_scratch, st, b.err);
+  b2.queue = qs;
+  const int grid = L.blend_ctas_per_sm * num_sms();
+  switch (L.footprint) {
+    case 0: k_blend_persist<16><<<grid, kBlendThreads, 0, st>>>(b2); break;
+    case 2: k_blend_persist<4><<<grid, kBlendThreads, 0, st>>>(b2); break;
+    default: k_blend_persist<8><<<grid, kBlendThreads, 0, st>>>(b2); break;
+  }
+}
+
+int batch_blend_max_ctas_per_sm() {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_persist<8>, kBlendThreads, 0);
+  return std::max(1, per_sm);
+}
+
+}  // namespace fdgs

@@ -61,7 +61,7 @@ struct BlendTile {
   uint32_t *n_contrib;         // [H][W]
   float bg0, bg1, bg2;
   float *w_sum;                // per-rank weights (score pass) or null
-  unsigned long long *evals;   // evaluation counter (profiling) or null
+  unsigned long long *evals;   // [2] evaluations, culling tests (profiling) or null
 };
 
 template <typename K, int FW, bool kWeights, bool kCount>
@@ -81,7 +81,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
   const bool inside = px < bt.W && py < bt.H;
   const float fpx = (float)px, fpy = (float)py;
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0, nevals = 0;
+  uint32_t last = 0, nevals = 0, ntests = 0;
   bool done = !inside;
   bool warp_done = __all_sync(0xffffffffu, done);
 
@@ -123,6 +123,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     const uint32_t pos0 = (uint32_t)b * kBlendBatch;
     // 1. tile-level test of the thread's own staged Gaussian, block compaction
     bool keep = false;
+    if (kCount && tid < cnt) ++ntests;
     if (tid < cnt) {
       const float4 g0 = sm.g0[st][tid];
       const float2 g1 = *reinterpret_cast<const float2 *>(&sm.g1[st][tid]);
@@ -148,6 +149,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     // 2. warp footprint tests on the survivors, evaluation of the hits
     for (int c0 = 0; c0 < ncomp && !warp_done; c0 += 32) {
       bool hit = false;
+      if (kCount && c0 + lane < ncomp) ++ntests;
       if (c0 + lane < ncomp) {
         const int j = sm.idx[c0 + lane];
         const float4 g0 = sm.g0[st][j];
@@ -194,8 +196,9 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     }
   }
   if (kCount) {
-    const uint32_t ws = warp_sum(nevals);
-    if (lane == 0 && ws) atomicAdd(bt.evals, (unsigned long long)ws);
+    const uint32_t ws = warp_sum(nevals), wt = warp_sum(ntests);
+    if (lane == 0 && ws) atomicAdd(&bt.evals[0], (unsigned long long)ws);
+    if (lane == 0 && wt) atomicAdd(&bt.evals[1], (unsigned long long)wt);
   }
   if (inside) {
     const size_t hw = (size_t)bt.W * bt.H;

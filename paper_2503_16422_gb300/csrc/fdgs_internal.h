@@ -123,6 +123,58 @@ void launch_score_keys(const float *score, uint32_t n, uint64_t *keys, cudaStrea
 void launch_keep_from_sorted(const uint64_t *sorted, uint32_t n, uint32_t n_drop,
                              uint8_t *keep, cudaStream_t st);
 
+// ---- batched rendering (fdgs_batch.cu) -------------------------------------------------
+// One request of a batch, as the kernels read it (uploaded once per batch).
+struct ReqDesc {
+  DevCam cam;
+  float t;
+  const uint32_t *mask_l, *mask_r;   // null = unmasked
+  float bg[3];
+  float *rgb;                        // [3][H][W]
+  uint32_t tile_base;                // first global tile id of the request
+  uint32_t diff_base;                // offset of its coverage difference array (ints)
+  uint64_t pix_base;                 // offset of its pixels in T_final / n_contrib
+  uint64_t mask_base;                // offset of its row and column bitmasks (words)
+};
+enum BatchCounter {
+  BC_PRE_ITEM = 0, BC_NVIS = 1, BC_NSLOTS = 2, BC_NTILES = 3, BC_GATHER_PART = 4,
+  BC_NKEYS_LO = 5, BC_NKEYS_HI = 6, BC_QUEUE = 7, BC_COUNT = 16
+};
+struct BatchDev {
+  const ReqDesc *reqs;
+  int nreq;
+  uint32_t n, ntiles, mask_words;
+  uint64_t key_cap;
+  const float4 *mean4, *ls4, *ql, *qr;
+  const float *opacity, *sh;
+  int deg;
+  uint32_t *ctr, *err;
+  uint64_t *pre_status, *scan_status;
+  float *rec;                        // [nreq][n][12] by Gaussian id
+  uint64_t *vis_seg, *vis, *vis_alt; // visible keys: per-request segments, contiguous, alt
+  const uint64_t *vis_sorted;
+  uint32_t *nv, *vis_base, *slot_base;
+  uint64_t *key_base;
+  float *rec_sorted;                 // [slots][16] blend-ready
+  int *diff;
+  uint32_t *masks;
+  uint2 *ranges;                     // [ntiles]
+  uint64_t *qkeys, *qkeys_alt;
+  const uint64_t *queue;
+  uint32_t *lists;                   // [key_cap] slot indices
+  float *T_final;
+  uint32_t *n_contrib;
+  unsigned long long *done_ns, *t0_ns;
+};
+struct BatchLaunch {
+  size_t pre_status_bytes, scan_status_bytes, diff_bytes;
+  void *sort_scratch;
+  int footprint;                     // warp footprint of the blend (0, 1, 2)
+  int blend_ctas_per_sm;             // persistent blend grid = this x SMs
+};
+void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st);
+int batch_blend_max_ctas_per_sm();
+
 int num_sms();
 extern int g_blend_shape;   // warp footprint of the forward blend: 0 16x2, 1 8x4, 2 4x8
 

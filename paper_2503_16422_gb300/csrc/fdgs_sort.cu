@@ -19,6 +19,7 @@ constexpr int kSortWarps = kSortBlock / 32;
 constexpr int kRadix = 256;
 constexpr int kItems = 16;
 constexpr int kTileKeys = kSortBlock * kItems;   // keys per partition
+constexpr int kMaxPasses = 8;                    // digit passes supported (64 bits)
 
 // Per-digit status word of the onesweep look-back: 2-bit flag | 30-bit count.
 constexpr uint32_t kStAgg = 1u << 30, kStPrefix = 2u << 30, kStValue = (1u << 30) - 1;
@@ -27,7 +28,7 @@ template <typename K>
 __global__ void __launch_bounds__(kSortBlock)
 k_histogram(const K *__restrict__ keys, const uint32_t *__restrict__ n_dev, int lo, int dbits,
             int npass, uint32_t *__restrict__ hist) {
-  __shared__ uint32_t sh[4 * kRadix];
+  __shared__ uint32_t sh[kMaxPasses * kRadix];
   for (int i = threadIdx.x; i < npass * kRadix; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const uint32_t n = *n_dev;
@@ -195,7 +196,7 @@ int sort_digit_bits(int bits) {
 size_t sort_scratch_bytes(uint64_t n_cap, int bits) {
   const int np = std::max(1, sort_passes(bits));
   // hist [4][256] + part counters [4] (padded) + one status region per pass
-  return 4 * kRadix * sizeof(uint32_t) + 256 + np * status_bytes(n_cap);
+  return kMaxPasses * kRadix * sizeof(uint32_t) + 256 + np * status_bytes(n_cap);
 }
 
 template <typename K>
@@ -203,12 +204,13 @@ K *radix_sort(K *a, K *b, const uint32_t *n_dev, uint64_t n_cap, int lo, int bit
               void *scratch, cudaStream_t st, uint32_t *err_dev, bool hist_ready) {
   const int np = sort_passes(bits);
   if (np == 0 || n_cap == 0) return a;
+  if (np > kMaxPasses) return a;   // wider than 64 bits: the histogram holds 8 passes
   const int dbits = (bits + np - 1) / np;
   uint32_t *hist = (uint32_t *)scratch;
-  uint32_t *ctr = hist + 4 * kRadix;
-  uint8_t *status0 = (uint8_t *)scratch + 4 * kRadix * sizeof(uint32_t) + 256;
+  uint32_t *ctr = hist + kMaxPasses * kRadix;
+  uint8_t *status0 = (uint8_t *)scratch + kMaxPasses * kRadix * sizeof(uint32_t) + 256;
   const size_t sb = status_bytes(n_cap);
-  const size_t hist_bytes = 4 * kRadix * sizeof(uint32_t);
+  const size_t hist_bytes = kMaxPasses * kRadix * sizeof(uint32_t);
   if (hist_ready) {
     cudaMemsetAsync((uint8_t *)scratch + hist_bytes, 0,
                     sort_scratch_bytes(n_cap, bits) - hist_bytes, st);

@@ -75,6 +75,11 @@ _SIGNATURES = {
     "fdgs_profile_enable": [_P, ctypes.c_int],
     "fdgs_set_blend_shape": [ctypes.c_int],
     "fdgs_set_list_builder": [ctypes.c_int],
+    "fdgs_batch_autotune": [_P, ctypes.POINTER(fdgs_camera), ctypes.POINTER(ctypes.c_float),
+                            ctypes.c_int, ctypes.POINTER(fdgs_render_opts), ctypes.POINTER(_P),
+                            _P],
+    "fdgs_batch_info": [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
 }
 PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "tile_scan", "emit",
@@ -311,6 +316,26 @@ class Scene:
                                       _stream(stream)))
         return outs
 
+    def batch_autotune(self, cams, ts, use_mask=True, bg=(0.0, 0.0, 0.0), outs=None,
+                       stream=None):
+        n = len(cams)
+        carr = (fdgs_camera * max(n, 1))(*[make_camera(c) for c in cams])
+        tarr = (ctypes.c_float * max(n, 1))(*[float(t) for t in ts])
+        if outs is None:
+            outs = [torch.empty((3, int(c.height), int(c.width)), dtype=torch.float32,
+                                device=self.device) for c in cams]
+        parr = (ctypes.c_void_p * max(n, 1))(*[o.data_ptr() for o in outs])
+        o = _opts(use_mask, bg)
+        check(lib().fdgs_batch_autotune(self.handle, carr, tarr, n, ctypes.byref(o), parr,
+                                        _stream(stream)))
+        return outs
+
+    def batch_info(self, n):
+        lat = (ctypes.c_float * max(n, 1))()
+        fp, ctas = ctypes.c_int(), ctypes.c_int()
+        check(lib().fdgs_batch_info(self.handle, lat, n, ctypes.byref(fp), ctypes.byref(ctas)))
+        return dict(latency_ms=list(lat)[:n], footprint=fp.value, ctas_per_sm=ctas.value)
+
     def variation_score(self, cams, ts, batch=8, out=None, stream=None):
         carr = (fdgs_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
         tarr = (ctypes.c_float * max(len(ts), 1))(*[float(t) for t in ts])
@@ -333,13 +358,9 @@ class Scene:
 
     def profile_read(self):
         ms = (ctypes.c_float * len(PROFILE_STAGES))()
-        ev = ctypes.c_uint64()
-        check(lib().fdgs_profile_read(self.handle, ms if self._prof_stages() else None,
-                                      ctypes.byref(ev)))
-        return dict(zip(PROFILE_STAGES, list(ms))), int(ev.value)
-
-    def _prof_stages(self):
-        return True
+        ev = (ctypes.c_uint64 * 2)()
+        check(lib().fdgs_profile_read(self.handle, ms, ev))
+        return dict(zip(PROFILE_STAGES, list(ms))), int(ev[0]), int(ev[1])
 
     def status_sync(self):
         check(lib().fdgs_status_sync(self.handle))
