@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the comparison workloads")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default batch launch shape (for profiling runs)")
     return ap.parse_args()
 
 
@@ -245,7 +247,7 @@ def roofline(stage_ms, counts, bytes_mean):
             "frac": ach / pk["hbm"], "traffic": None, "peak_src": pk["src"] + " copy GB/s"}
 
 
-def timed_batches(sc, cams_list, ts_list, outs_list, masked, flush, stream):
+def timed_batches(sc, cams_list, ts_list, outs_list, masked, flush, stream, stages=None):
     import torch
     ms = []
     lat = []
@@ -258,8 +260,25 @@ def timed_batches(sc, cams_list, ts_list, outs_list, masked, flush, stream):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
-        lat += sc.batch_info(len(cams))["latency_ms"]
+        info = sc.batch_info(len(cams))
+        lat += info["latency_ms"]
+        if stages is not None:
+            stages.append(info["stage_ms"])
     return ms, lat
+
+
+def batch_counts(sc, cams_list, ts_list, outs):
+    """Blend evaluations and culling tests of the given batches (counting profile: eager
+    runs with the counting blend variant; untimed)."""
+    sc.profile(2)
+    ev = te = 0
+    for cams, ts in zip(cams_list, ts_list):
+        sc.render_batch(cams, ts, outs=outs)
+        _, e, t = sc.profile_read()
+        ev += e
+        te += t
+    sc.profile(0)
+    return ev, te
 
 
 def run_ours(args):
@@ -291,7 +310,10 @@ def run_ours(args):
 
     # autotune the batch launch shape once (untimed), then warm up (graph replays)
     c0, t0 = batch_args(0, 5000 + rank)
-    sc.batch_autotune(c0, t0, outs=outs)
+    if args.no_autotune:
+        sc.render_batch(c0, t0, outs=outs)
+    else:
+        sc.batch_autotune(c0, t0, outs=outs)
     shape = sc.batch_info(B)
     for w in range(args.warmup):
         c_, t_ = batch_args(w, 6000 + rank)
@@ -303,8 +325,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    step_stages = []
     step_ms, lat = timed_batches(sc, [a for a, _ in steps], [b for _, b in steps],
-                                 [outs] * len(steps), True, flush, stream)
+                                 [outs] * len(steps), True, flush, stream, step_stages)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -335,13 +358,29 @@ def run_ours(args):
                       d2h_bytes_per_step=B * 3 * H_FULL * W_FULL * 4)
 
     if rank == 0:
+        # batch stages: CUDA events recorded inside the replayed graph, every timed step
+        bst = {k: float(np.mean([s_[k] for s_ in step_stages])) for k in step_stages[0]}
+        ev, te = batch_counts(sc, [a for a, _ in steps], [b for _, b in steps], outs)
+        blend_s = sum(s_["blend"] for s_ in step_stages) / 1e3
+        pk = peaks()
+        ach = (ev * EVAL_FLOP + te * TEST_FLOP) / blend_s / 1e12
+        peak = fp32_peak_tflops(pk["sm_mhz"])
+        res["roofline"] = {
+            "bound": "alu", "kernel": "k_blend_persist", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_mhz']:.0f} MHz",
+            "work": "executed (Gaussian, pixel) evaluations x 20 FLOP + culling tests x 36 FLOP,"
+                    " counted on the same batches; time = in-graph %globaltimer stage stamps, timed steps",
+            "blend_ms_per_batch": blend_s * 1e3 / len(steps),
+            "evals_per_frame": ev / frames_done, "tests_per_frame": te / frames_done}
+        res["batch_stages_ms"] = bst
         # per-kernel profile on single renders of the same frames
         out1 = outs[0]
         fr_prof = frame_list(24, 11)
         stage_ms, counts, bytes_mean = profile_single(sc, cams, times, fr_prof, True, out1,
                                                       flush, scene)
         res.update(stage_ms=stage_ms, counts=counts,
-                   roofline=roofline(stage_ms, counts, bytes_mean),
+                   single_roofline=roofline(stage_ms, counts, bytes_mean),
                    stage_gbs={s_: bytes_mean[s_] / (stage_ms[s_] / 1e3) / 1e9
                               for s_ in bytes_mean if stage_ms[s_] > 1e-4})
         if not args.no_extra:
@@ -401,6 +440,11 @@ def comparisons(sc, cams, times, flush, stream):
         sequential_p50_ms=float(np.percentile(seq_lat, 50)),
         sequential_p99_ms=float(np.percentile(seq_lat, 99)),
         shape=sc.batch_info(64))
+    # backward (fine-tuning step): L1 loss against a render of the scene with means perturbed
+    # by N(0, 0.01); render with a frame, then the reverse replay + per-Gaussian chain
+    res["backward"] = backward_timing(sc, cams, times, flush, stream)
+    # spatial-temporal variation score pass: 1M Gaussians, 50 timestamps x 4 cameras
+    res["variation_score"] = score_timing(stream)
     # unpruned 3M scene, single requests
     big = scenes.unpruned_scene()
     kt = scenes.keyframe_times()
@@ -412,6 +456,61 @@ def comparisons(sc, cams, times, flush, stream):
     del big
     torch.cuda.empty_cache()
     return res
+
+
+def backward_timing(sc, cams, times, flush, stream, n_frames=6):
+    import torch
+
+    from paper_2503_16422_gb300 import fdgs
+    p = sc.params
+    rng = np.random.default_rng(55)
+    pert = p.mean4.clone()
+    pert[:, :3] += torch.as_tensor(rng.normal(0, 0.01, (sc.n, 3)).astype(np.float32)).cuda()
+    target_scene = fdgs.Scene(fdgs.SceneTensors(pert, p.logscale4, p.q_left, p.q_right,
+                                                p.opacity_logit, p.sh, p.sh_degree))
+    grads = fdgs.SceneTensors(*[torch.zeros_like(x) for x in p.list()], p.sh_degree)
+    fwd_ms, bwd_ms = [], []
+    for k in frame_list(n_frames, 40):
+        cam, t = cams[k], float(times[k])
+        target = target_scene.render(cam, t, use_mask=False)
+        _flush(flush)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        img, fr = sc.render(cam, t, use_mask=False, keep_frame=True)
+        e1.record(stream)
+        dL = torch.sign(img - target) / img.numel()
+        e1b = torch.cuda.Event(enable_timing=True)
+        e1b.record(stream)
+        sc.render_backward(fr, dL, grads=grads)
+        e2.record(stream)
+        e2.synchronize()
+        fwd_ms.append(e0.elapsed_time(e1))
+        bwd_ms.append(e1b.elapsed_time(e2))
+        fr.release()
+    target_scene.close()
+    return dict(frames=n_frames, scene="pruned 200k, unmasked, 1352x1014",
+                forward_ms=float(np.mean(fwd_ms)), backward_ms=float(np.mean(bwd_ms)))
+
+
+def score_timing(stream):
+    import torch
+
+    from paper_2503_16422_gb300 import fdgs, scenes
+    s = scenes.stvs_scene()
+    sc = fdgs.Scene.from_host(s)
+    cams = [scenes.arc_camera(th) for th in (-10.0, -3.3, 3.3, 10.0)]
+    ts = [float(x) for x in np.linspace(0.0, 1.0, 50)]
+    sc.variation_score(cams[:1], ts[:2])            # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    score = sc.variation_score(cams, ts, batch=8)
+    keep = sc.select_keep(score, 0.8)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    kept = int(keep.sum())
+    sc.close()
+    return dict(n_gaussians=s.n, renders=len(cams) * len(ts), resolution="1352x1014",
+                wall_s=wall, ms_per_render=wall * 1e3 / (len(cams) * len(ts)), kept=kept)
 
 
 def launches_per_batch():
@@ -458,8 +557,10 @@ def main():
             "gpu_launches": launches_per_batch() * args.steps,
             "latency_ms": {"p50": float(np.percentile(lat, 50)),
                            "p99": float(np.percentile(lat, 99))},
-            "batch_shape": res["batch_shape"],
+            "batch_shape": {k: v for k, v in res["batch_shape"].items() if k != "latency_ms"},
+            "batch_stages_ms": res["batch_stages_ms"],
             "single_frame_stages_ms": res["stage_ms"], "stage_gbs": res["stage_gbs"],
+            "single_frame_roofline": res["single_roofline"],
             "counts_per_frame": res["counts"]}
     if "comparisons" in res:
         line["comparisons"] = res["comparisons"]

@@ -197,10 +197,16 @@ int fdgs_batch_autotune(fdgs_scene *scene, const fdgs_camera *cams, const float 
                         fdgs_stream stream);
 
 /* Last batch: per-request latency in ms (%globaltimer, from the start of the batch to the
- * completion of the request's last tile) for the first n requests, and the launch shape in
- * use. Any pointer may be NULL. FDGS_ERR_STATE if no batch was rendered. */
+ * completion of the request's last tile) for the first n requests, the launch shape in use,
+ * and stage_ms[FDGS_BATCH_STAGES], the durations of its stages from device timestamps
+ * (%globaltimer written in stream order between the stages inside the graph; in order:
+ * preprocess, depth_sort, gather, tile_scan, lists, queue_sort, blend).
+ * Any pointer may be NULL. FDGS_ERR_STATE if no batch was rendered. With a counting profile
+ * enabled (fdgs_profile_enable bit1) the next batch runs eagerly with the counting blend and
+ * fdgs_profile_read returns its counts. */
+#define FDGS_BATCH_STAGES 7
 int fdgs_batch_info(fdgs_scene *scene, float *latency_ms, int n, int *footprint,
-                    int *ctas_per_sm);
+                    int *ctas_per_sm, float *stage_ms);
 
 /*
  * Spatial-Temporal Variation Score (Sec. 4.2.1, Eqs. 4-7), reading "per-t product":

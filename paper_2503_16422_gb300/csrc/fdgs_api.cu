@@ -138,7 +138,12 @@ struct BatchPlan {
   int footprint = 1, ctas = 0;
   bool tuned = false;
   std::vector<float> lat_ms;
+  Buf stamps;                                  // u64[kBatchStages + 1] %globaltimer
+  unsigned long long *h_stamps = nullptr;      // pinned mirror
+  float stage_ms[kBatchStages] = {};
   ~BatchPlan() {
+    stamps.release();
+    if (h_stamps) cudaFreeHost(h_stamps);
     Buf *all[] = {&reqs, &ctr, &pre_status, &scan_status, &rec, &vis_seg, &vis, &vis_alt,
                   &nv, &vis_base, &slot_base, &key_base, &rec_sorted, &diff, &masks,
                   &ranges, &qkeys, &qkeys_alt, &lists, &Tf, &nc, &done, &t0, &scratch};
@@ -510,6 +515,8 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   CK(cudaMallocHost(&p.h_ctr, BC_COUNT * 4));
   CK(cudaMallocHost(&p.h_done, (n + 1) * 8));
   CK(cudaStreamCreateWithFlags(&p.cap, cudaStreamNonBlocking));
+  TRY(grow(p.stamps, (kBatchStages + 1) * 8));
+  CK(cudaMallocHost(&p.h_stamps, (kBatchStages + 1) * 8));
   p.ctas = std::min(4, batch_blend_max_ctas_per_sm());
   return FDGS_OK;
 }
@@ -575,6 +582,8 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.n_contrib = p.nc.as<uint32_t>();
   b.done_ns = p.done.as<unsigned long long>();
   b.t0_ns = p.t0.as<unsigned long long>();
+  b.evals = nullptr;
+  b.stamps = p.stamps.as<unsigned long long>();
   const uint64_t P = ((uint64_t)s->d.n + 255) / 256;
   L.pre_status_bytes = std::max<uint64_t>(P * p.nreq, 1) * 8;
   L.scan_status_bytes = std::max<uint64_t>(p.slot_cap / 256, 1) * 8;
@@ -610,13 +619,17 @@ int plan_capture(fdgs_scene *s, BatchPlan &p) {
 // Runs the batch (graph replay when captured, else eagerly), synchronises the stream, grows
 // the list capacity and reruns if it overflowed, records per-request latencies.
 int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
+  // a counting profile (fdgs_profile_enable bit1) runs the batch eagerly with the counting
+  // blend variant, so that fdgs_profile_read returns its evaluation and test counts
+  const bool count = (s->prof & 2) && s->evals.p;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    if (p.exec) {
+    if (p.exec && !count) {
       CK(cudaGraphLaunch(p.exec, st));
     } else {
       BatchDev b;
       BatchLaunch L;
       plan_dev(s, p, b, L);
+      if (count) b.evals = s->evals.as<unsigned long long>();
       CK(cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice,
                          st));
       launch_batch(b, L, st);
@@ -625,6 +638,8 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
     CK(cudaMemcpyAsync(p.h_ctr, p.ctr.p, BC_COUNT * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(p.h_done, p.done.p, p.nreq * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(p.h_done + p.nreq, p.t0.p, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(p.h_stamps, p.stamps.p, (kBatchStages + 1) * 8, cudaMemcpyDeviceToHost,
+                       st));
     uint32_t e = 0;
     CK(cudaMemcpyAsync(&e, s->status.p, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -641,6 +656,10 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
       if (p.exec) TRY(plan_capture(s, p));
       continue;
     }
+    for (int i = 0; i < kBatchStages; ++i)
+      p.stage_ms[i] = p.h_stamps[i + 1] > p.h_stamps[i]
+                          ? (float)((p.h_stamps[i + 1] - p.h_stamps[i]) * 1e-6)
+                          : 0.f;
     p.lat_ms.resize(p.nreq);
     const unsigned long long t0 = p.h_done[p.nreq];
     for (int i = 0; i < p.nreq; ++i)
@@ -953,10 +972,12 @@ int fdgs_batch_autotune(fdgs_scene *s, const fdgs_camera *cams, const float *ts,
 }
 
 int fdgs_batch_info(fdgs_scene *s, float *latency_ms, int n, int *footprint,
-                    int *ctas_per_sm) {
+                    int *ctas_per_sm, float *stage_ms) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   if (!s->plan) return fail(FDGS_ERR_STATE, "no batch has been rendered");
   BatchPlan &p = *s->plan;
+  if (stage_ms)
+    for (int i = 0; i < kBatchStages; ++i) stage_ms[i] = p.stage_ms[i];
   if (latency_ms)
     for (int i = 0; i < std::min(n, (int)p.lat_ms.size()); ++i) latency_ms[i] = p.lat_ms[i];
   if (footprint) *footprint = p.footprint;
@@ -1056,9 +1077,10 @@ int fdgs_profile_read(fdgs_scene *s, float *stage_ms, uint64_t *blend_counts) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   CK(cudaDeviceSynchronize());
   if (stage_ms) {
-    if (!s->ev[0]) return fail(FDGS_ERR_STATE, "stage profiling was never enabled");
-    for (int i = 0; i < FDGS_PROFILE_STAGES; ++i)
-      CK(cudaEventElapsedTime(&stage_ms[i], s->ev[i], s->ev[i + 1]));
+    for (int i = 0; i < FDGS_PROFILE_STAGES; ++i) {
+      stage_ms[i] = 0.f;   // zeros when stage profiling was never enabled
+      if (s->ev[0]) CK(cudaEventElapsedTime(&stage_ms[i], s->ev[i], s->ev[i + 1]));
+    }
   }
   if (blend_counts) {
     blend_counts[0] = blend_counts[1] = 0;

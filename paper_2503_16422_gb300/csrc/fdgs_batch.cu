@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kB) k_lists_batch(BatchDev b) {
 }
 
 // Persistent blend over the longest-first queue of all requests' tiles.
-template <int FW>
+template <int FW, bool kCount>
 __global__ void __launch_bounds__(kBlendThreads) k_blend_persist(BatchDev b) {
   __shared__ BlendSmem sm;
   __shared__ uint32_t s_q;
@@ -369,8 +369,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_persist(BatchDev b) {
     bt.bg1 = q.bg[1];
     bt.bg2 = q.bg[2];
     bt.w_sum = nullptr;
-    bt.evals = nullptr;
-    blend_tile<uint32_t, FW, false, false>(bt, b.lists, 0xFFFFFFFFu, sm);
+    bt.evals = b.evals;
+    blend_tile<uint32_t, FW, false, kCount>(bt, b.lists, 0xFFFFFFFFu, sm);
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(&b.done_ns[r], (unsigned long long)global_timer_ns());
   }
@@ -379,6 +379,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_persist(BatchDev b) {
 __global__ void k_batch_start(BatchDev b) {
   if (threadIdx.x == 0) *b.t0_ns = global_timer_ns();
 }
+
+__global__ void k_stamp(unsigned long long *stamps, int i) { stamps[i] = global_timer_ns(); }
 
 int grid_of(const void *kernel, int threads, int per_sm_cap) {
   int per_sm = 0;
@@ -397,39 +399,60 @@ void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
   cudaMemsetAsync(b.scan_status, 0, L.scan_status_bytes, st);
   cudaMemsetAsync(b.diff, 0, L.diff_bytes, st);
   cudaMemsetAsync(b.done_ns, 0, b.nreq * sizeof(unsigned long long), st);
+  if (b.evals) cudaMemsetAsync(b.evals, 0, 2 * sizeof(unsigned long long), st);
+  // stage boundaries: a one-thread kernel stamps %globaltimer (events recorded inside a
+  // captured graph cannot be timed); stream order makes each difference a stage duration
+  auto mark = [&](int i) { k_stamp<<<1, 1, 0, st>>>(b.stamps, i); };
   k_batch_start<<<1, 32, 0, st>>>(b);
+  mark(0);
   static int g_pre = 0, g_gather = 0;
   if (!g_pre) g_pre = grid_of((const void *)k_pre_batch, kB, 64);
   if (!g_gather) g_gather = grid_of((const void *)k_gather_batch, kB, 64);
   const uint64_t pre_items = (uint64_t)((b.n + kB - 1) / kB) * b.nreq;
   k_pre_batch<<<(int)std::min<uint64_t>(pre_items, g_pre), kB, 0, st>>>(b);
+  mark(1);
   k_batch_bases<<<1, 32, 0, st>>>(b);
   const uint64_t rn = (uint64_t)b.nreq * b.n;
   k_seg_compact<<<(int)std::min<uint64_t>((rn + kB - 1) / kB, (uint64_t)num_sms() * 16), kB, 0,
                   st>>>(b);
   uint64_t *srt = radix_sort<uint64_t>(b.vis, b.vis_alt, b.ctr + BC_NVIS, rn, kIdBits,
                                        64 - kIdBits, L.sort_scratch, st, b.err);
+  mark(2);
   BatchDev b2 = b;
   b2.vis_sorted = srt;
   const uint64_t slot_parts = (rn + (uint64_t)b.nreq * kB) / kB;
   k_gather_batch<<<(int)std::min<uint64_t>(slot_parts, g_gather), kB, 0, st>>>(b2);
+  mark(3);
   k_tile_scan_batch<<<b.nreq, kTS, 0, st>>>(b2);
+  mark(4);
   k_lists_batch<<<(int)std::min<uint64_t>((b.ntiles + kW - 1) / kW, (uint64_t)num_sms() * 8),
                   kB, 0, st>>>(b2);
+  mark(5);
   uint64_t *qs = radix_sort<uint64_t>(b.qkeys, b.qkeys_alt, b.ctr + BC_NTILES, b.ntiles, 32, 24,
                                       L.sort_scratch, st, b.err);
   b2.queue = qs;
+  mark(6);
   const int grid = L.blend_ctas_per_sm * num_sms();
-  switch (L.footprint) {
-    case 0: k_blend_persist<16><<<grid, kBlendThreads, 0, st>>>(b2); break;
-    case 2: k_blend_persist<4><<<grid, kBlendThreads, 0, st>>>(b2); break;
-    default: k_blend_persist<8><<<grid, kBlendThreads, 0, st>>>(b2); break;
+  if (b.evals) {
+    switch (L.footprint) {
+      case 0: k_blend_persist<16, true><<<grid, kBlendThreads, 0, st>>>(b2); break;
+      case 2: k_blend_persist<4, true><<<grid, kBlendThreads, 0, st>>>(b2); break;
+      default: k_blend_persist<8, true><<<grid, kBlendThreads, 0, st>>>(b2); break;
+    }
+  } else {
+    switch (L.footprint) {
+      case 0: k_blend_persist<16, false><<<grid, kBlendThreads, 0, st>>>(b2); break;
+      case 2: k_blend_persist<4, false><<<grid, kBlendThreads, 0, st>>>(b2); break;
+      default: k_blend_persist<8, false><<<grid, kBlendThreads, 0, st>>>(b2); break;
+    }
   }
+  mark(7);
 }
 
 int batch_blend_max_ctas_per_sm() {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_persist<8>, kBlendThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_persist<8, false>,
+                                                kBlendThreads, 0);
   return std::max(1, per_sm);
 }
 

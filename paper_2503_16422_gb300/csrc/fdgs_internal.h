@@ -165,6 +165,8 @@ struct BatchDev {
   float *T_final;
   uint32_t *n_contrib;
   unsigned long long *done_ns, *t0_ns;
+  unsigned long long *evals;         // [2] blend evaluations / culling tests, or null
+  unsigned long long *stamps;        // [kBatchStages + 1] %globaltimer at stage boundaries
 };
 struct BatchLaunch {
   size_t pre_status_bytes, scan_status_bytes, diff_bytes;
@@ -172,6 +174,9 @@ struct BatchLaunch {
   int footprint;                     // warp footprint of the blend (0, 1, 2)
   int blend_ctas_per_sm;             // persistent blend grid = this x SMs
 };
+// Stages timed by the device stamps: preprocess, depth_sort (bases, compaction, sort),
+// gather, tile_scan, lists, queue_sort, blend.
+constexpr int kBatchStages = 7;
 void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st);
 int batch_blend_max_ctas_per_sm();
 

@@ -79,11 +79,14 @@ _SIGNATURES = {
                             ctypes.c_int, ctypes.POINTER(fdgs_render_opts), ctypes.POINTER(_P),
                             _P],
     "fdgs_batch_info": [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
-                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                        ctypes.POINTER(ctypes.c_float)],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
 }
 PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "tile_scan", "emit",
                   "tile_sort", "blend")
+BATCH_STAGES = ("preprocess", "depth_sort", "gather", "tile_scan", "lists", "queue_sort",
+                "blend")
 
 _lib = None
 
@@ -332,9 +335,12 @@ class Scene:
 
     def batch_info(self, n):
         lat = (ctypes.c_float * max(n, 1))()
+        st = (ctypes.c_float * len(BATCH_STAGES))()
         fp, ctas = ctypes.c_int(), ctypes.c_int()
-        check(lib().fdgs_batch_info(self.handle, lat, n, ctypes.byref(fp), ctypes.byref(ctas)))
-        return dict(latency_ms=list(lat)[:n], footprint=fp.value, ctas_per_sm=ctas.value)
+        check(lib().fdgs_batch_info(self.handle, lat, n, ctypes.byref(fp), ctypes.byref(ctas),
+                                    st))
+        return dict(latency_ms=list(lat)[:n], footprint=fp.value, ctas_per_sm=ctas.value,
+                    stage_ms=dict(zip(BATCH_STAGES, list(st))))
 
     def variation_score(self, cams, ts, batch=8, out=None, stream=None):
         carr = (fdgs_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
