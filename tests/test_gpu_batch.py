@@ -81,3 +81,21 @@ def test_batch_of_one_and_empty_view(fd):
     one = sc.render_batch(cams[:1], ts[:1], use_mask=False)
     assert torch.equal(one[0], outs[0])
     sc.close()
+
+
+def test_batch_full_size_dense_tiles_match_sequential(fd):
+    """200k-Gaussian pruned scene at 1352x1014: tiles hold thousands of entries, several per
+    bitmask word, so the blend's read-out rounds end inside words (straddling cursor) and
+    many tiles stop early; the images must still equal the per-request renders."""
+    s = scenes.pruned_scene()
+    sc = fd.Scene.from_host(s)
+    kt = scenes.keyframe_times(300, 6)
+    sc.set_active_mask(torch.as_tensor(scenes.keyframe_masks(s, kt)).cuda(), kt)
+    ts = scenes.frame_times()
+    ks = (0, 77, 150, 299)
+    cams = [scenes.arc_camera(scenes.frame_theta(k), 1352, 1014) for k in ks]
+    tt = [float(ts[k]) for k in ks]
+    outs = sc.render_batch(cams, tt, use_mask=True)
+    for i, (c, t) in enumerate(zip(cams, tt)):
+        assert torch.equal(outs[i], sc.render(c, t, use_mask=True)), i
+    sc.close()
