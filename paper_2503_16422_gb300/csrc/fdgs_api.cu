@@ -125,11 +125,10 @@ struct BatchPlan {
   bool masked = false;
   fdgs_scene_desc d{};
   uint32_t ntiles = 0, mask_words = 0;
-  uint64_t npix = 0, key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
+  uint64_t key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
   std::vector<ReqDesc> tmpl;
-  Buf reqs, ctr, pre_status, scan_status, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base,
-      key_base, rec_sorted, diff, masks, ranges, qkeys, qkeys_alt, lists, Tf, nc, done, t0,
-      scratch;
+  Buf reqs, ctr, pre_status, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base, key_cnt,
+      rec_sorted, diff, masks, ranges, qkeys, qkeys_alt, lists, Tf, nc, done, t0, scratch;
   ReqDesc *h_reqs = nullptr;
   uint32_t *h_ctr = nullptr;
   unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
@@ -144,9 +143,9 @@ struct BatchPlan {
   ~BatchPlan() {
     stamps.release();
     if (h_stamps) cudaFreeHost(h_stamps);
-    Buf *all[] = {&reqs, &ctr, &pre_status, &scan_status, &rec, &vis_seg, &vis, &vis_alt,
-                  &nv, &vis_base, &slot_base, &key_base, &rec_sorted, &diff, &masks,
-                  &ranges, &qkeys, &qkeys_alt, &lists, &Tf, &nc, &done, &t0, &scratch};
+    Buf *all[] = {&reqs, &ctr, &pre_status, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
+                  &slot_base, &key_cnt, &rec_sorted, &diff, &masks, &ranges, &qkeys,
+                  &qkeys_alt, &lists, &Tf, &nc, &done, &t0, &scratch};
     for (Buf *b : all) b->release();
     if (h_reqs) cudaFreeHost(h_reqs);
     if (h_ctr) cudaFreeHost(h_ctr);
@@ -468,9 +467,9 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
     ReqDesc &q = p.tmpl[i];
     memset(&q, 0, sizeof q);
     q.tile_base = (uint32_t)tiles;
-    q.pix_base = pix;
     q.diff_base = (uint32_t)diff;
     q.mask_base = mask;
+    q.pix_base = pix;
     tiles += (uint64_t)dc.gx * dc.gy;
     pix += (uint64_t)dc.W * dc.H;
     diff += (uint64_t)(dc.gx + 1) * (dc.gy + 1);
@@ -479,7 +478,6 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   if (tiles >= (1ull << 32) || diff >= (1ull << 31))
     return fail(FDGS_ERR_INVALID, "batch too large");
   p.ntiles = (uint32_t)tiles;
-  p.npix = pix;
   p.diff_ints = diff;
   p.mask_total = mask;
   p.rn = (uint64_t)n * N;
@@ -489,7 +487,6 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   TRY(grow(p.reqs, n * sizeof(ReqDesc)));
   TRY(grow(p.ctr, BC_COUNT * 4));
   TRY(grow(p.pre_status, std::max<uint64_t>(P * n, 1) * 8));
-  TRY(grow(p.scan_status, std::max<uint64_t>(p.slot_cap / 256, 1) * 8));
   TRY(grow(p.rec, std::max<uint64_t>(p.rn, 1) * kRec * 4));
   TRY(grow(p.vis_seg, std::max<uint64_t>(p.rn, 1) * 8));
   TRY(grow(p.vis, std::max<uint64_t>(p.rn, 1) * 8));
@@ -497,15 +494,15 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   TRY(grow(p.nv, n * 4));
   TRY(grow(p.vis_base, n * 4));
   TRY(grow(p.slot_base, n * 4));
-  TRY(grow(p.key_base, n * 8));
+  TRY(grow(p.key_cnt, n * 8));
   TRY(grow(p.rec_sorted, p.slot_cap * kRecS * 4));
   TRY(grow(p.diff, diff * 4));
+  TRY(grow(p.Tf, pix * 4));
+  TRY(grow(p.nc, pix * 4));
   TRY(grow(p.masks, std::max<uint64_t>(mask, 1) * 4));
   TRY(grow(p.ranges, tiles * 8));
   TRY(grow(p.qkeys, tiles * 8));
   TRY(grow(p.qkeys_alt, tiles * 8));
-  TRY(grow(p.Tf, pix * 4));
-  TRY(grow(p.nc, pix * 4));
   TRY(grow(p.done, n * 8));
   TRY(grow(p.t0, 8));
   TRY(grow(p.scratch, std::max(sort_scratch_bytes(std::max<uint64_t>(p.rn, 1), 39),
@@ -560,7 +557,6 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.ctr = p.ctr.as<uint32_t>();
   b.err = s->status.as<uint32_t>();
   b.pre_status = p.pre_status.as<uint64_t>();
-  b.scan_status = p.scan_status.as<uint64_t>();
   b.rec = p.rec.as<float>();
   b.vis_seg = p.vis_seg.as<uint64_t>();
   b.vis = p.vis.as<uint64_t>();
@@ -569,7 +565,7 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.nv = p.nv.as<uint32_t>();
   b.vis_base = p.vis_base.as<uint32_t>();
   b.slot_base = p.slot_base.as<uint32_t>();
-  b.key_base = p.key_base.as<uint64_t>();
+  b.key_cnt = p.key_cnt.as<unsigned long long>();
   b.rec_sorted = p.rec_sorted.as<float>();
   b.diff = p.diff.as<int>();
   b.masks = p.masks.as<uint32_t>();
@@ -586,7 +582,6 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.stamps = p.stamps.as<unsigned long long>();
   const uint64_t P = ((uint64_t)s->d.n + 255) / 256;
   L.pre_status_bytes = std::max<uint64_t>(P * p.nreq, 1) * 8;
-  L.scan_status_bytes = std::max<uint64_t>(p.slot_cap / 256, 1) * 8;
   L.diff_bytes = p.diff_ints * 4;
   L.sort_scratch = p.scratch.p;
   L.footprint = p.footprint;

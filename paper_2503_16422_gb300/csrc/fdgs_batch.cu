@@ -5,8 +5,8 @@
 //   k_batch_bases    per-request visible counts -> contiguous bases and 256-aligned slots
 //   k_seg_compact    request segments -> one contiguous array of (request, depth, id) keys
 //   radix_sort       one global depth sort (request bits on top keep requests apart)
-//   k_gather_batch   blend-ready records per slot, key offsets, coverage difference arrays
-//                    and row/column bitmasks per request
+//   k_gather_batch   blend-ready records per slot, per-request key counts, coverage
+//                    difference arrays and row/column bitmasks per request
 //   k_tile_scan_batch  per-request tile ranges (capacity-checked) and longest-first queue keys
 //   k_lists_batch    per-tile lists from the bitmasks, for every request's tiles
 //   radix_sort       queue keys by list length (descending)
@@ -181,20 +181,12 @@ __device__ __forceinline__ void tighten_rect(float u, float v, float A, float B,
 
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kB) k_gather_batch(BatchDev b) {
-  __shared__ uint32_t s_part;
-  __shared__ uint32_t s_wtot[kW];
-  __shared__ uint64_t s_base;
   __shared__ uint32_t s_slot_base[kMaxReq];
   for (int r = threadIdx.x; r < b.nreq; r += kB) s_slot_base[r] = b.slot_base[r];
   __syncthreads();
-  const uint32_t nslots = b.ctr[BC_NSLOTS];
-  const uint32_t nparts = nslots / kB;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (;;) {
-    if (tid == 0) s_part = atomicAdd(&b.ctr[BC_GATHER_PART], 1u);
-    __syncthreads();
-    const uint32_t part = s_part;
-    if (part >= nparts) break;
+  const uint32_t nparts = b.ctr[BC_NSLOTS] / kB;
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (uint32_t part = blockIdx.x; part < nparts; part += gridDim.x) {
     const uint32_t s = part * kB + tid;
     const int r = find_segment(s_slot_base, b.nreq, part * kB);   // one request per partition
     const ReqDesc &q = b.reqs[r];
@@ -241,26 +233,9 @@ __global__ void __launch_bounds__(kB) k_gather_batch(BatchDev b) {
         if (lane == (x & 31)) cols[(size_t)x * b.mask_words + word] = bb;
       }
     }
-    const uint32_t inc = warp_incl_scan(cnt);
-    if (lane == 31) s_wtot[warp] = inc;
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t tot = 0;
-      for (int w = 0; w < kW; ++w) {
-        const uint32_t c = s_wtot[w];
-        s_wtot[w] = tot;
-        tot += c;
-      }
-      const uint64_t base = lookback_single(b.scan_status, part, tot, b.err);
-      s_base = base;
-      if (part == nparts - 1) {
-        b.ctr[BC_NKEYS_LO] = (uint32_t)(base + tot);
-        b.ctr[BC_NKEYS_HI] = (uint32_t)((base + tot) >> 32);
-      }
-    }
-    __syncthreads();
-    if (l == 0 && valid) b.key_base[r] = s_base;   // first slot of the request
-    __syncthreads();
+    // the request's key count (its lists' total length); the partition's part of it
+    const uint32_t ws = warp_sum(cnt);
+    if (lane == 0 && ws) atomicAdd(&b.key_cnt[r], (unsigned long long)ws);
   }
 }
 
@@ -294,8 +269,17 @@ __global__ void __launch_bounds__(kTS) k_tile_scan_batch(BatchDev b) {
     }
   }
   __syncthreads();
-  const uint64_t base = b.nv[r] ? b.key_base[r] : 0;
-  const uint64_t nkeys = (uint64_t)b.ctr[BC_NKEYS_LO] | ((uint64_t)b.ctr[BC_NKEYS_HI] << 32);
+  // the request's first list slot: key counts of the requests before it
+  uint64_t base = 0, nkeys = 0;
+  for (int i = 0; i < b.nreq; ++i) {
+    const uint64_t c = b.key_cnt[i];
+    if (i < r) base += c;
+    nkeys += c;
+  }
+  if (r == 0 && tid == 0) {
+    b.ctr[BC_NKEYS_LO] = (uint32_t)nkeys;
+    b.ctr[BC_NKEYS_HI] = (uint32_t)(nkeys >> 32);
+  }
   const bool overflow = nkeys > b.key_cap;
   if (overflow && tid == 0) atomicOr(b.err, kErrCapacity);
   const uint32_t tiles = (uint32_t)gx * gy;
@@ -427,7 +411,7 @@ int grid_of(const void *kernel, int threads, int per_sm_cap) {
 void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
   cudaMemsetAsync(b.ctr, 0, BC_COUNT * sizeof(uint32_t), st);
   cudaMemsetAsync(b.pre_status, 0, L.pre_status_bytes, st);
-  cudaMemsetAsync(b.scan_status, 0, L.scan_status_bytes, st);
+  cudaMemsetAsync(b.key_cnt, 0, b.nreq * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.diff, 0, L.diff_bytes, st);
   cudaMemsetAsync(b.done_ns, 0, b.nreq * sizeof(unsigned long long), st);
   if (b.evals) cudaMemsetAsync(b.evals, 0, 2 * sizeof(unsigned long long), st);

@@ -133,12 +133,12 @@ struct ReqDesc {
   float *rgb;                        // [3][H][W]
   uint32_t tile_base;                // first global tile id of the request
   uint32_t diff_base;                // offset of its coverage difference array (ints)
-  uint64_t pix_base;                 // offset of its pixels in T_final / n_contrib
   uint64_t mask_base;                // offset of its row and column bitmasks (words)
+  uint64_t pix_base;                 // offset of its pixels in T_final / n_contrib
 };
 enum BatchCounter {
-  BC_PRE_ITEM = 0, BC_NVIS = 1, BC_NSLOTS = 2, BC_NTILES = 3, BC_GATHER_PART = 4,
-  BC_NKEYS_LO = 5, BC_NKEYS_HI = 6, BC_QUEUE = 7, BC_COUNT = 16
+  BC_PRE_ITEM = 0, BC_NVIS = 1, BC_NSLOTS = 2, BC_NTILES = 3, BC_NKEYS_LO = 5,
+  BC_NKEYS_HI = 6, BC_QUEUE = 7, BC_COUNT = 16
 };
 struct BatchDev {
   const ReqDesc *reqs;
@@ -149,12 +149,12 @@ struct BatchDev {
   const float *opacity, *sh;
   int deg;
   uint32_t *ctr, *err;
-  uint64_t *pre_status, *scan_status;
+  uint64_t *pre_status;
   float *rec;                        // [nreq][n][12] by Gaussian id
   uint64_t *vis_seg, *vis, *vis_alt; // visible keys: per-request segments, contiguous, alt
   const uint64_t *vis_sorted;
   uint32_t *nv, *vis_base, *slot_base;
-  uint64_t *key_base;
+  unsigned long long *key_cnt;       // [nreq] list entries per request
   float *rec_sorted;                 // [slots][16] blend-ready
   int *diff;
   uint32_t *masks;
@@ -162,14 +162,14 @@ struct BatchDev {
   uint64_t *qkeys, *qkeys_alt;
   const uint64_t *queue;
   uint32_t *lists;                   // [key_cap] slot indices
-  float *T_final;
+  float *T_final;                    // per-pixel outputs of the blend (kept in the plan)
   uint32_t *n_contrib;
   unsigned long long *done_ns, *t0_ns;
   unsigned long long *evals;         // [2] blend evaluations / culling tests, or null
   unsigned long long *stamps;        // [kBatchStages + 1] %globaltimer at stage boundaries
 };
 struct BatchLaunch {
-  size_t pre_status_bytes, scan_status_bytes, diff_bytes;
+  size_t pre_status_bytes, diff_bytes;
   void *sort_scratch;
   int footprint;                     // warp footprint of the blend (0, 1, 2)
   int blend_ctas_per_sm;             // persistent blend grid = this x SMs
