@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kB) k_lists_batch(BatchDev b) {
   __shared__ uint32_t s_tile_base[kMaxReq];
   for (int r = threadIdx.x; r < b.nreq; r += kB) s_tile_base[r] = b.reqs[r].tile_base;
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   for (uint32_t gt = blockIdx.x * kW + warp; gt < b.ntiles; gt += gridDim.x * kW) {
     const int r = find_segment(s_tile_base, b.nreq, gt);
     const ReqDesc &q = b.reqs[r];
@@ -328,29 +328,7 @@ __global__ void __launch_bounds__(kB) k_lists_batch(BatchDev b) {
     const uint32_t *rows = b.masks + q.mask_base + (size_t)(t / q.cam.gx) * b.mask_words;
     const uint32_t *cols = b.masks + q.mask_base + (size_t)q.cam.gy * b.mask_words +
                            (size_t)(t % q.cam.gx) * b.mask_words;
-    const uint32_t sb = b.slot_base[r];
-    uint32_t off = rg.x;
-    uint32_t nr0 = lane < words ? __ldg(&rows[lane]) : 0u;
-    uint32_t nc0 = lane < words ? __ldg(&cols[lane]) : 0u;
-    uint32_t nr1 = lane + 32 < words ? __ldg(&rows[lane + 32]) : 0u;
-    uint32_t nc1 = lane + 32 < words ? __ldg(&cols[lane + 32]) : 0u;
-    for (uint32_t c0 = 0; c0 < words; c0 += 32) {
-      const uint32_t c = c0 + lane;
-      uint32_t m = nr0 & nc0;
-      nr0 = nr1;
-      nc0 = nc1;
-      nr1 = c + 64 < words ? __ldg(&rows[c + 64]) : 0u;
-      nc1 = c + 64 < words ? __ldg(&cols[c + 64]) : 0u;
-      const uint32_t pc = __popc(m);
-      const uint32_t inc = warp_incl_scan(pc);
-      uint32_t o = off + inc - pc;
-      while (m) {
-        const int bit = __ffs(m) - 1;
-        m &= m - 1;
-        b.lists[o++] = sb + c * 32 + bit;
-      }
-      off += __shfl_sync(0xffffffffu, inc, 31);
-    }
+    warp_list_from_masks(rows, cols, words, rg.x, b.slot_base[r], b.lists);
   }
 }
 
