@@ -514,9 +514,10 @@ def score_timing(stream):
 
 
 def launches_per_batch():
-    # start, preprocess, bases, segment compaction, depth sort (histogram, scan, 5 passes),
-    # gather, tile scan, lists, queue sort (histogram, scan, 3 passes), persistent blend
-    return 1 + 1 + 1 + 1 + 7 + 1 + 1 + 1 + 5 + 1
+    # start, preprocess, partition scan, bases, segment compaction, depth sort (histogram,
+    # scan, 5 passes), gather, tile scan, lists, queue sort (histogram, scan, 3 passes),
+    # persistent blend, and the 8 one-thread %globaltimer stamps between the stages
+    return 1 + 1 + 1 + 1 + 1 + 7 + 1 + 1 + 1 + 5 + 1 + 8
 
 
 def main():

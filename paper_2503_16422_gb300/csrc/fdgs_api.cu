@@ -127,7 +127,7 @@ struct BatchPlan {
   uint32_t ntiles = 0, mask_words = 0;
   uint64_t key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
   std::vector<ReqDesc> tmpl;
-  Buf reqs, ctr, pre_status, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base, key_cnt,
+  Buf reqs, ctr, part, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base, key_cnt,
       rec_sorted, diff, masks, ranges, qkeys, qkeys_alt, lists, Tf, nc, done, t0, scratch;
   ReqDesc *h_reqs = nullptr;
   uint32_t *h_ctr = nullptr;
@@ -143,7 +143,7 @@ struct BatchPlan {
   ~BatchPlan() {
     stamps.release();
     if (h_stamps) cudaFreeHost(h_stamps);
-    Buf *all[] = {&reqs, &ctr, &pre_status, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
+    Buf *all[] = {&reqs, &ctr, &part, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
                   &slot_base, &key_cnt, &rec_sorted, &diff, &masks, &ranges, &qkeys,
                   &qkeys_alt, &lists, &Tf, &nc, &done, &t0, &scratch};
     for (Buf *b : all) b->release();
@@ -486,9 +486,9 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   const uint64_t P = (N + 255) / 256;
   TRY(grow(p.reqs, n * sizeof(ReqDesc)));
   TRY(grow(p.ctr, BC_COUNT * 4));
-  TRY(grow(p.pre_status, std::max<uint64_t>(P * n, 1) * 8));
+  TRY(grow(p.part, std::max<uint64_t>(P * n, 1) * 8));
   TRY(grow(p.rec, std::max<uint64_t>(p.rn, 1) * kRec * 4));
-  TRY(grow(p.vis_seg, std::max<uint64_t>(p.rn, 1) * 8));
+  TRY(grow(p.vis_seg, std::max<uint64_t>(P * n * 256, 1) * 8));
   TRY(grow(p.vis, std::max<uint64_t>(p.rn, 1) * 8));
   TRY(grow(p.vis_alt, std::max<uint64_t>(p.rn, 1) * 8));
   TRY(grow(p.nv, n * 4));
@@ -556,7 +556,7 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.deg = s->d.sh_degree;
   b.ctr = p.ctr.as<uint32_t>();
   b.err = s->status.as<uint32_t>();
-  b.pre_status = p.pre_status.as<uint64_t>();
+  b.part = p.part.as<uint2>();
   b.rec = p.rec.as<float>();
   b.vis_seg = p.vis_seg.as<uint64_t>();
   b.vis = p.vis.as<uint64_t>();
@@ -580,8 +580,6 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.t0_ns = p.t0.as<unsigned long long>();
   b.evals = nullptr;
   b.stamps = p.stamps.as<unsigned long long>();
-  const uint64_t P = ((uint64_t)s->d.n + 255) / 256;
-  L.pre_status_bytes = std::max<uint64_t>(P * p.nreq, 1) * 8;
   L.diff_bytes = p.diff_ints * 4;
   L.sort_scratch = p.scratch.p;
   L.footprint = p.footprint;

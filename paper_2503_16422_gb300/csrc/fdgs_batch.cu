@@ -1,7 +1,8 @@
 // Batched rendering of many (camera, t, resolution) requests in one device-driven pipeline
 // that is captured once in a CUDA graph and replayed:
-//   k_pre_batch      per-Gaussian stage over all (request, partition) items, compaction of
-//                    each request's visible Gaussians with a per-request chained scan
+//   k_pre_batch      per-Gaussian stage over all (request, partition) items; each item
+//                    writes its visible keys to its own 256-key segment
+//   k_part_scan      per-request scan of the segments' counts -> offsets, visible counts
 //   k_batch_bases    per-request visible counts -> contiguous bases and 256-aligned slots
 //   k_seg_compact    request segments -> one contiguous array of (request, depth, id) keys
 //   radix_sort       one global depth sort (request bits on top keep requests apart)
@@ -51,7 +52,6 @@ __device__ __forceinline__ int find_segment(const uint32_t *bases, int n, uint32
 __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
   __shared__ uint32_t s_item;
   __shared__ uint32_t s_wcnt[kW];
-  __shared__ uint64_t s_base;
   const uint32_t P = (b.n + kB - 1) / kB;
   const uint32_t items = P * b.nreq;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -111,14 +111,44 @@ __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
         s_wcnt[w] = tot;
         tot += c;
       }
-      const uint64_t base = lookback_single(b.pre_status + (size_t)r * P, part, tot, b.err);
-      s_base = base;
-      if (part == P - 1) b.nv[r] = (uint32_t)(base + tot);
+      b.part[item].x = tot;
     }
     __syncthreads();
-    if (vis) b.vis_seg[(size_t)r * b.n + s_base + s_wcnt[warp] + __popc(vb & lanemask_lt())] = key;
+    // the item's own 256-key segment, in id order; placed by k_seg_compact
+    if (vis) b.vis_seg[(size_t)item * kB + s_wcnt[warp] + __popc(vb & lanemask_lt())] = key;
     __syncthreads();
   }
+}
+
+// One CTA per request: exclusive scan of its partitions' visible counts -> segment offsets
+// and the request's visible count.
+constexpr int kPS = 1024;
+__global__ void __launch_bounds__(kPS) k_part_scan(BatchDev b) {
+  __shared__ uint32_t s_wsum[kPS / 32];
+  __shared__ uint32_t s_carry;
+  const uint32_t P = (b.n + kB - 1) / kB;
+  uint2 *part = b.part + (size_t)blockIdx.x * P;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t p0 = 0; p0 < P; p0 += kPS) {
+    const uint32_t i = p0 + tid;
+    const uint32_t c = i < P ? part[i].x : 0u;
+    const uint32_t inc = warp_incl_scan(c);
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = s_wsum[lane];
+      s_wsum[lane] = warp_incl_scan(w) - w;
+    }
+    __syncthreads();
+    const uint32_t excl = s_carry + s_wsum[warp] + inc - c;
+    if (i < P) part[i].y = excl;
+    __syncthreads();
+    if (tid == kPS - 1) s_carry = excl + c;
+    __syncthreads();
+  }
+  if (tid == 0) b.nv[blockIdx.x] = s_carry;
 }
 
 // Per-request bases (one warp; nreq <= 128): contiguous visible bases and 256-aligned slots.
@@ -145,11 +175,13 @@ __global__ void k_batch_bases(BatchDev b) {
 }
 
 __global__ void k_seg_compact(BatchDev b) {
-  const uint64_t total = (uint64_t)b.nreq * b.n;
+  const uint32_t P = (b.n + kB - 1) / kB;
+  const uint64_t total = (uint64_t)b.nreq * P * kB;
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
        k += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t r = (uint32_t)(k / b.n), i = (uint32_t)(k % b.n);
-    if (i < b.nv[r]) b.vis[b.vis_base[r] + i] = b.vis_seg[k];
+    const uint32_t item = (uint32_t)(k / kB), i = (uint32_t)(k % kB);
+    const uint2 pc = b.part[item];
+    if (i < pc.x) b.vis[b.vis_base[item / P] + pc.y + i] = b.vis_seg[k];
   }
 }
 
@@ -388,7 +420,6 @@ int grid_of(const void *kernel, int threads, int per_sm_cap) {
 // only on the plan). The caller zeroes nothing: the memsets are part of the sequence.
 void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
   cudaMemsetAsync(b.ctr, 0, BC_COUNT * sizeof(uint32_t), st);
-  cudaMemsetAsync(b.pre_status, 0, L.pre_status_bytes, st);
   cudaMemsetAsync(b.key_cnt, 0, b.nreq * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.diff, 0, L.diff_bytes, st);
   cudaMemsetAsync(b.done_ns, 0, b.nreq * sizeof(unsigned long long), st);
@@ -404,10 +435,11 @@ void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
   const uint64_t pre_items = (uint64_t)((b.n + kB - 1) / kB) * b.nreq;
   k_pre_batch<<<(int)std::min<uint64_t>(pre_items, g_pre), kB, 0, st>>>(b);
   mark(1);
+  k_part_scan<<<b.nreq, kPS, 0, st>>>(b);
   k_batch_bases<<<1, 32, 0, st>>>(b);
   const uint64_t rn = (uint64_t)b.nreq * b.n;
-  k_seg_compact<<<(int)std::min<uint64_t>((rn + kB - 1) / kB, (uint64_t)num_sms() * 16), kB, 0,
-                  st>>>(b);
+  const uint64_t segs = (pre_items * kB + kB - 1) / kB;
+  k_seg_compact<<<(int)std::min<uint64_t>(segs, (uint64_t)num_sms() * 16), kB, 0, st>>>(b);
   uint64_t *srt = radix_sort<uint64_t>(b.vis, b.vis_alt, b.ctr + BC_NVIS, rn, kIdBits,
                                        64 - kIdBits, L.sort_scratch, st, b.err);
   mark(2);

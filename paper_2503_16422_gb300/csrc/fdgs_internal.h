@@ -149,9 +149,9 @@ struct BatchDev {
   const float *opacity, *sh;
   int deg;
   uint32_t *ctr, *err;
-  uint64_t *pre_status;
+  uint2 *part;                       // [nreq][partitions]: visible count, segment offset
   float *rec;                        // [nreq][n][12] by Gaussian id
-  uint64_t *vis_seg, *vis, *vis_alt; // visible keys: per-request segments, contiguous, alt
+  uint64_t *vis_seg, *vis, *vis_alt; // visible keys: per-partition segments, contiguous, alt
   const uint64_t *vis_sorted;
   uint32_t *nv, *vis_base, *slot_base;
   unsigned long long *key_cnt;       // [nreq] list entries per request
@@ -169,7 +169,7 @@ struct BatchDev {
   unsigned long long *stamps;        // [kBatchStages + 1] %globaltimer at stage boundaries
 };
 struct BatchLaunch {
-  size_t pre_status_bytes, diff_bytes;
+  size_t diff_bytes;
   void *sort_scratch;
   int footprint;                     // warp footprint of the blend (0, 1, 2)
   int blend_ctas_per_sm;             // persistent blend grid = this x SMs
