@@ -367,7 +367,11 @@ def run_ours(args):
         peak = fp32_peak_tflops(pk["sm_mhz"])
         res["roofline"] = {
             "bound": "alu", "kernel": "k_blend_persist", "achieved": ach, "peak": peak,
-            "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": BLEND_PERSIST_DRAM_BYTES_PER_FRAME * B,
+            "traffic_src": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 8-frame "
+                           "launch (profiles/k_blend_persist_batched_1352x1014.md), per frame "
+                           f"x {B} frames per launch",
             "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_mhz']:.0f} MHz",
             "work": "executed (Gaussian, pixel) evaluations x 20 FLOP + culling tests x 36 FLOP,"
                     " counted on the same batches; time = in-graph %globaltimer stage stamps, timed steps",
@@ -511,6 +515,12 @@ def score_timing(stream):
     sc.close()
     return dict(n_gaussians=s.n, renders=len(cams) * len(ts), resolution="1352x1014",
                 wall_s=wall, ms_per_render=wall * 1e3 / (len(cams) * len(ts)), kept=kept)
+
+
+# DRAM bytes the persistent blend moves per frame of a batch at 1352x1014 on the 200k pruned
+# scene, from one ncu capture of an 8-frame launch (301.0 MB); to be re-captured whenever the
+# blend kernel changes.
+BLEND_PERSIST_DRAM_BYTES_PER_FRAME = 301.0e6 / 8
 
 
 def launches_per_batch():

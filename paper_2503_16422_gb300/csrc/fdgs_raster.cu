@@ -302,12 +302,36 @@ __global__ void __launch_bounds__(kBlock)
 k_tile_lists(const uint32_t *__restrict__ rowmask, const uint32_t *__restrict__ colmask,
              uint32_t mask_words, uint32_t words, int gx, int gy,
              const uint2 *__restrict__ ranges, uint32_t *__restrict__ lists) {
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tiles = (uint32_t)gx * gy;
   for (uint32_t t = blockIdx.x * kWarps + warp; t < tiles; t += gridDim.x * kWarps) {
     const uint32_t *rows = rowmask + (size_t)(t / gx) * mask_words;
     const uint32_t *cols = colmask + (size_t)(t % gx) * mask_words;
-    warp_list_from_masks(rows, cols, words, ranges[t].x, 0u, lists);
+    // one word per lane per step: a frame has one wave of tile warps, so the shorter steps
+    // (and lower register count) win here; the batched builder reads four words per lane
+    uint32_t off = ranges[t].x;
+    // the words of group g+2 are loading while group g is written out
+    uint32_t nr0 = lane < words ? __ldg(&rows[lane]) : 0u;
+    uint32_t nc0 = lane < words ? __ldg(&cols[lane]) : 0u;
+    uint32_t nr1 = lane + 32 < words ? __ldg(&rows[lane + 32]) : 0u;
+    uint32_t nc1 = lane + 32 < words ? __ldg(&cols[lane + 32]) : 0u;
+    for (uint32_t c0 = 0; c0 < words; c0 += 32) {
+      const uint32_t c = c0 + lane;
+      uint32_t m = nr0 & nc0;
+      nr0 = nr1;
+      nc0 = nc1;
+      nr1 = c + 64 < words ? __ldg(&rows[c + 64]) : 0u;
+      nc1 = c + 64 < words ? __ldg(&cols[c + 64]) : 0u;
+      const uint32_t pc = __popc(m);
+      const uint32_t inc = warp_incl_scan(pc);
+      uint32_t o = off + inc - pc;
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        lists[o++] = c * 32 + b;
+      }
+      off += __shfl_sync(0xffffffffu, inc, 31);
+    }
   }
 }
 
