@@ -61,6 +61,19 @@ def frame_list(n, offset=0):
     return [((offset + i) * 7) % 300 for i in range(n)]
 
 
+def rank_requests(rank, steps, batch):
+    """Frame indices of every timed step of one replica: each rank walks the frames from its
+    own offset, so the ranks render independent request streams (weak scaling)."""
+    return [frame_list(batch, rank * 1000 + s * batch) for s in range(steps)]
+
+
+def job_fps(local_ms, frames_per_rank, world, reduce_max=None):
+    """Whole-job throughput: the frames of all ranks over the slowest rank's time.
+    reduce_max maps this rank's time to the maximum over ranks (None on one GPU)."""
+    t_ms = reduce_max(local_ms) if reduce_max is not None else local_ms
+    return world * frames_per_rank / (t_ms / 1e3), t_ms
+
+
 def pruned_masked():
     from paper_2503_16422_gb300 import scenes
     scene = scenes.pruned_scene()
@@ -319,7 +332,8 @@ def run_ours(args):
         c_, t_ = batch_args(w, 6000 + rank)
         sc.render_batch(c_, t_, outs=outs)
     torch.cuda.synchronize()
-    steps = [batch_args(s, rank * 1000) for s in range(args.steps)]
+    steps = [([cams[k] for k in fr], [float(times[k]) for k in fr])
+             for fr in rank_requests(rank, args.steps, B)]
     clocks = Clocks(local)
     clocks.start()
     if world > 1:
@@ -332,13 +346,14 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
+    def max_over_ranks(ms):
+        tt = torch.tensor([ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        return float(tt.item())
+
     frames_done = B * len(steps)
-    value = world * frames_done / (total_ms / 1e3)
+    value, total_ms = job_fps(sum(step_ms), frames_done, world,
+                              max_over_ranks if world > 1 else None)
     res = dict(clocks=clk, batch_shape=shape, lat=lat)
 
     # end to end through the public API: per step the cameras and times go host->device (the
