@@ -401,7 +401,22 @@ def run_ours(args):
         res.update(stage_ms=stage_ms, counts=counts,
                    single_roofline=roofline(stage_ms, counts, bytes_mean),
                    stage_gbs={s_: bytes_mean[s_] / (stage_ms[s_] / 1e3) / 1e9
-                              for s_ in bytes_mean if stage_ms[s_] > 1e-4})
+                              for s_ in bytes_mean if stage_ms[s_] > 1e-4},
+                   stage_rates={
+                       "depth_sort_keys_per_s": counts["n_visible"] / (stage_ms["depth_sort"] / 1e3),
+                       "tile_list_keys_per_s": counts["n_keys"] / (stage_ms["emit"] / 1e3),
+                       "blend_evals_per_s": counts["blend_evals"] / (stage_ms["blend"] / 1e3)})
+        # the batch's stages in the units of their rooflines: the preprocess in GB/s (the
+        # per-request algorithmic bytes of the same frames, times the requests), the depth
+        # sort (with its segment scan and compaction) and the list build in keys/s, the
+        # blend in Gaussian-pixel evaluations/s
+        bc = sc.batch_counts()
+        res["batch_rates"] = {
+            "preprocess_gbs": B * bytes_mean["preprocess"] / (bst["preprocess"] / 1e3) / 1e9,
+            "depth_sort_keys_per_s": bc["n_visible"] / (bst["depth_sort"] / 1e3),
+            "tile_list_keys_per_s": bc["n_keys"] / (bst["lists"] / 1e3),
+            "blend_evals_per_s": ev / len(steps) / (bst["blend"] / 1e3),
+            "n_visible_per_batch": bc["n_visible"], "n_keys_per_batch": bc["n_keys"]}
         if not args.no_extra:
             res["comparisons"] = comparisons(sc, cams, times, flush, stream)
     sc.close()
@@ -585,7 +600,9 @@ def main():
                            "p99": float(np.percentile(lat, 99))},
             "batch_shape": {k: v for k, v in res["batch_shape"].items() if k != "latency_ms"},
             "batch_stages_ms": res["batch_stages_ms"],
+            "batch_rates": res["batch_rates"],
             "single_frame_stages_ms": res["stage_ms"], "stage_gbs": res["stage_gbs"],
+            "stage_rates": res["stage_rates"],
             "single_frame_roofline": res["single_roofline"],
             "counts_per_frame": res["counts"]}
     if "comparisons" in res:

@@ -208,6 +208,13 @@ int fdgs_batch_autotune(fdgs_scene *scene, const fdgs_camera *cams, const float 
 int fdgs_batch_info(fdgs_scene *scene, float *latency_ms, int n, int *footprint,
                     int *ctas_per_sm, float *stage_ms);
 
+/* Last batch: visible Gaussians and tile-list entries summed over its requests. The batched
+ * lists use, per Gaussian, the 3-sigma tile square intersected with the tiles its
+ * alpha >= 1/255 ellipse can reach, so n_keys is at most the per-request renders' total
+ * (images are identical). Either pointer may be NULL. FDGS_ERR_STATE if no batch was
+ * rendered. */
+int fdgs_batch_counts(fdgs_scene *scene, uint64_t *n_visible, uint64_t *n_keys);
+
 /*
  * Spatial-Temporal Variation Score (Sec. 4.2.1, Eqs. 4-7), reading "per-t product":
  *   S_i = sum over t in ts, camera in cams of  w_i(t, cam) * f_i(t) * gamma_i

@@ -978,6 +978,15 @@ int fdgs_batch_info(fdgs_scene *s, float *latency_ms, int n, int *footprint,
   return FDGS_OK;
 }
 
+int fdgs_batch_counts(fdgs_scene *s, uint64_t *n_visible, uint64_t *n_keys) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (!s->plan) return fail(FDGS_ERR_STATE, "no batch has been rendered");
+  const BatchPlan &p = *s->plan;
+  if (n_visible) *n_visible = p.h_ctr[BC_NVIS];
+  if (n_keys) *n_keys = (uint64_t)p.h_ctr[BC_NKEYS_LO] | ((uint64_t)p.h_ctr[BC_NKEYS_HI] << 32);
+  return FDGS_OK;
+}
+
 int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, const float *ts,
                          int n_t, int batch, float *score_out_dev, fdgs_stream stream) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");

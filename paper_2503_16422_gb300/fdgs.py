@@ -82,6 +82,7 @@ _SIGNATURES = {
                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                         ctypes.POINTER(ctypes.c_float)],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
+    "fdgs_batch_counts": [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
 }
 PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "tile_scan", "emit",
                   "tile_sort", "blend")
@@ -341,6 +342,12 @@ class Scene:
                                     st))
         return dict(latency_ms=list(lat)[:n], footprint=fp.value, ctas_per_sm=ctas.value,
                     stage_ms=dict(zip(BATCH_STAGES, list(st))))
+
+    def batch_counts(self):
+        """Visible Gaussians and tile-list entries of the last batch, over all requests."""
+        nv, nk = ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib().fdgs_batch_counts(self.handle, ctypes.byref(nv), ctypes.byref(nk)))
+        return dict(n_visible=nv.value, n_keys=nk.value)
 
     def variation_score(self, cams, ts, batch=8, out=None, stream=None):
         carr = (fdgs_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])

@@ -96,6 +96,17 @@ def test_batch_full_size_dense_tiles_match_sequential(fd):
     cams = [scenes.arc_camera(scenes.frame_theta(k), 1352, 1014) for k in ks]
     tt = [float(ts[k]) for k in ks]
     outs = sc.render_batch(cams, tt, use_mask=True)
+    counts = sc.batch_counts()
+    nv = nk = 0
     for i, (c, t) in enumerate(zip(cams, tt)):
-        assert torch.equal(outs[i], sc.render(c, t, use_mask=True)), i
+        img, fr = sc.render(c, t, use_mask=True, keep_frame=True)
+        assert torch.equal(outs[i], img), i
+        st = fr.stats()
+        nv += st["n_visible"]
+        nk += st["n_keys"]
+        fr.release()
+    # same visibility decisions; the batch's alpha-tight tile sets are subsets of the squares
+    assert counts["n_visible"] == nv
+    assert 0 < counts["n_keys"] <= nk
+    print(f"batch keys {counts['n_keys']} vs per-request 3-sigma keys {nk}")
     sc.close()
