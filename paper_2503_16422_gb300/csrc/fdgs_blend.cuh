@@ -9,7 +9,8 @@
 //   1. staging: each thread tests its staged Gaussian against the whole tile; survivors are
 //      compacted (block ballot + prefix) into an index list that keeps list order;
 //   2. warps: lanes test 32 survivors at a time against the warp's footprint and
-//      __ballot_sync the hits; the warp evaluates only those, one at a time, for 32 pixels.
+//      __ballot_sync the hits; each hitting lane writes its record to the warp's hit list, and
+//      the warp evaluates the list in order, one Gaussian at a time, for 32 pixels.
 // A culled Gaussian has alpha < 1/255 at every pixel it is culled for, so it would have been
 // skipped pixel by pixel anyway: results equal evaluating every entry at every pixel.
 #pragma once
@@ -49,6 +50,11 @@ struct BlendSmem {
   uint16_t idx[kBlendBatch];   // compacted survivors of the tile test
   uint32_t wcnt[kBlendThreads / 32];
   uint32_t ncomp;
+  // per warp, the records of the footprint-test hits in hit order, written by the lanes that
+  // tested them: u, v, a2, b2 | c2, lga, r, g | b, stage index
+  float4 h0[kBlendThreads / 32][32];
+  float4 h1[kBlendThreads / 32][32];
+  float2 h2[kBlendThreads / 32][32];
 };
 
 // Where one tile's inputs and outputs live.
@@ -149,45 +155,55 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     // 2. warp footprint tests on the survivors, evaluation of the hits
     for (int c0 = 0; c0 < ncomp && !warp_done; c0 += 32) {
       bool hit = false;
+      int j = 0;
+      float4 g0, g1, g2;
       if (kCount && c0 + lane < ncomp) ++ntests;
       if (c0 + lane < ncomp) {
-        const int j = sm.idx[c0 + lane];
-        const float4 g0 = sm.g0[st][j];
-        const float2 g1 = *reinterpret_cast<const float2 *>(&sm.g1[st][j]);
-        const float4 g2 = sm.g2[st][j];
+        j = sm.idx[c0 + lane];
+        g0 = sm.g0[st][j];
+        g1 = sm.g1[st][j];
+        g2 = sm.g2[st][j];
         hit = may_hit_rect(g0, g1.x, g1.y, g2.y, g2.z, fxl, fxh, fyl, fyh);
       }
-      uint32_t m = __ballot_sync(0xffffffffu, hit);
-      while (m) {
-        const int j = sm.idx[c0 + __ffs(m) - 1];
-        m &= m - 1;
+      const uint32_t m = __ballot_sync(0xffffffffu, hit);
+      if (hit) {                       // hand the record to the warp's hit list
+        const int p = __popc(m & lanemask_lt());
+        sm.h0[warp][p] = g0;
+        sm.h1[warp][p] = g1;
+        sm.h2[warp][p] = make_float2(g2.x, __int_as_float(j));
+      }
+      __syncwarp();
+      const int nh = __popc(m);
+      for (int k = 0; k < nh; ++k) {
         float w = 0.f;
         if (!done) {
           if (kCount) ++nevals;
-          const float4 g0 = sm.g0[st][j];
-          const float4 g1 = sm.g1[st][j];
+          const float4 h0 = sm.h0[warp][k];
+          const float4 h1 = sm.h1[warp][k];
           float alpha, raw, dx, dy;
-          if (splat_alpha(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, fpx, fpy, alpha, raw, dx, dy)) {
+          if (splat_alpha(h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, fpx, fpy, alpha, raw, dx, dy)) {
             const float nT = T * (1.f - alpha);
             if (nT < kTStop) {
               done = true;
             } else {
+              const float2 h2 = sm.h2[warp][k];
               w = alpha * T;
-              C0 = fmaf(g1.z, w, C0);
-              C1 = fmaf(g1.w, w, C1);
-              C2 = fmaf(sm.g2[st][j].x, w, C2);
+              C0 = fmaf(h1.z, w, C0);
+              C1 = fmaf(h1.w, w, C1);
+              C2 = fmaf(h2.x, w, C2);
               T = nT;
-              last = pos0 + j + 1;
+              last = pos0 + (uint32_t)__float_as_int(h2.y) + 1;
             }
           }
         }
         if (kWeights) {
           if (__any_sync(0xffffffffu, w != 0.f)) {
             const float s = warp_sum(w);
-            if (lane == 0) atomicAdd(&bt.w_sum[sm.rk[st][j]], s);
+            if (lane == 0) atomicAdd(&bt.w_sum[sm.rk[st][__float_as_int(sm.h2[warp][k].y)]], s);
           }
         }
       }
+      __syncwarp();                    // the list is rewritten by the next round
       warp_done = __all_sync(0xffffffffu, done);
     }
     if (__syncthreads_and(warp_done)) {
