@@ -211,8 +211,26 @@ __device__ __forceinline__ void tighten_rect(float u, float v, float A, float B,
   y1 = min(y1, (int)floorf((v + hy) * inv) + 1);
 }
 
+// Coverage words of one warp's 32 ranks: for each row r < n, bit `lane` of word r is set when
+// the lane's interval [lo, hi) holds r; word r goes to dst[r * stride]. One ballot per row;
+// lane k keeps the word of row 32 c + k and stores it once per 32 rows.
+__device__ __forceinline__ void warp_coverage_words(int lo, int hi, int n, uint32_t *dst,
+                                                    size_t stride) {
+  const uint32_t lane = lane_id();
+  const uint32_t span = (uint32_t)max(hi - lo, 0);
+  for (int c = 0; c < n; c += 32) {
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const uint32_t bb = __ballot_sync(0xffffffffu, (uint32_t)(c + k - lo) < span);
+      if (lane == (uint32_t)k) mine = bb;
+    }
+    if (c + (int)lane < n) dst[(size_t)(c + lane) * stride] = mine;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kB) k_gather_batch(BatchDev b) {
+__global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
   __shared__ uint32_t s_slot_base[kMaxReq];
   for (int r = threadIdx.x; r < b.nreq; r += kB) s_slot_base[r] = b.slot_base[r];
   __syncthreads();
@@ -253,17 +271,12 @@ __global__ void __launch_bounds__(kB) k_gather_batch(BatchDev b) {
     }
     // coverage bitmasks of the request; the warp owns local word l / 32
     {
-      uint32_t *rows = b.masks + q.mask_base;
-      uint32_t *cols = rows + (size_t)q.cam.gy * b.mask_words;
-      const uint32_t word = l >> 5;
-      for (int y = 0; y < q.cam.gy; ++y) {
-        const uint32_t bb = __ballot_sync(0xffffffffu, y >= y0 && y < y1);
-        if (lane == (y & 31)) rows[(size_t)y * b.mask_words + word] = bb;
-      }
-      for (int x = 0; x < q.cam.gx; ++x) {
-        const uint32_t bb = __ballot_sync(0xffffffffu, x >= x0 && x < x1);
-        if (lane == (x & 31)) cols[(size_t)x * b.mask_words + word] = bb;
-      }
+      const int gx = q.cam.gx, gy = q.cam.gy;
+      const size_t mw = b.mask_words;
+      uint32_t *rows = b.masks + q.mask_base + (l >> 5);
+      uint32_t *cols = rows + (size_t)gy * mw;
+      warp_coverage_words(y0, y1, gy, rows, mw);
+      warp_coverage_words(x0, x1, gx, cols, mw);
     }
     // the request's key count (its lists' total length); the partition's part of it
     const uint32_t ws = warp_sum(cnt);
