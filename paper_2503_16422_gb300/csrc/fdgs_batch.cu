@@ -211,24 +211,6 @@ __device__ __forceinline__ void tighten_rect(float u, float v, float A, float B,
   y1 = min(y1, (int)floorf((v + hy) * inv) + 1);
 }
 
-// Coverage words of one warp's 32 ranks: for each row r < n, bit `lane` of word r is set when
-// the lane's interval [lo, hi) holds r; word r goes to dst[r * stride]. One ballot per row;
-// lane k keeps the word of row 32 c + k and stores it once per 32 rows.
-__device__ __forceinline__ void warp_coverage_words(int lo, int hi, int n, uint32_t *dst,
-                                                    size_t stride) {
-  const uint32_t lane = lane_id();
-  const uint32_t span = (uint32_t)max(hi - lo, 0);
-  for (int c = 0; c < n; c += 32) {
-    uint32_t mine = 0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const uint32_t bb = __ballot_sync(0xffffffffu, (uint32_t)(c + k - lo) < span);
-      if (lane == (uint32_t)k) mine = bb;
-    }
-    if (c + (int)lane < n) dst[(size_t)(c + lane) * stride] = mine;
-  }
-}
-
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
   __shared__ uint32_t s_slot_base[kMaxReq];

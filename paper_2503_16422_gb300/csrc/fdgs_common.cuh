@@ -187,6 +187,24 @@ __device__ __forceinline__ float quad_max_rect(float a2, float b2, float c2, flo
   }
   return best;
 }
+// Coverage words of one warp's 32 ranks: for each row r < n, bit `lane` of word r is set when
+// the lane's interval [lo, hi) holds r; word r goes to dst[r * stride]. One ballot per row;
+// lane k keeps the word of row 32 c + k and stores it once per 32 rows.
+__device__ __forceinline__ void warp_coverage_words(int lo, int hi, int n, uint32_t *dst,
+                                                    size_t stride) {
+  const uint32_t lane = lane_id();
+  const uint32_t span = (uint32_t)max(hi - lo, 0);
+  for (int c = 0; c < n; c += 32) {
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const uint32_t bb = __ballot_sync(0xffffffffu, (uint32_t)(c + k - lo) < span);
+      if (lane == (uint32_t)k) mine = bb;
+    }
+    if (c + (int)lane < n) dst[(size_t)(c + lane) * stride] = mine;
+  }
+}
+
 // One warp writes a tile's list from coverage bitmasks over depth ranks: the ranks r < 32 words
 // whose bit is set in both the tile row's and the tile column's mask, ascending, as base + r,
 // to lists[off ..]. Each lane takes four consecutive words per step (one 128-bit load per

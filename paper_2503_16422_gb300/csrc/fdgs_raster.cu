@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kBlock) k_preprocess(PreArgs a) {
 // tile counts (key offsets) + per-tile coverage counts as a 2D difference array (four
 // atomics per Gaussian; k_tile_scan integrates it).
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 4)
 k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ nv_dev,
               const float *__restrict__ rec, float *__restrict__ rec_sorted,
               uint32_t *__restrict__ offsets, uint64_t *status, uint32_t *ctr, uint32_t *err,
@@ -154,14 +154,8 @@ k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ 
         tile_rect(src[R_U], src[R_V], src[R_RADIUS], gx, gy, x0, y0, x1, y1);
       }
       const uint32_t word = r >> 5;
-      for (int y = 0; y < gy; ++y) {
-        const uint32_t b = __ballot_sync(0xffffffffu, y >= y0 && y < y1);
-        if (lane == (y & 31)) rowmask[(size_t)y * mask_words + word] = b;
-      }
-      for (int x = 0; x < gx; ++x) {
-        const uint32_t b = __ballot_sync(0xffffffffu, x >= x0 && x < x1);
-        if (lane == (x & 31)) colmask[(size_t)x * mask_words + word] = b;
-      }
+      warp_coverage_words(y0, y1, gy, rowmask + word, mask_words);
+      warp_coverage_words(x0, x1, gx, colmask + word, mask_words);
     }
     if (r < nv) {
       const uint32_t id = (uint32_t)sorted[r];
