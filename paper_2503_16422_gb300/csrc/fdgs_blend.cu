@@ -30,6 +30,35 @@ k_blend(BlendArgs a, const K *__restrict__ keys, uint32_t rmask) {
   blend_tile<K, FW, kWeights, kCount>(bt, keys, rmask, sm);
 }
 
+// Sums of eight per-lane values over the warp by a transposed butterfly: at offsets 16, 8
+// and 4 each lane keeps half of its partial sums and adds its partner's copy of them (7
+// shuffles for 8 values instead of 40), then offsets 2 and 1 finish one sum per lane. Lane L
+// ends with the full sum of value fi = 4 ((L >> 4) & 1) + 2 ((L >> 3) & 1) + ((L >> 2) & 1),
+// so lanes 0, 4, ..., 28 hold the eight sums.
+__device__ __forceinline__ float warp_sum8_transposed(const float v[8], int &fi) {
+  const int lane = (int)lane_id();
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  float w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = h16 ? v[i] : v[i + 4];
+    const float keep = h16 ? v[i + 4] : v[i];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float x[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h8 ? w[i] : w[i + 2];
+    const float keep = h8 ? w[i + 2] : w[i];
+    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float y = (h4 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, h4 ? x[0] : x[1], 4);
+  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  y += __shfl_xor_sync(0xffffffffu, y, 1);
+  fi = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
+  return y;
+}
+
 // Reverse replay of each tile list from the largest n_contrib down to 0, one pixel per
 // lane, with the warp-footprint culling of the forward (a culled Gaussian was skipped by
 // every pixel of the footprint). Transmittance is recovered as T_i = T_{i+1} / (1 - alpha_i).
@@ -140,14 +169,12 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
           }
         }
         if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-          for (int f = 0; f < 9; ++f) g[f] = warp_sum(g[f]);
-          if (lane == 0) {
-            float *dst = a.g2d + (size_t)s_rk[jj] * 9;
-#pragma unroll
-            for (int f = 0; f < 9; ++f)
-              if (g[f] != 0.f) atomicAdd(&dst[f], g[f]);
-          }
+          float *dst = a.g2d + (size_t)s_rk[jj] * 9;
+          int fi;
+          const float s8 = warp_sum8_transposed(g, fi);   // g[0..7]: lane owns sum fi
+          const float s9 = warp_sum(g[8]);
+          if ((lane & 3) == 0 && s8 != 0.f) atomicAdd(&dst[fi], s8);
+          if (lane == 4 && s9 != 0.f) atomicAdd(&dst[8], s9);
         }
       }
     }
