@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
       dst[0] = make_float4(a0.x, a0.y, qa, qb);
       dst[1] = make_float4(qc, log2f(a1.y), a1.z, a1.w);
       dst[2] = make_float4(a2.x, -qb / (2.f * qa), -qb / (2.f * qc), a2.z);
-      dst[3] = make_float4(a0.z, a0.w, a1.x, a1.y);
+      dst[3] = make_float4(a0.z, a0.w, a1.x, 1.f / a1.y);
       tile_rect(a0.x, a0.y, a2.z, q.cam.gx, q.cam.gy, x0, y0, x1, y1);
       tighten_rect(a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, x0, y0, x1, y1);
       if (x1 > x0 && y1 > y0) {

@@ -71,7 +71,7 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
   __shared__ __align__(16) float4 s_g0[kB];   // u, v, a2, b2
   __shared__ __align__(16) float4 s_g1[kB];   // c2, lga, r, g
   __shared__ __align__(16) float4 s_g2[kB];   // b, kx, ky, radius
-  __shared__ __align__(16) float4 s_g3[kB];   // A, B, C, a
+  __shared__ __align__(16) float4 s_g3[kB];   // A, B, C, 1/a
   __shared__ uint32_t s_rk[kB];
   __shared__ uint32_t s_max;
   const int tile = blockIdx.x;
@@ -144,21 +144,24 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
             contrib = true;
             const float cb = s_g2[jj].x;
             const float om = 1.f - alpha;
-            T = T / om;
+            // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp, far inside the
+            // gradient tolerance, and replaces three IEEE divisions per hit
+            const float iom = __fdividef(1.f, om);
+            T = T * iom;
             const float wgt = alpha * T;
             acc0 = last_a * lc0 + (1.f - last_a) * acc0;
             acc1 = last_a * lc1 + (1.f - last_a) * acc1;
             acc2 = last_a * lc2 + (1.f - last_a) * acc2;
             float dLda = (g1.z - acc0) * dL0 + (g1.w - acc1) * dL1 + (cb - acc2) * dL2;
-            dLda = dLda * T - Tf / om * bg_dot;
+            dLda = dLda * T - Tf * iom * bg_dot;
             g[6] = wgt * dL0;
             g[7] = wgt * dL1;
             g[8] = wgt * dL2;
             last_a = alpha;
             lc0 = g1.z; lc1 = g1.w; lc2 = cb;
             if (raw < kAlphaMax) {
-              const float4 g3 = s_g3[jj];          // A, B, C, a
-              g[5] = raw / g3.w * dLda;            // d alpha / d a = exp(power)
+              const float4 g3 = s_g3[jj];          // A, B, C, 1/a
+              g[5] = raw * g3.w * dLda;            // d alpha / d a = exp(power)
               const float gp = alpha * dLda;       // d alpha / d power = alpha
               g[0] = gp * (-g3.x * dx - g3.y * dy);
               g[1] = gp * (-g3.z * dy - g3.y * dx);

@@ -154,7 +154,7 @@ __device__ __forceinline__ void tile_rect(float u, float v, float r, int gx, int
 // [0..3]  u, v, a2 = -A/2 log2(e), b2 = -B log2(e)       (image centre, scaled conic)
 // [4..7]  c2 = -C/2 log2(e), lga = log2(a), r, g        (a = sigmoid(o) p(t))
 // [8..11] b, kx = -b2 / (2 a2), ky = -b2 / (2 c2), radius
-// [12..15] A, B, C, a                                   (raw conic and opacity, backward)
+// [12..15] A, B, C, 1/a                                 (raw conic, inverse opacity: backward)
 constexpr int kRecS = 16;
 constexpr int kRecSRadius = 11;
 // Footprint culling margin (log2 units): a Gaussian is culled for a pixel footprint only if

@@ -167,7 +167,7 @@ k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ 
       dst[0] = make_float4(a0.x, a0.y, qa, qb);
       dst[1] = make_float4(qc, log2f(a1.y), a1.z, a1.w);
       dst[2] = make_float4(a2.x, -qb / (2.f * qa), -qb / (2.f * qc), a2.z);
-      dst[3] = make_float4(a0.z, a0.w, a1.x, a1.y);
+      dst[3] = make_float4(a0.z, a0.w, a1.x, 1.f / a1.y);
       cnt = (uint32_t)a2.w;
       int x0, y0, x1, y1;
       tile_rect(a0.x, a0.y, a2.z, gx, gy, x0, y0, x1, y1);
