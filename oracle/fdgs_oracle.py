@@ -14,6 +14,8 @@ Method steps and where they come from:
   * marginal temporal weight p_i(t), alpha ... Sec. 3, Eq. 3
   * depth-sorted front-to-back compositing ... Sec. 3, Eq. 2
   * spatial score, temporal variation score, pruning ... Sec. 4.2.1, Eqs. 4-7
+  * key-frame masks from the training views .. Sec. 4.2.2 ("Key-frame based Temporal
+    Filtering"); active ratio and activation IoU ... Sec. 4.1 ("Inactive Gaussians")
 The paper leaves the projection, thresholds and colour model to the 3DGS/4DGS renderer it
 builds on; the readings used for those are listed where they are used (constants below).
 
@@ -473,6 +475,56 @@ def variation_scores(scene, cams, ts, reading="R1", return_parts=False):
     if return_parts:
         return S.numpy(), dict(gamma=gamma.numpy(), spatial=SS.numpy(), ftsum=FT.numpy())
     return S.numpy()
+
+
+# ----------------------------------------------------------------------------------------
+# Key-frame masks (Sec. 4.2.2, "Key-frame based Temporal Filtering") and the active-set
+# metrics of Sec. 4.1 ("Inactive Gaussians")
+# ----------------------------------------------------------------------------------------
+
+def contributing(P: Params, cam, t):
+    """Visibility mask m_{i,j} of one view at time t, "obtained by Eq. 2": the Gaussians that
+    are blended in at least one pixel (alpha >= 1/255 and before the pixel's stop). A blended
+    entry has weight alpha*T >= (1/255)(1e-4) > 0, so this is w_i = sum alpha_i T_i > 0.
+    Rendered without the temporal filter (the masks are what the filter later reads)."""
+    with torch.no_grad():
+        w = render(P, cam, float(t), None, weights=True)["w_sum"]
+    return (w > 0).numpy()
+
+
+def build_keyframe_masks(scene, cams, key_times):
+    """For each key-frame time t_i, the union over the training views j of m_{i,j}, packed
+    LSB-first (bit g of row i is bit g % 8 of byte g // 8): uint8 [n_key][ceil(N/8)], the
+    layout the mask gate reads."""
+    P = Params.from_scene(scene)
+    n = P.mean4.shape[0]
+    rows = []
+    for t in key_times:
+        m = np.zeros(n, bool)
+        for cam in cams:
+            m |= contributing(P, cam, t)
+        rows.append(np.packbits(m, bitorder="little"))
+    if not rows:
+        return np.zeros((0, (n + 7) // 8), np.uint8)
+    return np.stack(rows)
+
+
+def mask_row_bools(row, n):
+    """Unpacked active flags [n] of one packed mask row."""
+    return np.unpackbits(np.asarray(row, np.uint8), bitorder="little")[:n].astype(bool)
+
+
+def active_ratio(row, n):
+    """Active ratio (Sec. 4.1): active Gaussians over all views at one moment / all Gaussians."""
+    return float(mask_row_bools(row, n).sum()) / max(n, 1)
+
+
+def activation_iou(row_a, row_b, n):
+    """Activation IoU (Sec. 4.1): |A and B| / |A or B| of two active sets (1 for two empty
+    sets)."""
+    a, b = mask_row_bools(row_a, n), mask_row_bools(row_b, n)
+    union = int((a | b).sum())
+    return 1.0 if union == 0 else float((a & b).sum()) / union
 
 
 def keep_set(scores, prune_ratio=0.8):

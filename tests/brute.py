@@ -21,10 +21,11 @@ def tile_covered(u, r, tile_index):
     return (u - r < lo + 16) and (lo + 1 <= u + r)
 
 
-def composite_pixels(mean2d, conic, a, rgb, depth, radius, visible, W, H):
+def composite_pixels(mean2d, conic, a, rgb, depth, radius, visible, W, H, blended=None):
     """Per-pixel front-to-back compositing over all visible Gaussians whose rectangle covers
     the pixel's tile, in (depth, id) order. Returns image [3,H,W], T [H,W], n_contrib [H,W]
-    (1 + position in the candidate list of the last blended Gaussian)."""
+    (1 + position in the candidate list of the last blended Gaussian). If ``blended`` is a
+    set, the ids blended at one pixel at least are added to it."""
     n = len(a)
     img = np.zeros((3, H, W))
     Tout = np.ones((H, W))
@@ -57,6 +58,8 @@ def composite_pixels(mean2d, conic, a, rgb, depth, radius, visible, W, H):
                 C += np.asarray(rgb[i]) * alpha * T
                 T = nT
                 last = pos
+                if blended is not None:
+                    blended.add(i)
             img[:, py, px] = C
             Tout[py, px] = T
             nc[py, px] = last
