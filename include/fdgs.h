@@ -208,6 +208,21 @@ int fdgs_batch_autotune(fdgs_scene *scene, const fdgs_camera *cams, const float 
 int fdgs_batch_info(fdgs_scene *scene, float *latency_ms, int n, int *footprint,
                     int *ctas_per_sm, float *stage_ms);
 
+/*
+ * Key-frame masks (Sec. 4.2.2, "Key-frame based Temporal Filtering"): for each key-frame time
+ * key_times[k] (host array), renders the n_cam training views (host array of cameras) without
+ * the filter and marks every Gaussian that takes part in some pixel's compositing in one view:
+ * blended there (alpha >= 1/255 before the pixel's stop, a positive blend weight) or the
+ * entry whose alpha would take T below 1e-4 (it ends that pixel's list, so a filter without it
+ * would change the pixel). The union over the views is
+ * row k of bits_out_dev, [n_key][ceil(n/8)] bytes on the device, bit i of row k = bit i % 8 of
+ * byte i / 8: the layout fdgs_set_active_mask takes. Stream-ordered, asynchronous.
+ * FDGS_ERR_INVALID on bad arguments.
+ */
+int fdgs_build_keyframe_masks(fdgs_scene *scene, const fdgs_camera *cams, int n_cam,
+                              const float *key_times, int n_key, uint8_t *bits_out_dev,
+                              fdgs_stream stream);
+
 /* Last batch: visible Gaussians and tile-list entries summed over its requests. The batched
  * lists use, per Gaussian, the 3-sigma tile square intersected with the tiles its
  * alpha >= 1/255 ellipse can reach, so n_keys is at most the per-request renders' total

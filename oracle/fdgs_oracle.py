@@ -308,21 +308,23 @@ def tile_list(pre, tile_id):
 # Front-to-back compositing of one tile (Eq. 2, Eq. 3)
 # ----------------------------------------------------------------------------------------
 
-def blend_tile(pre, ids, px, py):
+def blend_tile(pre, ids, px, py, return_stop=False):
     """Composite the tile list ``ids`` at pixel coordinates (px, py) [P].
 
     Per pixel, entries in list order: power = -1/2 d^T Sigma_2D^-1 d with d = mean2D - pixel;
     skip when power > 0; alpha = min(0.99, a exp(power)); skip when alpha < 1/255; if
     T (1 - alpha) < 1e-4 stop before blending this entry; else C += c alpha T,
     T <- T (1 - alpha). Returns colour [P,3], T_final [P], n_contrib [P] (1 + list position
-    of the last blended entry), and the blend weights alpha*T [P,L] (zero where not blended).
+    of the last blended entry), and the blend weights alpha*T [P,L] (zero where not blended);
+    with ``return_stop``, also the list position of the entry that stopped each pixel [P] (L
+    where the list ran out).
     """
     P_ = px.shape[0]
     L = len(ids)
     if L == 0:
-        z = torch.zeros(P_, dtype=F64)
-        return (torch.zeros(P_, 3, dtype=F64), torch.ones(P_, dtype=F64),
-                torch.zeros(P_, dtype=torch.long), torch.zeros(P_, 0, dtype=F64))
+        out = (torch.zeros(P_, 3, dtype=F64), torch.ones(P_, dtype=F64),
+               torch.zeros(P_, dtype=torch.long), torch.zeros(P_, 0, dtype=F64))
+        return out + (torch.zeros(P_, dtype=torch.long),) if return_stop else out
     idx = torch.as_tensor(ids, dtype=torch.long)
     m2 = pre["mean2d"][idx]
     con = pre["conic"][idx]
@@ -349,6 +351,8 @@ def blend_tile(pre, ids, px, py):
     T_final = torch.prod(one_minus, dim=1)
     with torch.no_grad():
         last = torch.where(blended, pos + 1, torch.zeros_like(pos)).max(dim=1).values
+    if return_stop:
+        return color, T_final, last, w, first_stop
     return color, T_final, last, w
 
 
@@ -484,12 +488,26 @@ def variation_scores(scene, cams, ts, reading="R1", return_parts=False):
 
 def contributing(P: Params, cam, t):
     """Visibility mask m_{i,j} of one view at time t, "obtained by Eq. 2": the Gaussians that
-    are blended in at least one pixel (alpha >= 1/255 and before the pixel's stop). A blended
-    entry has weight alpha*T >= (1/255)(1e-4) > 0, so this is w_i = sum alpha_i T_i > 0.
+    take part in some pixel's compositing, i.e. blended there (alpha >= 1/255 before the
+    pixel's stop; its weight alpha*T is then > 0) or the entry whose alpha would take T below
+    the stop (it ends that pixel's list: without it the pixel would go on compositing).
     Rendered without the temporal filter (the masks are what the filter later reads)."""
+    n = P.mean4.shape[0]
+    mark = np.zeros(n, bool)
     with torch.no_grad():
-        w = render(P, cam, float(t), None, weights=True)["w_sum"]
-    return (w > 0).numpy()
+        pre = preprocess(P, cam, float(t), None)
+        gx, gy = pre["grid"]
+        offs, ids = tile_lists(pre)
+        for tid in range(gx * gy):
+            tl = np.asarray(ids[offs[tid]:offs[tid + 1]])
+            if len(tl) == 0:
+                continue
+            px, py = tile_pixels(tid, gx, cam.width, cam.height)
+            _, _, _, w, stop = blend_tile(pre, tl, px.to(F64), py.to(F64), return_stop=True)
+            mark[tl[(w > 0).any(dim=0).numpy()]] = True
+            s_ = stop.numpy()
+            mark[tl[s_[s_ < len(tl)]]] = True
+    return mark
 
 
 def build_keyframe_masks(scene, cams, key_times):

@@ -89,12 +89,13 @@ struct Workspace {
   Buf scratch;                   // sort scratch
   Buf g2d;                       // f32[n][9] backward accumulators
   Buf wsum;                      // f32[n] per-rank blend weights (score pass)
+  Buf stopmark;                  // u32[n] per-rank "stopped a pixel" flags (with wsum)
   Buf diff;                      // i32[gy + 1][gx + 1] tile-coverage difference array
   Buf rowmask, colmask;          // u32 coverage bitmasks by depth rank per tile row / column
   ~Workspace() {
     Buf *all[] = {&ctr, &pre_status, &scan_status, &rec, &rec_sorted, &vis[0], &vis[1],
                   &offsets, &flags, &keys[0], &keys[1], &ranges, &Tf, &nc, &scratch, &g2d,
-                  &wsum, &diff, &rowmask, &colmask};
+                  &wsum, &stopmark, &diff, &rowmask, &colmask};
     for (Buf *b : all) b->release();
     if (hctr) cudaFreeHost(hctr);
   }
@@ -170,7 +171,7 @@ struct fdgs_scene {
   std::set<fdgs_frame *> live;
   Buf status;     // u32 device error bits
   Buf aux[6];     // score pass / keep-set buffers: 0 keys, 1 gamma, 2 sort scratch,
-                  // 3 device scalar, 4 score-pass image
+                  // 3 device scalar, 4 score-pass image, 5 key-frame mask word row
   int prof = 0;   // profiling flags (fdgs_profile_enable)
   cudaEvent_t ev[FDGS_PROFILE_STAGES + 1] = {};
   Buf evals;      // u64[2] blend evaluations and culling tests
@@ -293,7 +294,10 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   TRY(grow(ws.Tf, pixels * 4));
   TRY(grow(ws.nc, pixels * 4));
   TRY(grow(ws.scratch, sort_scratch_bytes(n1, 32)));
-  if (want_wsum) TRY(grow(ws.wsum, n1 * 4));
+  if (want_wsum) {
+    TRY(grow(ws.wsum, n1 * 4));
+    TRY(grow(ws.stopmark, n1 * 4));
+  }
 
   const bool use_mask = use_mask_override && opts && opts->use_mask && s->n_key > 0;
   const uint32_t *ml = nullptr, *mr = nullptr;
@@ -369,7 +373,10 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   TRY(grow(ws.keys[0], k1 * kb));
   if (!use_masks) TRY(grow(ws.keys[1], k1 * kb));
   TRY(grow(ws.scratch, std::max(sort_scratch_bytes(n1, 32), sort_scratch_bytes(k1, tb))));
-  if (want_wsum) CK(cudaMemsetAsync(ws.wsum.p, 0, n1 * 4, st));
+  if (want_wsum) {
+    CK(cudaMemsetAsync(ws.wsum.p, 0, n1 * 4, st));
+    CK(cudaMemsetAsync(ws.stopmark.p, 0, n1 * 4, st));
+  }
   const uint32_t rmask = (uint32_t)((1ull << rb) - 1);
   BlendArgs ba;
   ba.ranges = ws.ranges.as<uint2>();
@@ -380,6 +387,7 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   ba.T_final = ws.Tf.as<float>();
   ba.n_contrib = ws.nc.as<uint32_t>();
   ba.w_sum = want_wsum ? ws.wsum.as<float>() : nullptr;
+  ba.stop_mark = want_wsum ? ws.stopmark.as<uint32_t>() : nullptr;
   ba.evals = count ? s->evals.as<unsigned long long>() : nullptr;
   if (prof) CK(cudaEventRecord(s->ev[4], st));   // ev[3] -> ev[4]: the host synchronisation
   // tile ranges and the tile sort's digit offsets, straight from the coverage counts
@@ -975,6 +983,40 @@ int fdgs_batch_info(fdgs_scene *s, float *latency_ms, int n, int *footprint,
     for (int i = 0; i < std::min(n, (int)p.lat_ms.size()); ++i) latency_ms[i] = p.lat_ms[i];
   if (footprint) *footprint = p.footprint;
   if (ctas_per_sm) *ctas_per_sm = p.ctas;
+  return FDGS_OK;
+}
+
+int fdgs_build_keyframe_masks(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
+                              const float *key_times, int n_key, uint8_t *bits_out_dev,
+                              fdgs_stream stream) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (n_cam < 0 || n_key < 0 || (n_key > 0 && (!key_times || !bits_out_dev)) ||
+      (n_cam > 0 && !cams))
+    return fail(FDGS_ERR_INVALID, "bad key-frame mask arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t N = (uint32_t)s->d.n;
+  const uint32_t nbytes = (N + 7) / 8, words = (N + 31) / 32;
+  if (n_key == 0) return FDGS_OK;
+  CK(cudaMemsetAsync(bits_out_dev, 0, (size_t)n_key * nbytes, st));
+  if (N == 0 || n_cam == 0) return FDGS_OK;
+  TRY(grow(s->aux[5], (size_t)words * 4));
+  uint32_t *row = s->aux[5].as<uint32_t>();
+  fdgs_render_opts o{};
+  o.use_mask = 0;   // the masks are built from unfiltered renders
+  for (int k = 0; k < n_key; ++k) {
+    CK(cudaMemsetAsync(row, 0, (size_t)words * 4, st));
+    for (int ic = 0; ic < n_cam; ++ic) {
+      Workspace &ws = s->main;
+      TRY(grow(s->aux[4], (size_t)cams[ic].width * cams[ic].height * 12));
+      FrameMeta m;
+      TRY(render_impl(s, ws, &cams[ic], key_times[k], &o, s->aux[4].as<float>(), false, true,
+                      false, m, st));
+      launch_mark_contributors(m.sorted, ws.ctr.as<uint32_t>() + C_NVIS, m.nv,
+                               ws.wsum.as<float>(), ws.stopmark.as<uint32_t>(), row, st);
+    }
+    launch_pack_mask_row(row, nbytes, bits_out_dev + (size_t)k * nbytes, st);
+  }
+  CK(cudaGetLastError());
   return FDGS_OK;
 }
 

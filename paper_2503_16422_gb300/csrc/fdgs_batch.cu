@@ -389,6 +389,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_persist(BatchDev b) {
     bt.bg1 = q.bg[1];
     bt.bg2 = q.bg[2];
     bt.w_sum = nullptr;
+    bt.stop_mark = nullptr;
     bt.evals = b.evals;
     blend_tile<uint32_t, FW, false, kCount>(bt, b.lists, 0xFFFFFFFFu, sm);
     __syncthreads();

@@ -26,6 +26,7 @@ k_blend(BlendArgs a, const K *__restrict__ keys, uint32_t rmask) {
   bt.bg1 = a.bg[1];
   bt.bg2 = a.bg[2];
   bt.w_sum = a.w_sum;
+  bt.stop_mark = a.stop_mark;
   bt.evals = a.evals;
   blend_tile<K, FW, kWeights, kCount>(bt, keys, rmask, sm);
 }

@@ -67,6 +67,7 @@ struct BlendTile {
   uint32_t *n_contrib;         // [H][W]
   float bg0, bg1, bg2;
   float *w_sum;                // per-rank weights (score pass) or null
+  uint32_t *stop_mark;         // per-rank flag: the entry stopped a pixel (with w_sum)
   unsigned long long *evals;   // [2] evaluations, culling tests (profiling) or null
 };
 
@@ -185,6 +186,8 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
             const float nT = T * (1.f - alpha);
             if (nT < kTStop) {
               done = true;
+              // the entry ends this pixel's list: the key-frame masks keep it
+              if (kWeights) bt.stop_mark[sm.rk[st][__float_as_int(sm.h2[warp][k].y)]] = 1u;
             } else {
               const float2 h2 = sm.h2[warp][k];
               w = alpha * T;

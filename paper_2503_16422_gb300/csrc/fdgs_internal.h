@@ -72,6 +72,7 @@ struct BlendArgs {
   float *T_final;      // [H][W]
   uint32_t *n_contrib; // [H][W]
   float *w_sum;        // optional [nv] per-rank blend-weight sums (score pass)
+  uint32_t *stop_mark; // with w_sum: [nv] per-rank flag, set where the entry stopped a pixel
   unsigned long long *evals;  // optional evaluation counter (profiling)
 };
 template <typename K>
@@ -120,6 +121,12 @@ void launch_score_accumulate(const uint64_t *sorted, const uint32_t *nv_dev, uin
                              const float4 *ql, const float4 *qr, const float *gamma, float t,
                              float *score, cudaStream_t st);
 void launch_score_keys(const float *score, uint32_t n, uint64_t *keys, cudaStream_t st);
+// key-frame masks: row[id / 32] |= bit id % 32 for visible ranks blended somewhere
+// (w_sum > 0) or that stopped a pixel (stop_mark); rows packed into LSB-first bytes
+void launch_mark_contributors(const uint64_t *sorted, const uint32_t *nv_dev, uint32_t nv_cap,
+                              const float *w_sum, const uint32_t *stop_mark, uint32_t *row,
+                              cudaStream_t st);
+void launch_pack_mask_row(const uint32_t *row, uint32_t nbytes, uint8_t *out, cudaStream_t st);
 void launch_keep_from_sorted(const uint64_t *sorted, uint32_t n, uint32_t n_drop,
                              uint8_t *keep, cudaStream_t st);
 

@@ -90,6 +90,28 @@ __global__ void k_score_accumulate(const uint64_t *__restrict__ sorted,
   }
 }
 
+// Visibility mask of one view (Sec. 4.2.2): every visible rank blended at one pixel at least
+// (positive blend weight) or that stopped a pixel sets its Gaussian's bit in the word row.
+__global__ void k_mark_contributors(const uint64_t *__restrict__ sorted,
+                                    const uint32_t *__restrict__ nv_dev,
+                                    const float *__restrict__ w_sum,
+                                    const uint32_t *__restrict__ stop_mark, uint32_t *row) {
+  const uint32_t nv = *nv_dev;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
+    if (!(w_sum[r] > 0.f) && !stop_mark[r]) continue;
+    const uint32_t id = (uint32_t)sorted[r];
+    atomicOr(&row[id >> 5], 1u << (id & 31));
+  }
+}
+
+// Word row -> packed bytes, LSB first: byte b holds bits 8b .. 8b + 7.
+__global__ void k_pack_mask_row(const uint32_t *__restrict__ row, uint32_t nbytes,
+                                uint8_t *__restrict__ out) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nbytes;
+       b += gridDim.x * blockDim.x)
+    out[b] = (uint8_t)(row[b >> 2] >> ((b & 3) * 8));
+}
+
 __global__ void k_score_keys(const float *__restrict__ score, uint32_t n, uint64_t *keys) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     keys[i] = ((uint64_t)__float_as_uint(score[i]) << 32) | i;
@@ -138,6 +160,18 @@ void launch_score_accumulate(const uint64_t *sorted, const uint32_t *nv_dev, uin
   if (nv_cap == 0) return;
   k_score_accumulate<<<grid_for(nv_cap), kB, 0, st>>>(sorted, nv_dev, w_sum, mean4, ls4, ql, qr,
                                                       gamma, t, score);
+}
+
+void launch_mark_contributors(const uint64_t *sorted, const uint32_t *nv_dev, uint32_t nv_cap,
+                              const float *w_sum, const uint32_t *stop_mark, uint32_t *row,
+                              cudaStream_t st) {
+  if (nv_cap == 0) return;
+  k_mark_contributors<<<grid_for(nv_cap), kB, 0, st>>>(sorted, nv_dev, w_sum, stop_mark, row);
+}
+
+void launch_pack_mask_row(const uint32_t *row, uint32_t nbytes, uint8_t *out, cudaStream_t st) {
+  if (nbytes == 0) return;
+  k_pack_mask_row<<<grid_for(nbytes), kB, 0, st>>>(row, nbytes, out);
 }
 
 void launch_score_keys(const float *score, uint32_t n, uint64_t *keys, cudaStream_t st) {

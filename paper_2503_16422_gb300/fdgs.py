@@ -83,6 +83,8 @@ _SIGNATURES = {
                         ctypes.POINTER(ctypes.c_float)],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
     "fdgs_batch_counts": [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
+    "fdgs_build_keyframe_masks": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P, _P],
 }
 PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "tile_scan", "emit",
                   "tile_sort", "blend")
@@ -342,6 +344,18 @@ class Scene:
                                     st))
         return dict(latency_ms=list(lat)[:n], footprint=fp.value, ctas_per_sm=ctas.value,
                     stage_ms=dict(zip(BATCH_STAGES, list(st))))
+
+    def build_keyframe_masks(self, cams, key_times, out=None, stream=None):
+        """Key-frame masks from the training views ``cams`` at ``key_times``: uint8
+        [n_key][ceil(n/8)] on the device, in the layout ``set_active_mask`` takes."""
+        carr = (fdgs_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
+        tarr = (ctypes.c_float * max(len(key_times), 1))(*[float(t) for t in key_times])
+        if out is None:
+            out = torch.empty((len(key_times), (self.n + 7) // 8), dtype=torch.uint8,
+                              device=self.device)
+        check(lib().fdgs_build_keyframe_masks(self.handle, carr, len(cams), tarr,
+                                              len(key_times), _ptr(out), _stream(stream)))
+        return out
 
     def batch_counts(self):
         """Visible Gaussians and tile-list entries of the last batch, over all requests."""

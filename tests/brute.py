@@ -21,11 +21,13 @@ def tile_covered(u, r, tile_index):
     return (u - r < lo + 16) and (lo + 1 <= u + r)
 
 
-def composite_pixels(mean2d, conic, a, rgb, depth, radius, visible, W, H, blended=None):
+def composite_pixels(mean2d, conic, a, rgb, depth, radius, visible, W, H, blended=None,
+                     stoppers=None):
     """Per-pixel front-to-back compositing over all visible Gaussians whose rectangle covers
     the pixel's tile, in (depth, id) order. Returns image [3,H,W], T [H,W], n_contrib [H,W]
-    (1 + position in the candidate list of the last blended Gaussian). If ``blended`` is a
-    set, the ids blended at one pixel at least are added to it."""
+    (1 + position in the candidate list of the last blended Gaussian). If ``blended`` /
+    ``stoppers`` are sets, the ids blended at one pixel at least / that stopped a pixel are
+    added to them."""
     n = len(a)
     img = np.zeros((3, H, W))
     Tout = np.ones((H, W))
@@ -54,6 +56,8 @@ def composite_pixels(mean2d, conic, a, rgb, depth, radius, visible, W, H, blende
                     continue
                 nT = T * (1.0 - alpha)
                 if nT < T_MIN:
+                    if stoppers is not None:
+                        stoppers.add(i)
                     break
                 C += np.asarray(rgb[i]) * alpha * T
                 T = nT

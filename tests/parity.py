@@ -103,3 +103,21 @@ def image_metrics(gpu, ref, tol=1e-3):
 
 def to_np(t):
     return t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else np.asarray(t)
+
+
+def contribution_exempt(P, cam, t, eps=1e-4):
+    """The oracle's visibility mask of one view and the Gaussians whose blended-somewhere
+    status flips when the alpha floor or the stop threshold moves by eps (relative): cases a
+    float32 renderer may decide either way. Returns (mask [N], exempt [N])."""
+    import oracle.fdgs_oracle as om
+    base = oracle.contributing(P, cam, t)
+    ex = np.zeros_like(base)
+    a0, t0 = om.ALPHA_MIN, om.T_STOP
+    try:
+        for fa in (1 - eps, 1 + eps):
+            for ft in (1 - eps, 1 + eps):
+                om.ALPHA_MIN, om.T_STOP = a0 * fa, t0 * ft
+                ex |= oracle.contributing(P, cam, t) != base
+    finally:
+        om.ALPHA_MIN, om.T_STOP = a0, t0
+    return base, ex
