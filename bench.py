@@ -495,6 +495,8 @@ def comparisons(sc, cams, times, flush, stream):
     res["backward"] = backward_timing(sc, cams, times, flush, stream)
     # spatial-temporal variation score pass: 1M Gaussians, 50 timestamps x 4 cameras
     res["variation_score"] = score_timing(stream)
+    # key-frame masks built from 4 training views (Sec. 4.2.2) instead of the 3-sigma recipe
+    res["keyframe_masks_from_views"] = keyframe_mask_timing(sc, cams, times, flush, stream)
     # unpruned 3M scene, single requests
     big = scenes.unpruned_scene()
     kt = scenes.keyframe_times()
@@ -506,6 +508,47 @@ def comparisons(sc, cams, times, flush, stream):
     del big
     torch.cuda.empty_cache()
     return res
+
+
+def keyframe_mask_timing(sc, cams, times, flush, stream, B=64):
+    """Masks of the 50 key-frames from 4 training views on the arc: build time, realised
+    active ratio, activation IoU of key-frame 0 with later ones (Sec. 4.1), and the batched
+    render through them (64 frames at 1352x1014); the scene's synthetic masks are restored."""
+    import torch
+
+    from paper_2503_16422_gb300 import scenes
+    views = [scenes.arc_camera(th, W_FULL, H_FULL) for th in (-10.0, -10.0 / 3, 10.0 / 3, 10.0)]
+    kt = scenes.keyframe_times()
+    sc.build_keyframe_masks(views[:1], kt[:2])       # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    masks = sc.build_keyframe_masks(views, kt)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    rows = np.unpackbits(masks.cpu().numpy(), axis=1, bitorder="little")[:, :sc.n] > 0
+    ratio = rows.mean(axis=1)
+
+    def iou(a, b):
+        u = (a | b).sum()
+        return float((a & b).sum() / u) if u else 1.0
+
+    synthetic = sc.active_mask
+    sc.set_active_mask(masks, kt)
+    outs = [torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device="cuda")
+            for _ in range(B)]
+    steps = [rank_requests(0, 1, B)[0], frame_list(B, 3 * B), frame_list(B, 5 * B)]
+    args = [([cams[k] for k in fr], [float(times[k]) for k in fr]) for fr in steps]
+    sc.render_batch(*args[0], outs=outs)
+    ms, _ = timed_batches(sc, [a for a, _ in args], [b for _, b in args], [outs] * 3, True,
+                          flush, stream)
+    sc.set_active_mask(synthetic, kt)
+    return dict(views=4, key_frames=len(kt), build_s=build_s,
+                build_ms_per_render=build_s * 1e3 / (4 * len(kt)),
+                active_ratio={"min": float(ratio.min()), "median": float(np.median(ratio)),
+                              "max": float(ratio.max())},
+                activation_iou_vs_key0={f"+{6 * d} frames": iou(rows[0], rows[d])
+                                        for d in (1, 3, 10, 49)},
+                batch_fps_through_these_masks=B / (statistics.median(ms) / 1e3))
 
 
 def backward_timing(sc, cams, times, flush, stream, n_frames=6):

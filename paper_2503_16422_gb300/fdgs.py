@@ -345,6 +345,11 @@ class Scene:
         return dict(latency_ms=list(lat)[:n], footprint=fp.value, ctas_per_sm=ctas.value,
                     stage_ms=dict(zip(BATCH_STAGES, list(st))))
 
+    @property
+    def active_mask(self):
+        """The mask bits last given to ``set_active_mask`` (None if cleared)."""
+        return self._mask_hold
+
     def build_keyframe_masks(self, cams, key_times, out=None, stream=None):
         """Key-frame masks from the training views ``cams`` at ``key_times``: uint8
         [n_key][ceil(n/8)] on the device, in the layout ``set_active_mask`` takes."""
