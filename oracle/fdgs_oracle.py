@@ -189,9 +189,40 @@ def camera_f64(cam):
 # Per-Gaussian stage: gate, slice, cull, project (EWA), colour, tile rectangle
 # ----------------------------------------------------------------------------------------
 
-def preprocess(P: Params, cam, t, active=None):
+def tight_tile_rect(mean2d, conic, a, rect):
+    """The alpha-tight tile set (the per-frame option and the batched path): the 3-sigma
+    rectangle ``rect`` [N,4] (xmin, ymin, xmax, ymax) intersected with the tiles of the
+    bounding box of the ellipse d^T Sigma^-1 d <= Q', Q' = 1.001 * 2 ln(255 a) + 0.1, the
+    region where a pixel can take alpha >= 1/255 from the Gaussian, widened for a float32
+    renderer. Half-widths sqrt(Q' Sigma_xx), sqrt(Q' Sigma_yy) with Sigma = conic^-1. An empty
+    result is (0, 0, 0, 0); a degenerate conic keeps the rectangle. Returns (rect, the four
+    box edges in pixels)."""
+    A, B, C = conic.unbind(-1)
+    dc = A * C - B * B
+    Q = 2.0 * torch.log(255.0 * a) * 1.001 + 0.1
+    ok = dc > 0
+    dcs = torch.where(ok, dc, torch.ones_like(dc))
+    Qp = torch.clamp(Q, min=0.0)
+    hx = torch.sqrt(Qp * C / dcs)
+    hy = torch.sqrt(Qp * A / dcs)
+    u, v = mean2d.unbind(-1)
+    edges = torch.stack([u - hx, v - hy, u + hx, v + hy], -1)
+    box = torch.stack([torch.floor(edges[:, 0] / TILE), torch.floor(edges[:, 1] / TILE),
+                       torch.floor(edges[:, 2] / TILE) + 1, torch.floor(edges[:, 3] / TILE) + 1],
+                      -1).long()
+    lo = torch.maximum(rect[:, :2], box[:, :2])
+    hi = torch.minimum(rect[:, 2:], box[:, 2:])
+    out = torch.where(ok[:, None], torch.cat([lo, hi], -1), rect)
+    empty = (Q <= 0) | (out[:, 2] <= out[:, 0]) | (out[:, 3] <= out[:, 1])
+    return torch.where(empty[:, None], torch.zeros_like(out), out), edges
+
+
+def preprocess(P: Params, cam, t, active=None, tile_sets="square"):
     """Per-Gaussian preparation for one (camera, t). Returns a dict of float64 tensors
     (differentiable where the method is) and boolean/int decisions (detached).
+    ``tile_sets``: "square" (the 3DGS-family 3-sigma rectangle, the reference) or "tight"
+    (that rectangle cut to the tiles the alpha >= 1/255 ellipse can reach, see
+    tight_tile_rect; the image is the same, the lists shorter).
 
     Order (Sec. 3 and 4.2.2): mask gate -> 4D covariance -> Eq. 1 slice and p(t) (Eq. 3) ->
     a = sigmoid(o) p(t), culled when a < 1/255 (then alpha < 1/255 everywhere) -> camera
@@ -247,7 +278,17 @@ def preprocess(P: Params, cam, t, active=None):
         pass_near = pass_temporal & (z > cam.znear)
         pass_det = pass_near & (det > 0)
         visible = pass_det & (xmax > xmin) & (ymax > ymin)
-        ntiles = torch.where(visible, (xmax - xmin) * (ymax - ymin), torch.zeros_like(xmax))
+        rect = torch.stack([xmin, ymin, xmax, ymax], -1)
+        rect_tight, tight_edges = None, None
+        if tile_sets == "tight":
+            rect_tight, tight_edges = tight_tile_rect(
+                torch.stack([u, v], -1).detach(),
+                torch.stack([conA, conB, conC], -1).detach(), a.detach(), rect)
+            rect = rect_tight
+        elif tile_sets != "square":
+            raise ValueError("tile_sets must be 'square' or 'tight'")
+        ntiles = torch.where(visible, (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]),
+                             torch.zeros_like(xmax))
     # colour from SH at the view direction of the conditional mean
     eye = -Rv.T @ tv
     dvec = mu3 - eye
@@ -258,8 +299,10 @@ def preprocess(P: Params, cam, t, active=None):
     return dict(active=act, cov4=cov4, mu3=mu3, cov3=cov3, s_tt=s_tt, p=p, sigma=sigma, a=a,
                 xc=xc, depth=z, J=J, cov2=torch.stack([c00, c01, c11], -1), det=det,
                 conic=torch.stack([conA, conB, conC], -1), mean2d=torch.stack([u, v], -1),
-                lam=lam, r3=r3, radius=radius, rect=torch.stack([xmin, ymin, xmax, ymax], -1),
+                lam=lam, r3=r3, radius=radius, rect=rect,
+                rect_square=torch.stack([xmin, ymin, xmax, ymax], -1),
                 rect_edges=torch.stack([xlo_f, ylo_f, xhi_f, yhi_f], -1),
+                tight_edges=tight_edges, tile_sets=tile_sets,
                 pass_mask=pass_mask, pass_temporal=pass_temporal, pass_near=pass_near,
                 pass_det=pass_det, visible=visible, ntiles=ntiles, rgb=rgb, rgb_raw=raw,
                 grid=(gx, gy))
@@ -365,14 +408,14 @@ def tile_pixels(tile_id, gx, W, H):
 
 
 def render(P: Params, cam, t, active=None, tiles=None, bg=(0.0, 0.0, 0.0), weights=False,
-           pre=None):
+           pre=None, tile_sets="square"):
     """Render one frame (or only the tiles listed in ``tiles``).
 
     Returns dict: image [3,H,W] (float64; NaN outside the rendered tiles when ``tiles`` is
     given), T_final [H,W], n_contrib [H,W], lists {tile: ids}, pre, and, with
     ``weights=True``, w_sum [N] = sum over the rendered pixels of alpha_i T_i (Eq. 4)."""
     if pre is None:
-        pre = preprocess(P, cam, t, active)
+        pre = preprocess(P, cam, t, active, tile_sets)
     gx, gy = pre["grid"]
     W, H = cam.width, cam.height
     todo = range(gx * gy) if tiles is None else tiles

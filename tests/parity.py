@@ -54,6 +54,19 @@ def exempt_gaussians(pre, cam, edge_band=1e-3, a_rel=2e-5, z_band=1e-5, r_rel=5e
         near_edge |= inside & _near_multiple(x, 16.0, edge_band)
     near_r = np.abs(r3 - np.round(r3)) <= r_rel * np.maximum(r3, 1.0)
     ex |= live & (near_edge | near_r)
+    if pre.get("tight_edges") is not None:
+        # alpha-tight tile sets: the ellipse box edges against tile boundaries; the float32
+        # half-widths carry a relative error ~1e-6 on top of the u, v error
+        te = pre["tight_edges"].detach().numpy()
+        half = np.maximum(np.abs(te[:, 2] - te[:, 0]), np.abs(te[:, 3] - te[:, 1])) * 0.5
+        band = edge_band + 1e-5 * half
+        near_t = np.zeros(len(a), bool)
+        for k, lim in ((0, W), (1, H), (2, W), (3, H)):
+            x = te[:, k]
+            inside = (x > -16) & (x < lim + 16)
+            r = np.mod(x, 16.0)
+            near_t |= inside & (np.minimum(r, 16.0 - r) <= band)
+        ex |= live & near_t
     return ex
 
 
