@@ -90,6 +90,10 @@ typedef struct {
 typedef struct {
   int use_mask;
   float bg[3];
+  int tile_sets;  /* fdgs_render: 0 = 3-sigma squares (the reference lists), 1 = the squares
+                     cut to the tiles the alpha >= 1/255 ellipse can reach (same image,
+                     shorter lists; fdgs_frame_export then returns these). Batches always
+                     use 1. */
 } fdgs_render_opts;
 
 /* Counts of one rendered frame, for reports and tests. */

@@ -245,11 +245,12 @@ int check_device_errors(fdgs_scene *s, cudaStream_t st) {
 // offsets were written by the tile scan). Returns the buffer holding the sorted keys.
 template <typename K>
 K *emit_and_sort(Workspace &ws, uint32_t nv, uint64_t nkeys, int gx, int gy, int rb, int tb,
-                 uint32_t *ctr, uint32_t *err, cudaEvent_t *ev, cudaStream_t st) {
+                 int tight, uint32_t *ctr, uint32_t *err, cudaEvent_t *ev, cudaStream_t st) {
   K *k0 = ws.keys[0].as<K>(), *k1 = ws.keys[1].as<K>();
   K *out = k0;
   if (nkeys)
-    launch_emit<K>(ws.rec_sorted.as<float>(), ws.offsets.as<uint32_t>(), nv, gx, gy, rb, k0, st);
+    launch_emit<K>(ws.rec_sorted.as<float>(), ws.offsets.as<uint32_t>(), nv, gx, gy, rb, tight,
+                   k0, st);
   if (ev) cudaEventRecord(ev[6], st);
   if (nkeys)
     out = radix_sort<K>(k0, k1, ctr + C_NKEYS_LO, nkeys, rb, tb, ws.scratch.p, st, err, true);
@@ -270,6 +271,7 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   const uint64_t tiles = (uint64_t)gx * gy, pixels = (uint64_t)W * H;
   const uint64_t parts = std::max<uint64_t>(1, (N + 255) / 256);
   const uint64_t n1 = std::max<uint64_t>(N, 1);
+  const int tight = opts && opts->tile_sets == 1;
   TRY(grow(ws.ctr, C_COUNT * 4));
   if (!ws.hctr) CK(cudaMallocHost(&ws.hctr, C_COUNT * 4));
   TRY(grow(ws.pre_status, parts * 8));
@@ -345,7 +347,7 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   launch_gather_scan(sorted, ctr + C_NVIS, N, ws.rec.as<float>(), ws.rec_sorted.as<float>(),
                      ws.offsets.as<uint32_t>(), ws.scan_status.as<uint64_t>(), ctr, err, gx, gy,
                      ws.diff.as<int>(), want_masks ? ws.rowmask.as<uint32_t>() : nullptr,
-                     want_masks ? ws.colmask.as<uint32_t>() : nullptr, mask_words, st);
+                     want_masks ? ws.colmask.as<uint32_t>() : nullptr, mask_words, tight, st);
   if (prof) CK(cudaEventRecord(s->ev[3], st));
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(ws.hctr, ctr, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
@@ -403,10 +405,10 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
     if (prof) CK(cudaEventRecord(s->ev[7], st));
     skeys = ws.keys[0].p;
   } else {
-    skeys = key64 ? (void *)emit_and_sort<uint64_t>(ws, nv, nkeys, gx, gy, rb, tb, ctr, err,
-                                                     prof ? s->ev : nullptr, st)
-                  : (void *)emit_and_sort<uint32_t>(ws, nv, nkeys, gx, gy, rb, tb, ctr, err,
-                                                     prof ? s->ev : nullptr, st);
+    skeys = key64 ? (void *)emit_and_sort<uint64_t>(ws, nv, nkeys, gx, gy, rb, tb, tight, ctr,
+                                                     err, prof ? s->ev : nullptr, st)
+                  : (void *)emit_and_sort<uint32_t>(ws, nv, nkeys, gx, gy, rb, tb, tight, ctr,
+                                                     err, prof ? s->ev : nullptr, st);
   }
   if (key64)
     launch_blend<uint64_t>(ba, (const uint64_t *)skeys, rmask, st);
@@ -1003,6 +1005,7 @@ int fdgs_build_keyframe_masks(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
   uint32_t *row = s->aux[5].as<uint32_t>();
   fdgs_render_opts o{};
   o.use_mask = 0;   // the masks are built from unfiltered renders
+  o.tile_sets = 1;  // same blend decisions as the 3-sigma squares, shorter lists
   for (int k = 0; k < n_key; ++k) {
     CK(cudaMemsetAsync(row, 0, (size_t)words * 4, st));
     for (int ic = 0; ic < n_cam; ++ic) {
@@ -1053,6 +1056,7 @@ int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, cons
   launch_gamma((const float4 *)s->d.logscale4, N, vs, k, s->aux[1].as<float>(), st);
   fdgs_render_opts o{};
   o.use_mask = 0;
+  o.tile_sets = 1;   // same weights as the 3-sigma squares, shorter lists
   int done = 0;
   for (int it = 0; it < n_t; ++it)
     for (int ic = 0; ic < n_cam; ++ic) {

@@ -185,32 +185,8 @@ __global__ void k_seg_compact(BatchDev b) {
   }
 }
 
-// Batched lists are internal (only images leave the batched path), so they may use a tighter
-// tile set than the 3-sigma square of the per-frame lists: a pixel p of the square can only
-// take alpha >= 1/255 from the Gaussian where its exponent reaches log2(1/255), i.e. inside
-// the ellipse d^T Sigma^-1 d <= 2 ln(255 a), d = p - (u, v), whose bounding box has
-// half-widths sqrt(Q Sigma_xx), sqrt(Q Sigma_yy). The box (Q widened by 0.1% + 0.1, far more
-// than the float error of the blend's exponent) is intersected with the square's tiles
-// [x0, x1) x [y0, y1); every (pixel, Gaussian) pair the blend would composite keeps its
-// tile, so images are unchanged. Conic A, B, C = Sigma^-1; a = opacity x temporal weight.
-__device__ __forceinline__ void tighten_rect(float u, float v, float A, float B, float C, float a,
-                                             int &x0, int &y0, int &x1, int &y1) {
-  const float det = A * C - B * B;
-  if (!(det > 0.f)) return;                 // degenerate conic: keep the square
-  const float Q = 2.f * logf(255.f * a) * 1.001f + 0.1f;
-  if (!(Q > 0.f)) {
-    x1 = x0;
-    y1 = y0;
-    return;
-  }
-  const float hx = sqrtf(Q * C / det), hy = sqrtf(Q * A / det);
-  const float inv = 1.f / (float)kTile;
-  x0 = max(x0, (int)floorf((u - hx) * inv));
-  x1 = min(x1, (int)floorf((u + hx) * inv) + 1);
-  y0 = max(y0, (int)floorf((v - hy) * inv));
-  y1 = min(y1, (int)floorf((v + hy) * inv) + 1);
-}
-
+// The batched lists never leave the library, so they always use the alpha-tight tile sets
+// (tighten_rect); images are those of the 3-sigma squares.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
   __shared__ uint32_t s_slot_base[kMaxReq];
@@ -236,7 +212,7 @@ __global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
       dst[0] = make_float4(a0.x, a0.y, qa, qb);
       dst[1] = make_float4(qc, log2f(a1.y), a1.z, a1.w);
       dst[2] = make_float4(a2.x, -qb / (2.f * qa), -qb / (2.f * qc), a2.z);
-      dst[3] = make_float4(a0.z, a0.w, a1.x, 1.f / a1.y);
+      dst[3] = make_float4(a0.z, a0.w, a1.x, a1.y);
       tile_rect(a0.x, a0.y, a2.z, q.cam.gx, q.cam.gy, x0, y0, x1, y1);
       tighten_rect(a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, x0, y0, x1, y1);
       if (x1 > x0 && y1 > y0) {

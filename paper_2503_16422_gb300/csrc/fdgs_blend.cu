@@ -72,7 +72,7 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
   __shared__ __align__(16) float4 s_g0[kB];   // u, v, a2, b2
   __shared__ __align__(16) float4 s_g1[kB];   // c2, lga, r, g
   __shared__ __align__(16) float4 s_g2[kB];   // b, kx, ky, radius
-  __shared__ __align__(16) float4 s_g3[kB];   // A, B, C, 1/a
+  __shared__ __align__(16) float4 s_g3[kB];   // A, B, C, 1/a (from the record's a)
   __shared__ uint32_t s_rk[kB];
   __shared__ uint32_t s_max;
   const int tile = blockIdx.x;
@@ -113,7 +113,9 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
       s_g0[tid] = rp[0];
       s_g1[tid] = rp[1];
       s_g2[tid] = rp[2];
-      s_g3[tid] = rp[3];
+      float4 g3 = rp[3];
+      g3.w = 1.f / g3.w;                      // once per staged entry, not per hit
+      s_g3[tid] = g3;
       s_rk[tid] = r;
     }
     __syncthreads();

@@ -154,7 +154,8 @@ __device__ __forceinline__ void tile_rect(float u, float v, float r, int gx, int
 // [0..3]  u, v, a2 = -A/2 log2(e), b2 = -B log2(e)       (image centre, scaled conic)
 // [4..7]  c2 = -C/2 log2(e), lga = log2(a), r, g        (a = sigmoid(o) p(t))
 // [8..11] b, kx = -b2 / (2 a2), ky = -b2 / (2 c2), radius
-// [12..15] A, B, C, 1/a                                 (raw conic, inverse opacity: backward)
+// [12..15] A, B, C, a                                   (raw conic and opacity: backward, and
+//                                                        the alpha-tight tile sets)
 constexpr int kRecS = 16;
 constexpr int kRecSRadius = 11;
 // Footprint culling margin (log2 units): a Gaussian is culled for a pixel footprint only if
@@ -203,6 +204,32 @@ __device__ __forceinline__ void warp_coverage_words(int lo, int hi, int n, uint3
     }
     if (c + (int)lane < n) dst[(size_t)(c + lane) * stride] = mine;
   }
+}
+
+// Alpha-tight tile set (the batched path always; the per-frame API on request): a pixel p of
+// the 3-sigma square can only take alpha >= 1/255 from the Gaussian where its exponent
+// reaches log2(1/255), i.e. inside
+// the ellipse d^T Sigma^-1 d <= 2 ln(255 a), d = p - (u, v), whose bounding box has
+// half-widths sqrt(Q Sigma_xx), sqrt(Q Sigma_yy). The box (Q widened by 0.1% + 0.1, far more
+// than the float error of the blend's exponent) is intersected with the square's tiles
+// [x0, x1) x [y0, y1); every (pixel, Gaussian) pair the blend would composite keeps its
+// tile, so images are unchanged. Conic A, B, C = Sigma^-1; a = opacity x temporal weight.
+__device__ __forceinline__ void tighten_rect(float u, float v, float A, float B, float C, float a,
+                                             int &x0, int &y0, int &x1, int &y1) {
+  const float det = A * C - B * B;
+  if (!(det > 0.f)) return;                 // degenerate conic: keep the square
+  const float Q = 2.f * logf(255.f * a) * 1.001f + 0.1f;
+  if (!(Q > 0.f)) {
+    x1 = x0;
+    y1 = y0;
+    return;
+  }
+  const float hx = sqrtf(Q * C / det), hy = sqrtf(Q * A / det);
+  const float inv = 1.f / (float)kTile;
+  x0 = max(x0, (int)floorf((u - hx) * inv));
+  x1 = min(x1, (int)floorf((u + hx) * inv) + 1);
+  y0 = max(y0, (int)floorf((v - hy) * inv));
+  y1 = min(y1, (int)floorf((v + hy) * inv) + 1);
 }
 
 // One warp writes a tile's list from coverage bitmasks over depth ranks: the ranks r < 32 words

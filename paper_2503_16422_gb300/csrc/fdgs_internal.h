@@ -42,12 +42,13 @@ struct PreArgs {
 void launch_preprocess(const PreArgs &a, cudaStream_t st);
 
 // rec_sorted is the blend-ready record [nv][16] (see fdgs_common.cuh); diff is the
-// [gy + 1][gx + 1] tile-coverage difference array (zeroed by the caller).
+// [gy + 1][gx + 1] tile-coverage difference array (zeroed by the caller). tight: tile sets
+// cut to the alpha >= 1/255 ellipse (tighten_rect), else the 3-sigma squares.
 void launch_gather_scan(const uint64_t *sorted, const uint32_t *ctr_nvis, uint32_t n_cap,
                         const float *rec, float *rec_sorted, uint32_t *offsets,
                         uint64_t *status, uint32_t *ctr, uint32_t *err, int gx, int gy,
                         int *diff, uint32_t *rowmask, uint32_t *colmask, uint32_t mask_words,
-                        cudaStream_t st);
+                        int tight, cudaStream_t st);
 // Tile lists by coverage bitmasks (rowmask/colmask written by the gather when non-null,
 // [gy or gx][mask_words] words): lists[ranges[t].x ..] = ranks covering tile t, ascending.
 void launch_tile_lists(const uint32_t *rowmask, const uint32_t *colmask, uint32_t mask_words,
@@ -61,7 +62,7 @@ void launch_tile_scan(int *diff, int gx, int gy, int npass, int dbits, uint2 *ra
 
 template <typename K>
 void launch_emit(const float *rec_sorted, const uint32_t *offsets, uint32_t nv, int gx, int gy,
-                 int rb, K *keys, cudaStream_t st);
+                 int rb, int tight, K *keys, cudaStream_t st);
 
 struct BlendArgs {
   const uint2 *ranges;

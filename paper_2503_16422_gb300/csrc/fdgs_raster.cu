@@ -131,7 +131,7 @@ k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ 
               const float *__restrict__ rec, float *__restrict__ rec_sorted,
               uint32_t *__restrict__ offsets, uint64_t *status, uint32_t *ctr, uint32_t *err,
               int gx, int gy, int *__restrict__ diff, uint32_t *__restrict__ rowmask,
-              uint32_t *__restrict__ colmask, uint32_t mask_words) {
+              uint32_t *__restrict__ colmask, uint32_t mask_words, int tight) {
   __shared__ uint32_t s_part;
   __shared__ uint32_t s_wtot[kWarps];
   __shared__ uint64_t s_base;
@@ -145,18 +145,7 @@ k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ 
     if (part >= nparts) break;
     const uint32_t r = part * kBlock + tid;
     uint32_t cnt = 0;
-    if (rowmask) {
-      // coverage bitmasks by depth rank: bit (r & 31) of word r / 32 of tile row y / column x
-      // is set iff the Gaussian of rank r covers that row / column. Each warp owns one word.
-      int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-      if (r < nv) {
-        const float *src = rec + (size_t)((uint32_t)sorted[r]) * kRec;
-        tile_rect(src[R_U], src[R_V], src[R_RADIUS], gx, gy, x0, y0, x1, y1);
-      }
-      const uint32_t word = r >> 5;
-      warp_coverage_words(y0, y1, gy, rowmask + word, mask_words);
-      warp_coverage_words(x0, x1, gx, colmask + word, mask_words);
-    }
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     if (r < nv) {
       const uint32_t id = (uint32_t)sorted[r];
       const float4 *src = reinterpret_cast<const float4 *>(rec + (size_t)id * kRec);
@@ -167,15 +156,26 @@ k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ 
       dst[0] = make_float4(a0.x, a0.y, qa, qb);
       dst[1] = make_float4(qc, log2f(a1.y), a1.z, a1.w);
       dst[2] = make_float4(a2.x, -qb / (2.f * qa), -qb / (2.f * qc), a2.z);
-      dst[3] = make_float4(a0.z, a0.w, a1.x, 1.f / a1.y);
-      cnt = (uint32_t)a2.w;
-      int x0, y0, x1, y1;
+      dst[3] = make_float4(a0.z, a0.w, a1.x, a1.y);
       tile_rect(a0.x, a0.y, a2.z, gx, gy, x0, y0, x1, y1);
-      const int W1 = gx + 1;
-      atomicAdd(&diff[y0 * W1 + x0], 1);
-      atomicAdd(&diff[y0 * W1 + x1], -1);
-      atomicAdd(&diff[y1 * W1 + x0], -1);
-      atomicAdd(&diff[y1 * W1 + x1], 1);
+      if (tight) tighten_rect(a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, x0, y0, x1, y1);
+      if (x1 > x0 && y1 > y0) {
+        cnt = (uint32_t)((x1 - x0) * (y1 - y0));
+        const int W1 = gx + 1;
+        atomicAdd(&diff[y0 * W1 + x0], 1);
+        atomicAdd(&diff[y0 * W1 + x1], -1);
+        atomicAdd(&diff[y1 * W1 + x0], -1);
+        atomicAdd(&diff[y1 * W1 + x1], 1);
+      } else {
+        x0 = y0 = x1 = y1 = 0;
+      }
+    }
+    if (rowmask) {
+      // coverage bitmasks by depth rank: bit (r & 31) of word r / 32 of tile row y / column x
+      // is set iff the Gaussian of rank r covers that row / column. Each warp owns one word.
+      const uint32_t word = r >> 5;
+      warp_coverage_words(y0, y1, gy, rowmask + word, mask_words);
+      warp_coverage_words(x0, x1, gx, colmask + word, mask_words);
     }
     const uint32_t inc = warp_incl_scan(cnt);
     if (lane == 31) s_wtot[warp] = inc;
@@ -333,7 +333,7 @@ k_tile_lists(const uint32_t *__restrict__ rowmask, const uint32_t *__restrict__ 
 template <typename K>
 __global__ void __launch_bounds__(kBlock)
 k_emit(const float *__restrict__ rec_sorted, const uint32_t *__restrict__ offsets, uint32_t nv,
-       int gx, int gy, int rb, K *__restrict__ keys) {
+       int gx, int gy, int rb, int tight, K *__restrict__ keys) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t total_warps = gridDim.x * kWarps;
   for (uint32_t chunk = blockIdx.x * kWarps + warp; (uint64_t)chunk * 32 < nv;
@@ -346,8 +346,18 @@ k_emit(const float *__restrict__ rec_sorted, const uint32_t *__restrict__ offset
       const float rad = rec_sorted[(size_t)r * kRecS + kRecSRadius];
       int x1, y1;
       tile_rect(g0.x, g0.y, rad, gx, gy, x0, y0, x1, y1);
-      w = x1 - x0;
-      cnt = (uint32_t)(w * (y1 - y0));
+      if (tight) {
+        const float4 g3 = *reinterpret_cast<const float4 *>(rec_sorted + (size_t)r * kRecS + 12);
+        tighten_rect(g0.x, g0.y, g3.x, g3.y, g3.z, g3.w, x0, y0, x1, y1);
+      }
+      if (x1 > x0 && y1 > y0) {
+        w = x1 - x0;
+        cnt = (uint32_t)(w * (y1 - y0));
+      } else {
+        x0 = y0 = 0;
+        w = 1;
+        cnt = 0;
+      }
       off = offsets[r];
     }
     const uint32_t nlanes = min(32u, nv - chunk * 32);
@@ -428,14 +438,14 @@ void launch_gather_scan(const uint64_t *sorted, const uint32_t *ctr_nvis, uint32
                         const float *rec, float *rec_sorted, uint32_t *offsets,
                         uint64_t *status, uint32_t *ctr, uint32_t *err, int gx, int gy,
                         int *diff, uint32_t *rowmask, uint32_t *colmask, uint32_t mask_words,
-                        cudaStream_t st) {
+                        int tight, cudaStream_t st) {
   if (n_cap == 0) return;
   const uint64_t parts = (n_cap + kBlock - 1) / kBlock;
   static int grid_cap = 0;
   if (!grid_cap) grid_cap = persistent_grid(k_gather_scan, ~0ull);
   k_gather_scan<<<(int)std::min<uint64_t>(parts, grid_cap), kBlock, 0, st>>>(
       sorted, ctr_nvis, rec, rec_sorted, offsets, status, ctr, err, gx, gy, diff, rowmask,
-      colmask, mask_words);
+      colmask, mask_words, tight);
 }
 
 void launch_tile_scan(int *diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
@@ -456,12 +466,12 @@ void launch_tile_lists(const uint32_t *rowmask, const uint32_t *colmask, uint32_
 
 template <typename K>
 void launch_emit(const float *rec_sorted, const uint32_t *offsets, uint32_t nv, int gx, int gy,
-                 int rb, K *keys, cudaStream_t st) {
+                 int rb, int tight, K *keys, cudaStream_t st) {
   if (nv == 0) return;
   const uint64_t chunks = (nv + 31) / 32;
   const int grid = (int)std::min<uint64_t>((chunks + kWarps - 1) / kWarps,
                                            (uint64_t)num_sms() * 8);
-  k_emit<K><<<grid, kBlock, 0, st>>>(rec_sorted, offsets, nv, gx, gy, rb, keys);
+  k_emit<K><<<grid, kBlock, 0, st>>>(rec_sorted, offsets, nv, gx, gy, rb, tight, keys);
 }
 
 void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st) {
@@ -471,8 +481,8 @@ void launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t st) {
 }
 
 template void launch_emit<uint32_t>(const float *, const uint32_t *, uint32_t, int, int, int,
-                                    uint32_t *, cudaStream_t);
+                                    int, uint32_t *, cudaStream_t);
 template void launch_emit<uint64_t>(const float *, const uint32_t *, uint32_t, int, int, int,
-                                    uint64_t *, cudaStream_t);
+                                    int, uint64_t *, cudaStream_t);
 
 }  // namespace fdgs

@@ -41,7 +41,7 @@ class fdgs_camera(ctypes.Structure):
 
 
 class fdgs_render_opts(ctypes.Structure):
-    _fields_ = [("use_mask", ctypes.c_int), ("bg", ctypes.c_float * 3)]
+    _fields_ = [("use_mask", ctypes.c_int), ("bg", ctypes.c_float * 3), ("tile_sets", ctypes.c_int)]
 
 
 class fdgs_frame_stats(ctypes.Structure):
@@ -139,11 +139,12 @@ def make_camera(cam) -> fdgs_camera:
     return c
 
 
-def _opts(use_mask, bg):
+def _opts(use_mask, bg, tight=False):
     o = fdgs_render_opts()
     o.use_mask = int(bool(use_mask))
     for k in range(3):
         o.bg[k] = float(bg[k])
+    o.tile_sets = int(bool(tight))
     return o
 
 
@@ -284,12 +285,13 @@ class Scene:
             _stream(stream)))
 
     def render(self, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0), keep_frame=False, out=None,
-               stream=None):
-        """Render [3,H,W] float32. With keep_frame=True also returns the Frame."""
+               stream=None, tight=False):
+        """Render [3,H,W] float32. With keep_frame=True also returns the Frame. tight: build
+        the alpha-tight tile sets instead of the 3-sigma squares (same image)."""
         c = make_camera(cam)
         if out is None:
             out = torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.device)
-        o = _opts(use_mask, bg)
+        o = _opts(use_mask, bg, tight)
         fh = ctypes.c_void_p()
         check(lib().fdgs_render(self.handle, ctypes.byref(c), float(t), ctypes.byref(o),
                                 _ptr(out), ctypes.byref(fh) if keep_frame else None,
@@ -414,9 +416,10 @@ class _RenderFn(torch.autograd.Function):
     fdgs_render_backward (hand-written reverse kernels)."""
 
     @staticmethod
-    def forward(ctx, scene, cam, t, use_mask, bg, mean4, logscale4, q_left, q_right,
+    def forward(ctx, scene, cam, t, use_mask, bg, tight, mean4, logscale4, q_left, q_right,
                 opacity_logit, sh):
-        img, frame = scene.render(cam, t, use_mask=use_mask, bg=bg, keep_frame=True)
+        img, frame = scene.render(cam, t, use_mask=use_mask, bg=bg, keep_frame=True,
+                                  tight=tight)
         ctx.scene = scene
         ctx.frame = frame
         return img
@@ -426,14 +429,15 @@ class _RenderFn(torch.autograd.Function):
         scene, frame = ctx.scene, ctx.frame
         grads = scene.render_backward(frame, dL)
         frame.release()
-        return (None, None, None, None, None, *grads.list())
+        return (None, None, None, None, None, None, *grads.list())
 
 
-def render(scene: Scene, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0)):
-    """Differentiable render of ``scene`` (its parameter tensors may require grad)."""
+def render(scene: Scene, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0), tight=False):
+    """Differentiable render of ``scene`` (its parameter tensors may require grad). tight:
+    alpha-tight tile sets (same image and gradients, shorter lists)."""
     p = scene.params
-    return _RenderFn.apply(scene, cam, float(t), use_mask, tuple(bg), p.mean4, p.logscale4,
-                           p.q_left, p.q_right, p.opacity_logit, p.sh)
+    return _RenderFn.apply(scene, cam, float(t), use_mask, tuple(bg), bool(tight), p.mean4,
+                           p.logscale4, p.q_left, p.q_right, p.opacity_logit, p.sh)
 
 
 def version():

@@ -65,7 +65,7 @@ class FineTuner:
 
     def step(self, cam, t, target, use_mask=True):
         """One iteration: L1 loss of the render against ``target``; returns the loss."""
-        img = fdgs.render(self.scene, cam, t, use_mask=use_mask)
+        img = fdgs.render(self.scene, cam, t, use_mask=use_mask, tight=True)
         loss = torch.mean(torch.abs(img - target))
         self.opt.zero_grad(set_to_none=False)
         loss.backward()
