@@ -447,16 +447,16 @@ def comparisons(sc, cams, times, flush, stream):
     res = {}
     fr = frame_list(24, 3)
 
-    def single(scene_obj, masked, frames):
+    def single(scene_obj, masked, frames, tight=False):
         for k in frames[:2]:
-            scene_obj.render(cams[k], float(times[k]), use_mask=masked, out=out)
+            scene_obj.render(cams[k], float(times[k]), use_mask=masked, out=out, tight=tight)
         ms = []
         for k in frames:
             _flush(flush)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            scene_obj.render(cams[k], float(times[k]), use_mask=masked, out=out)
+            scene_obj.render(cams[k], float(times[k]), use_mask=masked, out=out, tight=tight)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -464,6 +464,9 @@ def comparisons(sc, cams, times, flush, stream):
 
     res["single_masked"] = single(sc, True, fr)
     res["single_unmasked"] = single(sc, False, fr)
+    # the same frames with the alpha-tight tile sets (same images, shorter lists)
+    res["single_masked_tight"] = single(sc, True, fr, tight=True)
+    res["single_unmasked_tight"] = single(sc, False, fr, tight=True)
     # serving batch: 64 requests of mixed resolutions vs 64 sequential renders
     reqs, rts = scenes.random_requests(64, 4)
     outs = [torch.empty((3, c.height, c.width), dtype=torch.float32, device="cuda")
@@ -493,6 +496,7 @@ def comparisons(sc, cams, times, flush, stream):
     # backward (fine-tuning step): L1 loss against a render of the scene with means perturbed
     # by N(0, 0.01); render with a frame, then the reverse replay + per-Gaussian chain
     res["backward"] = backward_timing(sc, cams, times, flush, stream)
+    res["backward_tight"] = backward_timing(sc, cams, times, flush, stream, tight=True)
     # spatial-temporal variation score pass: 1M Gaussians, 50 timestamps x 4 cameras
     res["variation_score"] = score_timing(stream)
     # key-frame masks built from 4 training views (Sec. 4.2.2) instead of the 3-sigma recipe
@@ -602,7 +606,7 @@ def finetune_timing(iters=1000, prune_ratio=0.9, lr_scale=0.3):
     return out
 
 
-def backward_timing(sc, cams, times, flush, stream, n_frames=6):
+def backward_timing(sc, cams, times, flush, stream, n_frames=6, tight=False):
     import torch
 
     from paper_2503_16422_gb300 import fdgs
@@ -620,7 +624,7 @@ def backward_timing(sc, cams, times, flush, stream, n_frames=6):
         _flush(flush)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        img, fr = sc.render(cam, t, use_mask=False, keep_frame=True)
+        img, fr = sc.render(cam, t, use_mask=False, keep_frame=True, tight=tight)
         e1.record(stream)
         dL = torch.sign(img - target) / img.numel()
         e1b = torch.cuda.Event(enable_timing=True)
@@ -633,6 +637,7 @@ def backward_timing(sc, cams, times, flush, stream, n_frames=6):
         fr.release()
     target_scene.close()
     return dict(frames=n_frames, scene="pruned 200k, unmasked, 1352x1014",
+                tile_sets="alpha-tight" if tight else "3-sigma squares",
                 forward_ms=float(np.mean(fwd_ms)), backward_ms=float(np.mean(bwd_ms)))
 
 
