@@ -110,3 +110,16 @@ def test_batch_full_size_dense_tiles_match_sequential(fd):
     assert 0 < counts["n_keys"] <= nk
     print(f"batch keys {counts['n_keys']} vs per-request 3-sigma keys {nk}")
     sc.close()
+
+
+def test_batch_of_128_requests_and_the_limit(fd):
+    _, sc = _scene_gpu(fd, True, n=6000, seed=45)
+    res = [(64, 48), (48, 64), (33, 17), (96, 96)]
+    cams, ts = _requests(7, 128, res)
+    outs = sc.render_batch(cams, ts, use_mask=True)
+    for i in range(0, 128, 9):
+        assert torch.equal(outs[i], sc.render(cams[i], ts[i], use_mask=True)), i
+    assert len(sc.batch_info(128)["latency_ms"]) == 128
+    with pytest.raises(fd.FdgsError):
+        sc.render_batch(cams + cams[:1], ts + ts[:1], use_mask=True)
+    sc.close()
