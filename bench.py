@@ -503,6 +503,8 @@ def comparisons(sc, cams, times, flush, stream):
     res["keyframe_masks_from_views"] = keyframe_mask_timing(sc, cams, times, flush, stream)
     # the 4DGS-1K pipeline on a self-distillation target: score, prune 80%, masks, fine-tune
     res["prune_and_finetune"] = finetune_timing()
+    # vector-quantised SH decoded in the per-Gaussian kernel (Ours-PP)
+    res["sh_vector_quantised"] = vq_timing(sc, cams, times, flush, stream)
     # unpruned 3M scene, single requests
     big = scenes.unpruned_scene()
     kt = scenes.keyframe_times()
@@ -555,6 +557,37 @@ def keyframe_mask_timing(sc, cams, times, flush, stream, B=64):
                 activation_iou_vs_key0={f"+{6 * d} frames": iou(rows[0], rows[d])
                                         for d in (1, 3, 10, 49)},
                 batch_fps_through_these_masks=B / (statistics.median(ms) / 1e3))
+
+
+def vq_timing(sc, cams, times, flush, stream, n_code=4096, B=64):
+    """SH of the 200k scene quantised to n_code codes: encode time, colour storage, batched
+    FPS through the codebook (64 masked frames at 1352x1014) and PSNR against the renders
+    with full coefficients; the codebook is cleared afterwards."""
+    import torch
+
+    from paper_2503_16422_gb300 import finetune, vq
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cb, codes = vq.quantize_sh(sc.params.sh, n_code=n_code, iters=10)
+    torch.cuda.synchronize()
+    enc_s = time.perf_counter() - t0
+    fr = frame_list(6, 17)
+    full = [sc.render(cams[k], float(times[k])) for k in fr]
+    sc.set_sh_codebook(cb, codes)
+    psnrs = [finetune.psnr(sc.render(cams[k], float(times[k])), f) for k, f in zip(fr, full)]
+    outs = [torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device="cuda")
+            for _ in range(B)]
+    steps = [frame_list(B, 7 * B), frame_list(B, 9 * B), frame_list(B, 11 * B)]
+    args = [([cams[k] for k in f_], [float(times[k]) for k in f_]) for f_ in steps]
+    sc.render_batch(*args[0], outs=outs)
+    ms, _ = timed_batches(sc, [a for a, _ in args], [b for _, b in args], [outs] * 3, True,
+                          flush, stream)
+    sc.set_sh_codebook(None, None)
+    st = vq.storage_bytes(sc.n, sc.params.sh_degree, int(cb.shape[0]))
+    return dict(n_code=int(cb.shape[0]), encode_s=enc_s,
+                colour_bytes_full=st["full"], colour_bytes_quantised=st["quantised"],
+                psnr_vs_full_sh=float(np.mean(psnrs)),
+                batch_fps=B / (statistics.median(ms) / 1e3))
 
 
 def finetune_timing(iters=1000, prune_ratio=0.9, lr_scale=0.3):

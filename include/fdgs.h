@@ -227,6 +227,19 @@ int fdgs_build_keyframe_masks(fdgs_scene *scene, const fdgs_camera *cams, int n_
                               const float *key_times, int n_key, uint8_t *bits_out_dev,
                               fdgs_stream stream);
 
+/*
+ * Vector-quantised SH (the post-processing of Sec. 5, "Implementation Details", Ours-PP):
+ * from now on the renders take the DC coefficients from plane 0 of the description's sh
+ * array (only that plane is read, so it may be a [1][3][n] array) and bands k = 1..K-1 from
+ * codebook_dev[codes_dev[i]][k - 1][c], codebook_dev [n_code][K - 1][3] float, codes_dev [n]
+ * uint16, both device, BORROWED (valid until cleared or the scene is destroyed). A NULL
+ * codebook clears it. Needs sh_degree >= 1 and 1 <= n_code <= 65536, else FDGS_ERR_INVALID.
+ * fdgs_render_backward on a scene with a codebook returns FDGS_ERR_STATE (the gradients are
+ * defined for full coefficients).
+ */
+int fdgs_set_sh_codebook(fdgs_scene *scene, const float *codebook_dev, int n_code,
+                         const uint16_t *codes_dev);
+
 /* Last batch: visible Gaussians and tile-list entries summed over its requests. The batched
  * lists use, per Gaussian, the 3-sigma tile square intersected with the tiles its
  * alpha >= 1/255 ellipse can reach, so n_keys is at most the per-request renders' total

@@ -125,6 +125,8 @@ struct BatchPlan {
   std::vector<int> W, H;
   bool masked = false;
   fdgs_scene_desc d{};
+  const float *sh_cb = nullptr;            // codebook pointers captured in the graph
+  const uint16_t *sh_code = nullptr;
   uint32_t ntiles = 0, mask_words = 0;
   uint64_t key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
   std::vector<ReqDesc> tmpl;
@@ -175,6 +177,9 @@ struct fdgs_scene {
   int prof = 0;   // profiling flags (fdgs_profile_enable)
   cudaEvent_t ev[FDGS_PROFILE_STAGES + 1] = {};
   Buf evals;      // u64[2] blend evaluations and culling tests
+  const float *sh_cb = nullptr;        // borrowed SH codebook (fdgs_set_sh_codebook) or null
+  const uint16_t *sh_code = nullptr;
+  int n_code = 0;
 };
 
 struct fdgs_frame {
@@ -327,6 +332,8 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   pa.qr = (const float4 *)s->d.q_right;
   pa.opacity = s->d.opacity_logit;
   pa.sh = s->d.sh;
+  pa.sh_cb = s->sh_cb;
+  pa.sh_code = s->sh_code;
   pa.deg = s->d.sh_degree;
   pa.n = N;
   pa.mask_l = ml;
@@ -445,7 +452,8 @@ Workspace *take_workspace(fdgs_scene *s) {
 
 bool plan_matches(const BatchPlan *p, const fdgs_scene *s, const fdgs_camera *cams, int n,
                   bool masked) {
-  if (!p || p->nreq != n || p->masked != masked || memcmp(&p->d, &s->d, sizeof(s->d)) != 0)
+  if (!p || p->nreq != n || p->masked != masked || memcmp(&p->d, &s->d, sizeof(s->d)) != 0 ||
+      p->sh_cb != s->sh_cb || p->sh_code != s->sh_code)
     return false;
   for (int i = 0; i < n; ++i)
     if (p->W[i] != cams[i].width || p->H[i] != cams[i].height) return false;
@@ -465,6 +473,8 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   p.nreq = n;
   p.masked = masked;
   p.d = s->d;
+  p.sh_cb = s->sh_cb;
+  p.sh_code = s->sh_code;
   const uint32_t N = (uint32_t)s->d.n;
   p.mask_words = (N + 255) / 256 * 8;
   p.tmpl.resize(n);
@@ -563,6 +573,8 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.qr = (const float4 *)s->d.q_right;
   b.opacity = s->d.opacity_logit;
   b.sh = s->d.sh;
+  b.sh_cb = s->sh_cb;
+  b.sh_code = s->sh_code;
   b.deg = s->d.sh_degree;
   b.ctr = p.ctr.as<uint32_t>();
   b.err = s->status.as<uint32_t>();
@@ -854,6 +866,8 @@ int fdgs_render_backward(fdgs_scene *s, fdgs_frame *f, const float *dL_drgb_dev,
   if (!s || !f) return fail(FDGS_ERR_INVALID, "null argument");
   if (f->scene != s || !s->live.count(f)) return fail(FDGS_ERR_STATE, "frame not of this scene");
   if (!dL_drgb_dev) return fail(FDGS_ERR_INVALID, "null dL/drgb");
+  if (s->sh_cb)
+    return fail(FDGS_ERR_STATE, "backward needs full SH coefficients (a codebook is set)");
   cudaStream_t st = (cudaStream_t)stream;
   const FrameMeta &m = f->m;
   Workspace &ws = *f->ws;
@@ -1020,6 +1034,24 @@ int fdgs_build_keyframe_masks(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
     launch_pack_mask_row(row, nbytes, bits_out_dev + (size_t)k * nbytes, st);
   }
   CK(cudaGetLastError());
+  return FDGS_OK;
+}
+
+int fdgs_set_sh_codebook(fdgs_scene *s, const float *codebook_dev, int n_code,
+                         const uint16_t *codes_dev) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (!codebook_dev) {
+    s->sh_cb = nullptr;
+    s->sh_code = nullptr;
+    s->n_code = 0;
+    return FDGS_OK;
+  }
+  if (s->d.sh_degree < 1) return fail(FDGS_ERR_INVALID, "a codebook needs sh_degree >= 1");
+  if (n_code < 1 || n_code > 65536 || (s->d.n > 0 && !codes_dev))
+    return fail(FDGS_ERR_INVALID, "n_code must be 1..65536 and codes non-null");
+  s->sh_cb = codebook_dev;
+  s->sh_code = codes_dev;
+  s->n_code = n_code;
   return FDGS_OK;
 }
 

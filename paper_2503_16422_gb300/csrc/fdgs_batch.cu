@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
           if (x1 > x0 && y1 > y0) {
             vis = true;
             float rgb[3];
-            gauss_colour(q.cam, b.sh, b.deg, b.n, i, g, rgb);
+            gauss_colour(q.cam, b.sh, b.sh_cb, b.sh_code, b.deg, b.n, i, g, rgb);
             const float idet = 1.f / g.det;
             float4 *rp = reinterpret_cast<float4 *>(b.rec + ((size_t)r * b.n + i) * kRec);
             rp[0] = make_float4(u, v, g.c11 * idet, -g.c01 * idet);

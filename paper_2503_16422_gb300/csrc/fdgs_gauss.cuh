@@ -200,8 +200,12 @@ __device__ __forceinline__ uint8_t gauss_forward(const DevCam &cam, float t, flo
 }
 
 // Colour of a Gaussian that reached the projection (state has mu3). sh is [K][3][n].
+// SH coefficients are read from sh [K][3][n], or, with a codebook (cb non-null), the DC
+// plane from sh and bands k >= 1 from cb[code[i]][k - 1][c] (vector-quantised SH).
 __device__ __forceinline__ void gauss_colour(const DevCam &cam, const float *__restrict__ sh,
-                                             int deg, int64_t n, int64_t i, GaussState &g,
+                                             const float *__restrict__ cb,
+                                             const uint16_t *__restrict__ code, int deg,
+                                             int64_t n, int64_t i, GaussState &g,
                                              float rgb[3]) {
   float d0 = g.mu3[0] - cam.eye[0], d1 = g.mu3[1] - cam.eye[1], d2 = g.mu3[2] - cam.eye[2];
   g.dlen = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -210,10 +214,15 @@ __device__ __forceinline__ void gauss_colour(const DevCam &cam, const float *__r
   float Y[16];
   sh_eval(deg, g.dn[0], g.dn[1], g.dn[2], Y);
   const int K = (deg + 1) * (deg + 1);
+  const float *row = cb ? cb + (size_t)__ldg(&code[i]) * (size_t)(K - 1) * 3 : nullptr;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float acc = 0.5f;
-    for (int k = 0; k < K; ++k) acc = fmaf(Y[k], __ldg(&sh[((int64_t)k * 3 + c) * n + i]), acc);
+    for (int k = 0; k < K; ++k) {
+      const float f = (row && k > 0) ? __ldg(&row[(k - 1) * 3 + c])
+                                     : __ldg(&sh[((int64_t)k * 3 + c) * n + i]);
+      acc = fmaf(Y[k], f, acc);
+    }
     g.raw[c] = acc;
     rgb[c] = fmaxf(acc, 0.f);
   }

@@ -27,6 +27,8 @@ constexpr uint64_t kSortMaxKeys = (1ull << 30) - 1;
 struct PreArgs {
   const float4 *mean4, *ls4, *ql, *qr;
   const float *opacity, *sh;
+  const float *sh_cb;                // SH codebook [n_code][K-1][3] or null
+  const uint16_t *sh_code;           // [n] codes (with sh_cb)
   int deg;
   uint32_t n;
   const uint32_t *mask_l, *mask_r;   // null = no mask
@@ -155,6 +157,8 @@ struct BatchDev {
   uint64_t key_cap;
   const float4 *mean4, *ls4, *ql, *qr;
   const float *opacity, *sh;
+  const float *sh_cb;                // SH codebook or null
+  const uint16_t *sh_code;
   int deg;
   uint32_t *ctr, *err;
   uint2 *part;                       // [nreq][partitions]: visible count, segment offset

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kBlock) k_preprocess(PreArgs a) {
             vis = true;
             fl |= kFlagVisible;
             float rgb[3];
-            gauss_colour(a.cam, a.sh, a.deg, a.n, i, g, rgb);
+            gauss_colour(a.cam, a.sh, a.sh_cb, a.sh_code, a.deg, a.n, i, g, rgb);
             const float idet = 1.f / g.det;
             float4 *rp = reinterpret_cast<float4 *>(a.rec + (size_t)i * kRec);
             rp[0] = make_float4(u, v, g.c11 * idet, -g.c01 * idet);
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
                                      __ldg(&a.ql[i]), __ldg(&a.qr[i]), __ldg(&a.opacity[i]), g);
     if (!(fl & kFlagDet)) continue;
     float rgb[3];
-    gauss_colour(a.cam, a.sh, a.deg, a.n, i, g, rgb);
+    gauss_colour(a.cam, a.sh, nullptr, nullptr, a.deg, a.n, i, g, rgb);
     GaussGrad out;
     const float grgb[3] = {gg[6], gg[7], gg[8]};
     gauss_backward(a.cam, a.sh, a.deg, a.n, i, g, gg[0], gg[1], gg[2], gg[3], gg[4], gg[5],

@@ -83,6 +83,7 @@ _SIGNATURES = {
                         ctypes.POINTER(ctypes.c_float)],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
     "fdgs_batch_counts": [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
+    "fdgs_set_sh_codebook": [_P, _P, ctypes.c_int, _P],
     "fdgs_build_keyframe_masks": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P, _P],
 }
@@ -346,6 +347,25 @@ class Scene:
                                     st))
         return dict(latency_ms=list(lat)[:n], footprint=fp.value, ctas_per_sm=ctas.value,
                     stage_ms=dict(zip(BATCH_STAGES, list(st))))
+
+    def set_sh_codebook(self, codebook, codes):
+        """Vector-quantised SH: codebook float CUDA tensor [n_code, K-1, 3], codes int16/uint16
+        CUDA tensor [n] (the bit pattern is read as uint16). None clears. The tensors are
+        borrowed (kept referenced here)."""
+        if codebook is None:
+            check(lib().fdgs_set_sh_codebook(self.handle, None, 0, None))
+            self._cb_hold = None
+            return
+        k = (self.params.sh_degree + 1) ** 2
+        if not (codebook.is_cuda and codebook.dtype == torch.float32 and codebook.is_contiguous()
+                and codebook.dim() == 3 and tuple(codebook.shape[1:]) == (k - 1, 3)):
+            raise ValueError(f"codebook must be a contiguous float32 CUDA tensor [n_code,{k - 1},3]")
+        if not (codes.is_cuda and codes.dtype in (torch.int16, torch.uint16)
+                and codes.is_contiguous() and tuple(codes.shape) == (self.n,)):
+            raise ValueError(f"codes must be a contiguous 16-bit CUDA tensor [{self.n}]")
+        self._cb_hold = (codebook, codes)
+        check(lib().fdgs_set_sh_codebook(self.handle, _ptr(codebook), int(codebook.shape[0]),
+                                         _ptr(codes)))
 
     @property
     def active_mask(self):
