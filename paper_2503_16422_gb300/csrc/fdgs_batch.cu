@@ -49,6 +49,7 @@ __device__ __forceinline__ int find_segment(const uint32_t *bases, int n, uint32
 }
 
 // ---------------------------------------------------------------------------------------
+template <bool kVQ>
 __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
   __shared__ uint32_t s_item;
   __shared__ uint32_t s_wcnt[kW];
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
           if (x1 > x0 && y1 > y0) {
             vis = true;
             float rgb[3];
-            gauss_colour(q.cam, b.sh, b.sh_cb, b.sh_code, b.deg, b.n, i, g, rgb);
+            gauss_colour<kVQ>(q.cam, b.sh, b.sh_cb, b.sh_code, b.deg, b.n, i, g, rgb);
             const float idet = 1.f / g.det;
             float4 *rp = reinterpret_cast<float4 *>(b.rec + ((size_t)r * b.n + i) * kRec);
             rp[0] = make_float4(u, v, g.c11 * idet, -g.c01 * idet);
@@ -402,10 +403,13 @@ void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
   k_batch_start<<<1, 32, 0, st>>>(b);
   mark(0);
   static int g_pre = 0, g_gather = 0;
-  if (!g_pre) g_pre = grid_of((const void *)k_pre_batch, kB, 64);
+  if (!g_pre) g_pre = grid_of((const void *)k_pre_batch<false>, kB, 64);
   if (!g_gather) g_gather = grid_of((const void *)k_gather_batch, kB, 64);
   const uint64_t pre_items = (uint64_t)((b.n + kB - 1) / kB) * b.nreq;
-  k_pre_batch<<<(int)std::min<uint64_t>(pre_items, g_pre), kB, 0, st>>>(b);
+  if (b.sh_cb)
+    k_pre_batch<true><<<(int)std::min<uint64_t>(pre_items, g_pre), kB, 0, st>>>(b);
+  else
+    k_pre_batch<false><<<(int)std::min<uint64_t>(pre_items, g_pre), kB, 0, st>>>(b);
   mark(1);
   k_part_scan<<<b.nreq, kPS, 0, st>>>(b);
   k_batch_bases<<<1, 32, 0, st>>>(b);

@@ -200,8 +200,10 @@ __device__ __forceinline__ uint8_t gauss_forward(const DevCam &cam, float t, flo
 }
 
 // Colour of a Gaussian that reached the projection (state has mu3). sh is [K][3][n].
-// SH coefficients are read from sh [K][3][n], or, with a codebook (cb non-null), the DC
-// plane from sh and bands k >= 1 from cb[code[i]][k - 1][c] (vector-quantised SH).
+// SH coefficients are read from sh [K][3][n], or, with kVQ, the DC plane from sh and bands
+// k >= 1 from cb[code[i]][k - 1][c] (vector-quantised SH). kVQ is a template parameter so
+// that the full-coefficient kernels carry none of the codebook path.
+template <bool kVQ = false>
 __device__ __forceinline__ void gauss_colour(const DevCam &cam, const float *__restrict__ sh,
                                              const float *__restrict__ cb,
                                              const uint16_t *__restrict__ code, int deg,
@@ -214,12 +216,12 @@ __device__ __forceinline__ void gauss_colour(const DevCam &cam, const float *__r
   float Y[16];
   sh_eval(deg, g.dn[0], g.dn[1], g.dn[2], Y);
   const int K = (deg + 1) * (deg + 1);
-  const float *row = cb ? cb + (size_t)__ldg(&code[i]) * (size_t)(K - 1) * 3 : nullptr;
+  const float *row = kVQ ? cb + (size_t)__ldg(&code[i]) * (size_t)(K - 1) * 3 : nullptr;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float acc = 0.5f;
     for (int k = 0; k < K; ++k) {
-      const float f = (row && k > 0) ? __ldg(&row[(k - 1) * 3 + c])
+      const float f = (kVQ && k > 0) ? __ldg(&row[(k - 1) * 3 + c])
                                      : __ldg(&sh[((int64_t)k * 3 + c) * n + i]);
       acc = fmaf(Y[k], f, acc);
     }

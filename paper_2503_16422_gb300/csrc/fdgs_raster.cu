@@ -46,6 +46,7 @@ int persistent_grid(F kernel, uint64_t parts) {
 // ---------------------------------------------------------------------------------------
 // Per-Gaussian stage with fused compaction of the visible Gaussians.
 // ---------------------------------------------------------------------------------------
+template <bool kVQ>
 __global__ void __launch_bounds__(kBlock) k_preprocess(PreArgs a) {
   __shared__ uint32_t s_part;
   __shared__ uint32_t s_wcnt[kWarps];
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kBlock) k_preprocess(PreArgs a) {
             vis = true;
             fl |= kFlagVisible;
             float rgb[3];
-            gauss_colour(a.cam, a.sh, a.sh_cb, a.sh_code, a.deg, a.n, i, g, rgb);
+            gauss_colour<kVQ>(a.cam, a.sh, a.sh_cb, a.sh_code, a.deg, a.n, i, g, rgb);
             const float idet = 1.f / g.det;
             float4 *rp = reinterpret_cast<float4 *>(a.rec + (size_t)i * kRec);
             rp[0] = make_float4(u, v, g.c11 * idet, -g.c01 * idet);
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
                                      __ldg(&a.ql[i]), __ldg(&a.qr[i]), __ldg(&a.opacity[i]), g);
     if (!(fl & kFlagDet)) continue;
     float rgb[3];
-    gauss_colour(a.cam, a.sh, nullptr, nullptr, a.deg, a.n, i, g, rgb);
+    gauss_colour<false>(a.cam, a.sh, nullptr, nullptr, a.deg, a.n, i, g, rgb);
     GaussGrad out;
     const float grgb[3] = {gg[6], gg[7], gg[8]};
     gauss_backward(a.cam, a.sh, a.deg, a.n, i, g, gg[0], gg[1], gg[2], gg[3], gg[4], gg[5],
@@ -430,8 +431,11 @@ void launch_preprocess(const PreArgs &a, cudaStream_t st) {
   if (a.n == 0) return;
   const uint64_t parts = (a.n + kBlock - 1) / kBlock;
   static int grid_cap = 0;
-  if (!grid_cap) grid_cap = persistent_grid(k_preprocess, ~0ull);
-  k_preprocess<<<(int)std::min<uint64_t>(parts, grid_cap), kBlock, 0, st>>>(a);
+  if (!grid_cap) grid_cap = persistent_grid(k_preprocess<false>, ~0ull);
+  if (a.sh_cb)
+    k_preprocess<true><<<(int)std::min<uint64_t>(parts, grid_cap), kBlock, 0, st>>>(a);
+  else
+    k_preprocess<false><<<(int)std::min<uint64_t>(parts, grid_cap), kBlock, 0, st>>>(a);
 }
 
 void launch_gather_scan(const uint64_t *sorted, const uint32_t *ctr_nvis, uint32_t n_cap,
