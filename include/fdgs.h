@@ -193,9 +193,10 @@ int fdgs_render_batch(fdgs_scene *scene, const fdgs_camera *cams, const float *t
                       const fdgs_render_opts *opts, float *const *rgb_out_dev,
                       fdgs_stream stream);
 
-/* Autotuner of the batched path: renders the batch once per candidate launch shape (warp
- * footprint of the blend x persistent CTAs per SM), keeps the fastest for this batch
- * geometry, and leaves the outputs of a final render in rgb_out_dev. Synchronises. */
+/* Autotuner of the batched path: renders the batch once per candidate launch shape (each of
+ * the blend shapes of fdgs_set_blend_shape x {half, all} of its resident persistent CTAs per
+ * SM), keeps the fastest for this batch geometry, and leaves the outputs of a final render in
+ * rgb_out_dev. Synchronises. */
 int fdgs_batch_autotune(fdgs_scene *scene, const fdgs_camera *cams, const float *ts,
                         int n_req, const fdgs_render_opts *opts, float *const *rgb_out_dev,
                         fdgs_stream stream);
@@ -311,9 +312,11 @@ int fdgs_profile_read(fdgs_scene *scene, float *stage_ms, uint64_t *blend_counts
 int fdgs_set_list_builder(int mode);
 
 /* Launch shape of the forward blend, process-wide: the pixel footprint of one warp inside a
- * 16x16 tile (0: 16x2, 1: 8x4 (default), 2: 4x8). Each warp culls, by ballot, the Gaussians
- * that cannot reach alpha >= 1/255 anywhere in its footprint; results do not depend on the
- * shape. Returns FDGS_ERR_INVALID for other values. */
+ * 16x16 tile and the pixels each lane composites (one CTA of 256 / pixels-per-lane threads per
+ * tile): 0: 16x2, 1: 8x4, 2: 4x8 (one pixel per lane), 3: 8x8 (two, the default), 4: 16x8,
+ * 5: 8x16 (four). Each warp culls, by ballot, the Gaussians that cannot reach alpha >= 1/255
+ * anywhere in its footprint; results do not depend on the shape. Returns FDGS_ERR_INVALID for
+ * other values. */
 int fdgs_set_blend_shape(int footprint);
 
 /* Reads and clears the scene's device status word (synchronises the device): FDGS_OK, or

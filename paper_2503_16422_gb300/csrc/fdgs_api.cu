@@ -131,13 +131,13 @@ struct BatchPlan {
   uint64_t key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
   std::vector<ReqDesc> tmpl;
   Buf reqs, ctr, part, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base, key_cnt,
-      rec_sorted, diff, masks, ranges, qkeys, qkeys_alt, lists, Tf, nc, done, t0, scratch;
+      rec_sorted, diff, masks, ranges, qkeys, qkeys_alt, lists, done, t0, scratch;
   ReqDesc *h_reqs = nullptr;
   uint32_t *h_ctr = nullptr;
   unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int footprint = 1, ctas = 0;
+  int footprint = 4, ctas = 0;
   bool tuned = false;
   std::vector<float> lat_ms;
   Buf stamps;                                  // u64[kBatchStages + 1] %globaltimer
@@ -148,7 +148,7 @@ struct BatchPlan {
     if (h_stamps) cudaFreeHost(h_stamps);
     Buf *all[] = {&reqs, &ctr, &part, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
                   &slot_base, &key_cnt, &rec_sorted, &diff, &masks, &ranges, &qkeys,
-                  &qkeys_alt, &lists, &Tf, &nc, &done, &t0, &scratch};
+                  &qkeys_alt, &lists, &done, &t0, &scratch};
     for (Buf *b : all) b->release();
     if (h_reqs) cudaFreeHost(h_reqs);
     if (h_ctr) cudaFreeHost(h_ctr);
@@ -478,7 +478,7 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   const uint32_t N = (uint32_t)s->d.n;
   p.mask_words = (N + 255) / 256 * 8;
   p.tmpl.resize(n);
-  uint64_t tiles = 0, pix = 0, diff = 0, mask = 0;
+  uint64_t tiles = 0, diff = 0, mask = 0;
   for (int i = 0; i < n; ++i) {
     DevCam dc;
     TRY(make_cam(&cams[i], dc));
@@ -489,9 +489,7 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
     q.tile_base = (uint32_t)tiles;
     q.diff_base = (uint32_t)diff;
     q.mask_base = mask;
-    q.pix_base = pix;
     tiles += (uint64_t)dc.gx * dc.gy;
-    pix += (uint64_t)dc.W * dc.H;
     diff += (uint64_t)(dc.gx + 1) * (dc.gy + 1);
     mask += (uint64_t)(dc.gx + dc.gy) * p.mask_words;
   }
@@ -517,8 +515,6 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   TRY(grow(p.key_cnt, n * 8));
   TRY(grow(p.rec_sorted, p.slot_cap * kRecS * 4));
   TRY(grow(p.diff, diff * 4));
-  TRY(grow(p.Tf, pix * 4));
-  TRY(grow(p.nc, pix * 4));
   TRY(grow(p.masks, std::max<uint64_t>(mask, 1) * 4));
   TRY(grow(p.ranges, tiles * 8));
   TRY(grow(p.qkeys, tiles * 8));
@@ -534,7 +530,7 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   CK(cudaStreamCreateWithFlags(&p.cap, cudaStreamNonBlocking));
   TRY(grow(p.stamps, (kBatchStages + 1) * 8));
   CK(cudaMallocHost(&p.h_stamps, (kBatchStages + 1) * 8));
-  p.ctas = std::min(4, batch_blend_max_ctas_per_sm());
+  p.ctas = batch_blend_max_ctas_per_sm(p.footprint);
   return FDGS_OK;
 }
 
@@ -596,8 +592,6 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.qkeys_alt = p.qkeys_alt.as<uint64_t>();
   b.queue = nullptr;
   b.lists = p.lists.as<uint32_t>();
-  b.T_final = p.Tf.as<float>();
-  b.n_contrib = p.nc.as<uint32_t>();
   b.done_ns = p.done.as<unsigned long long>();
   b.t0_ns = p.t0.as<unsigned long long>();
   b.evals = nullptr;
@@ -947,18 +941,17 @@ int fdgs_batch_autotune(fdgs_scene *s, const fdgs_camera *cams, const float *ts,
   BatchPlan &p = *s->plan;
   TRY(plan_fill(s, p, cams, ts, opts, rgb_out_dev));
   TRY(plan_run(s, p, st));   // sizes the list capacity
-  const int maxc = batch_blend_max_ctas_per_sm();
-  std::vector<int> ctas = {1, 2, 4, maxc};
-  std::sort(ctas.begin(), ctas.end());
-  ctas.erase(std::unique(ctas.begin(), ctas.end()), ctas.end());
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_f = p.footprint, best_c = p.ctas;
-  for (int f = 0; f < 3; ++f)
+  for (int f = 0; f < kBlendShapes; ++f) {
+    // resident CTAs per SM: the occupancy limit and half of it
+    const int maxc = batch_blend_max_ctas_per_sm(f);
+    std::vector<int> ctas = {std::max(1, maxc / 2), maxc};
+    ctas.erase(std::unique(ctas.begin(), ctas.end()), ctas.end());
     for (int c : ctas) {
-      if (c > maxc) continue;
       p.footprint = f;
       p.ctas = c;
       TRY(plan_capture(s, p));
@@ -979,6 +972,7 @@ int fdgs_batch_autotune(fdgs_scene *s, const fdgs_camera *cams, const float *ts,
         best_c = c;
       }
     }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   p.footprint = best_f;
@@ -1138,8 +1132,9 @@ int fdgs_set_list_builder(int mode) {
 }
 
 int fdgs_set_blend_shape(int footprint) {
-  if (footprint < 0 || footprint > 2)
-    return fail(FDGS_ERR_INVALID, "footprint must be 0 (16x2), 1 (8x4) or 2 (4x8)");
+  if (footprint < 0 || footprint >= kBlendShapes)
+    return fail(FDGS_ERR_INVALID,
+                "blend shape must be 0 (16x2), 1 (8x4), 2 (4x8), 3 (8x8), 4 (16x8) or 5 (8x16)");
   g_blend_shape = footprint;
   return FDGS_OK;
 }

@@ -337,12 +337,13 @@ __global__ void __launch_bounds__(kB) k_lists_batch(BatchDev b) {
 }
 
 // Persistent blend over the longest-first queue of all requests' tiles.
-template <int FW, bool kCount>
-__global__ void __launch_bounds__(kBlendThreads) k_blend_persist(BatchDev b) {
-  __shared__ BlendSmem sm;
+// Only the images are written: nothing reads a batched frame's transmittance or n_contrib.
+template <int FW, int PX, bool kCount>
+__global__ void __launch_bounds__(256 / PX) k_blend_persist(BatchDev b) {
+  __shared__ BlendSmem<256 / PX> sm;
   __shared__ uint32_t s_q;
   __shared__ uint32_t s_tile_base[kMaxReq];
-  for (int r = threadIdx.x; r < b.nreq; r += kBlendThreads) s_tile_base[r] = b.reqs[r].tile_base;
+  for (int r = threadIdx.x; r < b.nreq; r += 256 / PX) s_tile_base[r] = b.reqs[r].tile_base;
   for (;;) {
     if (threadIdx.x == 0) s_q = atomicAdd(&b.ctr[BC_QUEUE], 1u);
     __syncthreads();
@@ -360,15 +361,15 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_persist(BatchDev b) {
     bt.range = b.ranges[gt];
     bt.rec_sorted = b.rec_sorted;
     bt.rgb = q.rgb;
-    bt.T_final = b.T_final + q.pix_base;
-    bt.n_contrib = b.n_contrib + q.pix_base;
+    bt.T_final = nullptr;
+    bt.n_contrib = nullptr;
     bt.bg0 = q.bg[0];
     bt.bg1 = q.bg[1];
     bt.bg2 = q.bg[2];
     bt.w_sum = nullptr;
     bt.stop_mark = nullptr;
     bt.evals = b.evals;
-    blend_tile<uint32_t, FW, false, kCount>(bt, b.lists, 0xFFFFFFFFu, sm);
+    blend_tile<uint32_t, FW, PX, false, kCount, false>(bt, b.lists, 0xFFFFFFFFu, sm);
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(&b.done_ns[r], (unsigned long long)global_timer_ns());
   }
@@ -434,26 +435,23 @@ void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
   b2.queue = qs;
   mark(6);
   const int grid = L.blend_ctas_per_sm * num_sms();
-  if (b.evals) {
-    switch (L.footprint) {
-      case 0: k_blend_persist<16, true><<<grid, kBlendThreads, 0, st>>>(b2); break;
-      case 2: k_blend_persist<4, true><<<grid, kBlendThreads, 0, st>>>(b2); break;
-      default: k_blend_persist<8, true><<<grid, kBlendThreads, 0, st>>>(b2); break;
-    }
-  } else {
-    switch (L.footprint) {
-      case 0: k_blend_persist<16, false><<<grid, kBlendThreads, 0, st>>>(b2); break;
-      case 2: k_blend_persist<4, false><<<grid, kBlendThreads, 0, st>>>(b2); break;
-      default: k_blend_persist<8, false><<<grid, kBlendThreads, 0, st>>>(b2); break;
-    }
-  }
+  with_blend_shape(L.footprint, [&](auto fw, auto px) {
+    constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
+    if (b.evals)
+      k_blend_persist<FW, PX, true><<<grid, 256 / PX, 0, st>>>(b2);
+    else
+      k_blend_persist<FW, PX, false><<<grid, 256 / PX, 0, st>>>(b2);
+  });
   mark(7);
 }
 
-int batch_blend_max_ctas_per_sm() {
+int batch_blend_max_ctas_per_sm(int shape) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_persist<8, false>,
-                                                kBlendThreads, 0);
+  with_blend_shape(shape, [&](auto fw, auto px) {
+    constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_persist<FW, PX, false>,
+                                                  256 / PX, 0);
+  });
   return std::max(1, per_sm);
 }
 

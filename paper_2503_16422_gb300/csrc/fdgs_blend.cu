@@ -8,10 +8,10 @@ namespace fdgs {
 
 namespace {
 
-template <typename K, int FW, bool kWeights, bool kCount>
-__global__ void __launch_bounds__(kBlendThreads)
+template <typename K, int FW, int PX, bool kWeights, bool kCount>
+__global__ void __launch_bounds__(256 / PX)
 k_blend(BlendArgs a, const K *__restrict__ keys, uint32_t rmask) {
-  __shared__ BlendSmem sm;
+  __shared__ BlendSmem<256 / PX> sm;
   BlendTile bt;
   bt.tx = blockIdx.x % a.gx;
   bt.ty = blockIdx.x / a.gx;
@@ -28,7 +28,7 @@ k_blend(BlendArgs a, const K *__restrict__ keys, uint32_t rmask) {
   bt.w_sum = a.w_sum;
   bt.stop_mark = a.stop_mark;
   bt.evals = a.evals;
-  blend_tile<K, FW, kWeights, kCount>(bt, keys, rmask, sm);
+  blend_tile<K, FW, PX, kWeights, kCount, true>(bt, keys, rmask, sm);
 }
 
 // Sums of eight per-lane values over the warp by a transposed butterfly: at offsets 16, 8
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256)
 k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
   constexpr int FH = 32 / FW;
   constexpr int WX = kTile / FW;
-  constexpr int kB = kBlendBatch;
+  constexpr int kB = 256;
   __shared__ __align__(16) float4 s_g0[kB];   // u, v, a2, b2
   __shared__ __align__(16) float4 s_g1[kB];   // c2, lga, r, g
   __shared__ __align__(16) float4 s_g2[kB];   // b, kx, ky, radius
@@ -187,29 +187,23 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
   }
 }
 
-template <typename K, int FW>
-void blend_fw(const BlendArgs &a, const K *keys, uint32_t rmask, cudaStream_t st) {
-  const int tiles = a.gx * a.gy;
-  if (a.w_sum)
-    k_blend<K, FW, true, false><<<tiles, kBlendThreads, 0, st>>>(a, keys, rmask);
-  else if (a.evals)
-    k_blend<K, FW, false, true><<<tiles, kBlendThreads, 0, st>>>(a, keys, rmask);
-  else
-    k_blend<K, FW, false, false><<<tiles, kBlendThreads, 0, st>>>(a, keys, rmask);
-}
-
 }  // namespace
 
-int g_blend_shape = 1;   // warp footprint: 0 -> 16x2, 1 -> 8x4, 2 -> 4x8 pixels
+int g_blend_shape = 3;   // launch shape of the forward blend (see with_blend_shape)
 
 template <typename K>
 void launch_blend(const BlendArgs &a, const K *keys, uint32_t rmask, cudaStream_t st) {
-  if (a.gx * a.gy == 0) return;
-  switch (g_blend_shape) {
-    case 0: blend_fw<K, 16>(a, keys, rmask, st); break;
-    case 2: blend_fw<K, 4>(a, keys, rmask, st); break;
-    default: blend_fw<K, 8>(a, keys, rmask, st); break;
-  }
+  const int tiles = a.gx * a.gy;
+  if (tiles == 0) return;
+  with_blend_shape(g_blend_shape, [&](auto fw, auto px) {
+    constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
+    if (a.w_sum)
+      k_blend<K, FW, PX, true, false><<<tiles, 256 / PX, 0, st>>>(a, keys, rmask);
+    else if (a.evals)
+      k_blend<K, FW, PX, false, true><<<tiles, 256 / PX, 0, st>>>(a, keys, rmask);
+    else
+      k_blend<K, FW, PX, false, false><<<tiles, 256 / PX, 0, st>>>(a, keys, rmask);
+  });
 }
 
 template <typename K>

@@ -1,25 +1,48 @@
 // Per-tile front-to-back compositing (Eq. 2 with Eq. 3's alpha): the device-side body shared
 // by the one-CTA-per-tile kernel and the persistent batched kernel.
 //
-// A CTA of 256 threads composites one 16x16 tile; each warp owns an FW x (32/FW) pixel
-// footprint, one pixel per lane. The tile's records are staged 256 at a time with cp.async
-// into a double buffer (the copy of batch b+1 is in flight while batch b is composited; the
-// keys of batch b+2 are already loading into registers). Two culling levels, both exact for
-// the concave exponent and conservative by a margin, so no per-pixel decision changes:
+// A CTA of 256 / PX threads composites one 16x16 tile; each warp owns an FW x (32 PX / FW)
+// pixel footprint and each lane PX pixels of one footprint row, FW / PX apart (so the row
+// terms of the exponent are shared). The tile's records are staged one per thread at a time
+// with cp.async into a double buffer (the copy of batch b+1 is in flight while batch b is
+// composited; the keys of batch b+2 are already loading into registers). Two culling levels,
+// both exact for the concave exponent and conservative by a margin, so no per-pixel decision
+// changes:
 //   1. staging: each thread tests its staged Gaussian against the whole tile; survivors are
 //      compacted (block ballot + prefix) into an index list that keeps list order;
 //   2. warps: lanes test 32 survivors at a time against the warp's footprint and
 //      __ballot_sync the hits; each hitting lane writes its record to the warp's hit list, and
-//      the warp evaluates the list in order, one Gaussian at a time, for 32 pixels.
+//      the warp evaluates the list in order, one Gaussian at a time, for 32 PX pixels.
 // A culled Gaussian has alpha < 1/255 at every pixel it is culled for, so it would have been
 // skipped pixel by pixel anyway: results equal evaluating every entry at every pixel.
+//
+// The per-pixel evaluation has no branches: a pixel whose exponent fails a test, or which has
+// already stopped, takes alpha = 0, and T * (1 - 0), fma(c, 0, C) leave its transmittance and
+// colour sums bit-for-bit unchanged. So the arithmetic of every pixel, and every result, is
+// the same for every footprint, every PX and the one-pixel-per-branch formulation.
 #pragma once
+#include <type_traits>
+
 #include "fdgs_internal.h"
 
 namespace fdgs {
 
-constexpr int kBlendBatch = 256;
-constexpr int kBlendThreads = 256;
+constexpr int kBlendThreads = 256;   // threads of a one-pixel-per-lane tile CTA
+
+// Launch shapes of the forward blend (kBlendShapes of them): warp footprint FW x (32 PX / FW)
+// pixels, PX pixels per lane.
+//   0: 16x2, 1: 8x4, 2: 4x8 (one pixel per lane), 3: 8x8 (two), 4: 16x8, 5: 8x16 (four)
+template <class F>
+inline void with_blend_shape(int shape, F &&f) {
+  switch (shape) {
+    case 0: f(std::integral_constant<int, 16>{}, std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 4>{}, std::integral_constant<int, 1>{}); break;
+    case 3: f(std::integral_constant<int, 8>{}, std::integral_constant<int, 2>{}); break;
+    case 4: f(std::integral_constant<int, 16>{}, std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{}); break;
+    default: f(std::integral_constant<int, 8>{}, std::integral_constant<int, 1>{}); break;
+  }
+}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
@@ -42,19 +65,20 @@ __device__ __forceinline__ bool may_hit_rect(float4 g0, float c2, float lga, flo
   return qmax + lga >= kLog2AlphaMin - kCullMargin;
 }
 
+template <int NT>
 struct BlendSmem {
-  float4 g0[2][kBlendBatch];   // u, v, a2, b2
-  float4 g1[2][kBlendBatch];   // c2, lga, r, g
-  float4 g2[2][kBlendBatch];   // b, kx, ky, radius
-  uint32_t rk[2][kBlendBatch]; // rank (score weights)
-  uint16_t idx[kBlendBatch];   // compacted survivors of the tile test
-  uint32_t wcnt[kBlendThreads / 32];
+  float4 g0[2][NT];            // u, v, a2, b2
+  float4 g1[2][NT];            // c2, lga, r, g
+  float4 g2[2][NT];            // b, kx, ky, radius
+  uint32_t rk[2][NT];          // rank (score weights)
+  uint16_t idx[NT];            // compacted survivors of the tile test
+  uint32_t wcnt[NT / 32];
   uint32_t ncomp;
   // per warp, the records of the footprint-test hits in hit order, written by the lanes that
   // tested them: u, v, a2, b2 | c2, lga, r, g | b, stage index
-  float4 h0[kBlendThreads / 32][32];
-  float4 h1[kBlendThreads / 32][32];
-  float2 h2[kBlendThreads / 32][32];
+  float4 h0[NT / 32][32];
+  float4 h1[NT / 32][32];
+  float2 h2[NT / 32][32];
 };
 
 // Where one tile's inputs and outputs live.
@@ -63,43 +87,56 @@ struct BlendTile {
   uint2 range;                 // [start, end) into keys
   const float *rec_sorted;     // blend-ready records [rank][16]
   float *rgb;                  // [3][H][W]
-  float *T_final;              // [H][W]
-  uint32_t *n_contrib;         // [H][W]
+  float *T_final;              // [H][W] (written when kAux)
+  uint32_t *n_contrib;         // [H][W] (written when kAux)
   float bg0, bg1, bg2;
   float *w_sum;                // per-rank weights (score pass) or null
   uint32_t *stop_mark;         // per-rank flag: the entry stopped a pixel (with w_sum)
   unsigned long long *evals;   // [2] evaluations, culling tests (profiling) or null
 };
 
-template <typename K, int FW, bool kWeights, bool kCount>
+// kAux: also write the final transmittance and 1 + the list position of the last blended
+// entry per pixel (what the reverse replay of the backward starts from).
+template <typename K, int FW, int PX, bool kWeights, bool kCount, bool kAux>
 __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restrict__ keys,
-                                           uint32_t rmask, BlendSmem &sm) {
-  constexpr int NT = kBlendThreads;
-  constexpr int FH = 32 / FW;
+                                           uint32_t rmask, BlendSmem<256 / PX> &sm) {
+  constexpr int NT = 256 / PX;   // threads = records staged per batch
+  constexpr int FH = 32 * PX / FW;
+  constexpr int HW = FW / PX;    // lanes per footprint row
   constexpr int WX = kTile / FW;
+  static_assert(FW % PX == 0 && FW <= kTile && FH * (NT / 32) == kTile * WX, "shape");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int fx0 = bt.tx * kTile + (warp % WX) * FW, fy0 = bt.ty * kTile + (warp / WX) * FH;
-  const int px = fx0 + lane % FW, py = fy0 + lane / FW;
+  const int px0 = fx0 + lane % HW, py = fy0 + lane / HW;
   const float tx0 = (float)(bt.tx * kTile), ty0 = (float)(bt.ty * kTile);
   const float fxl = (float)fx0, fxh = (float)(fx0 + FW - 1);
   const float fyl = (float)fy0, fyh = (float)(fy0 + FH - 1);
   const uint32_t n = bt.range.y - bt.range.x;
-  const int nb = (int)((n + kBlendBatch - 1) / kBlendBatch);
-  const bool inside = px < bt.W && py < bt.H;
-  const float fpx = (float)px, fpy = (float)py;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0, nevals = 0, ntests = 0;
-  bool done = !inside;
-  bool warp_done = __all_sync(0xffffffffu, done);
+  const int nb = (int)((n + NT - 1) / NT);
+  const float fpy = (float)py;
+  float T[PX], C0[PX], C1[PX], C2[PX];
+  uint32_t last[PX];
+  bool done[PX];
+  bool lane_done = true;
+#pragma unroll
+  for (int p = 0; p < PX; ++p) {
+    T[p] = 1.f;
+    C0[p] = C1[p] = C2[p] = 0.f;
+    last[p] = 0;
+    done[p] = !(px0 + p * HW < bt.W && py < bt.H);
+    lane_done = lane_done && done[p];
+  }
+  uint32_t nevals = 0, ntests = 0;
+  bool warp_done = __all_sync(0xffffffffu, lane_done);
 
   K kr = (K)0;
   auto load_key = [&](int b) {
-    const uint32_t i = (uint32_t)b * kBlendBatch + tid;
+    const uint32_t i = (uint32_t)b * NT + tid;
     kr = i < n ? keys[bt.range.x + i] : (K)0;
   };
   auto issue = [&](int b) {
     const int st = b & 1;
-    const uint32_t i = (uint32_t)b * kBlendBatch + tid;
+    const uint32_t i = (uint32_t)b * NT + tid;
     if (i < n) {
       const uint32_t r = (uint32_t)(kr & (K)rmask);
       const float *rp = bt.rec_sorted + (size_t)r * kRecS;
@@ -126,8 +163,8 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     }
     __syncthreads();
     const int st = b & 1;
-    const int cnt = (int)min((uint32_t)kBlendBatch, n - (uint32_t)b * kBlendBatch);
-    const uint32_t pos0 = (uint32_t)b * kBlendBatch;
+    const int cnt = (int)min((uint32_t)NT, n - (uint32_t)b * NT);
+    const uint32_t pos1 = (uint32_t)b * NT + 1;
     // 1. tile-level test of the thread's own staged Gaussian, block compaction
     bool keep = false;
     if (kCount && tid < cnt) ++ntests;
@@ -176,38 +213,49 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
       __syncwarp();
       const int nh = __popc(m);
       for (int k = 0; k < nh; ++k) {
+        const float4 h0 = sm.h0[warp][k];
+        const float4 h1 = sm.h1[warp][k];
+        const float2 h2 = sm.h2[warp][k];
+        // the exponent of splat_alpha, with the row terms shared by the lane's pixels
+        const float dy = __fsub_rn(h0.y, fpy);
+        const float b2dy = __fmul_rn(h0.w, dy);
+        const float c2dy2 = __fmul_rn(__fmul_rn(h1.x, dy), dy);
         float w = 0.f;
-        if (!done) {
-          if (kCount) ++nevals;
-          const float4 h0 = sm.h0[warp][k];
-          const float4 h1 = sm.h1[warp][k];
-          float alpha, raw, dx, dy;
-          if (splat_alpha(h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, fpx, fpy, alpha, raw, dx, dy)) {
-            const float nT = T * (1.f - alpha);
-            if (nT < kTStop) {
-              done = true;
-              // the entry ends this pixel's list: the key-frame masks keep it
-              if (kWeights) bt.stop_mark[sm.rk[st][__float_as_int(sm.h2[warp][k].y)]] = 1u;
-            } else {
-              const float2 h2 = sm.h2[warp][k];
-              w = alpha * T;
-              C0 = fmaf(h1.z, w, C0);
-              C1 = fmaf(h1.w, w, C1);
-              C2 = fmaf(h2.x, w, C2);
-              T = nT;
-              last = pos0 + (uint32_t)__float_as_int(h2.y) + 1;
-            }
-          }
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+          const float dx = __fsub_rn(h0.x, (float)(px0 + p * HW));
+          const float q = __fmaf_rn(dx, __fmaf_rn(h0.z, dx, b2dy), c2dy2);
+          const float e = __fadd_rn(q, h1.y);
+          const bool valid = !done[p] && q <= 0.f && e >= kLog2AlphaMin;
+          if (kCount && !done[p]) ++nevals;
+          const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
+          const float nT = T[p] * (1.f - alpha);
+          // only a valid entry can stop a pixel: an unfinished pixel has T >= kTStop
+          const bool stop = nT < kTStop;
+          // the entry that ends this pixel's list: the key-frame masks keep it
+          if (kWeights && stop) bt.stop_mark[sm.rk[st][__float_as_int(h2.y)]] = 1u;
+          done[p] = done[p] || stop;
+          const bool use = valid && !stop;
+          const float wi = use ? alpha * T[p] : 0.f;
+          C0[p] = fmaf(h1.z, wi, C0[p]);
+          C1[p] = fmaf(h1.w, wi, C1[p]);
+          C2[p] = fmaf(h2.x, wi, C2[p]);
+          T[p] = use ? nT : T[p];
+          if (kAux) last[p] = use ? pos1 + (uint32_t)__float_as_int(h2.y) : last[p];
+          if (kWeights) w += wi;
         }
         if (kWeights) {
           if (__any_sync(0xffffffffu, w != 0.f)) {
             const float s = warp_sum(w);
-            if (lane == 0) atomicAdd(&bt.w_sum[sm.rk[st][__float_as_int(sm.h2[warp][k].y)]], s);
+            if (lane == 0) atomicAdd(&bt.w_sum[sm.rk[st][__float_as_int(h2.y)]], s);
           }
         }
       }
       __syncwarp();                    // the list is rewritten by the next round
-      warp_done = __all_sync(0xffffffffu, done);
+      lane_done = true;
+#pragma unroll
+      for (int p = 0; p < PX; ++p) lane_done = lane_done && done[p];
+      warp_done = __all_sync(0xffffffffu, lane_done);
     }
     if (__syncthreads_and(warp_done)) {
       cp_async_wait<0>();
@@ -219,14 +267,20 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     if (lane == 0 && ws) atomicAdd(&bt.evals[0], (unsigned long long)ws);
     if (lane == 0 && wt) atomicAdd(&bt.evals[1], (unsigned long long)wt);
   }
-  if (inside) {
-    const size_t hw = (size_t)bt.W * bt.H;
-    const size_t pix = (size_t)py * bt.W + px;
-    bt.rgb[pix] = C0 + T * bt.bg0;
-    bt.rgb[hw + pix] = C1 + T * bt.bg1;
-    bt.rgb[2 * hw + pix] = C2 + T * bt.bg2;
-    bt.T_final[pix] = T;
-    bt.n_contrib[pix] = last;
+  const size_t hw = (size_t)bt.W * bt.H;
+#pragma unroll
+  for (int p = 0; p < PX; ++p) {
+    const int px = px0 + p * HW;
+    if (px < bt.W && py < bt.H) {
+      const size_t pix = (size_t)py * bt.W + px;
+      bt.rgb[pix] = C0[p] + T[p] * bt.bg0;
+      bt.rgb[hw + pix] = C1[p] + T[p] * bt.bg1;
+      bt.rgb[2 * hw + pix] = C2[p] + T[p] * bt.bg2;
+      if (kAux) {
+        bt.T_final[pix] = T[p];
+        bt.n_contrib[pix] = last[p];
+      }
+    }
   }
 }
 

@@ -144,7 +144,6 @@ struct ReqDesc {
   uint32_t tile_base;                // first global tile id of the request
   uint32_t diff_base;                // offset of its coverage difference array (ints)
   uint64_t mask_base;                // offset of its row and column bitmasks (words)
-  uint64_t pix_base;                 // offset of its pixels in T_final / n_contrib
 };
 enum BatchCounter {
   BC_PRE_ITEM = 0, BC_NVIS = 1, BC_NSLOTS = 2, BC_NTILES = 3, BC_NKEYS_LO = 5,
@@ -174,8 +173,6 @@ struct BatchDev {
   uint64_t *qkeys, *qkeys_alt;
   const uint64_t *queue;
   uint32_t *lists;                   // [key_cap] slot indices
-  float *T_final;                    // per-pixel outputs of the blend (kept in the plan)
-  uint32_t *n_contrib;
   unsigned long long *done_ns, *t0_ns;
   unsigned long long *evals;         // [2] blend evaluations / culling tests, or null
   unsigned long long *stamps;        // [kBatchStages + 1] %globaltimer at stage boundaries
@@ -183,17 +180,18 @@ struct BatchDev {
 struct BatchLaunch {
   size_t diff_bytes;
   void *sort_scratch;
-  int footprint;                     // warp footprint of the blend (0, 1, 2)
+  int footprint;                     // launch shape of the blend (with_blend_shape)
   int blend_ctas_per_sm;             // persistent blend grid = this x SMs
 };
 // Stages timed by the device stamps: preprocess, depth_sort (bases, compaction, sort),
 // gather, tile_scan, lists, queue_sort, blend.
 constexpr int kBatchStages = 7;
 void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st);
-int batch_blend_max_ctas_per_sm();
+int batch_blend_max_ctas_per_sm(int shape);
 
 int num_sms();
-extern int g_blend_shape;   // warp footprint of the forward blend: 0 16x2, 1 8x4, 2 4x8
+extern int g_blend_shape;   // launch shape of the forward blend (with_blend_shape)
+constexpr int kBlendShapes = 6;
 
 // Sets the message returned by fdgs_last_error() on this thread.
 void set_error_message(const char *msg);

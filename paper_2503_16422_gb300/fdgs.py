@@ -469,6 +469,12 @@ def set_list_builder(mode):
     check(lib().fdgs_set_list_builder(int(mode)))
 
 
+# launch shape of the forward blend when none is set (8x8 warp footprint, two pixels a lane)
+DEFAULT_BLEND_SHAPE = 3
+
+
 def set_blend_shape(footprint):
-    """Forward-blend warp footprint (0: 16x2, 1: 8x4, 2: 4x8 pixels), process-wide."""
+    """Forward-blend launch shape, process-wide: the warp footprint and pixels per lane (0:
+    16x2, 1: 8x4, 2: 4x8 with one pixel a lane; 3: 8x8 with two; 4: 16x8, 5: 8x16 with
+    four). Results do not depend on it."""
     check(lib().fdgs_set_blend_shape(int(footprint)))

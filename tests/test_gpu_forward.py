@@ -143,14 +143,16 @@ def test_background_colour(fd):
     sc.close()
 
 
-@pytest.mark.parametrize("builder,shape", [(1, 0), (1, 2), (2, 0), (2, 1), (2, 2)])
+@pytest.mark.parametrize("builder,shape", [(1, 0), (1, 2), (1, 3), (1, 4), (1, 5), (2, 0),
+                                           (2, 1), (2, 2), (2, 3)])
 def test_list_builders_and_blend_shapes_give_identical_frames(fd, builder, shape):
-    """Bitmask vs sort tile lists, and the three warp footprints of the blend (with their
-    ballot culling), must all give the same lists and bit-identical images."""
+    """Bitmask vs sort tile lists, and the six launch shapes of the blend (warp footprints
+    with their ballot culling, one, two or four pixels per lane), must all give the same lists
+    and bit-identical images, transmittances and n_contrib."""
     s = scenes.make_scene(6000, 17, sh_degree=1, lt_long=(-1.0, 0.5))
     cam = scenes.arc_camera(4.0, 200, 150)
     fd.set_list_builder(1)
-    fd.set_blend_shape(1)
+    fd.set_blend_shape(1)   # one pixel per lane, 8x4 footprint: the reference shape
     try:
         ref = _run(fd, s, cam, 0.4)
         fd.set_list_builder(builder)
@@ -158,7 +160,7 @@ def test_list_builders_and_blend_shapes_give_identical_frames(fd, builder, shape
         g = _run(fd, s, cam, 0.4)
     finally:
         fd.set_list_builder(0)
-        fd.set_blend_shape(1)
+        fd.set_blend_shape(fd.DEFAULT_BLEND_SHAPE)
     assert ref["stats"]["list_builder"] == 1 and g["stats"]["list_builder"] == builder
     for k in ("image", "T_final", "n_contrib", "tile_ranges", "tile_ids"):
         assert np.array_equal(g[k], ref[k]), k
