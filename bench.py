@@ -37,7 +37,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FPS at 1352x1014 (masked 4DGS render, 1 GB300)"
 FLUSH_BYTES = 256 << 20
-EVAL_FLOP = 20        # FP32 FLOP per (Gaussian, pixel) evaluation (FMA = 2)
+# FP32 FLOP per (Gaussian, pixel) evaluation (FMA = 2): offsets 2, exponent 7, log-opacity
+# add 1, alpha clamp 1, transmittance 2, weight 1, colour 6 (plus one MUFU exp2)
+EVAL_FLOP = 20
 TEST_FLOP = 36        # FP32 FLOP per footprint culling test (4 edges x 9)
 W_FULL, H_FULL = 1352, 1014
 
@@ -228,17 +230,19 @@ def profile_single(sc, cams, times, frames, masked, out, flush, scene):
         stats.append(fr.stats())
         fr.release()
     sc.profile(2)
-    ev = te = 0
+    ev = te = ep = 0
     for k in frames:
         sc.render(cams[k], float(times[k]), use_mask=masked, out=out)
-        _, e, t = sc.profile_read()
+        e, t, p = sc.blend_counts()
         ev += e / len(frames)
         te += t / len(frames)
+        ep += p / len(frames)
     sc.profile(0)
     counts = {f: float(np.mean([st[f] for st in stats])) for f in ("n_active", "n_visible",
                                                                   "n_keys")}
     counts["blend_evals"] = ev
     counts["blend_tests"] = te
+    counts["blend_evals_alpha_pass"] = ep
     sb = [stage_bytes(st, scene.n, scene.sh_degree, masked) for st in stats]
     bytes_mean = {s_: float(np.mean([b[s_] for b in sb])) for s_ in sb[0]}
     return acc, counts, bytes_mean
@@ -248,13 +252,16 @@ def roofline(stage_ms, counts, bytes_mean):
     pk = peaks()
     dom = max((s_ for s_ in stage_ms if s_ != "host_sync"), key=stage_ms.get)
     if dom == "blend":
-        flop = counts["blend_evals"] * EVAL_FLOP + counts["blend_tests"] * TEST_FLOP
+        flop = counts["blend_evals_alpha_pass"] * EVAL_FLOP
         ach = flop / (stage_ms["blend"] / 1e3) / 1e12
         peak = fp32_peak_tflops(pk["sm_mhz"])
+        executed = counts["blend_evals"] * EVAL_FLOP + counts["blend_tests"] * TEST_FLOP
         return {"bound": "alu", "kernel": "k_blend", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                 "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_mhz']:.0f} MHz",
-                "work": "executed evaluations x 20 FLOP + culling tests x 36 FLOP"}
+                "work": "(Gaussian, pixel) evaluations reaching alpha >= 1/255 at a pixel still "
+                        "compositing x 20 FLOP",
+                "executed_tflops": executed / (stage_ms["blend"] / 1e3) / 1e12}
     ach = bytes_mean[dom] / (stage_ms[dom] / 1e3) / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
             "frac": ach / pk["hbm"], "traffic": None, "peak_src": pk["src"] + " copy GB/s"}
@@ -284,14 +291,15 @@ def batch_counts(sc, cams_list, ts_list, outs):
     """Blend evaluations and culling tests of the given batches (counting profile: eager
     runs with the counting blend variant; untimed)."""
     sc.profile(2)
-    ev = te = 0
+    ev = te = ep = 0
     for cams, ts in zip(cams_list, ts_list):
         sc.render_batch(cams, ts, outs=outs)
-        _, e, t = sc.profile_read()
+        e, t, p = sc.blend_counts()
         ev += e
         te += t
+        ep += p
     sc.profile(0)
-    return ev, te
+    return ev, te, ep
 
 
 def run_ours(args):
@@ -391,10 +399,10 @@ def run_ours(args):
     if rank == 0:
         # batch stages: CUDA events recorded inside the replayed graph, every timed step
         bst = {k: float(np.mean([s_[k] for s_ in step_stages])) for k in step_stages[0]}
-        ev, te = batch_counts(sc, [a for a, _ in steps], [b for _, b in steps], outs)
+        ev, te, ep = batch_counts(sc, [a for a, _ in steps], [b for _, b in steps], outs)
         blend_s = sum(s_["blend"] for s_ in step_stages) / 1e3
         pk = peaks()
-        ach = (ev * EVAL_FLOP + te * TEST_FLOP) / blend_s / 1e12
+        ach = ep * EVAL_FLOP / blend_s / 1e12
         peak = fp32_peak_tflops(pk["sm_mhz"])
         res["roofline"] = {
             "bound": "alu", "kernel": "k_blend_persist", "achieved": ach, "peak": peak,
@@ -404,10 +412,13 @@ def run_ours(args):
                            "launch (profiles/k_blend_persist_batched_1352x1014.md), per frame "
                            f"x {B} frames per launch",
             "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_mhz']:.0f} MHz",
-            "work": "executed (Gaussian, pixel) evaluations x 20 FLOP + culling tests x 36 FLOP,"
-                    " counted on the same batches; time = in-graph %globaltimer stage stamps, timed steps",
+            "work": "(Gaussian, pixel) evaluations reaching alpha >= 1/255 at a pixel still "
+                    "compositing (the evaluations every blend order makes) x 20 FLOP, counted "
+                    "on the same batches; time = in-graph %globaltimer stage stamps, timed steps",
+            "executed_tflops": (ev * EVAL_FLOP + te * TEST_FLOP) / blend_s / 1e12,
             "blend_ms_per_batch": blend_s * 1e3 / len(steps),
-            "evals_per_frame": ev / frames_done, "tests_per_frame": te / frames_done}
+            "evals_per_frame": ev / frames_done, "tests_per_frame": te / frames_done,
+            "alpha_pass_evals_per_frame": ep / frames_done}
         res["batch_stages_ms"] = bst
         # per-kernel profile on single renders of the same frames
         out1 = outs[0]
@@ -696,9 +707,9 @@ def score_timing(stream):
 
 
 # DRAM bytes the persistent blend moves per frame of a batch at 1352x1014 on the 200k pruned
-# scene, from one ncu capture of an 8-frame launch (298.2 MB); to be re-captured whenever the
-# blend kernel changes.
-BLEND_PERSIST_DRAM_BYTES_PER_FRAME = 298.2e6 / 8
+# scene, from one ncu capture of an 8-frame launch of k_blend_persist<8, 4> (89.2 MB read +
+# 77.5 MB written); to be re-captured whenever the blend kernel changes.
+BLEND_PERSIST_DRAM_BYTES_PER_FRAME = (89230336 + 77507584) / 8
 
 
 def launches_per_batch():

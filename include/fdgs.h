@@ -299,9 +299,11 @@ int fdgs_select_keep_noalloc(const float *score_dev, int64_t n, float prune_rati
 #define FDGS_PROFILE_STAGES 8
 int fdgs_profile_enable(fdgs_scene *scene, int flags);
 
-/* Stage times in milliseconds of the last profiled render, and blend_counts[2] of the last
- * counted render: (Gaussian, pixel) evaluations executed and footprint culling tests
- * executed (either pointer may be NULL). Synchronises the device. */
+/* Stage times in milliseconds of the last profiled render, and blend_counts[3] of the last
+ * counted render or batch: (Gaussian, pixel) evaluations executed, footprint culling tests
+ * executed, and evaluations that reached alpha >= 1/255 at a pixel still compositing (the
+ * blended ones and the ones that stopped a pixel: the evaluations any blend order must
+ * make, whatever its culling). Either pointer may be NULL. Synchronises the device. */
 int fdgs_profile_read(fdgs_scene *scene, float *stage_ms, uint64_t *blend_counts);
 
 /* How renders build the per-tile lists, process-wide. 1: emit one (tile, depth-rank) key

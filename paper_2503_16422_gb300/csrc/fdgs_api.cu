@@ -137,7 +137,7 @@ struct BatchPlan {
   unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int footprint = 4, ctas = 0;
+  int footprint = 5, ctas = 0;
   bool tuned = false;
   std::vector<float> lat_ms;
   Buf stamps;                                  // u64[kBatchStages + 1] %globaltimer
@@ -176,7 +176,7 @@ struct fdgs_scene {
                   // 3 device scalar, 4 score-pass image, 5 key-frame mask word row
   int prof = 0;   // profiling flags (fdgs_profile_enable)
   cudaEvent_t ev[FDGS_PROFILE_STAGES + 1] = {};
-  Buf evals;      // u64[2] blend evaluations and culling tests
+  Buf evals;      // u64[3] blend evaluations, culling tests, alpha >= 1/255 evaluations
   const float *sh_cb = nullptr;        // borrowed SH codebook (fdgs_set_sh_codebook) or null
   const uint16_t *sh_code = nullptr;
   int n_code = 0;
@@ -316,7 +316,7 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   }
   const bool prof = (s->prof & 1) && s->ev[0];
   const bool count = (s->prof & 2) && s->evals.p;
-  if (count) CK(cudaMemsetAsync(s->evals.p, 0, 16, st));
+  if (count) CK(cudaMemsetAsync(s->evals.p, 0, 24, st));
   if (prof) CK(cudaEventRecord(s->ev[0], st));
   CK(cudaMemsetAsync(ws.ctr.p, 0, C_COUNT * 4, st));
   CK(cudaMemsetAsync(ws.pre_status.p, 0, parts * 8, st));
@@ -1143,7 +1143,7 @@ int fdgs_profile_enable(fdgs_scene *s, int flags) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   if ((flags & 1) && !s->ev[0])
     for (auto &e : s->ev) CK(cudaEventCreate(&e));
-  if (flags & 2) TRY(grow(s->evals, 16));
+  if (flags & 2) TRY(grow(s->evals, 24));
   s->prof = flags;
   return FDGS_OK;
 }
@@ -1158,8 +1158,8 @@ int fdgs_profile_read(fdgs_scene *s, float *stage_ms, uint64_t *blend_counts) {
     }
   }
   if (blend_counts) {
-    blend_counts[0] = blend_counts[1] = 0;
-    if (s->evals.p) CK(cudaMemcpy(blend_counts, s->evals.p, 16, cudaMemcpyDeviceToHost));
+    blend_counts[0] = blend_counts[1] = blend_counts[2] = 0;
+    if (s->evals.p) CK(cudaMemcpy(blend_counts, s->evals.p, 24, cudaMemcpyDeviceToHost));
   }
   return FDGS_OK;
 }

@@ -397,7 +397,7 @@ void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
   cudaMemsetAsync(b.key_cnt, 0, b.nreq * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.diff, 0, L.diff_bytes, st);
   cudaMemsetAsync(b.done_ns, 0, b.nreq * sizeof(unsigned long long), st);
-  if (b.evals) cudaMemsetAsync(b.evals, 0, 2 * sizeof(unsigned long long), st);
+  if (b.evals) cudaMemsetAsync(b.evals, 0, 3 * sizeof(unsigned long long), st);
   // stage boundaries: a one-thread kernel stamps %globaltimer (events recorded inside a
   // captured graph cannot be timed); stream order makes each difference a stage duration
   auto mark = [&](int i) { k_stamp<<<1, 1, 0, st>>>(b.stamps, i); };

@@ -92,7 +92,8 @@ struct BlendTile {
   float bg0, bg1, bg2;
   float *w_sum;                // per-rank weights (score pass) or null
   uint32_t *stop_mark;         // per-rank flag: the entry stopped a pixel (with w_sum)
-  unsigned long long *evals;   // [2] evaluations, culling tests (profiling) or null
+  unsigned long long *evals;   // [3] evaluations, culling tests, alpha >= 1/255 evaluations
+                               // (profiling) or null
 };
 
 // kAux: also write the final transmittance and 1 + the list position of the last blended
@@ -126,7 +127,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     done[p] = !(px0 + p * HW < bt.W && py < bt.H);
     lane_done = lane_done && done[p];
   }
-  uint32_t nevals = 0, ntests = 0;
+  uint32_t nevals = 0, ntests = 0, npass = 0;
   bool warp_done = __all_sync(0xffffffffu, lane_done);
 
   K kr = (K)0;
@@ -228,6 +229,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
           const float e = __fadd_rn(q, h1.y);
           const bool valid = !done[p] && q <= 0.f && e >= kLog2AlphaMin;
           if (kCount && !done[p]) ++nevals;
+          if (kCount && valid) ++npass;
           const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
           const float nT = T[p] * (1.f - alpha);
           // only a valid entry can stop a pixel: an unfinished pixel has T >= kTStop
@@ -263,9 +265,10 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     }
   }
   if (kCount) {
-    const uint32_t ws = warp_sum(nevals), wt = warp_sum(ntests);
+    const uint32_t ws = warp_sum(nevals), wt = warp_sum(ntests), wp = warp_sum(npass);
     if (lane == 0 && ws) atomicAdd(&bt.evals[0], (unsigned long long)ws);
     if (lane == 0 && wt) atomicAdd(&bt.evals[1], (unsigned long long)wt);
+    if (lane == 0 && wp) atomicAdd(&bt.evals[2], (unsigned long long)wp);
   }
   const size_t hw = (size_t)bt.W * bt.H;
 #pragma unroll

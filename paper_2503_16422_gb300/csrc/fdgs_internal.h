@@ -76,7 +76,7 @@ struct BlendArgs {
   uint32_t *n_contrib; // [H][W]
   float *w_sum;        // optional [nv] per-rank blend-weight sums (score pass)
   uint32_t *stop_mark; // with w_sum: [nv] per-rank flag, set where the entry stopped a pixel
-  unsigned long long *evals;  // optional evaluation counter (profiling)
+  unsigned long long *evals;  // optional evaluation counters [3] (profiling)
 };
 template <typename K>
 void launch_blend(const BlendArgs &a, const K *keys, uint32_t rmask, cudaStream_t st);
@@ -174,7 +174,7 @@ struct BatchDev {
   const uint64_t *queue;
   uint32_t *lists;                   // [key_cap] slot indices
   unsigned long long *done_ns, *t0_ns;
-  unsigned long long *evals;         // [2] blend evaluations / culling tests, or null
+  unsigned long long *evals;         // [3] blend counters (see BlendTile), or null
   unsigned long long *stamps;        // [kBatchStages + 1] %globaltimer at stage boundaries
 };
 struct BatchLaunch {

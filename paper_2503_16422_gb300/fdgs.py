@@ -412,9 +412,16 @@ class Scene:
 
     def profile_read(self):
         ms = (ctypes.c_float * len(PROFILE_STAGES))()
-        ev = (ctypes.c_uint64 * 2)()
+        ev = (ctypes.c_uint64 * 3)()
         check(lib().fdgs_profile_read(self.handle, ms, ev))
         return dict(zip(PROFILE_STAGES, list(ms))), int(ev[0]), int(ev[1])
+
+    def blend_counts(self):
+        """Counters of the last counted render or batch: evaluations executed, culling tests
+        executed, evaluations with alpha >= 1/255 at a pixel still compositing."""
+        ev = (ctypes.c_uint64 * 3)()
+        check(lib().fdgs_profile_read(self.handle, None, ev))
+        return int(ev[0]), int(ev[1]), int(ev[2])
 
     def status_sync(self):
         check(lib().fdgs_status_sync(self.handle))
