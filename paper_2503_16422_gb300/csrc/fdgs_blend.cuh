@@ -217,7 +217,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
         const float4 h0 = sm.h0[warp][k];
         const float4 h1 = sm.h1[warp][k];
         const float2 h2 = sm.h2[warp][k];
-        // the exponent of splat_alpha, with the row terms shared by the lane's pixels
+        // the row terms of the exponent are shared by the lane's pixels
         const float dy = __fsub_rn(h0.y, fpy);
         const float b2dy = __fmul_rn(h0.w, dy);
         const float c2dy2 = __fmul_rn(__fmul_rn(h1.x, dy), dy);
@@ -231,14 +231,17 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
           if (kCount && !done[p]) ++nevals;
           if (kCount && valid) ++npass;
           const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
-          const float nT = T[p] * (1.f - alpha);
+          // Eq. 2's transmittance step T (1 - alpha), taken as T - alpha T: the weight alpha T
+          // is needed anyway, so this saves the subtraction 1 - alpha
+          const float wa = alpha * T[p];
+          const float nT = T[p] - wa;
           // only a valid entry can stop a pixel: an unfinished pixel has T >= kTStop
           const bool stop = nT < kTStop;
           // the entry that ends this pixel's list: the key-frame masks keep it
           if (kWeights && stop) bt.stop_mark[sm.rk[st][__float_as_int(h2.y)]] = 1u;
           done[p] = done[p] || stop;
           const bool use = valid && !stop;
-          const float wi = use ? alpha * T[p] : 0.f;
+          const float wi = stop ? 0.f : wa;
           C0[p] = fmaf(h1.z, wi, C0[p]);
           C1[p] = fmaf(h1.w, wi, C1[p]);
           C2[p] = fmaf(h2.x, wi, C2[p]);
