@@ -127,11 +127,11 @@ struct BatchPlan {
   fdgs_scene_desc d{};
   const float *sh_cb = nullptr;            // codebook pointers captured in the graph
   const uint16_t *sh_code = nullptr;
-  uint32_t ntiles = 0, mask_words = 0;
+  uint32_t ntiles = 0, nblocks = 0, mask_words = 0;
   uint64_t key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
   std::vector<ReqDesc> tmpl;
   Buf reqs, ctr, part, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base, key_cnt,
-      rec_sorted, diff, masks, ranges, qkeys, qkeys_alt, lists, done, t0, scratch;
+      rec_sorted, rect, diff, masks, ranges, qkeys, qkeys_alt, lists, done, t0, scratch;
   ReqDesc *h_reqs = nullptr;
   uint32_t *h_ctr = nullptr;
   unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
@@ -147,7 +147,7 @@ struct BatchPlan {
     stamps.release();
     if (h_stamps) cudaFreeHost(h_stamps);
     Buf *all[] = {&reqs, &ctr, &part, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
-                  &slot_base, &key_cnt, &rec_sorted, &diff, &masks, &ranges, &qkeys,
+                  &slot_base, &key_cnt, &rec_sorted, &rect, &diff, &masks, &ranges, &qkeys,
                   &qkeys_alt, &lists, &done, &t0, &scratch};
     for (Buf *b : all) b->release();
     if (h_reqs) cudaFreeHost(h_reqs);
@@ -478,7 +478,7 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   const uint32_t N = (uint32_t)s->d.n;
   p.mask_words = (N + 255) / 256 * 8;
   p.tmpl.resize(n);
-  uint64_t tiles = 0, diff = 0, mask = 0;
+  uint64_t tiles = 0, blocks = 0, diff = 0, mask = 0;
   for (int i = 0; i < n; ++i) {
     DevCam dc;
     TRY(make_cam(&cams[i], dc));
@@ -489,13 +489,18 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
     q.tile_base = (uint32_t)tiles;
     q.diff_base = (uint32_t)diff;
     q.mask_base = mask;
+    q.block_base = (uint32_t)blocks;
+    const uint64_t bgx = (dc.gx + kListBlock - 1) / kListBlock;
+    const uint64_t bgy = (dc.gy + kListBlock - 1) / kListBlock;
+    blocks += bgx * bgy;
     tiles += (uint64_t)dc.gx * dc.gy;
     diff += (uint64_t)(dc.gx + 1) * (dc.gy + 1);
-    mask += (uint64_t)(dc.gx + dc.gy) * p.mask_words;
+    mask += (bgx + bgy) * p.mask_words;
   }
   if (tiles >= (1ull << 32) || diff >= (1ull << 31))
     return fail(FDGS_ERR_INVALID, "batch too large");
   p.ntiles = (uint32_t)tiles;
+  p.nblocks = (uint32_t)blocks;
   p.diff_ints = diff;
   p.mask_total = mask;
   p.rn = (uint64_t)n * N;
@@ -514,6 +519,7 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   TRY(grow(p.slot_base, n * 4));
   TRY(grow(p.key_cnt, n * 8));
   TRY(grow(p.rec_sorted, p.slot_cap * kRecS * 4));
+  TRY(grow(p.rect, p.slot_cap * 8));
   TRY(grow(p.diff, diff * 4));
   TRY(grow(p.masks, std::max<uint64_t>(mask, 1) * 4));
   TRY(grow(p.ranges, tiles * 8));
@@ -561,6 +567,7 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.nreq = p.nreq;
   b.n = (uint32_t)s->d.n;
   b.ntiles = p.ntiles;
+  b.nblocks = p.nblocks;
   b.mask_words = p.mask_words;
   b.key_cap = p.key_cap;
   b.mean4 = (const float4 *)s->d.mean4;
@@ -585,6 +592,7 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.slot_base = p.slot_base.as<uint32_t>();
   b.key_cnt = p.key_cnt.as<unsigned long long>();
   b.rec_sorted = p.rec_sorted.as<float>();
+  b.rect = p.rect.as<uint2>();
   b.diff = p.diff.as<int>();
   b.masks = p.masks.as<uint32_t>();
   b.ranges = p.ranges.as<uint2>();

@@ -6,10 +6,11 @@
 //   k_batch_bases    per-request visible counts -> contiguous bases and 256-aligned slots
 //   k_seg_compact    request segments -> one contiguous array of (request, depth, id) keys
 //   radix_sort       one global depth sort (request bits on top keep requests apart)
-//   k_gather_batch   blend-ready records per slot, per-request key counts, coverage
-//                    difference arrays and row/column bitmasks per request
+//   k_gather_batch   blend-ready records and tile rectangles per slot, per-request key
+//                    counts, coverage difference arrays and block-row/column bitmasks
 //   k_tile_scan_batch  per-request tile ranges (capacity-checked) and longest-first queue keys
-//   k_lists_batch    per-tile lists from the bitmasks, for every request's tiles
+//   k_lists_blocks   per-tile lists, a warp per 4x4 block of tiles: the block's entries from
+//                    its bitmasks, dealt to its tiles by their rectangles
 //   radix_sort       queue keys by list length (descending)
 //   k_blend_persist  persistent CTAs take tiles from the queue, longest first, and record
 //                    each request's completion time (%globaltimer)
@@ -216,6 +217,9 @@ __global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
       dst[3] = make_float4(a0.z, a0.w, a1.x, a1.y);
       tile_rect(a0.x, a0.y, a2.z, q.cam.gx, q.cam.gy, x0, y0, x1, y1);
       tighten_rect(a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, x0, y0, x1, y1);
+      if (!(x1 > x0 && y1 > y0)) x0 = y0 = x1 = y1 = 0;
+      b.rect[s] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16),
+                             (uint32_t)y0 | ((uint32_t)y1 << 16));
       if (x1 > x0 && y1 > y0) {
         cnt = (uint32_t)((x1 - x0) * (y1 - y0));
         int *diff = b.diff + q.diff_base;
@@ -224,18 +228,19 @@ __global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
         atomicAdd(&diff[y0 * W1 + x1], -1);
         atomicAdd(&diff[y1 * W1 + x0], -1);
         atomicAdd(&diff[y1 * W1 + x1], 1);
-      } else {
-        x0 = y0 = x1 = y1 = 0;
       }
     }
-    // coverage bitmasks of the request; the warp owns local word l / 32
+    // block-row and block-column coverage bitmasks of the request (a block row holds
+    // kListBlock tile rows); the warp owns local word l / 32
     {
-      const int gx = q.cam.gx, gy = q.cam.gy;
+      const int bgx = (q.cam.gx + kListBlock - 1) / kListBlock;
+      const int bgy = (q.cam.gy + kListBlock - 1) / kListBlock;
       const size_t mw = b.mask_words;
       uint32_t *rows = b.masks + q.mask_base + (l >> 5);
-      uint32_t *cols = rows + (size_t)gy * mw;
-      warp_coverage_words(y0, y1, gy, rows, mw);
-      warp_coverage_words(x0, x1, gx, cols, mw);
+      uint32_t *cols = rows + (size_t)bgy * mw;
+      const int e = kListBlock - 1;
+      warp_coverage_words(y0 / kListBlock, (y1 + e) / kListBlock, bgy, rows, mw);
+      warp_coverage_words(x0 / kListBlock, (x1 + e) / kListBlock, bgx, cols, mw);
     }
     // the request's key count (its lists' total length); the partition's part of it
     const uint32_t ws = warp_sum(cnt);
@@ -316,23 +321,133 @@ __global__ void __launch_bounds__(kTS) k_tile_scan_batch(BatchDev b) {
   }
 }
 
-// Per-tile lists of slot indices from the request's bitmasks (warp per global tile).
-__global__ void __launch_bounds__(kB) k_lists_batch(BatchDev b) {
-  __shared__ uint32_t s_tile_base[kMaxReq];
-  for (int r = threadIdx.x; r < b.nreq; r += kB) s_tile_base[r] = b.reqs[r].tile_base;
+// Per-tile lists of slot indices, one warp per block of kListBlock x kListBlock tiles. The
+// warp ANDs the block's row and column bitmasks 32 words at a time (one word per lane, the
+// next words in flight); each entry found (a Gaussian whose rectangle meets the block) goes
+// to a per-warp queue in rank order, then the block-local masks of the tiles the new entries'
+// rectangles cover are formed by all lanes together (independent loads). Every 32 queued
+// entries are dealt to the block's tiles: per tile, a ballot of the entries that cover it and
+// one coalesced store of their slots at the tile's running offset (held by lane t for tile
+// t). A tile thus receives exactly the Gaussians whose rectangles cover it, in rank order:
+// the same lists as ANDing per-tile row and column masks, for a sixteenth of the word scans.
+// The queue holds kLQ entries; a round of 32 words with more entries than fit is queued in
+// parts (each lane keeps its remaining bits), so the queue stays small and many warps fit.
+constexpr int kLW = 4;                          // warps per CTA
+constexpr uint32_t kLQ = 288;                   // queue entries per warp
+static_assert(kListBlock == 4, "the tile masks below hold 4 x 4 tiles in 16 bits");
+
+__device__ __forceinline__ void deal_to_tiles(uint32_t slot, uint32_t tm, uint32_t &off,
+                                              uint32_t *__restrict__ lists) {
+  const uint32_t lane = lane_id(), lt = lanemask_lt();
+  const uint32_t tiles = __reduce_or_sync(0xffffffffu, tm);
+#pragma unroll
+  for (int t = 0; t < kListBlock * kListBlock; ++t) {
+    if (!((tiles >> t) & 1u)) continue;          // warp-uniform
+    const bool hit = (tm >> t) & 1u;
+    const uint32_t bm = __ballot_sync(0xffffffffu, hit);
+    const uint32_t ot = __shfl_sync(0xffffffffu, off, t);
+    if (hit) lists[ot + __popc(bm & lt)] = slot;
+    if (lane == (uint32_t)t) off += __popc(bm);
+  }
+}
+
+__global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
+  __shared__ uint32_t s_slot[kLW][kLQ];
+  __shared__ uint16_t s_tm[kLW][kLQ];
+  __shared__ uint32_t s_block_base[kMaxReq];
+  for (int r = threadIdx.x; r < b.nreq; r += kLW * 32) s_block_base[r] = b.reqs[r].block_base;
   __syncthreads();
   const int warp = threadIdx.x >> 5;
-  for (uint32_t gt = blockIdx.x * kW + warp; gt < b.ntiles; gt += gridDim.x * kW) {
-    const int r = find_segment(s_tile_base, b.nreq, gt);
+  const uint32_t lane = lane_id();
+  uint32_t *qs = s_slot[warp];
+  uint16_t *qm = s_tm[warp];
+  const uint2 *__restrict__ rect = b.rect;
+  uint32_t *__restrict__ lists = b.lists;
+  const uint32_t *__restrict__ masks = b.masks;
+  const size_t mw = b.mask_words;
+  const int nreq = b.nreq;
+  for (uint32_t gb = blockIdx.x * kLW + warp; gb < b.nblocks; gb += gridDim.x * kLW) {
+    const int r = find_segment(s_block_base, nreq, gb);
     const ReqDesc &q = b.reqs[r];
-    const uint32_t t = gt - q.tile_base;
-    const uint2 rg = b.ranges[gt];
-    if (rg.y == rg.x) continue;
-    const uint32_t words = (b.nv[r] + 31) / 32;
-    const uint32_t *rows = b.masks + q.mask_base + (size_t)(t / q.cam.gx) * b.mask_words;
-    const uint32_t *cols = b.masks + q.mask_base + (size_t)q.cam.gy * b.mask_words +
-                           (size_t)(t % q.cam.gx) * b.mask_words;
-    warp_list_from_masks(rows, cols, words, rg.x, b.slot_base[r], b.lists);
+    const int gx = q.cam.gx, gy = q.cam.gy;
+    const int bgx = (gx + kListBlock - 1) / kListBlock;
+    const int bgy = (gy + kListBlock - 1) / kListBlock;
+    const uint32_t lb = gb - q.block_base;
+    const int bx0 = (int)(lb % bgx) * kListBlock, by0 = (int)(lb / bgx) * kListBlock;
+    // lane t < 16 holds tile t's write offset; live tiles exist and have a non-empty range
+    uint32_t off = 0;
+    bool live = false;
+    {
+      const int tx = bx0 + (int)(lane % kListBlock), ty = by0 + (int)(lane / kListBlock);
+      if (lane < kListBlock * kListBlock && tx < gx && ty < gy) {
+        const uint2 rg = b.ranges[q.tile_base + (uint32_t)(ty * gx + tx)];
+        off = rg.x;
+        live = rg.y > rg.x;
+      }
+    }
+    const uint32_t live_mask = __ballot_sync(0xffffffffu, live);
+    if (live_mask == 0) continue;
+    const uint32_t words = (b.nv[r] + 31) / 32, base = b.slot_base[r];
+    const uint32_t *rows = masks + q.mask_base + (size_t)(by0 / kListBlock) * mw;
+    const uint32_t *cols = masks + q.mask_base + (size_t)bgy * mw + (size_t)(bx0 / kListBlock) * mw;
+    uint32_t qn = 0;                             // queued entries (warp-uniform, < 32 here)
+    // the words of the next round are loaded while this round is processed
+    uint32_t nr = lane < words ? __ldg(&rows[lane]) : 0u;
+    uint32_t nc = lane < words ? __ldg(&cols[lane]) : 0u;
+    for (uint32_t w0 = 0; w0 < words; w0 += 32) {
+      const uint32_t sb = base + (w0 + lane) * 32;
+      uint32_t m = nr & nc;
+      const uint32_t wn = w0 + 32 + lane;
+      nr = wn < words ? __ldg(&rows[wn]) : 0u;
+      nc = wn < words ? __ldg(&cols[wn]) : 0u;
+      for (;;) {
+        const uint32_t pc = __popc(m);
+        const uint32_t inc = warp_incl_scan(pc);
+        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+        if (tot == 0) break;
+        uint32_t pos = qn + inc - pc;
+        while (m && pos < kLQ) {
+          qs[pos++] = sb + (uint32_t)(__ffs(m) - 1);
+          m &= m - 1;
+        }
+        const uint32_t qn1 = min(qn + tot, kLQ);
+        __syncwarp();
+        // tile masks of the new entries, from their rectangles (independent loads)
+        for (uint32_t e = qn + lane; e < qn1; e += 32) {
+          const uint2 rc = __ldg(&rect[qs[e]]);
+          const int rx0 = max((int)(rc.x & 0xFFFFu) - bx0, 0);
+          const int rx1 = min((int)(rc.x >> 16) - bx0, kListBlock);
+          const int ry0 = max((int)(rc.y & 0xFFFFu) - by0, 0);
+          const int ry1 = min((int)(rc.y >> 16) - by0, kListBlock);
+          uint32_t tm = 0;
+          if (rx1 > rx0 && ry1 > ry0) {
+            const uint32_t xm = (1u << rx1) - (1u << rx0);
+            const uint32_t ym = (1u << (kListBlock * ry1)) - (1u << (kListBlock * ry0));
+            tm = (xm * 0x1111u) & ym & live_mask;
+          }
+          qm[e] = (uint16_t)tm;
+        }
+        __syncwarp();
+        uint32_t c = 0;
+        for (; c + 32 <= qn1; c += 32) deal_to_tiles(qs[c + lane], qm[c + lane], off, lists);
+        // the remainder (< 32 entries) moves to the front of the queue
+        const uint32_t rem = qn1 - c;
+        uint32_t ks = 0, km = 0;
+        if (c > 0 && lane < rem) {
+          ks = qs[c + lane];
+          km = qm[c + lane];
+        }
+        __syncwarp();
+        if (c > 0 && lane < rem) {
+          qs[lane] = ks;
+          qm[lane] = (uint16_t)km;
+        }
+        qn = rem;
+        __syncwarp();
+      }
+    }
+    if (qn > 0) deal_to_tiles(lane < qn ? qs[lane] : 0u, lane < qn ? qm[lane] : 0u, off, lists);
+    __syncwarp();
   }
 }
 
@@ -427,8 +542,9 @@ void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
   mark(3);
   k_tile_scan_batch<<<b.nreq, kTS, 0, st>>>(b2);
   mark(4);
-  k_lists_batch<<<(int)std::min<uint64_t>((b.ntiles + kW - 1) / kW, (uint64_t)num_sms() * 8),
-                  kB, 0, st>>>(b2);
+  k_lists_blocks<<<(int)std::min<uint64_t>((b.nblocks + kLW - 1) / kLW,
+                                            (uint64_t)num_sms() * 32),
+                   kLW * 32, 0, st>>>(b2);
   mark(5);
   uint64_t *qs = radix_sort<uint64_t>(b.qkeys, b.qkeys_alt, b.ctr + BC_NTILES, b.ntiles, 32, 24,
                                       L.sort_scratch, st, b.err);

@@ -232,51 +232,6 @@ __device__ __forceinline__ void tighten_rect(float u, float v, float A, float B,
   y1 = min(y1, (int)floorf((v + hy) * inv) + 1);
 }
 
-// One warp writes a tile's list from coverage bitmasks over depth ranks: the ranks r < 32 words
-// whose bit is set in both the tile row's and the tile column's mask, ascending, as base + r,
-// to lists[off ..]. Each lane takes four consecutive words per step (one 128-bit load per
-// mask; both masks 16-byte aligned and readable up to words rounded up to 4); the loads of
-// step s+2 are in flight while step s is written out.
-__device__ __forceinline__ void warp_list_from_masks(const uint32_t *__restrict__ rows,
-                                                     const uint32_t *__restrict__ cols,
-                                                     uint32_t words, uint32_t off, uint32_t base,
-                                                     uint32_t *__restrict__ lists) {
-  const uint32_t lane = lane_id();
-  const uint32_t n4 = (words + 3) / 4;
-  const uint4 *r4 = reinterpret_cast<const uint4 *>(rows);
-  const uint4 *c4 = reinterpret_cast<const uint4 *>(cols);
-  const uint4 z = make_uint4(0, 0, 0, 0);
-  uint4 nr0 = lane < n4 ? __ldg(&r4[lane]) : z, nc0 = lane < n4 ? __ldg(&c4[lane]) : z;
-  uint4 nr1 = lane + 32 < n4 ? __ldg(&r4[lane + 32]) : z;
-  uint4 nc1 = lane + 32 < n4 ? __ldg(&c4[lane + 32]) : z;
-  for (uint32_t s0 = 0; s0 < n4; s0 += 32) {
-    const uint32_t q = s0 + lane, w0 = 4 * q;
-    uint32_t m0 = nr0.x & nc0.x, m1 = nr0.y & nc0.y, m2 = nr0.z & nc0.z, m3 = nr0.w & nc0.w;
-    nr0 = nr1;
-    nc0 = nc1;
-    nr1 = q + 64 < n4 ? __ldg(&r4[q + 64]) : z;
-    nc1 = q + 64 < n4 ? __ldg(&c4[q + 64]) : z;
-    if (w0 + 1 >= words) m1 = 0u;   // words past the end (the rounding up to 4) are not masks
-    if (w0 + 2 >= words) m2 = 0u;
-    if (w0 + 3 >= words) m3 = 0u;
-    const uint32_t pc = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
-    const uint32_t inc = warp_incl_scan(pc);
-    uint32_t o = off + inc - pc;
-    const uint32_t rb = base + w0 * 32;
-    auto emit = [&](uint32_t m, uint32_t r0) {
-      while (m) {
-        lists[o++] = r0 + (uint32_t)(__ffs(m) - 1);
-        m &= m - 1;
-      }
-    };
-    emit(m0, rb);
-    emit(m1, rb + 32);
-    emit(m2, rb + 64);
-    emit(m3, rb + 96);
-    off += __shfl_sync(0xffffffffu, inc, 31);
-  }
-}
-
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLog2AlphaMin = -7.9943534368588578f;   // log2(1/255)
 

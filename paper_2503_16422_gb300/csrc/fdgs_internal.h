@@ -142,9 +142,13 @@ struct ReqDesc {
   float bg[3];
   float *rgb;                        // [3][H][W]
   uint32_t tile_base;                // first global tile id of the request
+  uint32_t block_base;               // first global tile-block id (kListBlock^2 tiles each)
   uint32_t diff_base;                // offset of its coverage difference array (ints)
-  uint64_t mask_base;                // offset of its row and column bitmasks (words)
+  uint64_t mask_base;                // offset of its block-row and block-column bitmasks
 };
+// Side, in tiles, of the square tile blocks the batched list builder works on: bitmasks are
+// kept per block row and block column, and one warp builds the lists of a block's tiles.
+constexpr int kListBlock = 4;
 enum BatchCounter {
   BC_PRE_ITEM = 0, BC_NVIS = 1, BC_NSLOTS = 2, BC_NTILES = 3, BC_NKEYS_LO = 5,
   BC_NKEYS_HI = 6, BC_QUEUE = 7, BC_COUNT = 16
@@ -152,7 +156,7 @@ enum BatchCounter {
 struct BatchDev {
   const ReqDesc *reqs;
   int nreq;
-  uint32_t n, ntiles, mask_words;
+  uint32_t n, ntiles, nblocks, mask_words;
   uint64_t key_cap;
   const float4 *mean4, *ls4, *ql, *qr;
   const float *opacity, *sh;
@@ -167,6 +171,7 @@ struct BatchDev {
   uint32_t *nv, *vis_base, *slot_base;
   unsigned long long *key_cnt;       // [nreq] list entries per request
   float *rec_sorted;                 // [slots][16] blend-ready
+  uint2 *rect;                       // [slots] tile rectangle: x0 | x1 << 16, y0 | y1 << 16
   int *diff;
   uint32_t *masks;
   uint2 *ranges;                     // [ntiles]
