@@ -322,15 +322,15 @@ __global__ void __launch_bounds__(kTS) k_tile_scan_batch(BatchDev b) {
 }
 
 // Per-tile lists of slot indices, one warp per block of kListBlock x kListBlock tiles. The
-// warp ANDs the block's row and column bitmasks 32 words at a time (one word per lane, the
-// next words in flight); each entry found (a Gaussian whose rectangle meets the block) goes
+// warp ANDs the block's row and column bitmasks 64 words at a time (two per lane, the next
+// words in flight); each entry found (a Gaussian whose rectangle meets the block) goes
 // to a per-warp queue in rank order, then the block-local masks of the tiles the new entries'
 // rectangles cover are formed by all lanes together (independent loads). Every 32 queued
 // entries are dealt to the block's tiles: per tile, a ballot of the entries that cover it and
 // one coalesced store of their slots at the tile's running offset (held by lane t for tile
 // t). A tile thus receives exactly the Gaussians whose rectangles cover it, in rank order:
 // the same lists as ANDing per-tile row and column masks, for a sixteenth of the word scans.
-// The queue holds kLQ entries; a round of 32 words with more entries than fit is queued in
+// The queue holds kLQ entries; a round of 64 words with more entries than fit is queued in
 // parts (each lane keeps its remaining bits), so the queue stays small and many warps fit.
 constexpr int kLW = 4;                          // warps per CTA
 constexpr uint32_t kLQ = 288;                   // queue entries per warp
@@ -391,25 +391,30 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
     const uint32_t *rows = masks + q.mask_base + (size_t)(by0 / kListBlock) * mw;
     const uint32_t *cols = masks + q.mask_base + (size_t)bgy * mw + (size_t)(bx0 / kListBlock) * mw;
     uint32_t qn = 0;                             // queued entries (warp-uniform, < 32 here)
-    // the words of the next round are loaded while this round is processed
-    uint32_t nr = lane < words ? __ldg(&rows[lane]) : 0u;
-    uint32_t nc = lane < words ? __ldg(&cols[lane]) : 0u;
-    for (uint32_t w0 = 0; w0 < words; w0 += 32) {
-      const uint32_t sb = base + (w0 + lane) * 32;
-      uint32_t m = nr & nc;
-      const uint32_t wn = w0 + 32 + lane;
-      nr = wn < words ? __ldg(&rows[wn]) : 0u;
-      nc = wn < words ? __ldg(&cols[wn]) : 0u;
-      for (;;) {
-        const uint32_t pc = __popc(m);
-        const uint32_t inc = warp_incl_scan(pc);
-        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-        if (tot == 0) break;
+    // two words per lane per round (64-bit loads; the masks are zero up to the request's
+    // 256-slot boundary, so the pair of the last word is readable and empty); the words of
+    // the next round are loaded while this round is processed
+    const uint2 *rows2 = reinterpret_cast<const uint2 *>(rows);
+    const uint2 *cols2 = reinterpret_cast<const uint2 *>(cols);
+    const uint32_t pairs = (words + 1) / 2;
+    uint2 nr = lane < pairs ? __ldg(&rows2[lane]) : make_uint2(0u, 0u);
+    uint2 nc = lane < pairs ? __ldg(&cols2[lane]) : make_uint2(0u, 0u);
+    for (uint32_t p0 = 0; p0 < pairs; p0 += 32) {
+      const uint32_t sb = base + (p0 + lane) * 64;
+      uint64_t m = ((uint64_t)(nr.y & nc.y) << 32) | (nr.x & nc.x);
+      const uint32_t pn = p0 + 32 + lane;
+      nr = pn < pairs ? __ldg(&rows2[pn]) : make_uint2(0u, 0u);
+      nc = pn < pairs ? __ldg(&cols2[pn]) : make_uint2(0u, 0u);
+      uint32_t pc = __popcll(m);
+      uint32_t inc = warp_incl_scan(pc);
+      uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+      while (tot) {
         uint32_t pos = qn + inc - pc;
         while (m && pos < kLQ) {
-          qs[pos++] = sb + (uint32_t)(__ffs(m) - 1);
+          qs[pos++] = sb + (uint32_t)(__ffsll(m) - 1);
           m &= m - 1;
         }
+        const bool all_queued = qn + tot <= kLQ;
         const uint32_t qn1 = min(qn + tot, kLQ);
         __syncwarp();
         // tile masks of the new entries, from their rectangles (independent loads)
@@ -432,18 +437,24 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
         for (; c + 32 <= qn1; c += 32) deal_to_tiles(qs[c + lane], qm[c + lane], off, lists);
         // the remainder (< 32 entries) moves to the front of the queue
         const uint32_t rem = qn1 - c;
-        uint32_t ks = 0, km = 0;
-        if (c > 0 && lane < rem) {
-          ks = qs[c + lane];
-          km = qm[c + lane];
-        }
-        __syncwarp();
-        if (c > 0 && lane < rem) {
-          qs[lane] = ks;
-          qm[lane] = (uint16_t)km;
+        if (c > 0) {
+          uint32_t ks = 0, km = 0;
+          if (lane < rem) {
+            ks = qs[c + lane];
+            km = qm[c + lane];
+          }
+          __syncwarp();
+          if (lane < rem) {
+            qs[lane] = ks;
+            qm[lane] = (uint16_t)km;
+          }
+          __syncwarp();
         }
         qn = rem;
-        __syncwarp();
+        if (all_queued) break;
+        pc = __popcll(m);                          // bits the full queue could not take
+        inc = warp_incl_scan(pc);
+        tot = __shfl_sync(0xffffffffu, inc, 31);
       }
     }
     if (qn > 0) deal_to_tiles(lane < qn ? qs[lane] : 0u, lane < qn ? qm[lane] : 0u, off, lists);
