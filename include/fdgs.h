@@ -248,6 +248,18 @@ int fdgs_set_sh_codebook(fdgs_scene *scene, const float *codebook_dev, int n_cod
  * rendered. */
 int fdgs_batch_counts(fdgs_scene *scene, uint64_t *n_visible, uint64_t *n_keys);
 
+/* Last batch, request req (for tests and tools; synchronises the device): its tile lists in
+ * the layout of fdgs_frame_export, copied to HOST buffers.
+ *   tile_ranges_host [tiles_y*tiles_x][2] uint32 [start, end) into the request's id list
+ *   tile_ids_host    [ids_cap] uint32 Gaussian ids, tile-major, each tile's list in blend
+ *                    order (depth, then id)
+ * *n_tiles and *n_ids receive the request's tile count and entry count (0 entries if its
+ * lists overflowed and were emptied). Any pointer may be NULL. FDGS_ERR_INVALID for a bad
+ * request index or ids_cap < count, FDGS_ERR_STATE if no batch was rendered. */
+int fdgs_batch_tile_lists(fdgs_scene *scene, int req, uint32_t *tile_ranges_host,
+                          uint32_t *tile_ids_host, uint64_t ids_cap, uint64_t *n_tiles,
+                          uint64_t *n_ids);
+
 /*
  * Spatial-Temporal Variation Score (Sec. 4.2.1, Eqs. 4-7), reading "per-t product":
  *   S_i = sum over t in ts, camera in cams of  w_i(t, cam) * f_i(t) * gamma_i

@@ -125,6 +125,7 @@ struct BatchPlan {
   std::vector<int> W, H;
   bool masked = false;
   fdgs_scene_desc d{};
+  const uint64_t *vis_sorted = nullptr;    // sorted depth keys of the last batch (device)
   const float *sh_cb = nullptr;            // codebook pointers captured in the graph
   const uint16_t *sh_code = nullptr;
   uint32_t ntiles = 0, nblocks = 0, mask_words = 0;
@@ -622,6 +623,7 @@ int plan_capture(fdgs_scene *s, BatchPlan &p) {
   CK(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeRelaxed));
   cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice, p.cap);
   launch_batch(b, L, p.cap);
+  p.vis_sorted = L.vis_sorted;
   const cudaError_t e = cudaStreamEndCapture(p.cap, &g);
   if (e != cudaSuccess) return fail(FDGS_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
   const cudaError_t e2 = cudaGraphInstantiate(&p.exec, g, 0);
@@ -650,6 +652,7 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
       CK(cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice,
                          st));
       launch_batch(b, L, st);
+      p.vis_sorted = L.vis_sorted;
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(p.h_ctr, p.ctr.p, BC_COUNT * 4, cudaMemcpyDeviceToHost, st));
@@ -1063,6 +1066,50 @@ int fdgs_batch_counts(fdgs_scene *s, uint64_t *n_visible, uint64_t *n_keys) {
   const BatchPlan &p = *s->plan;
   if (n_visible) *n_visible = p.h_ctr[BC_NVIS];
   if (n_keys) *n_keys = (uint64_t)p.h_ctr[BC_NKEYS_LO] | ((uint64_t)p.h_ctr[BC_NKEYS_HI] << 32);
+  return FDGS_OK;
+}
+
+int fdgs_batch_tile_lists(fdgs_scene *s, int req, uint32_t *tile_ranges_host,
+                          uint32_t *tile_ids_host, uint64_t ids_cap, uint64_t *n_tiles,
+                          uint64_t *n_ids) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (!s->plan || !s->plan->vis_sorted) return fail(FDGS_ERR_STATE, "no batch has been rendered");
+  const BatchPlan &p = *s->plan;
+  if (req < 0 || req >= p.nreq) return fail(FDGS_ERR_INVALID, "request index out of range");
+  CK(cudaDeviceSynchronize());
+  const ReqDesc &q = p.h_reqs[req];
+  const size_t tiles = (size_t)q.cam.gx * q.cam.gy;
+  std::vector<uint2> rg(tiles);
+  CK(cudaMemcpy(rg.data(), p.ranges.as<uint2>() + q.tile_base, tiles * 8,
+                cudaMemcpyDeviceToHost));
+  // a request's lists are laid out tile-major from its first tile's start
+  const uint32_t lo = tiles ? rg[0].x : 0, hi = tiles ? rg[tiles - 1].y : 0;
+  const uint64_t n = hi >= lo ? hi - lo : 0;
+  if (n_tiles) *n_tiles = tiles;
+  if (n_ids) *n_ids = n;
+  if (tile_ranges_host)
+    for (size_t t = 0; t < tiles; ++t) {
+      tile_ranges_host[2 * t] = rg[t].x - lo;
+      tile_ranges_host[2 * t + 1] = rg[t].y - lo;
+    }
+  if (!tile_ids_host || n == 0) return FDGS_OK;
+  if (ids_cap < n) return fail(FDGS_ERR_INVALID, "tile_ids buffer holds %llu of %llu ids",
+                                (unsigned long long)ids_cap, (unsigned long long)n);
+  uint32_t nv = 0, vis_base = 0, slot_base = 0;
+  CK(cudaMemcpy(&nv, p.nv.as<uint32_t>() + req, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&vis_base, p.vis_base.as<uint32_t>() + req, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&slot_base, p.slot_base.as<uint32_t>() + req, 4, cudaMemcpyDeviceToHost));
+  std::vector<uint32_t> slots(n);
+  std::vector<uint64_t> keys(std::max<uint32_t>(nv, 1));
+  CK(cudaMemcpy(slots.data(), p.lists.as<uint32_t>() + lo, n * 4, cudaMemcpyDeviceToHost));
+  if (nv) CK(cudaMemcpy(keys.data(), p.vis_sorted + vis_base, (size_t)nv * 8,
+                        cudaMemcpyDeviceToHost));
+  const uint64_t id_mask = (1ull << kBatchIdBits) - 1;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint32_t rank = slots[i] - slot_base;
+    if (rank >= nv) return fail(FDGS_ERR_STATE, "list entry outside the request's slots");
+    tile_ids_host[i] = (uint32_t)(keys[rank] & id_mask);
+  }
   return FDGS_OK;
 }
 

@@ -30,7 +30,7 @@ namespace {
 constexpr int kB = 256;
 constexpr int kW = kB / 32;
 constexpr int kMaxReq = 128;
-constexpr int kIdBits = 25;                  // Gaussian id bits of the depth key
+constexpr int kIdBits = kBatchIdBits;        // Gaussian id bits of the depth key
 constexpr uint64_t kIdMask = (1ull << kIdBits) - 1;
 
 __device__ __forceinline__ uint64_t global_timer_ns() {
@@ -518,7 +518,7 @@ int grid_of(const void *kernel, int threads, int per_sm_cap) {
 
 // Enqueues the whole batch on `st` (capturable: no host synchronisation, grid sizes depend
 // only on the plan). The caller zeroes nothing: the memsets are part of the sequence.
-void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
+void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
   cudaMemsetAsync(b.ctr, 0, BC_COUNT * sizeof(uint32_t), st);
   cudaMemsetAsync(b.key_cnt, 0, b.nreq * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.diff, 0, L.diff_bytes, st);
@@ -548,6 +548,7 @@ void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st) {
   mark(2);
   BatchDev b2 = b;
   b2.vis_sorted = srt;
+  L.vis_sorted = srt;
   const uint64_t slot_parts = (rn + (uint64_t)b.nreq * kB) / kB;
   k_gather_batch<<<(int)std::min<uint64_t>(slot_parts, g_gather), kB, 0, st>>>(b2);
   mark(3);

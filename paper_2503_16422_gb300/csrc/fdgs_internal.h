@@ -187,11 +187,14 @@ struct BatchLaunch {
   void *sort_scratch;
   int footprint;                     // launch shape of the blend (with_blend_shape)
   int blend_ctas_per_sm;             // persistent blend grid = this x SMs
+  const uint64_t *vis_sorted;        // out: the buffer that holds the sorted depth keys
 };
+// Gaussian id bits at the bottom of the batched depth keys (request | depth | id).
+constexpr int kBatchIdBits = 25;
 // Stages timed by the device stamps: preprocess, depth_sort (bases, compaction, sort),
 // gather, tile_scan, lists, queue_sort, blend.
 constexpr int kBatchStages = 7;
-void launch_batch(const BatchDev &b, const BatchLaunch &L, cudaStream_t st);
+void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st);
 int batch_blend_max_ctas_per_sm(int shape);
 
 int num_sms();

@@ -83,6 +83,9 @@ _SIGNATURES = {
                         ctypes.POINTER(ctypes.c_float)],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
     "fdgs_batch_counts": [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
+    "fdgs_batch_tile_lists": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32),
+                              ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64,
+                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
     "fdgs_set_sh_codebook": [_P, _P, ctypes.c_int, _P],
     "fdgs_build_keyframe_masks": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P, _P],
@@ -389,6 +392,21 @@ class Scene:
         nv, nk = ctypes.c_uint64(), ctypes.c_uint64()
         check(lib().fdgs_batch_counts(self.handle, ctypes.byref(nv), ctypes.byref(nk)))
         return dict(n_visible=nv.value, n_keys=nk.value)
+
+    def batch_tile_lists(self, req):
+        """Tile lists of request ``req`` of the last batch, as numpy arrays in the layout of
+        Frame.export: ranges [tiles, 2] (start, end) and Gaussian ids (uint32)."""
+        import numpy as np
+        nt, n = ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib().fdgs_batch_tile_lists(self.handle, int(req), None, None, 0,
+                                          ctypes.byref(nt), ctypes.byref(n)))
+        ranges = np.zeros((nt.value, 2), dtype=np.uint32)
+        ids = np.zeros((max(n.value, 1),), dtype=np.uint32)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        check(lib().fdgs_batch_tile_lists(self.handle, int(req), ranges.ctypes.data_as(u32p),
+                                          ids.ctypes.data_as(u32p), ids.size,
+                                          ctypes.byref(nt), ctypes.byref(n)))
+        return ranges, ids[: n.value]
 
     def variation_score(self, cams, ts, batch=8, out=None, stream=None):
         carr = (fdgs_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])

@@ -83,10 +83,40 @@ def test_batch_of_one_and_empty_view(fd):
     sc.close()
 
 
+def _assert_lists_equal_tight_frame(sc, req, cam, t):
+    """The batch's tile lists of request ``req`` equal the per-frame alpha-tight lists (the
+    same tile rectangles, so the same entries in the same depth order) bit for bit."""
+    ranges, ids = sc.batch_tile_lists(req)
+    _, fr = sc.render(cam, t, use_mask=True, keep_frame=True, tight=True)
+    ex = fr.export()
+    torch.cuda.synchronize()
+    want_r = ex["tile_ranges"].cpu().numpy().astype(np.uint32)
+    want_i = ex["tile_ids"].cpu().numpy().astype(np.uint32)
+    fr.release()
+    assert ranges.shape == want_r.shape and np.array_equal(ranges, want_r), req
+    assert np.array_equal(ids, want_i), req
+
+
+def test_batch_lists_equal_per_frame_tight_lists_at_ragged_sizes(fd):
+    """Mixed resolutions whose tile grids are not multiples of the 4x4 list blocks (and one
+    smaller than a block): every request's lists equal its per-frame alpha-tight lists."""
+    _, sc = _scene_gpu(fd, True, n=6000, seed=46)
+    res = [(200, 150), (33, 17), (64, 48), (250, 130), (40, 40)]
+    cams, ts = _requests(11, len(res), res)
+    outs = sc.render_batch(cams, ts, use_mask=True)
+    for i in range(len(res)):
+        assert torch.equal(outs[i], sc.render(cams[i], ts[i], use_mask=True)), i
+        _assert_lists_equal_tight_frame(sc, i, cams[i], ts[i])
+    with pytest.raises(fd.FdgsError):
+        sc.batch_tile_lists(len(res))
+    sc.close()
+
+
 def test_batch_full_size_dense_tiles_match_sequential(fd):
-    """200k-Gaussian pruned scene at 1352x1014: tiles hold thousands of entries, several per
-    bitmask word, so the blend's read-out rounds end inside words (straddling cursor) and
-    many tiles stop early; the images must still equal the per-request renders."""
+    """200k-Gaussian pruned scene at 1352x1014: tiles hold thousands of entries and the 4x4
+    tile blocks of the list builder tens of thousands (rounds of 64 bitmask words overflow
+    the per-warp queue and are queued in parts); many tiles stop early. The images must
+    equal the per-request renders and the lists the per-frame alpha-tight lists."""
     s = scenes.pruned_scene()
     sc = fd.Scene.from_host(s)
     kt = scenes.keyframe_times(300, 6)
@@ -105,6 +135,8 @@ def test_batch_full_size_dense_tiles_match_sequential(fd):
         nv += st["n_visible"]
         nk += st["n_keys"]
         fr.release()
+        if i < 2:
+            _assert_lists_equal_tight_frame(sc, i, c, t)
     # same visibility decisions; the batch's alpha-tight tile sets are subsets of the squares
     assert counts["n_visible"] == nv
     assert 0 < counts["n_keys"] <= nk
