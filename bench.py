@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the comparison workloads")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default batch launch shape (for profiling runs)")
+    ap.add_argument("--only", choices=["backward"],
+                    help="run one side workload alone and print its line (for profiling runs)")
     return ap.parse_args()
 
 
@@ -719,9 +721,35 @@ def launches_per_batch():
     return 1 + 1 + 1 + 1 + 1 + 7 + 1 + 1 + 1 + 5 + 1 + 8
 
 
+def run_only(args):
+    """One side workload alone (the headline is not measured): small enough on the device to
+    profile a single kernel of it."""
+    import torch
+
+    from paper_2503_16422_gb300 import build, fdgs, scenes
+    build.build()
+    scene, _, _ = pruned_masked()
+    sc = fdgs.Scene.from_host(scene)
+    times = scenes.frame_times()
+    cams = {k: scenes.arc_camera(scenes.frame_theta(k)) for k in range(300)}
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    if args.only == "backward":
+        for tight in (False, True):
+            res["backward_tight" if tight else "backward"] = backward_timing(
+                sc, cams, times, flush, stream, n_frames=max(args.steps, 1), tight=tight)
+    sc.close()
+    print(json.dumps({"only": args.only, "impl": "ours", "data": "synthetic", **res}))
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
+    if args.only:
+        if rank == 0:
+            run_only(args)
+        return
     if args.impl == "reference":
         if rank != 0:
             return
