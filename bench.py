@@ -695,17 +695,22 @@ def score_timing(stream):
     sc = fdgs.Scene.from_host(s)
     cams = [scenes.arc_camera(th) for th in (-10.0, -3.3, 3.3, 10.0)]
     ts = [float(x) for x in np.linspace(0.0, 1.0, 50)]
-    sc.variation_score(cams[:1], ts[:2])            # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    score = sc.variation_score(cams, ts, batch=8)
-    keep = sc.select_keep(score, 0.8)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    kept = int(keep.sum())
+    walls = {}
+    for batch in (1, 8):
+        # warm-up with the timed batch geometry (8 renders: 2 times x 4 cameras)
+        sc.variation_score(cams, ts[:2], batch=batch)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        score = sc.variation_score(cams, ts, batch=batch)
+        keep = sc.select_keep(score, 0.8)
+        torch.cuda.synchronize()
+        walls[batch] = time.perf_counter() - t0
+        kept = int(keep.sum())
     sc.close()
-    return dict(n_gaussians=s.n, renders=len(cams) * len(ts), resolution="1352x1014",
-                wall_s=wall, ms_per_render=wall * 1e3 / (len(cams) * len(ts)), kept=kept)
+    n = len(cams) * len(ts)
+    return dict(n_gaussians=s.n, renders=n, resolution="1352x1014", batch=8,
+                wall_s=walls[8], ms_per_render=walls[8] * 1e3 / n, kept=kept,
+                per_frame_path_wall_s=walls[1])
 
 
 # DRAM bytes the persistent blend moves per frame of a batch at 1352x1014 on the 200k pruned

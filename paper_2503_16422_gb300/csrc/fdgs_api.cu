@@ -126,6 +126,9 @@ struct BatchPlan {
   bool masked = false;
   fdgs_scene_desc d{};
   const uint64_t *vis_sorted = nullptr;    // sorted depth keys of the last batch (device)
+  float *score_out = nullptr;              // score pass: accumulate into this (else null)
+  const float *gamma = nullptr;
+  Buf wsum, stop;                          // score pass: per-slot weights and stop flags
   const float *sh_cb = nullptr;            // codebook pointers captured in the graph
   const uint16_t *sh_code = nullptr;
   uint32_t ntiles = 0, nblocks = 0, mask_words = 0;
@@ -146,6 +149,8 @@ struct BatchPlan {
   float stage_ms[kBatchStages] = {};
   ~BatchPlan() {
     stamps.release();
+    wsum.release();
+    stop.release();
     if (h_stamps) cudaFreeHost(h_stamps);
     Buf *all[] = {&reqs, &ctr, &part, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
                   &slot_base, &key_cnt, &rec_sorted, &rect, &diff, &masks, &ranges, &qkeys,
@@ -605,6 +610,11 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.t0_ns = p.t0.as<unsigned long long>();
   b.evals = nullptr;
   b.stamps = p.stamps.as<unsigned long long>();
+  b.w_sum = p.score_out ? p.wsum.as<float>() : nullptr;
+  b.stop_mark = p.score_out ? p.stop.as<uint32_t>() : nullptr;
+  b.gamma = p.gamma;
+  b.score = p.score_out;
+  L.slot_cap = p.slot_cap;
   L.diff_bytes = p.diff_ints * 4;
   L.sort_scratch = p.scratch.p;
   L.footprint = p.footprint;
@@ -619,6 +629,10 @@ int plan_capture(fdgs_scene *s, BatchPlan &p) {
   BatchDev b;
   BatchLaunch L;
   plan_dev(s, p, b, L);
+  b.w_sum = nullptr;   // a graph never holds the score pass (it runs eagerly)
+  b.stop_mark = nullptr;
+  b.gamma = nullptr;
+  b.score = nullptr;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeRelaxed));
   cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice, p.cap);
@@ -642,7 +656,7 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
   // blend variant, so that fdgs_profile_read returns its evaluation and test counts
   const bool count = (s->prof & 2) && s->evals.p;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    if (p.exec && !count) {
+    if (p.exec && !count && !p.score_out) {
       CK(cudaGraphLaunch(p.exec, st));
     } else {
       BatchDev b;
@@ -1138,6 +1152,46 @@ int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, cons
   fdgs_render_opts o{};
   o.use_mask = 0;
   o.tile_sets = 1;   // same weights as the 3-sigma squares, shorter lists
+  if (batch > 1 && n_cam > 0 && n_t > 0 && N < (1u << kBatchIdBits)) {
+    // batches of up to `batch` (t, camera) renders through the batched pipeline, each with
+    // the weighted persistent blend and the batched accumulation
+    const int per = std::min(batch, 128);
+    std::vector<fdgs_camera> bc;
+    std::vector<float> bt;
+    std::vector<float *> outs;
+    const int total = n_t * n_cam;
+    for (int i0 = 0; i0 < total; i0 += per) {
+      const int n = std::min(per, total - i0);
+      bc.clear();
+      bt.clear();
+      size_t pix = 0;
+      for (int i = i0; i < i0 + n; ++i) {
+        bc.push_back(cams[i % n_cam]);
+        bt.push_back(ts[i / n_cam]);
+        pix += (size_t)cams[i % n_cam].width * cams[i % n_cam].height;
+      }
+      TRY(grow(s->aux[4], pix * 12));
+      outs.clear();
+      size_t off = 0;
+      for (int i = 0; i < n; ++i) {
+        outs.push_back(s->aux[4].as<float>() + off);
+        off += (size_t)bc[i].width * bc[i].height * 3;
+      }
+      TRY(batch_args_ok(s, bc.data(), bt.data(), n, outs.data()));
+      TRY(plan_prepare(s, bc.data(), n, false));
+      BatchPlan &p = *s->plan;
+      TRY(plan_fill(s, p, bc.data(), bt.data(), &o, outs.data()));
+      TRY(grow(p.wsum, p.slot_cap * 4));
+      TRY(grow(p.stop, p.slot_cap * 4));
+      p.score_out = score_out_dev;
+      p.gamma = s->aux[1].as<float>();
+      const int rc = plan_run(s, p, st);
+      p.score_out = nullptr;
+      p.gamma = nullptr;
+      TRY(rc);
+    }
+    return FDGS_OK;
+  }
   int done = 0;
   for (int it = 0; it < n_t; ++it)
     for (int ic = 0; ic < n_cam; ++ic) {

@@ -464,7 +464,8 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
 
 // Persistent blend over the longest-first queue of all requests' tiles.
 // Only the images are written: nothing reads a batched frame's transmittance or n_contrib.
-template <int FW, int PX, bool kCount>
+// kWeights (score pass): also the per-slot blend weights and stop flags.
+template <int FW, int PX, bool kCount, bool kWeights = false>
 __global__ void __launch_bounds__(256 / PX) k_blend_persist(BatchDev b) {
   __shared__ BlendSmem<256 / PX> sm;
   __shared__ uint32_t s_q;
@@ -492,10 +493,10 @@ __global__ void __launch_bounds__(256 / PX) k_blend_persist(BatchDev b) {
     bt.bg0 = q.bg[0];
     bt.bg1 = q.bg[1];
     bt.bg2 = q.bg[2];
-    bt.w_sum = nullptr;
-    bt.stop_mark = nullptr;
+    bt.w_sum = kWeights ? b.w_sum : nullptr;
+    bt.stop_mark = kWeights ? b.stop_mark : nullptr;
     bt.evals = b.evals;
-    blend_tile<uint32_t, FW, PX, false, kCount, false>(bt, b.lists, 0xFFFFFFFFu, sm);
+    blend_tile<uint32_t, FW, PX, kWeights, kCount, false>(bt, b.lists, 0xFFFFFFFFu, sm);
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(&b.done_ns[r], (unsigned long long)global_timer_ns());
   }
@@ -524,6 +525,10 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
   cudaMemsetAsync(b.diff, 0, L.diff_bytes, st);
   cudaMemsetAsync(b.done_ns, 0, b.nreq * sizeof(unsigned long long), st);
   if (b.evals) cudaMemsetAsync(b.evals, 0, 3 * sizeof(unsigned long long), st);
+  if (b.w_sum) {
+    cudaMemsetAsync(b.w_sum, 0, L.slot_cap * sizeof(float), st);
+    cudaMemsetAsync(b.stop_mark, 0, L.slot_cap * sizeof(uint32_t), st);
+  }
   // stage boundaries: a one-thread kernel stamps %globaltimer (events recorded inside a
   // captured graph cannot be timed); stream order makes each difference a stage duration
   auto mark = [&](int i) { k_stamp<<<1, 1, 0, st>>>(b.stamps, i); };
@@ -563,13 +568,26 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
   b2.queue = qs;
   mark(6);
   const int grid = L.blend_ctas_per_sm * num_sms();
-  with_blend_shape(L.footprint, [&](auto fw, auto px) {
-    constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
-    if (b.evals)
-      k_blend_persist<FW, PX, true><<<grid, 256 / PX, 0, st>>>(b2);
-    else
-      k_blend_persist<FW, PX, false><<<grid, 256 / PX, 0, st>>>(b2);
-  });
+  if (b.w_sum) {
+    // score pass: one weighted variant (8x16 footprint, four pixels per lane), then the
+    // per-Gaussian accumulation
+    static int per_sm = 0;
+    if (!per_sm) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_persist<8, 4, false, true>,
+                                                    64, 0);
+      per_sm = std::max(1, per_sm);
+    }
+    k_blend_persist<8, 4, false, true><<<per_sm * num_sms(), 64, 0, st>>>(b2);
+    launch_score_batch(b2, L.slot_cap, st);
+  } else {
+    with_blend_shape(L.footprint, [&](auto fw, auto px) {
+      constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
+      if (b.evals)
+        k_blend_persist<FW, PX, true><<<grid, 256 / PX, 0, st>>>(b2);
+      else
+        k_blend_persist<FW, PX, false><<<grid, 256 / PX, 0, st>>>(b2);
+    });
+  }
   mark(7);
 }
 

@@ -180,6 +180,12 @@ struct BatchDev {
   uint32_t *lists;                   // [key_cap] slot indices
   unsigned long long *done_ns, *t0_ns;
   unsigned long long *evals;         // [3] blend counters (see BlendTile), or null
+  // score pass (null for renders): per-slot blend weights and stop flags, the Gaussians'
+  // volume factors gamma and the score they accumulate into (Eqs. 4-7)
+  float *w_sum;
+  uint32_t *stop_mark;
+  const float *gamma;
+  float *score;
   unsigned long long *stamps;        // [kBatchStages + 1] %globaltimer at stage boundaries
 };
 struct BatchLaunch {
@@ -188,6 +194,7 @@ struct BatchLaunch {
   int footprint;                     // launch shape of the blend (with_blend_shape)
   int blend_ctas_per_sm;             // persistent blend grid = this x SMs
   const uint64_t *vis_sorted;        // out: the buffer that holds the sorted depth keys
+  uint64_t slot_cap;                 // slots of the plan (score pass buffers)
 };
 // Gaussian id bits at the bottom of the batched depth keys (request | depth | id).
 constexpr int kBatchIdBits = 25;
@@ -195,6 +202,9 @@ constexpr int kBatchIdBits = 25;
 // gather, tile_scan, lists, queue_sort, blend.
 constexpr int kBatchStages = 7;
 void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st);
+// Score pass of a batch: adds w_sum[slot] * f_i(t) * gamma_i to score[i] for every visible
+// slot of every request (after the weighted blend of the batch).
+void launch_score_batch(const BatchDev &b, uint64_t slot_cap, cudaStream_t st);
 int batch_blend_max_ctas_per_sm(int shape);
 
 int num_sms();

@@ -69,6 +69,17 @@ __device__ __forceinline__ float temporal_variance(float4 ls, float4 ql, float4 
   return v;
 }
 
+// f_i(t) of Eqs. 5-6: the second time derivative of the temporal opacity p_i(t) mapped
+// through tanh into [1, 2] (its reciprocal half-plus-half form).
+__device__ __forceinline__ float variation_factor(float t, float4 m4, float4 ls, float4 ql,
+                                                  float4 qr) {
+  const float st = temporal_variance(ls, ql, qr);
+  const float dt = t - m4.w;
+  const float p = expf(-0.5f * dt * dt / st);
+  const float p2 = (dt * dt / (st * st) - 1.f / st) * p;
+  return 1.f / (0.5f * tanhf(fabsf(p2)) + 0.5f);
+}
+
 __global__ void k_score_accumulate(const uint64_t *__restrict__ sorted,
                                    const uint32_t *__restrict__ nv_dev,
                                    const float *__restrict__ w_sum,
@@ -80,13 +91,35 @@ __global__ void k_score_accumulate(const uint64_t *__restrict__ sorted,
     const float w = w_sum[r];
     if (w == 0.f) continue;
     const uint32_t id = (uint32_t)sorted[r];
-    const float st = temporal_variance(ls4[id], ql[id], qr[id]);
-    const float dt = t - mean4[id].w;
-    const float p = expf(-0.5f * dt * dt / st);
-    // Eq. 5: second derivative of the temporal opacity; Eq. 6: its tanh-mapped reciprocal
-    const float p2 = (dt * dt / (st * st) - 1.f / st) * p;
-    const float f = 1.f / (0.5f * tanhf(fabsf(p2)) + 0.5f);
+    const float f = variation_factor(t, mean4[id], ls4[id], ql[id], qr[id]);
     score[id] += w * f * gamma[id];
+  }
+}
+
+// The batched score pass: slot s of request r (slot_base[r] <= s < slot_base[r] + nv[r]) holds
+// the visible Gaussian of depth rank s - slot_base[r]; its weight over the request's pixels
+// is added to the score with the request's f_i(t) (the requests of one batch may share
+// Gaussians, hence the atomics).
+constexpr int kMaxReqScore = 128;
+__global__ void k_score_batch(BatchDev b, uint64_t slot_cap) {
+  __shared__ uint32_t s_slot_base[kMaxReqScore];
+  for (int r = threadIdx.x; r < b.nreq; r += blockDim.x) s_slot_base[r] = b.slot_base[r];
+  __syncthreads();
+  const uint64_t id_mask = (1ull << kBatchIdBits) - 1;
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < slot_cap;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    const float w = b.w_sum[s];
+    if (w == 0.f) continue;
+    int lo = 0, hi = b.nreq - 1;   // the last request whose first slot is <= s
+    while (lo < hi) {
+      const int m = (lo + hi + 1) >> 1;
+      if (s_slot_base[m] <= s) lo = m; else hi = m - 1;
+    }
+    const uint32_t l = (uint32_t)(s - s_slot_base[lo]);
+    if (l >= b.nv[lo]) continue;
+    const uint32_t id = (uint32_t)(b.vis_sorted[b.vis_base[lo] + l] & id_mask);
+    const float f = variation_factor(b.reqs[lo].t, b.mean4[id], b.ls4[id], b.ql[id], b.qr[id]);
+    atomicAdd(&b.score[id], w * f * b.gamma[id]);
   }
 }
 
@@ -151,6 +184,10 @@ void launch_gamma(const float4 *ls4, uint32_t n, const uint32_t *vsorted, uint32
                   float *gamma, cudaStream_t st) {
   if (n == 0) return;
   k_gamma<<<grid_for(n), kB, 0, st>>>(ls4, n, vsorted, k, gamma);
+}
+
+void launch_score_batch(const BatchDev &b, uint64_t slot_cap, cudaStream_t st) {
+  k_score_batch<<<grid_for(slot_cap), kB, 0, st>>>(b, slot_cap);
 }
 
 void launch_score_accumulate(const uint64_t *sorted, const uint32_t *nv_dev, uint32_t nv_cap,
