@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the comparison workloads")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default batch launch shape (for profiling runs)")
-    ap.add_argument("--only", choices=["backward"],
+    ap.add_argument("--only", choices=["backward", "score"],
                     help="run one side workload alone and print its line (for profiling runs)")
     return ap.parse_args()
 
@@ -745,6 +745,8 @@ def run_only(args):
             res["backward_tight" if tight else "backward"] = backward_timing(
                 sc, cams, times, flush, stream, n_frames=max(args.steps, 1), tight=tight)
     sc.close()
+    if args.only == "score":
+        res["variation_score"] = score_timing(stream)
     print(json.dumps({"only": args.only, "impl": "ours", "data": "synthetic", **res}))
 
 
