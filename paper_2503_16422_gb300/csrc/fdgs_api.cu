@@ -126,9 +126,11 @@ struct BatchPlan {
   bool masked = false;
   fdgs_scene_desc d{};
   const uint64_t *vis_sorted = nullptr;    // sorted depth keys of the last batch (device)
+  bool weighted = false;                   // next runs: a weighted pass (eager, no graph)
   float *score_out = nullptr;              // score pass: accumulate into this (else null)
   const float *gamma = nullptr;
-  Buf wsum, stop;                          // score pass: per-slot weights and stop flags
+  bool mark = false;                       // mask pass: requests carry mark_row
+  Buf wsum, stop;                          // weighted passes: per-slot weights, stop flags
   const float *sh_cb = nullptr;            // codebook pointers captured in the graph
   const uint16_t *sh_code = nullptr;
   uint32_t ntiles = 0, nblocks = 0, mask_words = 0;
@@ -610,10 +612,11 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.t0_ns = p.t0.as<unsigned long long>();
   b.evals = nullptr;
   b.stamps = p.stamps.as<unsigned long long>();
-  b.w_sum = p.score_out ? p.wsum.as<float>() : nullptr;
-  b.stop_mark = p.score_out ? p.stop.as<uint32_t>() : nullptr;
+  b.w_sum = p.weighted ? p.wsum.as<float>() : nullptr;
+  b.stop_mark = p.weighted ? p.stop.as<uint32_t>() : nullptr;
   b.gamma = p.gamma;
   b.score = p.score_out;
+  b.mark = p.mark ? 1 : 0;
   L.slot_cap = p.slot_cap;
   L.diff_bytes = p.diff_ints * 4;
   L.sort_scratch = p.scratch.p;
@@ -629,10 +632,11 @@ int plan_capture(fdgs_scene *s, BatchPlan &p) {
   BatchDev b;
   BatchLaunch L;
   plan_dev(s, p, b, L);
-  b.w_sum = nullptr;   // a graph never holds the score pass (it runs eagerly)
+  b.w_sum = nullptr;   // a graph never holds a weighted pass (they run eagerly)
   b.stop_mark = nullptr;
   b.gamma = nullptr;
   b.score = nullptr;
+  b.mark = 0;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeRelaxed));
   cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice, p.cap);
@@ -656,7 +660,7 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
   // blend variant, so that fdgs_profile_read returns its evaluation and test counts
   const bool count = (s->prof & 2) && s->evals.p;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    if (p.exec && !count && !p.score_out) {
+    if (p.exec && !count && !p.weighted) {
       CK(cudaGraphLaunch(p.exec, st));
     } else {
       BatchDev b;
@@ -1034,11 +1038,58 @@ int fdgs_build_keyframe_masks(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
   if (n_key == 0) return FDGS_OK;
   CK(cudaMemsetAsync(bits_out_dev, 0, (size_t)n_key * nbytes, st));
   if (N == 0 || n_cam == 0) return FDGS_OK;
-  TRY(grow(s->aux[5], (size_t)words * 4));
-  uint32_t *row = s->aux[5].as<uint32_t>();
   fdgs_render_opts o{};
   o.use_mask = 0;   // the masks are built from unfiltered renders
   o.tile_sets = 1;  // same blend decisions as the 3-sigma squares, shorter lists
+  const int total = n_key * n_cam;
+  if (total > 1 && N < (1u << kBatchIdBits)) {
+    // every (key-frame, view) render through the batched pipeline, 16 per batch, with the
+    // weighted persistent blend marking its contributors in the key-frame's word row
+    TRY(grow(s->aux[5], (size_t)n_key * words * 4));
+    uint32_t *rows = s->aux[5].as<uint32_t>();
+    CK(cudaMemsetAsync(rows, 0, (size_t)n_key * words * 4, st));
+    std::vector<fdgs_camera> bc;
+    std::vector<float> bt;
+    std::vector<float *> outs;
+    for (int i0 = 0; i0 < total; i0 += 16) {
+      const int n = std::min(16, total - i0);
+      bc.clear();
+      bt.clear();
+      size_t pix = 0;
+      for (int i = i0; i < i0 + n; ++i) {
+        bc.push_back(cams[i % n_cam]);
+        bt.push_back(key_times[i / n_cam]);
+        pix += (size_t)cams[i % n_cam].width * cams[i % n_cam].height;
+      }
+      TRY(grow(s->aux[4], pix * 12));
+      outs.clear();
+      size_t off = 0;
+      for (int i = 0; i < n; ++i) {
+        outs.push_back(s->aux[4].as<float>() + off);
+        off += (size_t)bc[i].width * bc[i].height * 3;
+      }
+      TRY(batch_args_ok(s, bc.data(), bt.data(), n, outs.data()));
+      TRY(plan_prepare(s, bc.data(), n, false));
+      BatchPlan &p = *s->plan;
+      TRY(plan_fill(s, p, bc.data(), bt.data(), &o, outs.data()));
+      for (int i = 0; i < n; ++i) p.h_reqs[i].mark_row = rows + (size_t)((i0 + i) / n_cam) * words;
+      TRY(grow(p.wsum, p.slot_cap * 4));
+      TRY(grow(p.stop, p.slot_cap * 4));
+      p.weighted = true;
+      p.mark = true;
+      const int rc = plan_run(s, p, st);
+      p.weighted = false;
+      p.mark = false;
+      TRY(rc);
+    }
+    for (int k = 0; k < n_key; ++k)
+      launch_pack_mask_row(rows + (size_t)k * words, nbytes, bits_out_dev + (size_t)k * nbytes,
+                           st);
+    CK(cudaGetLastError());
+    return FDGS_OK;
+  }
+  TRY(grow(s->aux[5], (size_t)words * 4));
+  uint32_t *row = s->aux[5].as<uint32_t>();
   for (int k = 0; k < n_key; ++k) {
     CK(cudaMemsetAsync(row, 0, (size_t)words * 4, st));
     for (int ic = 0; ic < n_cam; ++ic) {
@@ -1183,9 +1234,11 @@ int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, cons
       TRY(plan_fill(s, p, bc.data(), bt.data(), &o, outs.data()));
       TRY(grow(p.wsum, p.slot_cap * 4));
       TRY(grow(p.stop, p.slot_cap * 4));
+      p.weighted = true;
       p.score_out = score_out_dev;
       p.gamma = s->aux[1].as<float>();
       const int rc = plan_run(s, p, st);
+      p.weighted = false;
       p.score_out = nullptr;
       p.gamma = nullptr;
       TRY(rc);

@@ -569,8 +569,8 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
   mark(6);
   const int grid = L.blend_ctas_per_sm * num_sms();
   if (b.w_sum) {
-    // score pass: one weighted variant (8x16 footprint, four pixels per lane), then the
-    // per-Gaussian accumulation
+    // weighted passes: one weighted variant (8x16 footprint, four pixels per lane), then
+    // the per-Gaussian score accumulation or contributor marks
     static int per_sm = 0;
     if (!per_sm) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_persist<8, 4, false, true>,
@@ -578,7 +578,8 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
       per_sm = std::max(1, per_sm);
     }
     k_blend_persist<8, 4, false, true><<<per_sm * num_sms(), 64, 0, st>>>(b2);
-    launch_score_batch(b2, L.slot_cap, st);
+    if (b.score) launch_score_batch(b2, L.slot_cap, st);
+    if (b.mark) launch_mark_batch(b2, L.slot_cap, st);
   } else {
     with_blend_shape(L.footprint, [&](auto fw, auto px) {
       constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;

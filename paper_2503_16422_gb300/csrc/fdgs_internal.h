@@ -145,6 +145,7 @@ struct ReqDesc {
   uint32_t block_base;               // first global tile-block id (kListBlock^2 tiles each)
   uint32_t diff_base;                // offset of its coverage difference array (ints)
   uint64_t mask_base;                // offset of its block-row and block-column bitmasks
+  uint32_t *mark_row;                // mask pass: the key-frame word row it marks, or null
 };
 // Side, in tiles, of the square tile blocks the batched list builder works on: bitmasks are
 // kept per block row and block column, and one warp builds the lists of a block's tiles.
@@ -180,12 +181,14 @@ struct BatchDev {
   uint32_t *lists;                   // [key_cap] slot indices
   unsigned long long *done_ns, *t0_ns;
   unsigned long long *evals;         // [3] blend counters (see BlendTile), or null
-  // score pass (null for renders): per-slot blend weights and stop flags, the Gaussians'
-  // volume factors gamma and the score they accumulate into (Eqs. 4-7)
+  // weighted passes (null for renders): per-slot blend weights and stop flags; the score
+  // pass adds them, with the Gaussians' volume factors gamma, into score (Eqs. 4-7); the
+  // mask pass marks the contributing Gaussians in each request's mark_row
   float *w_sum;
   uint32_t *stop_mark;
   const float *gamma;
   float *score;
+  int mark;
   unsigned long long *stamps;        // [kBatchStages + 1] %globaltimer at stage boundaries
 };
 struct BatchLaunch {
@@ -205,6 +208,9 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st);
 // Score pass of a batch: adds w_sum[slot] * f_i(t) * gamma_i to score[i] for every visible
 // slot of every request (after the weighted blend of the batch).
 void launch_score_batch(const BatchDev &b, uint64_t slot_cap, cudaStream_t st);
+// Mask pass of a batch: sets bit id of request r's mark_row for every visible Gaussian that
+// was blended somewhere (weight > 0) or stopped a pixel.
+void launch_mark_batch(const BatchDev &b, uint64_t slot_cap, cudaStream_t st);
 int batch_blend_max_ctas_per_sm(int shape);
 
 int num_sms();

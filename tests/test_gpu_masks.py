@@ -66,3 +66,22 @@ def test_filtered_training_views_equal_unfiltered_at_key_times(fd):
             filt = sc.render(cam, t, use_mask=True)
             assert torch.equal(full, filt), (k, cam.width)
     sc.close()
+
+
+def test_batched_masks_equal_one_render_at_a_time(fd):
+    """Several key-frames and views go through the batched pipeline (16 renders a batch, the
+    last one partial); one key-frame and one view at a time through the per-frame path. The
+    blend decisions are the same, so the masks are equal bit for bit."""
+    s = scenes.make_scene(5000, 33, sh_degree=1, lxyz=(-2.6, 0.4), lt_long=(-1.4, 0.4))
+    cams = [scenes.arc_camera(th, w, h) for th, w, h in ((-9.0, 96, 80), (-1.0, 130, 70),
+                                                         (7.0, 64, 112))]
+    kt = np.linspace(0.0, 1.0, 7).astype(np.float32)
+    sc = fd.Scene.from_host(s)
+    batched = sc.build_keyframe_masks(cams, kt).cpu().numpy()
+    single = np.zeros_like(batched)
+    for k in range(len(kt)):
+        for cam in cams:
+            single[k] |= sc.build_keyframe_masks([cam], kt[k:k + 1]).cpu().numpy()[0]
+    assert np.array_equal(batched, single)
+    assert _bools(batched, s.n).sum() > 100
+    sc.close()
