@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the comparison workloads")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default batch launch shape (for profiling runs)")
-    ap.add_argument("--only", choices=["backward", "score"],
+    ap.add_argument("--only", choices=["backward", "score", "masks"],
                     help="run one side workload alone and print its line (for profiling runs)")
     return ap.parse_args()
 
@@ -540,7 +540,7 @@ def keyframe_mask_timing(sc, cams, times, flush, stream, B=64):
     from paper_2503_16422_gb300 import scenes
     views = [scenes.arc_camera(th, W_FULL, H_FULL) for th in (-10.0, -10.0 / 3, 10.0 / 3, 10.0)]
     kt = scenes.keyframe_times()
-    sc.build_keyframe_masks(views[:1], kt[:2])       # warm-up
+    sc.build_keyframe_masks(views, kt[:4])           # warm-up: one batch of the timed geometry
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     masks = sc.build_keyframe_masks(views, kt)
@@ -733,8 +733,9 @@ def run_only(args):
 
     from paper_2503_16422_gb300 import build, fdgs, scenes
     build.build()
-    scene, _, _ = pruned_masked()
+    scene, kt, masks = pruned_masked()
     sc = fdgs.Scene.from_host(scene)
+    sc.set_active_mask(torch.as_tensor(masks).cuda(), kt)
     times = scenes.frame_times()
     cams = {k: scenes.arc_camera(scenes.frame_theta(k)) for k in range(300)}
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -744,6 +745,8 @@ def run_only(args):
         for tight in (False, True):
             res["backward_tight" if tight else "backward"] = backward_timing(
                 sc, cams, times, flush, stream, n_frames=max(args.steps, 1), tight=tight)
+    if args.only == "masks":
+        res["keyframe_masks_from_views"] = keyframe_mask_timing(sc, cams, times, flush, stream)
     sc.close()
     if args.only == "score":
         res["variation_score"] = score_timing(stream)

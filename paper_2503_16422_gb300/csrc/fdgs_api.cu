@@ -1044,19 +1044,23 @@ int fdgs_build_keyframe_masks(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
   const int total = n_key * n_cam;
   if (total > 1 && N < (1u << kBatchIdBits)) {
     // every (key-frame, view) render through the batched pipeline, 16 per batch, with the
-    // weighted persistent blend marking its contributors in the key-frame's word row
+    // weighted persistent blend marking its contributors in the key-frame's word row; a
+    // last, partial batch is padded with repeats that mark nothing, so every batch has the
+    // same geometry and reuses one plan
     TRY(grow(s->aux[5], (size_t)n_key * words * 4));
     uint32_t *rows = s->aux[5].as<uint32_t>();
     CK(cudaMemsetAsync(rows, 0, (size_t)n_key * words * 4, st));
     std::vector<fdgs_camera> bc;
     std::vector<float> bt;
     std::vector<float *> outs;
-    for (int i0 = 0; i0 < total; i0 += 16) {
-      const int n = std::min(16, total - i0);
+    const int per = std::min(16, total);
+    for (int i0 = 0; i0 < total; i0 += per) {
+      const int n = per;
       bc.clear();
       bt.clear();
       size_t pix = 0;
-      for (int i = i0; i < i0 + n; ++i) {
+      for (int j = i0; j < i0 + n; ++j) {
+        const int i = std::min(j, total - 1);
         bc.push_back(cams[i % n_cam]);
         bt.push_back(key_times[i / n_cam]);
         pix += (size_t)cams[i % n_cam].width * cams[i % n_cam].height;
@@ -1072,7 +1076,9 @@ int fdgs_build_keyframe_masks(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
       TRY(plan_prepare(s, bc.data(), n, false));
       BatchPlan &p = *s->plan;
       TRY(plan_fill(s, p, bc.data(), bt.data(), &o, outs.data()));
-      for (int i = 0; i < n; ++i) p.h_reqs[i].mark_row = rows + (size_t)((i0 + i) / n_cam) * words;
+      for (int i = 0; i < n; ++i)
+        p.h_reqs[i].mark_row =
+            i0 + i < total ? rows + (size_t)((i0 + i) / n_cam) * words : nullptr;
       TRY(grow(p.wsum, p.slot_cap * 4));
       TRY(grow(p.stop, p.slot_cap * 4));
       p.weighted = true;
