@@ -143,6 +143,35 @@ def make_camera(cam) -> fdgs_camera:
     return c
 
 
+# numpy image of fdgs_camera (same fields, same 4-byte packing), for marshalling many
+# cameras without building one ctypes structure each
+_CAM_DTYPE = np.dtype([("viewmat", np.float32, (16,)), ("fx", np.float32), ("fy", np.float32),
+                       ("cx", np.float32), ("cy", np.float32), ("width", np.int32),
+                       ("height", np.int32), ("znear", np.float32)])
+assert _CAM_DTYPE.itemsize == ctypes.sizeof(fdgs_camera)
+
+
+def make_cameras(cams):
+    """Array of fdgs_camera for a list of cameras, as (numpy record array, ctypes pointer);
+    keep the array alive while the pointer is in use."""
+    n = len(cams)
+    arr = np.zeros(max(n, 1), dtype=_CAM_DTYPE)
+    if n:
+        arr["viewmat"][:n] = np.asarray([c.viewmat for c in cams], np.float32).reshape(n, 16)
+        for f in ("fx", "fy", "cx", "cy", "znear"):
+            arr[f][:n] = [getattr(c, f) for c in cams]
+        arr["width"][:n] = [c.width for c in cams]
+        arr["height"][:n] = [c.height for c in cams]
+    return arr, arr.ctypes.data_as(ctypes.POINTER(fdgs_camera))
+
+
+def _times(ts):
+    a = np.ascontiguousarray(np.asarray(ts, np.float32).reshape(-1))
+    if a.size == 0:
+        a = np.zeros(1, np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
 def _opts(use_mask, bg, tight=False):
     o = fdgs_render_opts()
     o.use_mask = int(bool(use_mask))
@@ -317,12 +346,13 @@ class Scene:
 
     def render_batch(self, cams, ts, use_mask=True, bg=(0.0, 0.0, 0.0), outs=None, stream=None):
         n = len(cams)
-        carr = (fdgs_camera * max(n, 1))(*[make_camera(c) for c in cams])
-        tarr = (ctypes.c_float * max(n, 1))(*[float(t) for t in ts])
+        _ca, carr = make_cameras(cams)
+        _ta, tarr = _times(ts)
         if outs is None:
             outs = [torch.empty((3, int(c.height), int(c.width)), dtype=torch.float32,
                                 device=self.device) for c in cams]
-        parr = (ctypes.c_void_p * max(n, 1))(*[o.data_ptr() for o in outs])
+        _pa = np.asarray([o.data_ptr() for o in outs] or [0], dtype=np.uint64)
+        parr = _pa.ctypes.data_as(ctypes.POINTER(_P))
         o = _opts(use_mask, bg)
         check(lib().fdgs_render_batch(self.handle, carr, tarr, n, ctypes.byref(o), parr,
                                       _stream(stream)))
@@ -331,12 +361,13 @@ class Scene:
     def batch_autotune(self, cams, ts, use_mask=True, bg=(0.0, 0.0, 0.0), outs=None,
                        stream=None):
         n = len(cams)
-        carr = (fdgs_camera * max(n, 1))(*[make_camera(c) for c in cams])
-        tarr = (ctypes.c_float * max(n, 1))(*[float(t) for t in ts])
+        _ca, carr = make_cameras(cams)
+        _ta, tarr = _times(ts)
         if outs is None:
             outs = [torch.empty((3, int(c.height), int(c.width)), dtype=torch.float32,
                                 device=self.device) for c in cams]
-        parr = (ctypes.c_void_p * max(n, 1))(*[o.data_ptr() for o in outs])
+        _pa = np.asarray([o.data_ptr() for o in outs] or [0], dtype=np.uint64)
+        parr = _pa.ctypes.data_as(ctypes.POINTER(_P))
         o = _opts(use_mask, bg)
         check(lib().fdgs_batch_autotune(self.handle, carr, tarr, n, ctypes.byref(o), parr,
                                         _stream(stream)))
@@ -378,7 +409,7 @@ class Scene:
     def build_keyframe_masks(self, cams, key_times, out=None, stream=None):
         """Key-frame masks from the training views ``cams`` at ``key_times``: uint8
         [n_key][ceil(n/8)] on the device, in the layout ``set_active_mask`` takes."""
-        carr = (fdgs_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
+        _ca, carr = make_cameras(cams)
         tarr = (ctypes.c_float * max(len(key_times), 1))(*[float(t) for t in key_times])
         if out is None:
             out = torch.empty((len(key_times), (self.n + 7) // 8), dtype=torch.uint8,
@@ -409,7 +440,7 @@ class Scene:
         return ranges, ids[: n.value]
 
     def variation_score(self, cams, ts, batch=8, out=None, stream=None):
-        carr = (fdgs_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
+        _ca, carr = make_cameras(cams)
         tarr = (ctypes.c_float * max(len(ts), 1))(*[float(t) for t in ts])
         if out is None:
             out = torch.empty((self.n,), dtype=torch.float32, device=self.device)
