@@ -137,7 +137,8 @@ struct BatchPlan {
   uint64_t key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
   std::vector<ReqDesc> tmpl;
   Buf reqs, ctr, part, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base, key_cnt,
-      rec_sorted, rect, diff, masks, ranges, qkeys, qkeys_alt, lists, done, t0, scratch;
+      rec_sorted, rect, diff, masks, ranges, branges, bcount, bkey_cnt, qkeys, qkeys_alt, lists,
+      ltm, done, t0, scratch;
   ReqDesc *h_reqs = nullptr;
   uint32_t *h_ctr = nullptr;
   unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
@@ -155,8 +156,8 @@ struct BatchPlan {
     stop.release();
     if (h_stamps) cudaFreeHost(h_stamps);
     Buf *all[] = {&reqs, &ctr, &part, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
-                  &slot_base, &key_cnt, &rec_sorted, &rect, &diff, &masks, &ranges, &qkeys,
-                  &qkeys_alt, &lists, &done, &t0, &scratch};
+                  &slot_base, &key_cnt, &rec_sorted, &rect, &diff, &masks, &ranges, &branges,
+                  &bcount, &bkey_cnt, &qkeys, &qkeys_alt, &lists, &ltm, &done, &t0, &scratch};
     for (Buf *b : all) b->release();
     if (h_reqs) cudaFreeHost(h_reqs);
     if (h_ctr) cudaFreeHost(h_ctr);
@@ -470,6 +471,7 @@ bool plan_matches(const BatchPlan *p, const fdgs_scene *s, const fdgs_camera *ca
 
 int plan_alloc_lists(BatchPlan &p) {
   TRY(grow(p.lists, std::max<uint64_t>(p.key_cap, 1) * 4));
+  TRY(grow(p.ltm, std::max<uint64_t>(p.key_cap, 1) * 2));
   return FDGS_OK;
 }
 
@@ -513,7 +515,7 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   p.mask_total = mask;
   p.rn = (uint64_t)n * N;
   p.slot_cap = p.rn + (uint64_t)n * 256;
-  p.key_cap = std::max<uint64_t>(p.rn * 16, 1 << 20);
+  p.key_cap = std::max<uint64_t>(p.rn * 8, 1 << 20);   // block-list entries
   const uint64_t P = (N + 255) / 256;
   TRY(grow(p.reqs, n * sizeof(ReqDesc)));
   TRY(grow(p.ctr, BC_COUNT * 4));
@@ -531,6 +533,9 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   TRY(grow(p.diff, diff * 4));
   TRY(grow(p.masks, std::max<uint64_t>(mask, 1) * 4));
   TRY(grow(p.ranges, tiles * 8));
+  TRY(grow(p.branges, std::max<uint64_t>(blocks, 1) * 8));
+  TRY(grow(p.bcount, std::max<uint64_t>(blocks, 1) * 4));
+  TRY(grow(p.bkey_cnt, n * 8));
   TRY(grow(p.qkeys, tiles * 8));
   TRY(grow(p.qkeys_alt, tiles * 8));
   TRY(grow(p.done, n * 8));
@@ -604,6 +609,10 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.diff = p.diff.as<int>();
   b.masks = p.masks.as<uint32_t>();
   b.ranges = p.ranges.as<uint2>();
+  b.branges = p.branges.as<uint2>();
+  b.bcount = p.bcount.as<uint32_t>();
+  b.bkey_cnt = p.bkey_cnt.as<unsigned long long>();
+  b.ltm = p.ltm.as<uint16_t>();
   b.qkeys = p.qkeys.as<uint64_t>();
   b.qkeys_alt = p.qkeys_alt.as<uint64_t>();
   b.queue = nullptr;
@@ -687,8 +696,9 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
     }
     if (e & kErrCapacity) {
       CK(cudaMemset(s->status.p, 0, 4));
-      const uint64_t nkeys = (uint64_t)p.h_ctr[BC_NKEYS_LO] | ((uint64_t)p.h_ctr[BC_NKEYS_HI] << 32);
-      if (nkeys >= (1ull << 32)) return fail(FDGS_ERR_CAPACITY, "batch has >= 2^32 tile keys");
+      const uint64_t nkeys =
+          (uint64_t)p.h_ctr[BC_NBKEYS_LO] | ((uint64_t)p.h_ctr[BC_NBKEYS_HI] << 32);
+      if (nkeys >= (1ull << 32)) return fail(FDGS_ERR_CAPACITY, "batch has >= 2^32 list entries");
       p.key_cap = nkeys + nkeys / 8 + 1024;
       TRY(plan_alloc_lists(p));
       if (p.exec) TRY(plan_capture(s, p));
@@ -1170,16 +1180,39 @@ int fdgs_batch_tile_lists(fdgs_scene *s, int req, uint32_t *tile_ranges_host,
   CK(cudaMemcpy(&nv, p.nv.as<uint32_t>() + req, 4, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&vis_base, p.vis_base.as<uint32_t>() + req, 4, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&slot_base, p.slot_base.as<uint32_t>() + req, 4, cudaMemcpyDeviceToHost));
-  std::vector<uint32_t> slots(n);
   std::vector<uint64_t> keys(std::max<uint32_t>(nv, 1));
-  CK(cudaMemcpy(slots.data(), p.lists.as<uint32_t>() + lo, n * 4, cudaMemcpyDeviceToHost));
   if (nv) CK(cudaMemcpy(keys.data(), p.vis_sorted + vis_base, (size_t)nv * 8,
                         cudaMemcpyDeviceToHost));
+  // the request's block lists, then each tile's list: its block's entries holding its bit
+  const int gx = q.cam.gx;
+  const int bgx = (gx + kListBlock - 1) / kListBlock, bgy = (q.cam.gy + kListBlock - 1) / kListBlock;
+  const size_t nb = (size_t)bgx * bgy;
+  std::vector<uint2> br(nb);
+  CK(cudaMemcpy(br.data(), p.branges.as<uint2>() + q.block_base, nb * 8,
+                cudaMemcpyDeviceToHost));
+  const uint32_t blo = br[0].x, bhi = br[nb - 1].y;
+  std::vector<uint32_t> slots(std::max<uint32_t>(bhi - blo, 1));
+  std::vector<uint16_t> tms(std::max<uint32_t>(bhi - blo, 1));
+  if (bhi > blo) {
+    CK(cudaMemcpy(slots.data(), p.lists.as<uint32_t>() + blo, (size_t)(bhi - blo) * 4,
+                  cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tms.data(), p.ltm.as<uint16_t>() + blo, (size_t)(bhi - blo) * 2,
+                  cudaMemcpyDeviceToHost));
+  }
   const uint64_t id_mask = (1ull << kBatchIdBits) - 1;
-  for (uint64_t i = 0; i < n; ++i) {
-    const uint32_t rank = slots[i] - slot_base;
-    if (rank >= nv) return fail(FDGS_ERR_STATE, "list entry outside the request's slots");
-    tile_ids_host[i] = (uint32_t)(keys[rank] & id_mask);
+  for (size_t t = 0; t < tiles; ++t) {
+    const int tx = (int)(t % gx), ty = (int)(t / gx);
+    const uint2 b2 = br[(ty / kListBlock) * bgx + tx / kListBlock];
+    const int bit = (ty % kListBlock) * kListBlock + tx % kListBlock;
+    uint64_t o = rg[t].x - lo;
+    for (uint32_t e = b2.x; e < b2.y; ++e) {
+      if (!((tms[e - blo] >> bit) & 1u)) continue;
+      const uint32_t rank = slots[e - blo] - slot_base;
+      if (rank >= nv || o >= rg[t].y - lo)
+        return fail(FDGS_ERR_STATE, "block lists disagree with the tile counts");
+      tile_ids_host[o++] = (uint32_t)(keys[rank] & id_mask);
+    }
+    if (o != rg[t].y - lo) return fail(FDGS_ERR_STATE, "block lists disagree with the tile counts");
   }
   return FDGS_OK;
 }

@@ -17,7 +17,7 @@
 // skipped pixel by pixel anyway: results equal evaluating every entry at every pixel.
 //
 // The per-pixel evaluation has no branches: a pixel whose exponent fails a test, or which has
-// already stopped, takes alpha = 0, and T * (1 - 0), fma(c, 0, C) leave its transmittance and
+// already stopped, takes alpha = 0, and T - 0 T, fma(c, 0, C) leave its transmittance and
 // colour sums bit-for-bit unchanged. So the arithmetic of every pixel, and every result, is
 // the same for every footprint, every PX and the one-pixel-per-branch formulation.
 #pragma once
@@ -85,6 +85,8 @@ struct BlendSmem {
 struct BlendTile {
   int tx, ty, W, H;
   uint2 range;                 // [start, end) into keys
+  const uint16_t *tmask;       // block lists: per entry, the block's tiles it covers
+  int tbit;                    // block lists: this tile's bit in those masks
   const float *rec_sorted;     // blend-ready records [rank][16]
   float *rgb;                  // [3][H][W]
   float *T_final;              // [H][W] (written when kAux)
@@ -98,7 +100,11 @@ struct BlendTile {
 
 // kAux: also write the final transmittance and 1 + the list position of the last blended
 // entry per pixel (what the reverse replay of the backward starts from).
-template <typename K, int FW, int PX, bool kWeights, bool kCount, bool kAux>
+// kBlk: keys[range] is the list of the tile's block of tiles, entries in rank order with a
+// mask of the block's tiles each covers; only entries with bit tbit are staged (the others
+// get log2 opacity -inf, so the tile test drops them), and the tile composites exactly its
+// own list.
+template <typename K, int FW, int PX, bool kWeights, bool kCount, bool kAux, bool kBlk = false>
 __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restrict__ keys,
                                            uint32_t rmask, BlendSmem<256 / PX> &sm) {
   constexpr int NT = 256 / PX;   // threads = records staged per batch
@@ -130,15 +136,18 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
   uint32_t nevals = 0, ntests = 0, npass = 0;
   bool warp_done = __all_sync(0xffffffffu, lane_done);
 
+  constexpr K kNone = ~(K)0;     // block lists: the entry does not cover this tile
   K kr = (K)0;
   auto load_key = [&](int b) {
     const uint32_t i = (uint32_t)b * NT + tid;
     kr = i < n ? keys[bt.range.x + i] : (K)0;
+    if (kBlk && i < n && !((bt.tmask[bt.range.x + i] >> bt.tbit) & 1u)) kr = kNone;
   };
   auto issue = [&](int b) {
     const int st = b & 1;
     const uint32_t i = (uint32_t)b * NT + tid;
-    if (i < n) {
+    if (kBlk && i < n && kr == kNone) sm.g1[st][tid].y = -INFINITY;
+    if (i < n && (!kBlk || kr != kNone)) {
       const uint32_t r = (uint32_t)(kr & (K)rmask);
       const float *rp = bt.rec_sorted + (size_t)r * kRecS;
       cp_async16(&sm.g0[st][tid], rp);

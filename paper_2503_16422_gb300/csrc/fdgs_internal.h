@@ -152,7 +152,7 @@ struct ReqDesc {
 constexpr int kListBlock = 4;
 enum BatchCounter {
   BC_PRE_ITEM = 0, BC_NVIS = 1, BC_NSLOTS = 2, BC_NTILES = 3, BC_NKEYS_LO = 5,
-  BC_NKEYS_HI = 6, BC_QUEUE = 7, BC_COUNT = 16
+  BC_NKEYS_HI = 6, BC_QUEUE = 7, BC_NBKEYS_LO = 8, BC_NBKEYS_HI = 9, BC_COUNT = 16
 };
 struct BatchDev {
   const ReqDesc *reqs;
@@ -175,10 +175,14 @@ struct BatchDev {
   uint2 *rect;                       // [slots] tile rectangle: x0 | x1 << 16, y0 | y1 << 16
   int *diff;
   uint32_t *masks;
-  uint2 *ranges;                     // [ntiles]
+  uint2 *ranges;                     // [ntiles] tile-key ranges (counts; lists are per block)
+  uint2 *branges;                    // [nblocks] [start, end) into lists / ltm
+  uint32_t *bcount;                  // [nblocks] block-list entries
+  unsigned long long *bkey_cnt;      // [nreq] block-list entries per request
   uint64_t *qkeys, *qkeys_alt;
   const uint64_t *queue;
-  uint32_t *lists;                   // [key_cap] slot indices
+  uint32_t *lists;                   // [key_cap] block lists: slot indices, rank order
+  uint16_t *ltm;                     // [key_cap] block lists: the block's tiles each covers
   unsigned long long *done_ns, *t0_ns;
   unsigned long long *evals;         // [3] blend counters (see BlendTile), or null
   // weighted passes (null for renders): per-slot blend weights and stop flags; the score
