@@ -714,16 +714,16 @@ def score_timing(stream):
 
 
 # DRAM bytes the persistent blend moves per frame of a batch at 1352x1014 on the 200k pruned
-# scene, from one ncu capture of an 8-frame launch of k_blend_persist<8, 4> (89.3 MB read +
-# 77.8 MB written); to be re-captured whenever the blend kernel changes.
-BLEND_PERSIST_DRAM_BYTES_PER_FRAME = (89291264 + 77813760) / 8
+# scene, from one ncu capture of an 8-frame launch of k_blend_persist<8, 4> (32.6 MB read +
+# 76.9 MB written); to be re-captured whenever the blend kernel changes.
+BLEND_PERSIST_DRAM_BYTES_PER_FRAME = (32554240 + 76869120) / 8
 
 
 def launches_per_batch():
     # start, preprocess, partition scan, bases, segment compaction, depth sort (histogram,
-    # scan, 5 passes), gather, tile scan, block lists, queue sort (histogram, scan, 3 passes),
-    # persistent blend, and the 8 one-thread %globaltimer stamps between the stages
-    return 1 + 1 + 1 + 1 + 1 + 7 + 1 + 1 + 1 + 5 + 1 + 8
+    # scan, 5 passes), gather, block counts, tile scan, block lists, queue sort (histogram,
+    # scan, 3 passes), persistent blend, and the 8 one-thread %globaltimer stamps
+    return 1 + 1 + 1 + 1 + 1 + 7 + 1 + 1 + 1 + 1 + 5 + 1 + 8
 
 
 def run_only(args):
