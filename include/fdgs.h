@@ -241,6 +241,14 @@ int fdgs_build_keyframe_masks(fdgs_scene *scene, const fdgs_camera *cams, int n_
 int fdgs_set_sh_codebook(fdgs_scene *scene, const float *codebook_dev, int n_code,
                          const uint16_t *codes_dev);
 
+/* Capacity, in block-list entries (one per (Gaussian, 4x4 tile block) pair a request's
+ * rectangles meet), that batches of this scene start with; 0 restores the default
+ * (8 x requests x Gaussians, at least 2^20). Applies to the current batch plan too. A batch
+ * that needs more detects it on the device (its lists are left empty), grows the lists to
+ * 1.125 x the need and reruns before fdgs_render_batch returns, so the capacity only trades
+ * memory against a first-run retry. */
+int fdgs_set_batch_list_capacity(fdgs_scene *scene, uint64_t entries);
+
 /* Last batch: visible Gaussians and tile-list entries summed over its requests. The batched
  * lists use, per Gaussian, the 3-sigma tile square intersected with the tiles its
  * alpha >= 1/255 ellipse can reach, so n_keys is at most the per-request renders' total

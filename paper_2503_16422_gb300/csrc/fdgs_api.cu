@@ -173,6 +173,7 @@ struct fdgs_scene {
   fdgs_scene_desc d{};
   int device = 0;
   BatchPlan *plan = nullptr;
+  uint64_t list_cap_hint = 0;   // initial block-list capacity of new plans (0: heuristic)
   Buf masks;
   size_t row_words = 0;
   int n_key = 0;
@@ -515,7 +516,8 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   p.mask_total = mask;
   p.rn = (uint64_t)n * N;
   p.slot_cap = p.rn + (uint64_t)n * 256;
-  p.key_cap = std::max<uint64_t>(p.rn * 8, 1 << 20);   // block-list entries
+  // block-list entries; a batch that needs more regrows the lists and reruns
+  p.key_cap = s->list_cap_hint ? s->list_cap_hint : std::max<uint64_t>(p.rn * 8, 1 << 20);
   const uint64_t P = (N + 255) / 256;
   TRY(grow(p.reqs, n * sizeof(ReqDesc)));
   TRY(grow(p.ctr, BC_COUNT * 4));
@@ -1138,6 +1140,21 @@ int fdgs_set_sh_codebook(fdgs_scene *s, const float *codebook_dev, int n_code,
   s->sh_cb = codebook_dev;
   s->sh_code = codes_dev;
   s->n_code = n_code;
+  return FDGS_OK;
+}
+
+int fdgs_set_batch_list_capacity(fdgs_scene *s, uint64_t entries) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  s->list_cap_hint = entries;
+  if (s->plan && entries) {
+    BatchPlan &p = *s->plan;
+    p.key_cap = entries;
+    TRY(plan_alloc_lists(p));
+    if (p.exec) {                 // the captured graph holds the old capacity
+      cudaGraphExecDestroy(p.exec);
+      p.exec = nullptr;
+    }
+  }
   return FDGS_OK;
 }
 

@@ -83,6 +83,7 @@ _SIGNATURES = {
                         ctypes.POINTER(ctypes.c_float)],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
     "fdgs_batch_counts": [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
+    "fdgs_set_batch_list_capacity": [_P, ctypes.c_uint64],
     "fdgs_batch_tile_lists": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32),
                               ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64,
                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
@@ -423,6 +424,10 @@ class Scene:
         nv, nk = ctypes.c_uint64(), ctypes.c_uint64()
         check(lib().fdgs_batch_counts(self.handle, ctypes.byref(nv), ctypes.byref(nk)))
         return dict(n_visible=nv.value, n_keys=nk.value)
+
+    def set_batch_list_capacity(self, entries):
+        """Block-list capacity batches start with (0: default); see the C header."""
+        check(lib().fdgs_set_batch_list_capacity(self.handle, int(entries)))
 
     def batch_tile_lists(self, req):
         """Tile lists of request ``req`` of the last batch, as numpy arrays in the layout of

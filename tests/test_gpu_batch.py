@@ -155,3 +155,23 @@ def test_batch_of_128_requests_and_the_limit(fd):
     with pytest.raises(fd.FdgsError):
         sc.render_batch(cams + cams[:1], ts + ts[:1], use_mask=True)
     sc.close()
+
+
+def test_batch_list_capacity_overflow_regrows_and_reruns(fd):
+    """A batch whose block lists exceed the capacity is detected on the device, the lists
+    grow and the batch reruns inside the call: images and lists are those of a batch that
+    fit (twice: the capacity is reset to 1024 entries before each call)."""
+    _, sc = _scene_gpu(fd, True, n=8000, seed=47)
+    res = [(200, 150), (96, 96), (250, 130)]
+    cams, ts = _requests(12, 6, res)
+    want = sc.render_batch(cams, ts, use_mask=True)
+    lists = [sc.batch_tile_lists(i) for i in range(len(cams))]
+    for attempt in range(2):
+        sc.set_batch_list_capacity(1024)
+        outs = sc.render_batch(cams, ts, use_mask=True)
+        for i in range(len(cams)):
+            assert torch.equal(outs[i], want[i]), (attempt, i)
+            r, ids = sc.batch_tile_lists(i)
+            assert np.array_equal(r, lists[i][0]) and np.array_equal(ids, lists[i][1])
+    sc.set_batch_list_capacity(0)
+    sc.close()
