@@ -525,6 +525,21 @@ def comparisons(sc, cams, times, flush, stream):
     sc2.set_active_mask(torch.as_tensor(scenes.keyframe_masks(big, kt)).cuda(), kt)
     res["unpruned_masked"] = dict(single(sc2, True, fr[:12]), n_gaussians=big.n)
     res["unpruned_unmasked"] = dict(single(sc2, False, fr[:12]), n_gaussians=big.n)
+    # the same scene in batches of 64 frames (the headline's frame walk)
+    B = 64
+    outs = [torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device="cuda")
+            for _ in range(B)]
+    steps = [frame_list(B, 7 * B), frame_list(B, 9 * B), frame_list(B, 11 * B)]
+    bargs = [([cams[k] for k in f], [float(times[k]) for k in f]) for f in steps]
+    sc2.render_batch(*bargs[0], outs=outs)
+    stages = []
+    ms, _ = timed_batches(sc2, [a for a, _ in bargs], [b_ for _, b_ in bargs], [outs] * 3, True,
+                          flush, stream, stages)
+    res["unpruned_masked_batched"] = dict(
+        fps=B / (statistics.median(ms) / 1e3), ms_per_batch=statistics.median(ms), batch=B,
+        n_gaussians=big.n, stage_ms={k: statistics.median([x[k] for x in stages])
+                                     for k in stages[0]})
+    del outs
     sc2.close()
     del big
     torch.cuda.empty_cache()

@@ -583,6 +583,20 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.n = (uint32_t)s->d.n;
   b.ntiles = p.ntiles;
   b.nblocks = p.nblocks;
+  {
+    // partition-major preprocess when the attributes (and SH) outgrow half of L2: each
+    // partition's attributes are then read once from DRAM for all requests (measured on 3M
+    // Gaussians: 9.0 vs 11.3 ms per 64 requests; on 200k, which fits, 0.63 vs 0.60 ms)
+    static int l2 = -1;
+    if (l2 < 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) l2 = 0;
+    }
+    const uint64_t k = (uint64_t)(s->d.sh_degree + 1) * (s->d.sh_degree + 1);
+    const uint64_t bytes = (uint64_t)s->d.n * (68 + 12 * k);
+    b.part_major = l2 > 0 && bytes > (uint64_t)l2 / 2 ? 1 : 0;
+  }
   b.mask_words = p.mask_words;
   b.key_cap = p.key_cap;
   b.mean4 = (const float4 *)s->d.mean4;

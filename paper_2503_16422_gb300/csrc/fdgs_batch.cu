@@ -63,7 +63,12 @@ __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= items) break;
-    const uint32_t r = item / P, part = item % P;
+    // request-major order, or partition-major (the requests of one partition back to back,
+    // sharing its attributes in L2) for scenes too large for L2; segments and counts are
+    // stored request-major (si)
+    const uint32_t r = b.part_major ? item % b.nreq : item / P;
+    const uint32_t part = b.part_major ? item / b.nreq : item % P;
+    const uint32_t si = r * P + part;
     const ReqDesc &q = b.reqs[r];
     const uint32_t i = part * kB + tid;
     bool active = false, vis = false;
@@ -114,11 +119,11 @@ __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
         s_wcnt[w] = tot;
         tot += c;
       }
-      b.part[item].x = tot;
+      b.part[si].x = tot;
     }
     __syncthreads();
     // the item's own 256-key segment, in id order; placed by k_seg_compact
-    if (vis) b.vis_seg[(size_t)item * kB + s_wcnt[warp] + __popc(vb & lanemask_lt())] = key;
+    if (vis) b.vis_seg[(size_t)si * kB + s_wcnt[warp] + __popc(vb & lanemask_lt())] = key;
     __syncthreads();
   }
 }

@@ -158,6 +158,7 @@ struct BatchDev {
   const ReqDesc *reqs;
   int nreq;
   uint32_t n, ntiles, nblocks, mask_words;
+  int part_major;                    // preprocess order: partition-major (large scenes)
   uint64_t key_cap;
   const float4 *mean4, *ls4, *ql, *qr;
   const float *opacity, *sh;

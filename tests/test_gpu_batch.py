@@ -175,3 +175,18 @@ def test_batch_list_capacity_overflow_regrows_and_reruns(fd):
             assert np.array_equal(r, lists[i][0]) and np.array_equal(ids, lists[i][1])
     sc.set_batch_list_capacity(0)
     sc.close()
+
+
+def test_large_scene_batch_matches_sequential(fd):
+    """300k degree-3 Gaussians (78 MB of attributes, more than half of L2): the batched
+    preprocess runs partition-major; images still equal the per-request renders."""
+    s = scenes.make_scene(300_000, 48, sh_degree=3, lt_short=(-3.0, 0.5), lt_long=(-1.0, 0.5),
+                          short_frac=0.5)
+    sc = fd.Scene.from_host(s)
+    kt = scenes.keyframe_times(300, 6)
+    sc.set_active_mask(torch.as_tensor(scenes.keyframe_masks(s, kt)).cuda(), kt)
+    cams, ts = _requests(13, 5, [(160, 120), (96, 128), (200, 90)])
+    outs = sc.render_batch(cams, ts, use_mask=True)
+    for i in range(len(cams)):
+        assert torch.equal(outs[i], sc.render(cams[i], ts[i], use_mask=True)), i
+    sc.close()
