@@ -138,7 +138,7 @@ struct BatchPlan {
   std::vector<ReqDesc> tmpl;
   Buf reqs, ctr, part, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base, key_cnt,
       rec_sorted, rect, diff, masks, ranges, branges, bcount, bkey_cnt, qkeys, qkeys_alt, lists,
-      ltm, done, t0, scratch;
+      ltm, done, t0, scratch, cond;
   ReqDesc *h_reqs = nullptr;
   uint32_t *h_ctr = nullptr;
   unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
@@ -157,7 +157,8 @@ struct BatchPlan {
     if (h_stamps) cudaFreeHost(h_stamps);
     Buf *all[] = {&reqs, &ctr, &part, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
                   &slot_base, &key_cnt, &rec_sorted, &rect, &diff, &masks, &ranges, &branges,
-                  &bcount, &bkey_cnt, &qkeys, &qkeys_alt, &lists, &ltm, &done, &t0, &scratch};
+                  &bcount, &bkey_cnt, &qkeys, &qkeys_alt, &lists, &ltm, &done, &t0, &scratch,
+                  &cond};
     for (Buf *b : all) b->release();
     if (h_reqs) cudaFreeHost(h_reqs);
     if (h_ctr) cudaFreeHost(h_ctr);
@@ -532,6 +533,7 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   TRY(grow(p.key_cnt, n * 8));
   TRY(grow(p.rec_sorted, p.slot_cap * kRecS * 4));
   TRY(grow(p.rect, p.slot_cap * 8));
+  TRY(grow(p.cond, std::max<uint64_t>(N, 1) * 80));
   TRY(grow(p.diff, diff * 4));
   TRY(grow(p.masks, std::max<uint64_t>(mask, 1) * 4));
   TRY(grow(p.ranges, tiles * 8));
@@ -621,6 +623,7 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.slot_base = p.slot_base.as<uint32_t>();
   b.key_cnt = p.key_cnt.as<unsigned long long>();
   b.rec_sorted = p.rec_sorted.as<float>();
+  b.cond = p.cond.as<float4>();
   b.rect = p.rect.as<uint2>();
   b.diff = p.diff.as<int>();
   b.masks = p.masks.as<uint32_t>();

@@ -51,6 +51,17 @@ __device__ __forceinline__ int find_segment(const uint32_t *bases, int n, uint32
 }
 
 // ---------------------------------------------------------------------------------------
+// The time- and camera-independent part of every Gaussian's forward, once per batch.
+__global__ void __launch_bounds__(kB) k_cond_batch(BatchDev b) {
+  for (uint32_t i = blockIdx.x * kB + threadIdx.x; i < b.n; i += gridDim.x * kB) {
+    GaussState g;
+    float inv_nt;
+    gauss_cond(__ldg(&b.ls4[i]), __ldg(&b.ql[i]), __ldg(&b.qr[i]), __ldg(&b.opacity[i]), g,
+               inv_nt);
+    cond_store(g, inv_nt, b.cond + (size_t)i * kCond4);
+  }
+}
+
 template <bool kVQ>
 __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
   __shared__ uint32_t s_item;
@@ -81,9 +92,9 @@ __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
       }
       if (active) {
         GaussState g;
-        const uint8_t fl = gauss_forward(q.cam, q.t, __ldg(&b.mean4[i]), __ldg(&b.ls4[i]),
-                                         __ldg(&b.ql[i]), __ldg(&b.qr[i]),
-                                         __ldg(&b.opacity[i]), g);
+        float inv_nt;
+        cond_load(b.cond + (size_t)i * kCond4, g, inv_nt);
+        const uint8_t fl = gauss_forward_tail(q.cam, q.t, __ldg(&b.mean4[i]), inv_nt, g);
         if (fl & kFlagDet) {
           const float half = 0.5f * (g.c00 - g.c11);
           const float disc = half * half + g.c01 * g.c01;
@@ -578,6 +589,8 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
   k_batch_start<<<1, 32, 0, st>>>(b);
   mark(0);
   static int g_pre = 0, g_gather = 0;
+  k_cond_batch<<<(int)std::min<uint64_t>((b.n + kB - 1) / kB, (uint64_t)num_sms() * 8), kB, 0,
+                 st>>>(b);
   if (!g_pre) g_pre = grid_of((const void *)k_pre_batch<false>, kB, 64);
   if (!g_gather) g_gather = grid_of((const void *)k_gather_batch, kB, 64);
   const uint64_t pre_items = (uint64_t)((b.n + kB - 1) / kB) * b.nreq;

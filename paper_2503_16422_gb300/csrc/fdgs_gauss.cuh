@@ -108,12 +108,11 @@ __device__ __forceinline__ void sh_grad(int deg, float x, float y, float z, cons
   gx += kSH3a * (3.f * xx - 3.f * yy) * g[15]; gy -= kSH3a * 6.f * x * y * g[15];
 }
 
-// Forward of one Gaussian up to the cull tests. Returns the decision flags (kFlag*). The
-// state is filled as far as the Gaussian got; a Gaussian that fails a test stops there.
-__device__ __forceinline__ uint8_t gauss_forward(const DevCam &cam, float t, float4 mean,
-                                                 float4 ls, float4 ql, float4 qr, float o,
-                                                 GaussState &g) {
-  uint8_t flags = kFlagMask;
+// The time- and camera-independent part of a Gaussian's forward: the 4D frame from the two
+// quaternions and the scales, and Eq. 1's conditional factors (N with Sigma_xyz|t = N N^T,
+// w with mu(t) = mu_xyz + w (t - mu_t) / |m_t|, Sigma_t = |m_t|^2) and sigmoid(o).
+__device__ __forceinline__ void gauss_cond(float4 ls, float4 ql, float4 qr, float o,
+                                           GaussState &g, float &inv_nt) {
   quat_unit(ql, g.qn_l, g.inv_l);
   quat_unit(qr, g.qn_r, g.inv_r);
   left_mat(g.qn_l, g.Lm);
@@ -135,7 +134,7 @@ __device__ __forceinline__ uint8_t gauss_forward(const DevCam &cam, float t, flo
   // Eq. 1 / Eq. 3
   g.nt2 = g.M[12] * g.M[12] + g.M[13] * g.M[13] + g.M[14] * g.M[14] + g.M[15] * g.M[15];
   g.nt = sqrtf(g.nt2);
-  const float inv_nt = 1.f / g.nt;
+  inv_nt = 1.f / g.nt;
 #pragma unroll
   for (int m = 0; m < 4; ++m) g.mh[m] = g.M[12 + m] * inv_nt;
 #pragma unroll
@@ -145,9 +144,18 @@ __device__ __forceinline__ uint8_t gauss_forward(const DevCam &cam, float t, flo
 #pragma unroll
     for (int m = 0; m < 4; ++m) g.N[j * 4 + m] = g.M[j * 4 + m] - g.w[j] * g.mh[m];
   }
+  g.sig = 1.f / (1.f + expf(-o));
+}
+
+// The per-(t, camera) part of the forward, from the conditional factors (g.N, g.w, g.nt2,
+// g.sig and inv_nt): temporal weight, conditional mean, view transform, EWA projection, up
+// to the cull tests. Returns the decision flags (kFlag*); a Gaussian that fails a test stops
+// there.
+__device__ __forceinline__ uint8_t gauss_forward_tail(const DevCam &cam, float t, float4 mean,
+                                                      float inv_nt, GaussState &g) {
+  uint8_t flags = kFlagMask;
   g.dt = t - mean.w;
   g.p = expf(-0.5f * g.dt * g.dt / g.nt2);
-  g.sig = 1.f / (1.f + expf(-o));
   g.a = g.sig * g.p;
   if (!(g.a >= kAlphaMin)) return flags;
   flags |= kFlagTemporal;
@@ -197,6 +205,37 @@ __device__ __forceinline__ uint8_t gauss_forward(const DevCam &cam, float t, flo
   if (!(g.det > 0.f)) return flags;
   flags |= kFlagDet;
   return flags;
+}
+
+// Forward of one Gaussian up to the cull tests (both parts). Returns the decision flags
+// (kFlag*). The state is filled as far as the Gaussian got.
+__device__ __forceinline__ uint8_t gauss_forward(const DevCam &cam, float t, float4 mean,
+                                                 float4 ls, float4 ql, float4 qr, float o,
+                                                 GaussState &g) {
+  float inv_nt;
+  gauss_cond(ls, ql, qr, o, g, inv_nt);
+  return gauss_forward_tail(cam, t, mean, inv_nt, g);
+}
+
+// The conditional factors of gauss_cond as stored per Gaussian for the batched path
+// (5 x float4): N (12), w (3), inv_nt, nt2, sigmoid(o), 2 unused.
+constexpr int kCond4 = 5;
+__device__ __forceinline__ void cond_store(const GaussState &g, float inv_nt, float4 *dst) {
+  dst[0] = make_float4(g.N[0], g.N[1], g.N[2], g.N[3]);
+  dst[1] = make_float4(g.N[4], g.N[5], g.N[6], g.N[7]);
+  dst[2] = make_float4(g.N[8], g.N[9], g.N[10], g.N[11]);
+  dst[3] = make_float4(g.w[0], g.w[1], g.w[2], inv_nt);
+  dst[4] = make_float4(g.nt2, g.sig, 0.f, 0.f);
+}
+__device__ __forceinline__ void cond_load(const float4 *__restrict__ src, GaussState &g,
+                                          float &inv_nt) {
+  const float4 a = __ldg(&src[0]), b = __ldg(&src[1]), c = __ldg(&src[2]),
+               d = __ldg(&src[3]), e = __ldg(&src[4]);
+  g.N[0] = a.x; g.N[1] = a.y; g.N[2] = a.z; g.N[3] = a.w;
+  g.N[4] = b.x; g.N[5] = b.y; g.N[6] = b.z; g.N[7] = b.w;
+  g.N[8] = c.x; g.N[9] = c.y; g.N[10] = c.z; g.N[11] = c.w;
+  g.w[0] = d.x; g.w[1] = d.y; g.w[2] = d.z; inv_nt = d.w;
+  g.nt2 = e.x; g.sig = e.y;
 }
 
 // Colour of a Gaussian that reached the projection (state has mu3). sh is [K][3][n].

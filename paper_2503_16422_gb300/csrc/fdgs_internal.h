@@ -162,6 +162,7 @@ struct BatchDev {
   uint64_t key_cap;
   const float4 *mean4, *ls4, *ql, *qr;
   const float *opacity, *sh;
+  float4 *cond;                      // [n][5] conditional factors of every Gaussian
   const float *sh_cb;                // SH codebook or null
   const uint16_t *sh_code;
   int deg;
