@@ -461,7 +461,8 @@ def comparisons(sc, cams, times, flush, stream):
     fr = frame_list(24, 3)
 
     def single(scene_obj, masked, frames, tight=False):
-        for k in frames[:2]:
+        # warm-up over every timed frame, so no workspace grows inside the timed renders
+        for k in frames:
             scene_obj.render(cams[k], float(times[k]), use_mask=masked, out=out, tight=tight)
         ms = []
         for k in frames:
