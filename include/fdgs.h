@@ -180,10 +180,11 @@ int fdgs_frame_export(fdgs_frame *frame, uint32_t *tile_ranges_dev, uint32_t *ti
 
 /*
  * Renders n_req requests (cams[i], ts[i]; each camera has its own resolution; 1 <= n_req <=
- * 128; n < 2^25) in one device-driven pass: one per-Gaussian launch over all (request,
- * Gaussian) pairs, one global depth sort whose keys carry the request, per-request tile
- * lists, and ONE persistent blend launch over a queue of all requests' tiles, longest list
- * first. The first call for a batch geometry (request count, resolutions, mask use, scene
+ * 128; n < 2^25) in one device-driven pass: the time- and camera-independent part of the
+ * per-Gaussian work once, one launch over all (request, Gaussian) pairs, one global depth
+ * sort whose keys carry the request, per-request lists kept per 4x4 block of tiles (each
+ * entry with the block's tiles it covers), and ONE persistent blend launch over a queue of
+ * all requests' tiles, longest list first, each tile reading its block's list. The first call for a batch geometry (request count, resolutions, mask use, scene
  * attribute pointers) runs eagerly and captures the sequence in a CUDA graph; later calls
  * replay it. rgb_out_dev is a HOST array of n_req device pointers, each [3][h_i][w_i].
  * Results equal n_req calls of fdgs_render. Synchronises the stream once, at the end; if a
@@ -249,10 +250,10 @@ int fdgs_set_sh_codebook(fdgs_scene *scene, const float *codebook_dev, int n_cod
  * memory against a first-run retry. */
 int fdgs_set_batch_list_capacity(fdgs_scene *scene, uint64_t entries);
 
-/* Last batch: visible Gaussians and tile-list entries summed over its requests. The batched
- * lists use, per Gaussian, the 3-sigma tile square intersected with the tiles its
- * alpha >= 1/255 ellipse can reach, so n_keys is at most the per-request renders' total
- * (images are identical). Either pointer may be NULL. FDGS_ERR_STATE if no batch was
+/* Last batch: visible Gaussians and (tile, Gaussian) pairs summed over its requests (the
+ * entries the tiles composite from their block lists). The batched lists use, per Gaussian,
+ * the 3-sigma tile square intersected with the tiles its alpha >= 1/255 ellipse can reach,
+ * so n_keys is at most the per-request renders' total (images are identical). Either pointer may be NULL. FDGS_ERR_STATE if no batch was
  * rendered. */
 int fdgs_batch_counts(fdgs_scene *scene, uint64_t *n_visible, uint64_t *n_keys);
 
@@ -326,7 +327,7 @@ int fdgs_profile_enable(fdgs_scene *scene, int flags);
  * make, whatever its culling). Either pointer may be NULL. Synchronises the device. */
 int fdgs_profile_read(fdgs_scene *scene, float *stage_ms, uint64_t *blend_counts);
 
-/* How renders build the per-tile lists, process-wide. 1: emit one (tile, depth-rank) key
+/* How single-frame renders (fdgs_render) build the per-tile lists, process-wide. 1: emit one (tile, depth-rank) key
  * per covered tile and radix-sort the keys by tile; 2: AND per-tile-row and per-tile-column
  * coverage bitmasks over the depth ranks (no sort; wins when Gaussians cover many tiles);
  * 0 (default): choose per frame by a traffic estimate. The lists, and so every result, are
