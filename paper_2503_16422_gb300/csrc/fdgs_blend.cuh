@@ -27,8 +27,6 @@
 
 namespace fdgs {
 
-constexpr int kBlendThreads = 256;   // threads of a one-pixel-per-lane tile CTA
-
 // Launch shapes of the forward blend (kBlendShapes of them): warp footprint FW x (32 PX / FW)
 // pixels, PX pixels per lane.
 //   0: 16x2, 1: 8x4, 2: 4x8 (one pixel per lane), 3: 8x8 (two), 4: 16x8, 5: 8x16 (four)
