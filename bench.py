@@ -420,7 +420,11 @@ def run_ours(args):
             "executed_tflops": (ev * EVAL_FLOP + te * TEST_FLOP) / blend_s / 1e12,
             "blend_ms_per_batch": blend_s * 1e3 / len(steps),
             "evals_per_frame": ev / frames_done, "tests_per_frame": te / frames_done,
-            "alpha_pass_evals_per_frame": ep / frames_done}
+            "alpha_pass_evals_per_frame": ep / frames_done,
+            "issue_active": BLEND_PERSIST_ISSUE_ACTIVE,
+            "issue_src": "ncu smsp__issue_active of k_blend_persist<8, 4> on an 8-frame batch "
+                         "(profiles/k_blend_persist_batched_1352x1014.md): the kernel is "
+                         "bound by instruction issue, not by the FP32 pipes"}
         res["batch_stages_ms"] = bst
         # per-kernel profile on single renders of the same frames
         out1 = outs[0]
@@ -733,6 +737,9 @@ def score_timing(stream):
 # scene, from one ncu capture of an 8-frame launch of k_blend_persist<8, 4> (32.6 MB read +
 # 76.9 MB written); to be re-captured whenever the blend kernel changes.
 BLEND_PERSIST_DRAM_BYTES_PER_FRAME = (32554240 + 76869120) / 8
+# Fraction of cycles the persistent blend issues an instruction (ncu smsp__issue_active, same
+# capture).
+BLEND_PERSIST_ISSUE_ACTIVE = 0.859
 
 
 def launches_per_batch():
