@@ -137,8 +137,8 @@ struct BatchPlan {
   uint64_t key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
   std::vector<ReqDesc> tmpl;
   Buf reqs, ctr, part, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base, key_cnt,
-      rec_sorted, rect, diff, masks, ranges, branges, bcount, bkey_cnt, qkeys, qkeys_alt, lists,
-      ltm, done, t0, scratch, cond;
+      rect_id, ridx, rect, diff, masks, ranges, branges, bcount, bkey_cnt, qkeys, qkeys_alt,
+      lists, ltm, done, t0, scratch, cond;
   ReqDesc *h_reqs = nullptr;
   uint32_t *h_ctr = nullptr;
   unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
@@ -156,7 +156,7 @@ struct BatchPlan {
     stop.release();
     if (h_stamps) cudaFreeHost(h_stamps);
     Buf *all[] = {&reqs, &ctr, &part, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
-                  &slot_base, &key_cnt, &rec_sorted, &rect, &diff, &masks, &ranges, &branges,
+                  &slot_base, &key_cnt, &rect_id, &ridx, &rect, &diff, &masks, &ranges, &branges,
                   &bcount, &bkey_cnt, &qkeys, &qkeys_alt, &lists, &ltm, &done, &t0, &scratch,
                   &cond};
     for (Buf *b : all) b->release();
@@ -523,7 +523,10 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   TRY(grow(p.reqs, n * sizeof(ReqDesc)));
   TRY(grow(p.ctr, BC_COUNT * 4));
   TRY(grow(p.part, std::max<uint64_t>(P * n, 1) * 8));
+  if ((uint64_t)n * N >= (1ull << 32))
+    return fail(FDGS_ERR_INVALID, "batch too large: requests x Gaussians must stay below 2^32");
   TRY(grow(p.rec, std::max<uint64_t>(p.rn, 1) * kRec * 4));
+  TRY(grow(p.rect_id, std::max<uint64_t>(p.rn, 1) * 8));
   TRY(grow(p.vis_seg, std::max<uint64_t>(P * n * 256, 1) * 8));
   TRY(grow(p.vis, std::max<uint64_t>(p.rn, 1) * 8));
   TRY(grow(p.vis_alt, std::max<uint64_t>(p.rn, 1) * 8));
@@ -531,7 +534,7 @@ int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   TRY(grow(p.vis_base, n * 4));
   TRY(grow(p.slot_base, n * 4));
   TRY(grow(p.key_cnt, n * 8));
-  TRY(grow(p.rec_sorted, p.slot_cap * kRecS * 4));
+  TRY(grow(p.ridx, p.slot_cap * 4));
   TRY(grow(p.rect, p.slot_cap * 8));
   TRY(grow(p.cond, std::max<uint64_t>(N, 1) * 80));
   TRY(grow(p.diff, diff * 4));
@@ -622,7 +625,8 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.vis_base = p.vis_base.as<uint32_t>();
   b.slot_base = p.slot_base.as<uint32_t>();
   b.key_cnt = p.key_cnt.as<unsigned long long>();
-  b.rec_sorted = p.rec_sorted.as<float>();
+  b.rect_id = p.rect_id.as<uint2>();
+  b.ridx = p.ridx.as<uint32_t>();
   b.cond = p.cond.as<float4>();
   b.rect = p.rect.as<uint2>();
   b.diff = p.diff.as<int>();
@@ -645,7 +649,7 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.gamma = p.gamma;
   b.score = p.score_out;
   b.mark = p.mark ? 1 : 0;
-  L.slot_cap = p.slot_cap;
+  L.wsum_len = p.rn;
   L.diff_bytes = p.diff_ints * 4;
   L.sort_scratch = p.scratch.p;
   L.footprint = p.footprint;
@@ -1108,8 +1112,8 @@ int fdgs_build_keyframe_masks(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
       for (int i = 0; i < n; ++i)
         p.h_reqs[i].mark_row =
             i0 + i < total ? rows + (size_t)((i0 + i) / n_cam) * words : nullptr;
-      TRY(grow(p.wsum, p.slot_cap * 4));
-      TRY(grow(p.stop, p.slot_cap * 4));
+      TRY(grow(p.wsum, std::max<uint64_t>(p.rn, 1) * 4));
+      TRY(grow(p.stop, std::max<uint64_t>(p.rn, 1) * 4));
       p.weighted = true;
       p.mark = true;
       const int rc = plan_run(s, p, st);
@@ -1210,13 +1214,6 @@ int fdgs_batch_tile_lists(fdgs_scene *s, int req, uint32_t *tile_ranges_host,
   if (!tile_ids_host || n == 0) return FDGS_OK;
   if (ids_cap < n) return fail(FDGS_ERR_INVALID, "tile_ids buffer holds %llu of %llu ids",
                                 (unsigned long long)ids_cap, (unsigned long long)n);
-  uint32_t nv = 0, vis_base = 0, slot_base = 0;
-  CK(cudaMemcpy(&nv, p.nv.as<uint32_t>() + req, 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&vis_base, p.vis_base.as<uint32_t>() + req, 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&slot_base, p.slot_base.as<uint32_t>() + req, 4, cudaMemcpyDeviceToHost));
-  std::vector<uint64_t> keys(std::max<uint32_t>(nv, 1));
-  if (nv) CK(cudaMemcpy(keys.data(), p.vis_sorted + vis_base, (size_t)nv * 8,
-                        cudaMemcpyDeviceToHost));
   // the request's block lists, then each tile's list: its block's entries holding its bit
   const int gx = q.cam.gx;
   const int bgx = (gx + kListBlock - 1) / kListBlock, bgy = (q.cam.gy + kListBlock - 1) / kListBlock;
@@ -1225,15 +1222,16 @@ int fdgs_batch_tile_lists(fdgs_scene *s, int req, uint32_t *tile_ranges_host,
   CK(cudaMemcpy(br.data(), p.branges.as<uint2>() + q.block_base, nb * 8,
                 cudaMemcpyDeviceToHost));
   const uint32_t blo = br[0].x, bhi = br[nb - 1].y;
-  std::vector<uint32_t> slots(std::max<uint32_t>(bhi - blo, 1));
+  std::vector<uint32_t> ents(std::max<uint32_t>(bhi - blo, 1));
   std::vector<uint16_t> tms(std::max<uint32_t>(bhi - blo, 1));
   if (bhi > blo) {
-    CK(cudaMemcpy(slots.data(), p.lists.as<uint32_t>() + blo, (size_t)(bhi - blo) * 4,
+    CK(cudaMemcpy(ents.data(), p.lists.as<uint32_t>() + blo, (size_t)(bhi - blo) * 4,
                   cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(tms.data(), p.ltm.as<uint16_t>() + blo, (size_t)(bhi - blo) * 2,
                   cudaMemcpyDeviceToHost));
   }
-  const uint64_t id_mask = (1ull << kBatchIdBits) - 1;
+  // entries are record indices req x n + id
+  const uint64_t N = (uint64_t)p.d.n, rbase = (uint64_t)req * N;
   for (size_t t = 0; t < tiles; ++t) {
     const int tx = (int)(t % gx), ty = (int)(t / gx);
     const uint2 b2 = br[(ty / kListBlock) * bgx + tx / kListBlock];
@@ -1241,10 +1239,10 @@ int fdgs_batch_tile_lists(fdgs_scene *s, int req, uint32_t *tile_ranges_host,
     uint64_t o = rg[t].x - lo;
     for (uint32_t e = b2.x; e < b2.y; ++e) {
       if (!((tms[e - blo] >> bit) & 1u)) continue;
-      const uint32_t rank = slots[e - blo] - slot_base;
-      if (rank >= nv || o >= rg[t].y - lo)
+      const uint64_t ri = ents[e - blo];
+      if (ri < rbase || ri >= rbase + N || o >= rg[t].y - lo)
         return fail(FDGS_ERR_STATE, "block lists disagree with the tile counts");
-      tile_ids_host[o++] = (uint32_t)(keys[rank] & id_mask);
+      tile_ids_host[o++] = (uint32_t)(ri - rbase);
     }
     if (o != rg[t].y - lo) return fail(FDGS_ERR_STATE, "block lists disagree with the tile counts");
   }
@@ -1305,8 +1303,8 @@ int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, cons
       TRY(plan_prepare(s, bc.data(), n, false));
       BatchPlan &p = *s->plan;
       TRY(plan_fill(s, p, bc.data(), bt.data(), &o, outs.data()));
-      TRY(grow(p.wsum, p.slot_cap * 4));
-      TRY(grow(p.stop, p.slot_cap * 4));
+      TRY(grow(p.wsum, std::max<uint64_t>(p.rn, 1) * 4));
+      TRY(grow(p.stop, std::max<uint64_t>(p.rn, 1) * 4));
       p.weighted = true;
       p.score_out = score_out_dev;
       p.gamma = s->aux[1].as<float>();

@@ -109,11 +109,21 @@ __global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
             vis = true;
             float rgb[3];
             gauss_colour<kVQ>(q.cam, b.sh, b.sh_cb, b.sh_code, b.deg, b.n, i, g, rgb);
+            // the blend-ready record by (request, id), and the alpha-tight tile rectangle:
+            // the arithmetic of the per-frame record and gather, so records and lists equal
+            // those of fdgs_render
             const float idet = 1.f / g.det;
-            float4 *rp = reinterpret_cast<float4 *>(b.rec + ((size_t)r * b.n + i) * kRec);
-            rp[0] = make_float4(u, v, g.c11 * idet, -g.c01 * idet);
-            rp[1] = make_float4(g.c00 * idet, g.a, rgb[0], rgb[1]);
-            rp[2] = make_float4(rgb[2], g.xc[2], rad, (float)((x1 - x0) * (y1 - y0)));
+            const float A = g.c11 * idet, B = -g.c01 * idet, C = g.c00 * idet;
+            const float qa = -0.5f * kLog2e * A, qb = -kLog2e * B, qc = -0.5f * kLog2e * C;
+            const size_t ri = (size_t)r * b.n + i;
+            float4 *rp = reinterpret_cast<float4 *>(b.rec + ri * kRec);
+            rp[0] = make_float4(u, v, qa, qb);
+            rp[1] = make_float4(qc, log2f(g.a), rgb[0], rgb[1]);
+            rp[2] = make_float4(rgb[2], -qb / (2.f * qa), -qb / (2.f * qc), rad);
+            tighten_rect(u, v, A, B, C, g.a, x0, y0, x1, y1);
+            if (!(x1 > x0 && y1 > y0)) x0 = y0 = x1 = y1 = 0;
+            b.rect_id[ri] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16),
+                                       (uint32_t)y0 | ((uint32_t)y1 << 16));
             key = ((uint64_t)r << 57) | ((uint64_t)__float_as_uint(g.xc[2]) << kIdBits) |
                   (uint64_t)i;
           }
@@ -222,21 +232,16 @@ __global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
     uint32_t cnt = 0;
     int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     if (valid) {
+      // the slot's Gaussian and its tile rectangle (computed with its record)
       const uint64_t key = b.vis_sorted[b.vis_base[r] + l];
-      const uint32_t id = (uint32_t)(key & kIdMask);
-      const float4 *src = reinterpret_cast<const float4 *>(b.rec + ((size_t)r * b.n + id) * kRec);
-      float4 *dst = reinterpret_cast<float4 *>(b.rec_sorted + (size_t)s * kRecS);
-      const float4 a0 = src[0], a1 = src[1], a2 = src[2];
-      const float qa = -0.5f * kLog2e * a0.z, qb = -kLog2e * a0.w, qc = -0.5f * kLog2e * a1.x;
-      dst[0] = make_float4(a0.x, a0.y, qa, qb);
-      dst[1] = make_float4(qc, log2f(a1.y), a1.z, a1.w);
-      dst[2] = make_float4(a2.x, -qb / (2.f * qa), -qb / (2.f * qc), a2.z);
-      dst[3] = make_float4(a0.z, a0.w, a1.x, a1.y);
-      tile_rect(a0.x, a0.y, a2.z, q.cam.gx, q.cam.gy, x0, y0, x1, y1);
-      tighten_rect(a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, x0, y0, x1, y1);
-      if (!(x1 > x0 && y1 > y0)) x0 = y0 = x1 = y1 = 0;
-      b.rect[s] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16),
-                             (uint32_t)y0 | ((uint32_t)y1 << 16));
+      const uint32_t ri = r * b.n + (uint32_t)(key & kIdMask);
+      const uint2 rc = b.rect_id[ri];
+      b.rect[s] = rc;
+      b.ridx[s] = ri;
+      x0 = (int)(rc.x & 0xFFFFu);
+      x1 = (int)(rc.x >> 16);
+      y0 = (int)(rc.y & 0xFFFFu);
+      y1 = (int)(rc.y >> 16);
       if (x1 > x0 && y1 > y0) {
         cnt = (uint32_t)((x1 - x0) * (y1 - y0));
         int *diff = b.diff + q.diff_base;
@@ -372,8 +377,8 @@ __global__ void __launch_bounds__(kTS) k_tile_scan_batch(BatchDev b) {
 }
 
 // Block lists: one warp per block of kListBlock x kListBlock tiles writes, in rank order, the
-// slots of the Gaussians whose tile rectangles meet the block, each with the 16-bit mask of
-// the block's tiles the rectangle covers. The warp ANDs the block's row and column bitmasks
+// record indices (request x n + id) of the Gaussians whose tile rectangles meet the block,
+// each with the 16-bit mask of the block's tiles the rectangle covers. The warp ANDs the block's row and column bitmasks
 // 64 words at a time (two per lane, the next words in flight) and queues the entries found;
 // all lanes together then form the new entries' tile masks from their rectangles
 // (independent loads) and write the queue out with coalesced stores. A tile's list is the
@@ -428,6 +433,7 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
   const uint32_t lane = lane_id();
   uint32_t *qs = s_slot[warp];
   const uint2 *__restrict__ rect = b.rect;
+  const uint32_t *__restrict__ ridx = b.ridx;
   uint32_t *__restrict__ lists = b.lists;
   uint16_t *__restrict__ ltm = b.ltm;
   const uint32_t *__restrict__ masks = b.masks;
@@ -476,6 +482,7 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
         for (uint32_t e = lane; e < qn; e += 32) {
           const uint32_t slot = qs[e];
           const uint2 rc = __ldg(&rect[slot]);
+          const uint32_t ri = __ldg(&ridx[slot]);
           const int rx0 = max((int)(rc.x & 0xFFFFu) - bx0, 0);
           const int rx1 = min((int)(rc.x >> 16) - bx0, kListBlock);
           const int ry0 = max((int)(rc.y & 0xFFFFu) - by0, 0);
@@ -487,7 +494,7 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
             tm = (xm * 0x1111u) & ym;
           }
           if (out + e < brg.y) {                 // the block's range bounds every store
-            lists[out + e] = slot;
+            lists[out + e] = ri;
             ltm[out + e] = (uint16_t)tm;
           }
         }
@@ -539,7 +546,7 @@ __global__ void __launch_bounds__(256 / PX, PX == 4 ? 14 : (PX == 2 ? 7 : 4))
                    : make_uint2(0, 0);
     bt.tmask = b.ltm;
     bt.tbit = (bt.ty % kListBlock) * kListBlock + bt.tx % kListBlock;
-    bt.rec_sorted = b.rec_sorted;
+    bt.rec_sorted = b.rec;                       // blend-ready records by record index
     bt.rgb = q.rgb;
     bt.T_final = nullptr;
     bt.n_contrib = nullptr;
@@ -580,8 +587,8 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
   cudaMemsetAsync(b.done_ns, 0, b.nreq * sizeof(unsigned long long), st);
   if (b.evals) cudaMemsetAsync(b.evals, 0, 3 * sizeof(unsigned long long), st);
   if (b.w_sum) {
-    cudaMemsetAsync(b.w_sum, 0, L.slot_cap * sizeof(float), st);
-    cudaMemsetAsync(b.stop_mark, 0, L.slot_cap * sizeof(uint32_t), st);
+    cudaMemsetAsync(b.w_sum, 0, L.wsum_len * sizeof(float), st);
+    cudaMemsetAsync(b.stop_mark, 0, L.wsum_len * sizeof(uint32_t), st);
   }
   // stage boundaries: a one-thread kernel stamps %globaltimer (events recorded inside a
   // captured graph cannot be timed); stream order makes each difference a stage duration
@@ -637,8 +644,8 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
       per_sm = std::max(1, per_sm);
     }
     k_blend_persist<8, 4, false, true><<<per_sm * num_sms(), 64, 0, st>>>(b2);
-    if (b.score) launch_score_batch(b2, L.slot_cap, st);
-    if (b.mark) launch_mark_batch(b2, L.slot_cap, st);
+    if (b.score) launch_score_batch(b2, st);
+    if (b.mark) launch_mark_batch(b2, st);
   } else {
     with_blend_shape(L.footprint, [&](auto fw, auto px) {
       constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;

@@ -98,8 +98,8 @@ struct BlendTile {
 
 // kAux: also write the final transmittance and 1 + the list position of the last blended
 // entry per pixel (what the reverse replay of the backward starts from).
-// kBlk: keys[range] is the list of the tile's block of tiles, entries in rank order with a
-// mask of the block's tiles each covers; only entries with bit tbit are staged (the others
+// kBlk: keys[range] is the list of the tile's block of tiles, entries (indices of 12-float
+// records) in rank order with a mask of the block's tiles each covers; only entries with bit tbit are staged (the others
 // get log2 opacity -inf, so the tile test drops them), and the tile composites exactly its
 // own list.
 template <typename K, int FW, int PX, bool kWeights, bool kCount, bool kAux, bool kBlk = false>
@@ -147,7 +147,9 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     if (kBlk && i < n && kr == kNone) sm.g1[st][tid].y = -INFINITY;
     if (i < n && (!kBlk || kr != kNone)) {
       const uint32_t r = (uint32_t)(kr & (K)rmask);
-      const float *rp = bt.rec_sorted + (size_t)r * kRecS;
+      // block lists index the batch's 12-float records by (request, id); tile lists the
+      // per-frame 16-float records by depth rank
+      const float *rp = bt.rec_sorted + (size_t)r * (kBlk ? kRec : kRecS);
       cp_async16(&sm.g0[st][tid], rp);
       cp_async16(&sm.g1[st][tid], rp + 4);
       cp_async16(&sm.g2[st][tid], rp + 8);

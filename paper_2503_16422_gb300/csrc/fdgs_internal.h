@@ -168,12 +168,13 @@ struct BatchDev {
   int deg;
   uint32_t *ctr, *err;
   uint2 *part;                       // [nreq][partitions]: visible count, segment offset
-  float *rec;                        // [nreq][n][12] by Gaussian id
+  float *rec;                        // [nreq][n][12] blend-ready records by (request, id)
+  uint2 *rect_id;                    // [nreq][n] alpha-tight tile rectangles by (request, id)
+  uint32_t *ridx;                    // [slots] record index (request x n + id) of each slot
   uint64_t *vis_seg, *vis, *vis_alt; // visible keys: per-partition segments, contiguous, alt
   const uint64_t *vis_sorted;
   uint32_t *nv, *vis_base, *slot_base;
   unsigned long long *key_cnt;       // [nreq] list entries per request
-  float *rec_sorted;                 // [slots][16] blend-ready
   uint2 *rect;                       // [slots] tile rectangle: x0 | x1 << 16, y0 | y1 << 16
   int *diff;
   uint32_t *masks;
@@ -183,13 +184,14 @@ struct BatchDev {
   unsigned long long *bkey_cnt;      // [nreq] block-list entries per request
   uint64_t *qkeys, *qkeys_alt;
   const uint64_t *queue;
-  uint32_t *lists;                   // [key_cap] block lists: slot indices, rank order
+  uint32_t *lists;                   // [key_cap] block lists: record indices, rank order
   uint16_t *ltm;                     // [key_cap] block lists: the block's tiles each covers
   unsigned long long *done_ns, *t0_ns;
   unsigned long long *evals;         // [3] blend counters (see BlendTile), or null
-  // weighted passes (null for renders): per-slot blend weights and stop flags; the score
-  // pass adds them, with the Gaussians' volume factors gamma, into score (Eqs. 4-7); the
-  // mask pass marks the contributing Gaussians in each request's mark_row
+  // weighted passes (null for renders): blend weights and stop flags per record index
+  // [nreq][n]; the score pass adds them, with the Gaussians' volume factors gamma, into
+  // score (Eqs. 4-7); the mask pass marks the contributing Gaussians in each request's
+  // mark_row
   float *w_sum;
   uint32_t *stop_mark;
   const float *gamma;
@@ -203,7 +205,7 @@ struct BatchLaunch {
   int footprint;                     // launch shape of the blend (with_blend_shape)
   int blend_ctas_per_sm;             // persistent blend grid = this x SMs
   const uint64_t *vis_sorted;        // out: the buffer that holds the sorted depth keys
-  uint64_t slot_cap;                 // slots of the plan (score pass buffers)
+  uint64_t wsum_len;                 // entries of the weighted passes' buffers (nreq x n)
 };
 // Gaussian id bits at the bottom of the batched depth keys (request | depth | id).
 constexpr int kBatchIdBits = 25;
@@ -211,12 +213,12 @@ constexpr int kBatchIdBits = 25;
 // gather, tile_scan, lists, queue_sort, blend.
 constexpr int kBatchStages = 7;
 void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st);
-// Score pass of a batch: adds w_sum[slot] * f_i(t) * gamma_i to score[i] for every visible
-// slot of every request (after the weighted blend of the batch).
-void launch_score_batch(const BatchDev &b, uint64_t slot_cap, cudaStream_t st);
-// Mask pass of a batch: sets bit id of request r's mark_row for every visible Gaussian that
-// was blended somewhere (weight > 0) or stopped a pixel.
-void launch_mark_batch(const BatchDev &b, uint64_t slot_cap, cudaStream_t st);
+// Score pass of a batch: adds w_sum[r][i] * f_i(t_r) * gamma_i to score[i] for every request
+// r and Gaussian i (after the weighted blend of the batch).
+void launch_score_batch(const BatchDev &b, cudaStream_t st);
+// Mask pass of a batch: sets bit id of request r's mark_row for every Gaussian that was
+// blended somewhere in r (weight > 0) or stopped one of its pixels.
+void launch_mark_batch(const BatchDev &b, cudaStream_t st);
 int batch_blend_max_ctas_per_sm(int shape);
 
 int num_sms();

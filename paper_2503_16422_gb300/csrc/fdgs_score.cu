@@ -96,60 +96,31 @@ __global__ void k_score_accumulate(const uint64_t *__restrict__ sorted,
   }
 }
 
-// The batched score pass: slot s of request r (slot_base[r] <= s < slot_base[r] + nv[r]) holds
-// the visible Gaussian of depth rank s - slot_base[r]; its weight over the request's pixels
-// is added to the score with the request's f_i(t) (the requests of one batch may share
-// Gaussians, hence the atomics).
-constexpr int kMaxReqScore = 128;
-
-// Request and depth rank of slot s (slot_base ascending; false for a slot past nv).
-__device__ __forceinline__ bool slot_request(const BatchDev &b, const uint32_t *slot_base,
-                                             uint64_t s, int &r, uint32_t &l) {
-  int lo = 0, hi = b.nreq - 1;   // the last request whose first slot is <= s
-  while (lo < hi) {
-    const int m = (lo + hi + 1) >> 1;
-    if (slot_base[m] <= s) lo = m; else hi = m - 1;
-  }
-  r = lo;
-  l = (uint32_t)(s - slot_base[lo]);
-  return l < b.nv[lo];
-}
-
-__global__ void k_score_batch(BatchDev b, uint64_t slot_cap) {
-  __shared__ uint32_t s_slot_base[kMaxReqScore];
-  for (int r = threadIdx.x; r < b.nreq; r += blockDim.x) s_slot_base[r] = b.slot_base[r];
-  __syncthreads();
-  const uint64_t id_mask = (1ull << kBatchIdBits) - 1;
-  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < slot_cap;
-       s += (uint64_t)gridDim.x * blockDim.x) {
-    const float w = b.w_sum[s];
+// The batched score pass: the weight of Gaussian i over the pixels of request r sits at
+// record index r n + i; it is added to the score with the request's f_i(t) (the requests of
+// one batch share Gaussians, hence the atomics).
+__global__ void k_score_batch(BatchDev b) {
+  const uint64_t total = (uint64_t)b.nreq * b.n;
+  for (uint64_t ri = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; ri < total;
+       ri += (uint64_t)gridDim.x * blockDim.x) {
+    const float w = b.w_sum[ri];
     if (w == 0.f) continue;
-    int lo;
-    uint32_t l;
-    if (!slot_request(b, s_slot_base, s, lo, l)) continue;
-    const uint32_t id = (uint32_t)(b.vis_sorted[b.vis_base[lo] + l] & id_mask);
-    const float f = variation_factor(b.reqs[lo].t, b.mean4[id], b.ls4[id], b.ql[id], b.qr[id]);
+    const uint32_t r = (uint32_t)(ri / b.n), id = (uint32_t)(ri % b.n);
+    const float f = variation_factor(b.reqs[r].t, b.mean4[id], b.ls4[id], b.ql[id], b.qr[id]);
     atomicAdd(&b.score[id], w * f * b.gamma[id]);
   }
 }
 
 // The batched mask pass: the contributors of each request (blended at one pixel at least, or
 // stopped a pixel) set their bits in the request's key-frame row.
-__global__ void k_mark_batch(BatchDev b, uint64_t slot_cap) {
-  __shared__ uint32_t s_slot_base[kMaxReqScore];
-  for (int r = threadIdx.x; r < b.nreq; r += blockDim.x) s_slot_base[r] = b.slot_base[r];
-  __syncthreads();
-  const uint64_t id_mask = (1ull << kBatchIdBits) - 1;
-  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < slot_cap;
-       s += (uint64_t)gridDim.x * blockDim.x) {
-    if (!(b.w_sum[s] > 0.f) && !b.stop_mark[s]) continue;
-    int r;
-    uint32_t l;
-    if (!slot_request(b, s_slot_base, s, r, l)) continue;
+__global__ void k_mark_batch(BatchDev b) {
+  const uint64_t total = (uint64_t)b.nreq * b.n;
+  for (uint64_t ri = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; ri < total;
+       ri += (uint64_t)gridDim.x * blockDim.x) {
+    if (!(b.w_sum[ri] > 0.f) && !b.stop_mark[ri]) continue;
+    const uint32_t r = (uint32_t)(ri / b.n), id = (uint32_t)(ri % b.n);
     uint32_t *row = b.reqs[r].mark_row;
-    if (!row) continue;
-    const uint32_t id = (uint32_t)(b.vis_sorted[b.vis_base[r] + l] & id_mask);
-    atomicOr(&row[id >> 5], 1u << (id & 31));
+    if (row) atomicOr(&row[id >> 5], 1u << (id & 31));
   }
 }
 
@@ -216,12 +187,12 @@ void launch_gamma(const float4 *ls4, uint32_t n, const uint32_t *vsorted, uint32
   k_gamma<<<grid_for(n), kB, 0, st>>>(ls4, n, vsorted, k, gamma);
 }
 
-void launch_score_batch(const BatchDev &b, uint64_t slot_cap, cudaStream_t st) {
-  k_score_batch<<<grid_for(slot_cap), kB, 0, st>>>(b, slot_cap);
+void launch_score_batch(const BatchDev &b, cudaStream_t st) {
+  k_score_batch<<<grid_for((uint64_t)b.nreq * b.n), kB, 0, st>>>(b);
 }
 
-void launch_mark_batch(const BatchDev &b, uint64_t slot_cap, cudaStream_t st) {
-  k_mark_batch<<<grid_for(slot_cap), kB, 0, st>>>(b, slot_cap);
+void launch_mark_batch(const BatchDev &b, cudaStream_t st) {
+  k_mark_batch<<<grid_for((uint64_t)b.nreq * b.n), kB, 0, st>>>(b);
 }
 
 void launch_score_accumulate(const uint64_t *sorted, const uint32_t *nv_dev, uint32_t nv_cap,
