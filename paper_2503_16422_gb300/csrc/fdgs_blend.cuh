@@ -85,7 +85,8 @@ struct BlendTile {
   uint2 range;                 // [start, end) into keys
   const uint16_t *tmask;       // block lists: per entry, the block's tiles it covers
   int tbit;                    // block lists: this tile's bit in those masks
-  const float *rec_sorted;     // blend-ready records [rank][16]
+  const float *rec_sorted;     // blend-ready records: [rank][16] for tile lists, [record][12]
+                               // for block lists (kBlk)
   float *rgb;                  // [3][H][W]
   float *T_final;              // [H][W] (written when kAux)
   uint32_t *n_contrib;         // [H][W] (written when kAux)
