@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the comparison workloads")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default batch launch shape (for profiling runs)")
-    ap.add_argument("--only", choices=["backward", "score", "masks"],
+    ap.add_argument("--only", choices=["backward", "score", "masks", "unpruned"],
                     help="run one side workload alone and print its line (for profiling runs)")
     return ap.parse_args()
 
@@ -783,6 +783,24 @@ def run_only(args):
     if args.only == "masks":
         res["keyframe_masks_from_views"] = keyframe_mask_timing(sc, cams, times, flush, stream)
     sc.close()
+    if args.only == "unpruned":
+        # the 3M scene in batches of --batch frames (a small batch keeps a capture small)
+        big = scenes.unpruned_scene()
+        sc2 = fdgs.Scene.from_host(big)
+        sc2.set_active_mask(torch.as_tensor(scenes.keyframe_masks(big, kt)).cuda(), kt)
+        B = args.batch
+        outs = [torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device="cuda")
+                for _ in range(B)]
+        fr = [frame_list(B, (7 + 2 * i) * B) for i in range(max(args.steps, 1))]
+        bargs = [([cams[k] for k in f], [float(times[k]) for k in f]) for f in fr]
+        sc2.render_batch(*bargs[0], outs=outs)
+        stages = []
+        ms, _ = timed_batches(sc2, [a for a, _ in bargs], [b_ for _, b_ in bargs],
+                              [outs] * len(bargs), True, flush, stream, stages)
+        res["unpruned_masked_batched"] = dict(
+            fps=B / (statistics.median(ms) / 1e3), batch=B, n_gaussians=big.n,
+            stage_ms={k: statistics.median([x[k] for x in stages]) for k in stages[0]})
+        sc2.close()
     if args.only == "score":
         res["variation_score"] = score_timing(stream)
     print(json.dumps({"only": args.only, "impl": "ours", "data": "synthetic", **res}))
