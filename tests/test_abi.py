@@ -67,3 +67,23 @@ def test_invalid_arguments_fail_without_a_gpu(libpath):
     assert lib.fdgs_render(None, None, 0.0, None, None, None, None) == -1
     assert lib.fdgs_destroy_scene(None) == 0
     assert lib.fdgs_frame_release(None) == 0
+
+
+def test_batch_marshalling_matches_the_c_structs():
+    """The binding marshals a batch's cameras, times and output pointers through numpy; the
+    bytes must be exactly those of the ctypes fdgs_camera array the header describes."""
+    import numpy as np
+
+    from paper_2503_16422_gb300 import fdgs, scenes
+    cams = [scenes.arc_camera(th, w, h) for th, w, h in ((-9.5, 1352, 1014), (0.0, 33, 17),
+                                                         (7.25, 512, 512))]
+    arr, ptr = fdgs.make_cameras(cams)
+    ref = (fdgs.fdgs_camera * len(cams))(*[fdgs.make_camera(c) for c in cams])
+    assert arr.tobytes() == bytes(ref)
+    assert ctypes.addressof(ptr.contents) == arr.ctypes.data
+    ts = [0.0, 0.5, 1.0]
+    ta, tp = fdgs._times(ts)
+    assert ta.dtype == np.float32 and list(ta) == ts
+    assert ctypes.addressof(tp.contents) == ta.ctypes.data
+    empty, _ = fdgs.make_cameras([])
+    assert empty.shape == (1,)
