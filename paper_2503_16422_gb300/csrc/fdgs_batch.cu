@@ -556,7 +556,11 @@ __global__ void __launch_bounds__(256 / PX, PX == 4 ? 14 : (PX == 2 ? 7 : 4))
     bt.w_sum = kWeights ? b.w_sum : nullptr;
     bt.stop_mark = kWeights ? b.stop_mark : nullptr;
     bt.evals = b.evals;
-    blend_tile<uint32_t, FW, PX, kWeights, kCount, false, true>(bt, b.lists, 0xFFFFFFFFu, sm);
+    if (!kWeights && !kCount && q.bg[0] == 0.f && q.bg[1] == 0.f && q.bg[2] == 0.f)
+      blend_tile<uint32_t, FW, PX, false, false, false, true, true>(bt, b.lists, 0xFFFFFFFFu,
+                                                                    sm);
+    else
+      blend_tile<uint32_t, FW, PX, kWeights, kCount, false, true>(bt, b.lists, 0xFFFFFFFFu, sm);
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(&b.done_ns[r], (unsigned long long)global_timer_ns());
   }

@@ -103,7 +103,12 @@ struct BlendTile {
 // records) in rank order with a mask of the block's tiles each covers; only entries with bit tbit are staged (the others
 // get log2 opacity -inf, so the tile test drops them), and the tile composites exactly its
 // own list.
-template <typename K, int FW, int PX, bool kWeights, bool kCount, bool kAux, bool kBlk = false>
+// kTz (black background, no weights, counts or side outputs): a pixel that has stopped is
+// marked by T = 0 instead of a flag. Every later entry then gives alpha T = 0, so its colour
+// sums stay bit-for-bit the same, and the final C + T bg equals the flag form's C + T_stop bg
+// for bg = 0; the loop keeps no per-pixel flags.
+template <typename K, int FW, int PX, bool kWeights, bool kCount, bool kAux, bool kBlk = false,
+          bool kTz = false>
 __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restrict__ keys,
                                            uint32_t rmask, BlendSmem<256 / PX> &sm) {
   constexpr int NT = 256 / PX;   // threads = records staged per batch
@@ -111,6 +116,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
   constexpr int HW = FW / PX;    // lanes per footprint row
   constexpr int WX = kTile / FW;
   static_assert(FW % PX == 0 && FW <= kTile && FH * (NT / 32) == kTile * WX, "shape");
+  static_assert(!kTz || (!kWeights && !kCount && !kAux), "kTz: plain colour blend only");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int fx0 = bt.tx * kTile + (warp % WX) * FW, fy0 = bt.ty * kTile + (warp / WX) * FH;
   const int px0 = fx0 + lane % HW, py = fy0 + lane / HW;
@@ -130,6 +136,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     C0[p] = C1[p] = C2[p] = 0.f;
     last[p] = 0;
     done[p] = !(px0 + p * HW < bt.W && py < bt.H);
+    if (kTz) T[p] = done[p] ? 0.f : 1.f;
     lane_done = lane_done && done[p];
   }
   uint32_t nevals = 0, ntests = 0, npass = 0;
@@ -237,6 +244,20 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
           const float dx = __fsub_rn(h0.x, (float)(px0 + p * HW));
           const float q = __fmaf_rn(dx, __fmaf_rn(h0.z, dx, b2dy), c2dy2);
           const float e = __fadd_rn(q, h1.y);
+          if constexpr (kTz) {
+            const bool valid = q <= 0.f && e >= kLog2AlphaMin;
+            const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
+            const float wa = alpha * T[p];
+            const float nT = T[p] - wa;
+            // a stopped pixel (T = 0) stops again at every entry and blends nothing
+            const bool stop = nT < kTStop;
+            const float wi = stop ? 0.f : wa;
+            C0[p] = fmaf(h1.z, wi, C0[p]);
+            C1[p] = fmaf(h1.w, wi, C1[p]);
+            C2[p] = fmaf(h2.x, wi, C2[p]);
+            T[p] = stop ? 0.f : nT;
+            continue;
+          }
           const bool valid = !done[p] && q <= 0.f && e >= kLog2AlphaMin;
           if (kCount && !done[p]) ++nevals;
           if (kCount && valid) ++npass;
@@ -269,7 +290,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
       __syncwarp();                    // the list is rewritten by the next round
       lane_done = true;
 #pragma unroll
-      for (int p = 0; p < PX; ++p) lane_done = lane_done && done[p];
+      for (int p = 0; p < PX; ++p) lane_done = lane_done && (kTz ? T[p] == 0.f : done[p]);
       warp_done = __all_sync(0xffffffffu, lane_done);
     }
     if (__syncthreads_and(warp_done)) {
