@@ -829,9 +829,10 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / fps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
-                "config": workload_config(scene, kt, 1), "impl": "reference",
+                "config": workload_config(scene, kt, args.batch), "impl": "reference",
                 "cpu_baseline": {"value": fps, "unit": "FPS", "cores": cores, "kind": "oracle",
-                                 "sample": "per step: " + desc},
+                                 "sample": "per step: one frame of the batched workload, "
+                                           + desc},
                 "e2e": {"value": fps, "unit": "FPS", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
