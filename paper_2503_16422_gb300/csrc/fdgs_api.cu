@@ -85,6 +85,7 @@ struct Workspace {
   Buf flags;                     // u8[n]
   Buf keys[2];                   // packed (tile, rank) keys, ping-pong
   Buf ranges;                    // uint2[tiles]
+  Buf order;                     // u32[tiles] blend launch order (longest list first)
   Buf Tf, nc;                    // f32 / u32 [pixels]
   Buf scratch;                   // sort scratch
   Buf g2d;                       // f32[n][9] backward accumulators
@@ -94,7 +95,7 @@ struct Workspace {
   Buf rowmask, colmask;          // u32 coverage bitmasks by depth rank per tile row / column
   ~Workspace() {
     Buf *all[] = {&ctr, &pre_status, &scan_status, &rec, &rec_sorted, &vis[0], &vis[1],
-                  &offsets, &flags, &keys[0], &keys[1], &ranges, &Tf, &nc, &scratch, &g2d,
+                  &offsets, &flags, &keys[0], &keys[1], &ranges, &order, &Tf, &nc, &scratch, &g2d,
                   &wsum, &stopmark, &diff, &rowmask, &colmask};
     for (Buf *b : all) b->release();
     if (hctr) cudaFreeHost(hctr);
@@ -309,6 +310,7 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   TRY(grow(ws.offsets, n1 * 4));
   if (want_flags) TRY(grow(ws.flags, n1));
   TRY(grow(ws.ranges, tiles * 8));
+  TRY(grow(ws.order, tiles * 4));
   TRY(grow(ws.Tf, pixels * 4));
   TRY(grow(ws.nc, pixels * 4));
   TRY(grow(ws.scratch, sort_scratch_bytes(n1, 32)));
@@ -413,6 +415,8 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   // tile ranges and the tile sort's digit offsets, straight from the coverage counts
   launch_tile_scan(ws.diff.as<int>(), gx, gy, use_masks ? 0 : sort_passes(tb),
                    sort_digit_bits(tb), ws.ranges.as<uint2>(), sort_hist(ws.scratch.p), st);
+  launch_tile_order(ws.ranges.as<uint2>(), gx * gy, ws.order.as<uint32_t>(), st);
+  ba.order = ws.order.as<uint32_t>();
   if (prof) CK(cudaEventRecord(s->ev[5], st));
   void *skeys;
   if (use_masks) {

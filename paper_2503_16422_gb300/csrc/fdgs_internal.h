@@ -77,7 +77,11 @@ struct BlendArgs {
   float *w_sum;        // optional [nv] per-rank blend-weight sums (score pass)
   uint32_t *stop_mark; // with w_sum: [nv] per-rank flag, set where the entry stopped a pixel
   unsigned long long *evals;  // optional evaluation counters [3] (profiling)
+  const uint32_t *order = nullptr;  // optional [tiles] launch order (longest list first)
 };
+// Tile ids ordered by descending list length (buckets of 16 entries; order within a bucket
+// is unspecified): the one-CTA-per-tile blend then starts its longest tiles first.
+void launch_tile_order(const uint2 *ranges, int tiles, uint32_t *order, cudaStream_t st);
 template <typename K>
 void launch_blend(const BlendArgs &a, const K *keys, uint32_t rmask, cudaStream_t st);
 
