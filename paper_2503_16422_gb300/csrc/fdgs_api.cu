@@ -943,6 +943,7 @@ int fdgs_render_backward(fdgs_scene *s, fdgs_frame *f, const float *dL_drgb_dev,
   ba.T_final = ws.Tf.as<float>();
   ba.n_contrib = ws.nc.as<uint32_t>();
   ba.g2d = ws.g2d.as<float>();
+  ba.order = ws.order.as<uint32_t>();   // the forward's longest-first tile order
   const uint32_t rmask = (uint32_t)((1ull << m.rb) - 1);
   if (m.key64)
     launch_blend_bwd<uint64_t>(ba, (const uint64_t *)m.keys, rmask, st);

@@ -64,9 +64,10 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int &fi)
 // Reverse replay of each tile list from the largest n_contrib down to 0, with the
 // warp-footprint culling of the forward (a culled Gaussian was skipped by every pixel of the
 // footprint). Transmittance is recovered as T_i = T_{i+1} / (1 - alpha_i). A CTA of 256 / PX
-// threads replays one tile; each lane owns PX pixels of one footprint row, FW / PX apart, and
-// sums their gradient terms before the warp reduction. As in the forward, the evaluation has
-// no branches: an entry a pixel did not blend takes alpha = 0 and leaves its state unchanged.
+// threads replays one tile (tiles in the forward's longest-first order when it is given); each
+// lane owns PX pixels of one footprint row, FW / PX apart, and sums their gradient terms
+// before the warp reduction. As in the forward, the evaluation has no branches: an entry a
+// pixel did not blend takes alpha = 0 and leaves its state unchanged.
 template <typename K, int FW, int PX>
 __global__ void __launch_bounds__(256 / PX)
 k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
@@ -85,7 +86,7 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
   __shared__ __align__(16) float4 h0[NW][32], h1[NW][32], h3[NW][32];
   __shared__ float2 h2[NW][32];               // b, entry index within the batch
   __shared__ uint32_t s_max;
-  const int tile = blockIdx.x;
+  const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
   const int tx = tile % a.gx, ty = tile / a.gx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int fx0 = tx * kTile + (warp % WX) * FW, fy0 = ty * kTile + (warp / WX) * FH;

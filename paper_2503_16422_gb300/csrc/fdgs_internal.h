@@ -94,6 +94,7 @@ struct BlendBwdArgs {
   const float *T_final;
   const uint32_t *n_contrib;
   float *g2d;          // [nv][9] per rank: u, v, A, B, C, a, r, g, b
+  const uint32_t *order = nullptr;  // optional [tiles] launch order (the forward's)
 };
 template <typename K>
 void launch_blend_bwd(const BlendBwdArgs &a, const K *keys, uint32_t rmask, cudaStream_t st);
