@@ -414,8 +414,8 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   if (prof) CK(cudaEventRecord(s->ev[4], st));   // ev[3] -> ev[4]: the host synchronisation
   // tile ranges and the tile sort's digit offsets, straight from the coverage counts
   launch_tile_scan(ws.diff.as<int>(), gx, gy, use_masks ? 0 : sort_passes(tb),
-                   sort_digit_bits(tb), ws.ranges.as<uint2>(), sort_hist(ws.scratch.p), st);
-  launch_tile_order(ws.ranges.as<uint2>(), gx * gy, ws.order.as<uint32_t>(), st);
+                   sort_digit_bits(tb), ws.ranges.as<uint2>(), sort_hist(ws.scratch.p),
+                   ws.order.as<uint32_t>(), st);
   ba.order = ws.order.as<uint32_t>();
   if (prof) CK(cudaEventRecord(s->ev[5], st));
   void *skeys;

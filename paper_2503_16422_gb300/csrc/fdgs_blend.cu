@@ -226,49 +226,7 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
   }
 }
 
-// Counting sort of the tiles by descending list length, one CTA: a histogram of length
-// buckets, an exclusive scan of the buckets (two a thread), then each tile takes a slot of
-// its bucket.
-constexpr int kOrderThreads = 1024;
-constexpr int kOrderBuckets = 2 * kOrderThreads;
-
-__device__ __forceinline__ uint32_t order_bucket(uint2 r) {
-  const uint32_t len = r.y - r.x;
-  return (uint32_t)(kOrderBuckets - 1) - min(len >> 4, (uint32_t)(kOrderBuckets - 1));
-}
-
-__global__ void __launch_bounds__(kOrderThreads)
-k_tile_order(const uint2 *__restrict__ ranges, int tiles, uint32_t *__restrict__ order) {
-  __shared__ uint32_t hist[kOrderBuckets];
-  __shared__ uint32_t wsum[kOrderThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  hist[2 * tid] = 0;
-  hist[2 * tid + 1] = 0;
-  __syncthreads();
-  for (int t = tid; t < tiles; t += kOrderThreads) atomicAdd(&hist[order_bucket(ranges[t])], 1u);
-  __syncthreads();
-  const uint32_t h0 = hist[2 * tid], h1 = hist[2 * tid + 1];
-  const uint32_t inc = warp_incl_scan(h0 + h1);
-  if (lane == 31) wsum[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t v = wsum[lane];
-    wsum[lane] = warp_incl_scan(v) - v;
-  }
-  __syncthreads();
-  const uint32_t ex = wsum[warp] + inc - (h0 + h1);
-  hist[2 * tid] = ex;
-  hist[2 * tid + 1] = ex + h0;
-  __syncthreads();
-  for (int t = tid; t < tiles; t += kOrderThreads)
-    order[atomicAdd(&hist[order_bucket(ranges[t])], 1u)] = (uint32_t)t;
-}
-
 }  // namespace
-
-void launch_tile_order(const uint2 *ranges, int tiles, uint32_t *order, cudaStream_t st) {
-  if (tiles > 0) k_tile_order<<<1, kOrderThreads, 0, st>>>(ranges, tiles, order);
-}
 
 int g_blend_shape = 3;   // launch shape of the forward blend (see with_blend_shape)
 

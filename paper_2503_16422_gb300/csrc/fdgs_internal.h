@@ -59,8 +59,11 @@ void launch_tile_lists(const uint32_t *rowmask, const uint32_t *colmask, uint32_
 // Tile-list builder: 0 auto (cost model), 1 emit + radix sort, 2 coverage bitmasks.
 extern int g_list_mode;
 // Integrates diff into per-tile counts; writes tile ranges and the tile sort's digit offsets.
+// order (optional): tile ids by descending list length, in buckets of 16 entries (order
+// within a bucket unspecified), so that the one-CTA-per-tile blend starts its longest tiles
+// first.
 void launch_tile_scan(int *diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
-                      uint32_t *hist, cudaStream_t st);
+                      uint32_t *hist, uint32_t *order, cudaStream_t st);
 
 template <typename K>
 void launch_emit(const float *rec_sorted, const uint32_t *offsets, uint32_t nv, int gx, int gy,
@@ -79,9 +82,6 @@ struct BlendArgs {
   unsigned long long *evals;  // optional evaluation counters [3] (profiling)
   const uint32_t *order = nullptr;  // optional [tiles] launch order (longest list first)
 };
-// Tile ids ordered by descending list length (buckets of 16 entries; order within a bucket
-// is unspecified): the one-CTA-per-tile blend then starts its longest tiles first.
-void launch_tile_order(const uint2 *ranges, int tiles, uint32_t *order, cudaStream_t st);
 template <typename K>
 void launch_blend(const BlendArgs &a, const K *keys, uint32_t rmask, cudaStream_t st);
 

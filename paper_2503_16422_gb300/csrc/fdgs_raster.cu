@@ -208,15 +208,23 @@ k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ 
 // One CTA; diff is [gy + 1][gx + 1] and is integrated in place.
 // ---------------------------------------------------------------------------------------
 constexpr int kScanBlock = 1024;
+// Length buckets of the blend's longest-first tile order: 16 list entries each, two per
+// scan thread; lists of 32752 entries or more share the first bucket.
+constexpr int kOrderBuckets = 2 * kScanBlock;
+__device__ __forceinline__ uint32_t order_bucket(uint32_t len) {
+  return (uint32_t)(kOrderBuckets - 1) - min(len >> 4, (uint32_t)(kOrderBuckets - 1));
+}
 __global__ void __launch_bounds__(kScanBlock)
 k_tile_scan(int *__restrict__ diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
-            uint32_t *__restrict__ hist) {
+            uint32_t *__restrict__ hist, uint32_t *__restrict__ order) {
   __shared__ uint32_t s_hist[4 * 256];
+  __shared__ uint32_t s_ord[kOrderBuckets];
   __shared__ uint32_t s_wsum[kScanBlock / 32];
   __shared__ uint32_t s_carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int W1 = gx + 1;
   for (int i = tid; i < 4 * 256; i += kScanBlock) s_hist[i] = 0;
+  for (int i = tid; i < kOrderBuckets; i += kScanBlock) s_ord[i] = 0;
   // rows: prefix along x (one warp per row)
   for (int y = warp; y < gy; y += kScanBlock / 32) {
     int carry = 0;
@@ -259,6 +267,7 @@ k_tile_scan(int *__restrict__ diff, int gx, int gy, int npass, int dbits, uint2 
     const uint32_t start = s_carry + s_wsum[warp] + inc - c;
     if (t < tiles) {
       ranges[t] = make_uint2(start, start + c);
+      if (order) atomicAdd(&s_ord[order_bucket(c)], 1u);
       for (int p = 0; p < npass; ++p)
         if (c) atomicAdd(&s_hist[p * 256 + ((t >> (p * dbits)) & mask)], c);
     }
@@ -281,6 +290,27 @@ k_tile_scan(int *__restrict__ diff, int gx, int gy, int npass, int dbits, uint2 
       hist[p * 256 + tid] = wo + inc - v;
     }
     __syncthreads();
+  }
+  if (order) {
+    // longest lists first: exclusive scan of the length buckets (two a thread), then every
+    // tile takes a slot of its bucket (the ranges written above are visible to the block)
+    const uint32_t h0 = s_ord[2 * tid], h1 = s_ord[2 * tid + 1];
+    const uint32_t inc = warp_incl_scan(h0 + h1);
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = s_wsum[lane];
+      s_wsum[lane] = warp_incl_scan(w) - w;
+    }
+    __syncthreads();
+    const uint32_t ex = s_wsum[warp] + inc - (h0 + h1);
+    s_ord[2 * tid] = ex;
+    s_ord[2 * tid + 1] = ex + h0;
+    __syncthreads();
+    for (uint32_t t = tid; t < tiles; t += kScanBlock) {
+      const uint2 rg = ranges[t];
+      order[atomicAdd(&s_ord[order_bucket(rg.y - rg.x)], 1u)] = t;
+    }
   }
 }
 
@@ -453,8 +483,8 @@ void launch_gather_scan(const uint64_t *sorted, const uint32_t *ctr_nvis, uint32
 }
 
 void launch_tile_scan(int *diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
-                      uint32_t *hist, cudaStream_t st) {
-  k_tile_scan<<<1, kScanBlock, 0, st>>>(diff, gx, gy, npass, dbits, ranges, hist);
+                      uint32_t *hist, uint32_t *order, cudaStream_t st) {
+  k_tile_scan<<<1, kScanBlock, 0, st>>>(diff, gx, gy, npass, dbits, ranges, hist, order);
 }
 
 void launch_tile_lists(const uint32_t *rowmask, const uint32_t *colmask, uint32_t mask_words,
