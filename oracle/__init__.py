@@ -11,14 +11,19 @@ Parity status per function (what pins each one is in tests/test_oracle_pins.py):
                                             independent Hamilton-product construction)
   condition_on_time (Eq. 1, Eq. 3) ........ pinned (Schur complement of the precision
                                             matrix, density maximisation, finite differences)
-  sh_basis ................................ pinned (scipy complex spherical harmonics)
+  sh_basis ................................ pinned (scipy complex spherical harmonics,
+                                            closed-form degree-1 colours of known view
+                                            directions)
   preprocess / tile_lists / blend_tile .... pinned (NumPy brute-force renderer, single- and
                                             two-Gaussian closed forms, zero space-time
                                             correlation reducing to a static 3D splat,
-                                            tile-rectangle brute force)
+                                            tile-rectangle brute force, a hand-built
+                                            indefinite conic for the power > 0 skip)
   gradients ............................... pinned (float64 central finite differences)
   variation_scores, keep_set .............. pinned (weight identity, factor range, gamma
                                             range, permutation invariance, R1 = R2 at one t)
+tests/test_oracle_mutations.py plants plausible mistakes in these functions and checks that
+the pins catch each one.
 No values printed in the paper can pin any of them: the paper gives no worked example, so
 agreement with the paper's own numbers is "parity unpinned" for every function.
 """

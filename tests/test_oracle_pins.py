@@ -59,6 +59,10 @@ def test_covariance_eigen_structure():
     for i in range(16):
         ev = np.sort(np.linalg.eigvalsh(cov[i]))
         assert np.allclose(ev, np.sort(np.exp(2 * ls[i])), rtol=1e-10)
+        # each column of R (built here from Hamilton products) is an axis with its own scale
+        R = brute.rotation_by_products(ql[i], qr[i])
+        for k in range(4):
+            assert np.allclose(cov[i] @ R[:, k], np.exp(2 * ls[i, k]) * R[:, k], atol=1e-12)
 
 
 # ---- Eq. 1 / Eq. 3: conditional 3D Gaussian and temporal marginal ------------------------
@@ -246,6 +250,49 @@ def test_single_gaussian_closed_form():
     assert np.abs(out["image"].numpy() - want).max() < 1e-12
     assert np.abs(out["T_final"].numpy() - (1 - alpha)).max() < 1e-12
     assert col[2] == 0.0                                   # the SH clamp at zero is exercised
+
+
+def test_positive_power_is_skipped():
+    """Eq. 2 reading: an entry whose exponent is positive is skipped. An indefinite conic
+    (A > 0, C < 0), built by hand, makes the exponent -0.25 one pixel along x and +0.25 one
+    pixel along y: the first pixel blends the closed-form alpha, the second keeps T = 1."""
+    pre = {"mean2d": torch.tensor([[0.0, 0.0]], dtype=F64),
+           "conic": torch.tensor([[0.5, 0.0, -0.5]], dtype=F64),
+           "a": torch.tensor([0.5], dtype=F64),
+           "rgb": torch.tensor([[1.0, 0.5, 0.25]], dtype=F64)}
+    px = torch.tensor([1.0, 0.0], dtype=F64)
+    py = torch.tensor([0.0, 1.0], dtype=F64)
+    colour, T, last, _ = oracle.blend_tile(pre, [0], px, py)
+    alpha = 0.5 * math.exp(-0.25)
+    assert abs(float(T[0]) - (1.0 - alpha)) < 1e-15
+    assert np.allclose(colour[0].numpy(), alpha * np.array([1.0, 0.5, 0.25]), atol=1e-15)
+    assert int(last[0]) == 1
+    assert float(T[1]) == 1.0 and float(colour[1].abs().max()) == 0.0 and int(last[1]) == 0
+
+
+def test_degree1_colour_follows_the_view_direction():
+    """Colour reading: c = max(0, sum_k Y_k(d) f_k + 0.5) with d the unit vector from the
+    camera centre to the conditional mean. With only a degree-1 coefficient set, the textbook
+    real SH give Y_1^0 = sqrt(3 / 4 pi) d_z and Y_1^1 = sqrt(3 / 4 pi) d_x."""
+    cam = scenes.look_at_camera((0.0, 0.0, 4.0), 32, 32)
+    means = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]])
+    n = len(means)
+    mean4 = np.concatenate([means, np.full((n, 1), 0.5)], 1)
+    ls = np.tile([math.log(0.2)] * 3 + [math.log(0.3)], (n, 1))
+    ident = np.tile([1.0, 0, 0, 0], (n, 1))
+    sh = np.zeros((4, 3, n))
+    sh[2, :, 0] = [0.3, -0.2, 0.1]           # Y_1^0 (z) on the first Gaussian
+    sh[3, :, 1] = [0.4, 0.0, -0.4]           # Y_1^1 (x) on the second
+    sc = _scene64(mean4, ls, ident, ident, np.zeros(n), sh, 1)
+    pre = oracle.preprocess(oracle.Params.from_scene(sc), cam, 0.5)
+    c1 = math.sqrt(3.0 / (4.0 * math.pi))
+    d0 = np.array([0.0, 0.0, -1.0])          # camera at (0, 0, 4) looking at the origin
+    d1 = (means[1] - np.array([0.0, 0.0, 4.0])) / np.linalg.norm(means[1] - [0.0, 0.0, 4.0])
+    want0 = c1 * d0[2] * np.array([0.3, -0.2, 0.1]) + 0.5
+    want1 = c1 * d1[0] * np.array([0.4, 0.0, -0.4]) + 0.5
+    rgb = pre["rgb"].detach().numpy()
+    assert np.abs(rgb[0] - want0).max() < 1e-12
+    assert np.abs(rgb[1] - want1).max() < 1e-12
 
 
 def test_two_gaussians_and_the_stop_rule():
