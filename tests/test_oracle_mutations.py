@@ -11,11 +11,13 @@ import textwrap
 
 import pytest
 
+import importlib
+
 import oracle
 import oracle.fdgs_oracle as fo
-import test_oracle_pins as pins
 
-# (oracle function, text in its source, replacement, pins that must catch it)
+# (oracle function, text in its source, replacement, pins that must catch it: a function of
+# test_oracle_pins, or "module::function" for the pins kept beside another part)
 MUTATIONS = {
     "conditional mean sign (Eq. 1)": (
         "condition_on_time",
@@ -112,6 +114,26 @@ MUTATIONS = {
         "return ids[np.lexsort((ids, depth))]",
         "return ids[np.lexsort((ids, -depth))]",
         ["test_tile_lists_match_brute_force_coverage"]),
+    "p'' with the wrong sign on 1 / Sigma_t (Eq. 5)": (
+        "temporal_second_derivative",
+        "return (dt * dt / (s_tt * s_tt) - 1.0 / s_tt) * p",
+        "return (dt * dt / (s_tt * s_tt) + 1.0 / s_tt) * p",
+        ["test_temporal_marginal_and_second_derivative_by_finite_differences"]),
+    "volume percentile one rank low": (
+        "volume_gamma",
+        "p90 = srt[k - 1]",
+        "p90 = srt[k - 2]",
+        ["test_volume_gamma_range_and_percentile"]),
+    "visibility mask without the entries that stop a pixel (Sec. 4.2.2 reading)": (
+        "contributing",
+        "mark[tl[s_[s_ < len(tl)]]] = True",
+        "pass",
+        ["test_oracle_masks::test_a_gaussian_that_only_stops_pixels_is_marked"]),
+    "alpha-tight box without the float32 widening": (
+        "tight_tile_rect",
+        "Q = 2.0 * torch.log(255.0 * a) * 1.001 + 0.1",
+        "Q = 2.0 * torch.log(255.0 * a) * 0.9",
+        ["test_oracle_tight::test_tight_sets_keep_every_pixel_that_can_take_alpha"]),
     "keep-set ties broken by descending id": (
         "keep_set",
         "order = np.lexsort((np.arange(n), s))",
@@ -137,5 +159,6 @@ def test_pin_catches_planted_mistake(label, monkeypatch):
     if hasattr(oracle, name):
         monkeypatch.setattr(oracle, name, mutant)
     for pin in catchers:
+        mod, _, fn = pin.rpartition("::")
         with pytest.raises(AssertionError):
-            getattr(pins, pin)()
+            getattr(importlib.import_module(mod or "test_oracle_pins"), fn)()
