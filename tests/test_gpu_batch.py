@@ -190,3 +190,41 @@ def test_large_scene_batch_matches_sequential(fd):
     for i in range(len(cams)):
         assert torch.equal(outs[i], sc.render(cams[i], ts[i], use_mask=True)), i
     sc.close()
+
+
+@pytest.mark.slow
+def test_bench_batch_configuration_matches_oracle_on_sampled_tiles(fd):
+    """The configuration the benchmark times: the pruned 200k scene with the key-frame masks,
+    one batch of 64 frames of the 300-frame sequence at 1352x1014 (its stride-7 walk), the
+    autotuned launch shape, graph replay. The FP64 oracle renders sampled tiles (corners, the
+    centre, random) of three of the 64 frames."""
+    import oracle
+    import parity
+    s = scenes.pruned_scene()
+    kt = scenes.keyframe_times()
+    masks = scenes.keyframe_masks(s, kt)
+    sc = fd.Scene.from_host(s)
+    sc.set_active_mask(torch.as_tensor(masks).cuda(), kt)
+    ts = scenes.frame_times()
+    frames = [(7 * i) % 300 for i in range(64)]
+    cams = [scenes.arc_camera(scenes.frame_theta(k), 1352, 1014) for k in frames]
+    tt = [float(ts[k]) for k in frames]
+    outs = [torch.empty((3, 1014, 1352), dtype=torch.float32, device="cuda") for _ in frames]
+    sc.batch_autotune(cams, tt, outs=outs)
+    for o in outs:
+        o.fill_(float("nan"))
+    sc.render_batch(cams, tt, outs=outs)          # replay of the tuned graph
+    torch.cuda.synchronize()
+    P = oracle.Params.from_scene(s)
+    rng = np.random.default_rng(5)
+    for i in (0, 31, 63):
+        active = oracle.active_from_masks(masks, kt, tt[i], s.n)
+        pre = oracle.preprocess(P, cams[i], tt[i], active)
+        gx, gy = pre["grid"]
+        tiles = sorted(set([0, gx - 1, gx * gy - 1, (gy // 2) * gx + gx // 2] +
+                           rng.choice(gx * gy, 3, replace=False).tolist()))
+        ref = oracle.render(P, cams[i], tt[i], active, tiles=tiles, pre=pre)
+        im = parity.image_metrics(outs[i].cpu().numpy(), ref["image"].numpy())
+        assert im["n"] >= 3 * 48 * len(tiles)     # every sampled tile has at least 8x6 pixels
+        assert im["frac_bad"] <= 1e-4 and im["psnr"] >= 60.0, (frames[i], im)
+    sc.close()
