@@ -6,12 +6,11 @@ of the case, and checks that the pin named for that part of the method now fails
 mistake is planted in the oracle's own source text, so each case is the oracle with exactly
 one edit. Nothing here touches the GPU path.
 """
+import importlib
 import inspect
 import textwrap
 
 import pytest
-
-import importlib
 
 import oracle
 import oracle.fdgs_oracle as fo
