@@ -313,7 +313,8 @@ int fdgs_select_keep_noalloc(const float *score_dev, int64_t n, float prune_rati
  * Stage profiling of the scene's subsequent fdgs_render calls. flags bit0: record CUDA
  * events on the render stream between the stages (FDGS_PROFILE_STAGES of them, in order:
  * preprocess, depth_sort, gather_scan, host_sync (the one mid-frame wait for the key count),
- * tile_scan, emit, tile_sort, blend); bit1: count the
+ * tile_scan (tile ranges and the blend's longest-first tile order), emit, tile_sort,
+ * blend); bit1: count the
  * (Gaussian, pixel) evaluations of the blend (a slower kernel variant; use it in an
  * untimed pass). 0 turns profiling off.
  */
