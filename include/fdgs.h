@@ -94,6 +94,12 @@ typedef struct {
                      cut to the tiles the alpha >= 1/255 ellipse can reach (same image,
                      shorter lists; fdgs_frame_export then returns these). Batches always
                      use 1. */
+  int no_temporal_cull;  /* fdgs_render: 1 keeps the Gaussians whose a = sigmoid(o) p(t) is
+                            below 1/255 (Sec. 3, Eq. 3) in projection, binning and sorting,
+                            as a renderer without that cull would; they reach alpha >= 1/255
+                            at no pixel, so the image is the same, only the lists are longer.
+                            0 (default) culls them. Batches ignore it (their alpha-tight
+                            tile sets are empty for such Gaussians). */
 } fdgs_render_opts;
 
 /* Counts of one rendered frame, for reports and tests. */
@@ -299,12 +305,19 @@ int fdgs_select_keep(fdgs_scene *scene, const float *score_dev, int64_t n, float
  * 18 MiB device array that every GPU loading the library holds until the process exits.
  *   - n must be <= 1048576 (2^20); larger n returns FDGS_ERR_CAPACITY. Other argument errors
  *     return FDGS_ERR_INVALID. No scene is needed.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     and caches it; make that first call before any stream capture on that device.
+ *   - The array is reserved when the runtime loads the library's module on a device: by
+ *     default (lazy module loading) at the first call on that device, or when the library is
+ *     loaded under CUDA_MODULE_LOADING=EAGER. A caller that must allocate nothing after
+ *     start-up makes one warm-up call per device at start-up.
+ *   - The first call on a device also looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any stream capture on
+ *     that device. Calls after cudaDeviceReset of that device are not supported (the cached
+ *     address may be stale).
  *   - Every call on a device shares the one array and overwrites it (the parts that must start
  *     at zero are cleared by each call). Calls whose GPU work overlaps (different streams,
  *     or concurrent host threads) race on the array: serialise them.
- *   - A device spin-wait timeout inside the sort is not reported by this entry point.
+ *   - The call synchronises the stream before it returns, so that it can report a spin-wait
+ *     limit reached inside its sort as FDGS_ERR_TIMEOUT (the keep-set is then unspecified).
  */
 int fdgs_select_keep_noalloc(const float *score_dev, int64_t n, float prune_ratio,
                              uint8_t *keep_out_dev, fdgs_stream stream);
@@ -346,6 +359,31 @@ int fdgs_set_blend_shape(int footprint);
 /* Reads and clears the scene's device status word (synchronises the device): FDGS_OK, or
  * FDGS_ERR_CAPACITY / FDGS_ERR_TIMEOUT raised by a kernel since the last read. */
 int fdgs_status_sync(fdgs_scene *scene);
+
+/*
+ * Failure injection, process-wide, for tests of the error paths (the paper has no
+ * counterpart). Every injected failure is made on the host or by a bounded wait that gives up:
+ * none faults or hangs the GPU.
+ *   FDGS_INJECT_SPIN_LIMIT (value = polls, 0 = the default 2^20): the spin-wait limit of the
+ *     radix sort's decoupled look-back for later sorts. A look-back that reaches it gives up,
+ *     sets FDGS_ERR_TIMEOUT in the scene's status word (or, for fdgs_select_keep_noalloc, in
+ *     its own error word) and the sort's remaining passes skip their work; every access stays
+ *     in bounds, the sorted output is unspecified.
+ *   FDGS_INJECT_WITHHOLD_PUBLISH (value = partition index): the next sort pass launched
+ *     eagerly (not from a captured graph) has that partition publish nothing in its
+ *     look-back, so its successors wait until the spin limit. One-shot.
+ *   FDGS_INJECT_FAIL_ALLOCS (value = count): the next `value` device-buffer growths fail with
+ *     FDGS_ERR_OOM, as a refused cudaMalloc would.
+ *   FDGS_INJECT_NONE: clears all of the above.
+ * Returns FDGS_ERR_INVALID for an unknown kind or a value out of range. Not thread-safe.
+ */
+enum {
+  FDGS_INJECT_NONE = 0,
+  FDGS_INJECT_SPIN_LIMIT = 1,
+  FDGS_INJECT_WITHHOLD_PUBLISH = 2,
+  FDGS_INJECT_FAIL_ALLOCS = 3
+};
+int fdgs_debug_inject(int kind, int64_t value);
 
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char *fdgs_last_error(void);

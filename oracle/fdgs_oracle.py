@@ -217,7 +217,7 @@ def tight_tile_rect(mean2d, conic, a, rect):
     return torch.where(empty[:, None], torch.zeros_like(out), out), edges
 
 
-def preprocess(P: Params, cam, t, active=None, tile_sets="square"):
+def preprocess(P: Params, cam, t, active=None, tile_sets="square", temporal_cull=True):
     """Per-Gaussian preparation for one (camera, t). Returns a dict of float64 tensors
     (differentiable where the method is) and boolean/int decisions (detached).
     ``tile_sets``: "square" (the 3DGS-family 3-sigma rectangle, the reference) or "tight"
@@ -228,6 +228,9 @@ def preprocess(P: Params, cam, t, active=None, tile_sets="square"):
     a = sigmoid(o) p(t), culled when a < 1/255 (then alpha < 1/255 everywhere) -> camera
     transform, near-plane cull z <= znear -> EWA 2D covariance + 0.3 px^2 -> conic ->
     radius ceil(3 sqrt(lambda_max)) -> tile rectangle -> SH colour.
+    ``temporal_cull=False`` skips the a < 1/255 cull (a renderer without it: such Gaussians
+    are projected and binned but reach alpha >= 1/255 at no pixel); ``pass_temporal`` still
+    records a >= 1/255.
     """
     n = P.mean4.shape[0]
     t = float(t)
@@ -275,7 +278,8 @@ def preprocess(P: Params, cam, t, active=None, tile_sets="square"):
         ymax = torch.clamp(torch.floor(yhi_f / TILE), 0, gy).long()
         pass_mask = act.clone()
         pass_temporal = pass_mask & (a >= ALPHA_MIN)
-        pass_near = pass_temporal & (z > cam.znear)
+        alive = pass_temporal if temporal_cull else pass_mask
+        pass_near = alive & (z > cam.znear)
         pass_det = pass_near & (det > 0)
         visible = pass_det & (xmax > xmin) & (ymax > ymin)
         rect = torch.stack([xmin, ymin, xmax, ymax], -1)
@@ -408,14 +412,14 @@ def tile_pixels(tile_id, gx, W, H):
 
 
 def render(P: Params, cam, t, active=None, tiles=None, bg=(0.0, 0.0, 0.0), weights=False,
-           pre=None, tile_sets="square"):
+           pre=None, tile_sets="square", temporal_cull=True):
     """Render one frame (or only the tiles listed in ``tiles``).
 
     Returns dict: image [3,H,W] (float64; NaN outside the rendered tiles when ``tiles`` is
     given), T_final [H,W], n_contrib [H,W], lists {tile: ids}, pre, and, with
     ``weights=True``, w_sum [N] = sum over the rendered pixels of alpha_i T_i (Eq. 4)."""
     if pre is None:
-        pre = preprocess(P, cam, t, active, tile_sets)
+        pre = preprocess(P, cam, t, active, tile_sets, temporal_cull)
     gx, gy = pre["grid"]
     W, H = cam.width, cam.height
     todo = range(gx * gy) if tiles is None else tiles

@@ -55,8 +55,17 @@ struct Buf {
   }
 };
 
+// Host-side failure injection (fdgs_debug_inject): the next g_fail_allocs growths fail as a
+// refused cudaMalloc would.
+int g_fail_allocs = 0;
+
 int grow(Buf &b, size_t bytes) {
   if (bytes <= b.n && b.p) return FDGS_OK;
+  if (g_fail_allocs > 0) {
+    --g_fail_allocs;
+    return fail(FDGS_ERR_OOM, "device allocation of %zu bytes refused (injected failure)",
+                bytes + bytes / 4);
+  }
   b.release();
   const size_t nb = std::max<size_t>(bytes + bytes / 4, 256);
   if (cudaMalloc(&b.p, nb) != cudaSuccess) {
@@ -359,6 +368,7 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   pa.status = ws.pre_status.as<uint64_t>();
   pa.ctr = ctr;
   pa.err = err;
+  pa.no_cull = opts && opts->no_temporal_cull ? 1 : 0;
   launch_preprocess(pa, st);
   if (prof) CK(cudaEventRecord(s->ev[1], st));
   uint64_t *sorted = radix_sort<uint64_t>(ws.vis[0].as<uint64_t>(), ws.vis[1].as<uint64_t>(),
@@ -475,17 +485,40 @@ bool plan_matches(const BatchPlan *p, const fdgs_scene *s, const fdgs_camera *ca
   return true;
 }
 
+// Grows the block lists to the plan's capacity. On failure the plan is marked unusable (its
+// captured graph, which holds the old list pointers, is destroyed, and it matches no batch
+// geometry), so that the next batch call builds a new plan.
 int plan_alloc_lists(BatchPlan &p) {
-  TRY(grow(p.lists, std::max<uint64_t>(p.key_cap, 1) * 4));
-  TRY(grow(p.ltm, std::max<uint64_t>(p.key_cap, 1) * 2));
-  return FDGS_OK;
+  int rc = grow(p.lists, std::max<uint64_t>(p.key_cap, 1) * 4);
+  if (rc == FDGS_OK) rc = grow(p.ltm, std::max<uint64_t>(p.key_cap, 1) * 2);
+  if (rc != FDGS_OK) {
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    p.exec = nullptr;
+    p.W.clear();
+    p.H.clear();
+    p.nreq = -1;
+  }
+  return rc;
 }
 
+int plan_build(fdgs_scene *s, BatchPlan &p, const fdgs_camera *cams, int n, bool masked);
+
+// The plan of this batch geometry: the current one if it matches, else a new one. A plan
+// whose construction failed (a refused allocation, a bad camera) is discarded, so that the
+// next call starts again instead of matching a half-built plan.
 int plan_prepare(fdgs_scene *s, const fdgs_camera *cams, int n, bool masked) {
   if (plan_matches(s->plan, s, cams, n, masked)) return FDGS_OK;
   delete s->plan;
   s->plan = new BatchPlan();
-  BatchPlan &p = *s->plan;
+  const int rc = plan_build(s, *s->plan, cams, n, masked);
+  if (rc != FDGS_OK) {
+    delete s->plan;
+    s->plan = nullptr;
+  }
+  return rc;
+}
+
+int plan_build(fdgs_scene *s, BatchPlan &p, const fdgs_camera *cams, int n, bool masked) {
   p.nreq = n;
   p.masked = masked;
   p.d = s->d;
@@ -1400,6 +1433,32 @@ int fdgs_profile_read(fdgs_scene *s, float *stage_ms, uint64_t *blend_counts) {
     if (s->evals.p) CK(cudaMemcpy(blend_counts, s->evals.p, 24, cudaMemcpyDeviceToHost));
   }
   return FDGS_OK;
+}
+
+int fdgs_debug_inject(int kind, int64_t value) {
+  switch (kind) {
+    case FDGS_INJECT_NONE:
+      fdgs::g_debug_spin_limit = 0;
+      fdgs::g_debug_withhold = ~0u;
+      g_fail_allocs = 0;
+      return FDGS_OK;
+    case FDGS_INJECT_SPIN_LIMIT:
+      if (value < 0 || value > (int64_t)kSpinLimit)
+        return fail(FDGS_ERR_INVALID, "spin limit must be in [0, %u]", kSpinLimit);
+      fdgs::g_debug_spin_limit = (uint32_t)value;
+      return FDGS_OK;
+    case FDGS_INJECT_WITHHOLD_PUBLISH:
+      if (value < 0 || value >= (1ll << 30))
+        return fail(FDGS_ERR_INVALID, "partition index out of range");
+      fdgs::g_debug_withhold = (uint32_t)value;
+      return FDGS_OK;
+    case FDGS_INJECT_FAIL_ALLOCS:
+      if (value < 0 || value > (1 << 20)) return fail(FDGS_ERR_INVALID, "bad allocation count");
+      g_fail_allocs = (int)value;
+      return FDGS_OK;
+    default:
+      return fail(FDGS_ERR_INVALID, "unknown injection kind %d", kind);
+  }
 }
 
 int fdgs_status_sync(fdgs_scene *s) {

@@ -150,15 +150,19 @@ __device__ __forceinline__ void gauss_cond(float4 ls, float4 ql, float4 qr, floa
 // The per-(t, camera) part of the forward, from the conditional factors (g.N, g.w, g.nt2,
 // g.sig and inv_nt): temporal weight, conditional mean, view transform, EWA projection, up
 // to the cull tests. Returns the decision flags (kFlag*); a Gaussian that fails a test stops
-// there.
+// there. cull = false keeps a Gaussian whose a = sigmoid(o) p(t) is below 1/255 (it can
+// reach alpha >= 1/255 nowhere, so the image is the same; its flag bit stays clear).
 __device__ __forceinline__ uint8_t gauss_forward_tail(const DevCam &cam, float t, float4 mean,
-                                                      float inv_nt, GaussState &g) {
+                                                      float inv_nt, GaussState &g,
+                                                      bool cull = true) {
   uint8_t flags = kFlagMask;
   g.dt = t - mean.w;
   g.p = expf(-0.5f * g.dt * g.dt / g.nt2);
   g.a = g.sig * g.p;
-  if (!(g.a >= kAlphaMin)) return flags;
-  flags |= kFlagTemporal;
+  if (g.a >= kAlphaMin)
+    flags |= kFlagTemporal;
+  else if (cull)
+    return flags;
   const float k = g.dt * inv_nt;
   g.mu3[0] = mean.x + g.w[0] * k;
   g.mu3[1] = mean.y + g.w[1] * k;
@@ -211,10 +215,10 @@ __device__ __forceinline__ uint8_t gauss_forward_tail(const DevCam &cam, float t
 // (kFlag*). The state is filled as far as the Gaussian got.
 __device__ __forceinline__ uint8_t gauss_forward(const DevCam &cam, float t, float4 mean,
                                                  float4 ls, float4 ql, float4 qr, float o,
-                                                 GaussState &g) {
+                                                 GaussState &g, bool cull = true) {
   float inv_nt;
   gauss_cond(ls, ql, qr, o, g, inv_nt);
-  return gauss_forward_tail(cam, t, mean, inv_nt, g);
+  return gauss_forward_tail(cam, t, mean, inv_nt, g, cull);
 }
 
 // The conditional factors of gauss_cond as stored per Gaussian for the batched path

@@ -19,6 +19,11 @@ template <typename K>
 K *radix_sort(K *a, K *b, const uint32_t *n_dev, uint64_t n_cap, int lo, int bits,
               void *scratch, cudaStream_t st, uint32_t *err_dev, bool hist_ready = false);
 int sort_passes(int bits);
+// Failure injection for tests (fdgs_debug_inject): a spin-wait limit for the sort's look-backs
+// (0 = kSpinLimit) and a partition whose look-back publish the next sort pass withholds
+// (~0u = none; reset by that pass).
+extern uint32_t g_debug_spin_limit;
+extern uint32_t g_debug_withhold;
 int sort_digit_bits(int bits);
 inline uint32_t *sort_hist(void *scratch) { return static_cast<uint32_t *>(scratch); }
 constexpr uint64_t kSortMaxKeys = (1ull << 30) - 1;
@@ -40,6 +45,7 @@ struct PreArgs {
   uint64_t *status;    // chained-scan status [ceil(n/256)]
   uint32_t *ctr;       // frame counters
   uint32_t *err;       // scene status word (device error bits)
+  int no_cull = 0;     // keep Gaussians with a = sigmoid(o) p(t) < 1/255 (same image)
 };
 void launch_preprocess(const PreArgs &a, cudaStream_t st);
 

@@ -6,8 +6,11 @@
 // not pay the implicit device-wide synchronisation of cudaMalloc/cudaFree, and a process whose
 // HBM is already fully reserved by another allocator (a framework's caching pool, a fixed
 // serving budget) cannot obtain fresh device memory at all. fdgs_select_keep_noalloc does the
-// same selection with every scratch byte in one file-scope static device array, reserved when
-// the library is loaded on a device and held until the process exits.
+// same selection with every scratch byte in one file-scope static device array, held by every
+// device that loads this module until the process exits. The runtime reserves that array when
+// it loads the module on a device: at the module's first use there (its first call here, under
+// the default lazy module loading) or when the library is loaded (CUDA_MODULE_LOADING=EAGER).
+// A caller that can allow no allocation at all after start-up makes one warm-up call first.
 #include <mutex>
 
 #include "fdgs.h"
@@ -26,7 +29,9 @@ constexpr size_t kScratchBytes = 18ull << 20;   // 18 MiB in total
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Host code must not take the address of g_noalloc_scratch directly (that is a host-side
-// stand-in, not a device address): it asks the runtime, once per device.
+// stand-in, not a device address): it asks the runtime, once per device, and caches the
+// answer. After cudaDeviceReset the module may be reloaded elsewhere and the cached address
+// is stale, so calls after a reset of that device are not supported.
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 void *g_dev_ptr[kMaxDevices] = {};
@@ -96,10 +101,24 @@ extern "C" int fdgs_select_keep_noalloc(const float *score_dev, int64_t n, float
                                              words + 1);
   const uint32_t n_drop = (uint32_t)((double)prune_ratio * (double)N);
   fdgs::launch_keep_from_sorted(srt, N, n_drop, keep_out_dev, st);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     fdgs::set_error_message(cudaGetErrorString(e));
     return FDGS_ERR_CUDA;
+  }
+  // The call has no scene whose status word a later call could read, so it waits for its own
+  // work and reports a look-back that gave up (the keep-set is then unspecified).
+  uint32_t dev_err = 0;
+  e = cudaMemcpyAsync(&dev_err, words + 1, sizeof dev_err, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    fdgs::set_error_message(cudaGetErrorString(e));
+    return FDGS_ERR_CUDA;
+  }
+  if (dev_err & fdgs::kErrTimeout) {
+    fdgs::set_error_message("fdgs_select_keep_noalloc: a sort look-back reached its spin-wait "
+                            "limit; the keep-set is unspecified");
+    return FDGS_ERR_TIMEOUT;
   }
   return FDGS_OK;
 }

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kBlock) k_preprocess(PreArgs a) {
       if (active) {
         GaussState g;
         fl = gauss_forward(a.cam, a.t, __ldg(&a.mean4[i]), __ldg(&a.ls4[i]), __ldg(&a.ql[i]),
-                           __ldg(&a.qr[i]), __ldg(&a.opacity[i]), g);
+                           __ldg(&a.qr[i]), __ldg(&a.opacity[i]), g, !a.no_cull);
         if (fl & kFlagDet) {
           const float half = 0.5f * (g.c00 - g.c11);
           const float disc = half * half + g.c01 * g.c01;

@@ -151,10 +151,14 @@ __global__ void k_score_keys(const float *__restrict__ score, uint32_t n, uint64
     keys[i] = ((uint64_t)__float_as_uint(score[i]) << 32) | i;
 }
 
+// The id bounds check only matters after a sort whose look-back gave up (its output can hold
+// stale keys); a complete sort is a permutation of 0..n-1.
 __global__ void k_keep_from_sorted(const uint64_t *__restrict__ sorted, uint32_t n,
                                    uint32_t n_drop, uint8_t *keep) {
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-    keep[(uint32_t)sorted[j]] = j >= n_drop ? 1 : 0;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t id = (uint32_t)sorted[j];
+    if (id < n) keep[id] = j >= n_drop ? 1 : 0;
+  }
 }
 
 }  // namespace

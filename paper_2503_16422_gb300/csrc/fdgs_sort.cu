@@ -20,6 +20,7 @@ constexpr int kRadix = 256;
 constexpr int kItems = 16;
 constexpr int kTileKeys = kSortBlock * kItems;   // keys per partition
 constexpr int kMaxPasses = 8;                    // digit passes supported (64 bits)
+constexpr int kAbortWord = 32;                   // index of the abort word after the counters
 
 // Per-digit status word of the onesweep look-back: 2-bit flag | 30-bit count.
 constexpr uint32_t kStAgg = 1u << 30, kStPrefix = 2u << 30, kStValue = (1u << 30) - 1;
@@ -60,11 +61,19 @@ __global__ void __launch_bounds__(kRadix) k_hist_scan(uint32_t *hist) {
   h[threadIdx.x] = inc - v + warp_tot[threadIdx.x >> 5];
 }
 
+// Look-back waits give up after spin_limit polls; the first one to give up sets kErrTimeout in
+// err and the call's abort word, every other waiter that sees the abort word gives up too,
+// and later passes of the same sort skip their work. A waiter that gives up uses the partial
+// prefix it has (never more than the true one), so every scatter address stays inside
+// [0, n); the keys are then wrong but no access is out of bounds. withhold: a partition
+// whose index equals it publishes nothing (failure injection on the host's request; ~0u
+// otherwise).
 template <typename K>
 __global__ void __launch_bounds__(kSortBlock)
 k_onesweep(const K *__restrict__ in, K *__restrict__ out, const uint32_t *__restrict__ n_dev,
            int shift, int dbits, const uint32_t *__restrict__ goff, uint32_t *status,
-           uint32_t *part_ctr, uint32_t *err) {
+           uint32_t *part_ctr, uint32_t *err, uint32_t *abort_word, uint32_t spin_limit,
+           uint32_t withhold) {
   __shared__ K s_keys[kTileKeys];
   __shared__ uint32_t s_wh[kSortWarps][kRadix + 1];
   __shared__ uint32_t s_bstart[kRadix];
@@ -75,6 +84,7 @@ k_onesweep(const K *__restrict__ in, K *__restrict__ out, const uint32_t *__rest
   const uint32_t nparts = (n + kTileKeys - 1) / kTileKeys;
   const uint32_t mask = (1u << dbits) - 1u;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (ld_volatile_u32(abort_word)) return;   // an earlier pass of this sort timed out
   for (;;) {
     if (tid == 0) s_part = atomicAdd(part_ctr, 1u);
     for (int i = tid; i < kSortWarps * (kRadix + 1); i += kSortBlock) (&s_wh[0][0])[i] = 0;
@@ -127,20 +137,22 @@ k_onesweep(const K *__restrict__ in, K *__restrict__ out, const uint32_t *__rest
     // decoupled look-back for digit `tid`
     {
       uint32_t *st = status + (size_t)part * kRadix + tid;
+      const bool publish = part != withhold;
       uint32_t excl = 0;
       if (part == 0) {
-        st_volatile_u32(st, kStPrefix | cnt);
+        if (publish) st_volatile_u32(st, kStPrefix | cnt);
       } else {
-        st_volatile_u32(st, kStAgg | cnt);
+        if (publish) st_volatile_u32(st, kStAgg | cnt);
         int64_t j = (int64_t)part - 1;
         uint32_t spins = 0;
         while (j >= 0) {
           const uint32_t s = ld_volatile_u32(status + (size_t)j * kRadix + tid);
           const uint32_t f = s & ~kStValue;
           if (f == 0) {
-            if (++spins > kSpinLimit ||
-                ((spins & 255) == 0 && (ld_volatile_u32(err) & kErrTimeout))) {
+            if (++spins > spin_limit ||
+                ((spins & 255) == 0 && ld_volatile_u32(abort_word))) {
               atomicOr(err, kErrTimeout);
+              atomicOr(abort_word, 1u);
               break;
             }
             __nanosleep(20);
@@ -150,7 +162,7 @@ k_onesweep(const K *__restrict__ in, K *__restrict__ out, const uint32_t *__rest
           if (f == kStPrefix) break;
           --j;
         }
-        st_volatile_u32(st, kStPrefix | ((excl + cnt) & kStValue));
+        if (publish) st_volatile_u32(st, kStPrefix | ((excl + cnt) & kStValue));
       }
       s_gbase[tid] = goff[tid] + excl;
     }
@@ -163,7 +175,8 @@ k_onesweep(const K *__restrict__ in, K *__restrict__ out, const uint32_t *__rest
     for (uint32_t i = tid; i < nvalid; i += kSortBlock) {
       const K k = s_keys[i];
       const uint32_t d = (uint32_t)((k >> shift) & mask);
-      out[s_gbase[d] + (i - s_bstart[d])] = k;
+      const uint32_t pos = s_gbase[d] + (i - s_bstart[d]);
+      if (pos < n) out[pos] = k;   // always true unless a look-back gave up
     }
     __syncthreads();
   }
@@ -195,9 +208,13 @@ int sort_digit_bits(int bits) {
 
 size_t sort_scratch_bytes(uint64_t n_cap, int bits) {
   const int np = std::max(1, sort_passes(bits));
-  // hist [4][256] + part counters [4] (padded) + one status region per pass
+  // hist [8][256] + 256 bytes of words (partition counters of the passes, the abort word)
+  // + one status region per pass
   return kMaxPasses * kRadix * sizeof(uint32_t) + 256 + np * status_bytes(n_cap);
 }
+
+uint32_t g_debug_spin_limit = 0;
+uint32_t g_debug_withhold = ~0u;
 
 template <typename K>
 K *radix_sort(K *a, K *b, const uint32_t *n_dev, uint64_t n_cap, int lo, int bits,
@@ -222,11 +239,22 @@ K *radix_sort(K *a, K *b, const uint32_t *n_dev, uint64_t n_cap, int lo, int bit
   }
   const uint64_t parts = (n_cap + kTileKeys - 1) / kTileKeys;
   const int grid = (int)std::min<uint64_t>(parts, (uint64_t)onesweep_grid<K>());
+  // per-call words after the partition counters: ctr[kAbortWord] is the call's abort flag
+  // (zeroed with the rest of the scratch above)
+  uint32_t *abort_word = ctr + kAbortWord;
+  // injected failures apply to eager launches only: a captured graph would replay them
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  const bool eager = cap == cudaStreamCaptureStatusNone;
+  const uint32_t spin = eager && g_debug_spin_limit ? g_debug_spin_limit : kSpinLimit;
+  const uint32_t withhold = eager ? g_debug_withhold : ~0u;
+  if (eager) g_debug_withhold = ~0u;   // one-shot: only the next sort pass withholds
   K *src = a, *dst = b;
   for (int p = 0; p < np; ++p) {
     k_onesweep<K><<<std::max(1, grid), kSortBlock, 0, st>>>(
         src, dst, n_dev, lo + p * dbits, dbits, hist + p * kRadix,
-        (uint32_t *)(status0 + p * sb), ctr + p, err_dev);
+        (uint32_t *)(status0 + p * sb), ctr + p, err_dev, abort_word, spin,
+        p == 0 ? withhold : ~0u);
     std::swap(src, dst);
   }
   return src;

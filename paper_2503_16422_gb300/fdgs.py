@@ -41,7 +41,8 @@ class fdgs_camera(ctypes.Structure):
 
 
 class fdgs_render_opts(ctypes.Structure):
-    _fields_ = [("use_mask", ctypes.c_int), ("bg", ctypes.c_float * 3), ("tile_sets", ctypes.c_int)]
+    _fields_ = [("use_mask", ctypes.c_int), ("bg", ctypes.c_float * 3), ("tile_sets", ctypes.c_int),
+                ("no_temporal_cull", ctypes.c_int)]
 
 
 class fdgs_frame_stats(ctypes.Structure):
@@ -90,7 +91,10 @@ _SIGNATURES = {
     "fdgs_set_sh_codebook": [_P, _P, ctypes.c_int, _P],
     "fdgs_build_keyframe_masks": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P, _P],
+    "fdgs_debug_inject": [ctypes.c_int, ctypes.c_int64],
 }
+# fdgs_debug_inject kinds
+INJECT_NONE, INJECT_SPIN_LIMIT, INJECT_WITHHOLD_PUBLISH, INJECT_FAIL_ALLOCS = 0, 1, 2, 3
 PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "tile_scan", "emit",
                   "tile_sort", "blend")
 BATCH_STAGES = ("preprocess", "depth_sort", "gather", "tile_scan", "lists", "queue_sort",
@@ -173,12 +177,13 @@ def _times(ts):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 
-def _opts(use_mask, bg, tight=False):
+def _opts(use_mask, bg, tight=False, temporal_cull=True):
     o = fdgs_render_opts()
     o.use_mask = int(bool(use_mask))
     for k in range(3):
         o.bg[k] = float(bg[k])
     o.tile_sets = int(bool(tight))
+    o.no_temporal_cull = int(not temporal_cull)
     return o
 
 
@@ -319,13 +324,15 @@ class Scene:
             _stream(stream)))
 
     def render(self, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0), keep_frame=False, out=None,
-               stream=None, tight=False):
+               stream=None, tight=False, temporal_cull=True):
         """Render [3,H,W] float32. With keep_frame=True also returns the Frame. tight: build
-        the alpha-tight tile sets instead of the 3-sigma squares (same image)."""
+        the alpha-tight tile sets instead of the 3-sigma squares (same image).
+        temporal_cull=False: keep the Gaussians with sigmoid(o) p(t) < 1/255 in the lists
+        (same image, longer lists)."""
         c = make_camera(cam)
         if out is None:
             out = torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.device)
-        o = _opts(use_mask, bg, tight)
+        o = _opts(use_mask, bg, tight, temporal_cull)
         fh = ctypes.c_void_p()
         check(lib().fdgs_render(self.handle, ctypes.byref(c), float(t), ctypes.byref(o),
                                 _ptr(out), ctypes.byref(fh) if keep_frame else None,
@@ -539,3 +546,9 @@ def set_blend_shape(footprint):
     16x2, 1: 8x4, 2: 4x8 with one pixel a lane; 3: 8x8 with two; 4: 16x8, 5: 8x16 with
     four). Results do not depend on it."""
     check(lib().fdgs_set_blend_shape(int(footprint)))
+
+
+def debug_inject(kind, value=0):
+    """Failure injection for tests of the error paths (see fdgs_debug_inject in the header):
+    INJECT_SPIN_LIMIT, INJECT_WITHHOLD_PUBLISH, INJECT_FAIL_ALLOCS, or INJECT_NONE to clear."""
+    check(lib().fdgs_debug_inject(int(kind), int(value)))

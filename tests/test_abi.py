@@ -87,3 +87,18 @@ def test_batch_marshalling_matches_the_c_structs():
     assert ctypes.addressof(tp.contents) == ta.ctypes.data
     empty, _ = fdgs.make_cameras([])
     assert empty.shape == (1,)
+
+
+def test_failure_injection_arguments_are_checked_on_the_host(libpath):
+    """fdgs_debug_inject is a host-side setter: bad kinds and values are refused, and
+    clearing restores the defaults (no GPU needed)."""
+    from paper_2503_16422_gb300 import fdgs
+    lib = fdgs.lib()
+    assert lib.fdgs_debug_inject(99, 0) == -1 and b"unknown" in lib.fdgs_last_error()
+    assert lib.fdgs_debug_inject(fdgs.INJECT_SPIN_LIMIT, -1) == -1
+    assert lib.fdgs_debug_inject(fdgs.INJECT_SPIN_LIMIT, 1 << 21) == -1
+    assert lib.fdgs_debug_inject(fdgs.INJECT_WITHHOLD_PUBLISH, -2) == -1
+    assert lib.fdgs_debug_inject(fdgs.INJECT_FAIL_ALLOCS, -1) == -1
+    assert lib.fdgs_debug_inject(fdgs.INJECT_SPIN_LIMIT, 1000) == 0
+    assert lib.fdgs_debug_inject(fdgs.INJECT_FAIL_ALLOCS, 2) == 0
+    assert lib.fdgs_debug_inject(fdgs.INJECT_NONE, 0) == 0

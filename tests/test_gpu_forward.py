@@ -20,11 +20,11 @@ def fd():
     return fdgs
 
 
-def _run(fd, scene, cam, t, masks=None, key_times=None, use_mask=False):
+def _run(fd, scene, cam, t, masks=None, key_times=None, use_mask=False, temporal_cull=True):
     sc = fd.Scene.from_host(scene)
     if masks is not None:
         sc.set_active_mask(torch.as_tensor(masks).cuda(), key_times)
-    img, fr = sc.render(cam, t, use_mask=use_mask, keep_frame=True)
+    img, fr = sc.render(cam, t, use_mask=use_mask, keep_frame=True, temporal_cull=temporal_cull)
     ex = fr.export()
     torch.cuda.synchronize()
     out = {k: parity.to_np(v) if isinstance(v, torch.Tensor) else v for k, v in ex.items()}
@@ -34,9 +34,9 @@ def _run(fd, scene, cam, t, masks=None, key_times=None, use_mask=False):
     return out
 
 
-def _check_frame(g, scene, cam, t, active=None, strict_image=True):
+def _check_frame(g, scene, cam, t, active=None, strict_image=True, temporal_cull=True):
     P = oracle.Params.from_scene(scene)
-    ref = oracle.render(P, cam, t, active)
+    ref = oracle.render(P, cam, t, active, temporal_cull=temporal_cull)
     pre = ref["pre"]
     ex = parity.exempt_gaussians(pre, cam)
     nbad, nex, bad_ids = parity.compare_flags(g["flags"], pre, ex)
@@ -114,6 +114,22 @@ def test_all_ones_mask_equals_unmasked_and_all_zeros_is_black(fd):
     assert np.abs(gz["image"]).max() == 0.0
     assert gz["stats"]["n_keys"] == 0 and gz["stats"]["n_active"] == 0
     assert np.all(gz["T_final"] == 1.0)
+
+
+def test_no_temporal_cull_gives_the_same_image_with_longer_lists(fd):
+    """Without the exact a < 1/255 cull (the comparison renderer of the paper's speed-up) the
+    lists carry the Gaussians the cull would drop; the image and transmittance are the same
+    bit for bit, and flags and lists match the oracle run the same way."""
+    s = scenes.make_scene(4000, 9, sh_degree=1, lt_short=(-4.0, 0.5), lt_long=(-2.0, 0.5),
+                          short_frac=0.7)
+    cam = scenes.tiny_camera(96, 80)
+    on = _run(fd, s, cam, 0.5)
+    off = _run(fd, s, cam, 0.5, temporal_cull=False)
+    assert np.array_equal(on["image"], off["image"])
+    assert np.array_equal(on["T_final"], off["T_final"])
+    assert off["stats"]["n_visible"] > on["stats"]["n_visible"]
+    assert off["stats"]["n_keys"] > on["stats"]["n_keys"]
+    _check_frame(off, s, cam, 0.5, temporal_cull=False)
 
 
 def test_empty_and_fully_culled_scenes(fd):

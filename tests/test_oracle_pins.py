@@ -367,6 +367,29 @@ def test_zero_space_time_correlation_is_a_static_splat():
     assert float(out["image"].max()) > 0.1
 
 
+def test_temporal_cull_changes_lists_not_images():
+    """The exact temporal cull (a = sigmoid(o) p(t) < 1/255, Sec. 3 Eq. 3) is exact: a
+    renderer without it lists more Gaussians per tile, every extra one with a < 1/255, and
+    composites the same image (such an entry reaches alpha >= 1/255 at no pixel)."""
+    s = scenes.make_scene(1500, 31, sh_degree=1, lt_short=(-4.0, 0.5), lt_long=(-2.0, 0.5),
+                          short_frac=0.7)
+    cam = scenes.tiny_camera(80, 64)
+    P = oracle.Params.from_scene(s)
+    on = oracle.render(P, cam, 0.4)
+    off = oracle.render(P, cam, 0.4, temporal_cull=False)
+    a = on["pre"]["a"].detach().numpy()
+    assert np.abs(on["image"].numpy() - off["image"].numpy()).max() <= 1e-12
+    assert np.abs(on["T_final"].numpy() - off["T_final"].numpy()).max() <= 1e-12
+    extra = 0
+    for tid, ids in on["lists"].items():
+        more = np.setdiff1d(off["lists"][tid], ids)
+        assert set(ids.tolist()) <= set(off["lists"][tid].tolist())
+        assert np.all(a[more] < oracle.ALPHA_MIN)
+        extra += len(more)
+    assert extra > 100
+    assert np.array_equal(on["pre"]["pass_temporal"].numpy(), off["pre"]["pass_temporal"].numpy())
+
+
 # ---- gradients -------------------------------------------------------------------------------
 
 def _decisions(P, cam, t):
