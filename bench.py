@@ -42,7 +42,19 @@ E2E_COPY_STREAMS = 4   # device->host image copies run on this many streams at o
 # add 1, alpha clamp 1, transmittance 2, weight 1, colour 6 (plus one MUFU exp2)
 EVAL_FLOP = 20
 TEST_FLOP = 36        # FP32 FLOP per footprint culling test (4 edges x 9)
+# FP32 FLOP per blended (Gaussian, pixel) entry of the reverse replay (k_blend_bwd): exponent 6,
+# alpha clamp 1, 1/(1 - alpha) 2, transmittance 1, weight 1, the three colour accumulators 9,
+# dL/dalpha 8, colour gradients 6, opacity gradient 3, exponent gradient 1, and the five conic
+# and mean gradient terms 15 (plus one MUFU exp2 and one MUFU reciprocal)
+BWD_EVAL_FLOP = 53
 W_FULL, H_FULL = 1352, 1014
+# sources of the batched blend kernel: an ncu summary under profiles/ applies to the kernel
+# only while these files hash to the value recorded in it
+BLEND_SOURCES = ("paper_2503_16422_gb300/csrc/fdgs_blend.cuh",
+                 "paper_2503_16422_gb300/csrc/fdgs_batch.cu",
+                 "paper_2503_16422_gb300/csrc/fdgs_common.cuh",
+                 "paper_2503_16422_gb300/csrc/fdgs_internal.h")
+BLEND_PROFILE = "profiles/k_blend_persist_batched_1352x1014.md"
 
 
 def parse():
@@ -93,6 +105,36 @@ def workload_config(scene, kt, batch):
             "n_gaussians": scene.n, "width": W_FULL, "height": H_FULL, "tile": 16,
             "batch": batch, "masked": True,
             "l2": "flushed before every timed step (256 MiB write)"}
+
+
+# ---- profile summaries -------------------------------------------------------------------
+
+def source_sha(paths=BLEND_SOURCES):
+    import hashlib
+    h = hashlib.sha256()
+    for p_ in paths:
+        with open(os.path.join(ROOT, p_), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_blend_counters():
+    """DRAM bytes per frame and issue activity of k_blend_persist from the ncu summary under
+    profiles/, if that summary was captured from the current kernel sources (its
+    ``bench-data`` line records their hash); else None and the reason."""
+    path = os.path.join(ROOT, BLEND_PROFILE)
+    want = source_sha()
+    try:
+        for ln in open(path):
+            if ln.startswith("bench-data: "):
+                d = json.loads(ln[len("bench-data: "):])
+                if d.get("source_sha") != want:
+                    return None, (f"{BLEND_PROFILE} was captured from kernel sources "
+                                  f"{d.get('source_sha')}, not the current {want}")
+                return d, f"{BLEND_PROFILE} (ncu, kernel sources {want})"
+    except OSError as e:
+        return None, f"{BLEND_PROFILE}: {e}"
+    return None, f"{BLEND_PROFILE} has no bench-data line"
 
 
 # ---- peaks -----------------------------------------------------------------------------
@@ -166,33 +208,76 @@ class Clocks:
 
 # ---- CPU oracle baseline ---------------------------------------------------------------
 
-def cpu_oracle_frame(scene, kt, masks, frame=150, budget_s=12.0, min_tiles=8):
+def cpu_oracle_frame(scene, kt, masks, frame=150, budget_s=12.0, min_tiles=8, threads=None):
     """FP64 oracle on a bounded sample of one masked frame: the whole per-Gaussian stage,
     then the blend of randomly chosen tiles until ~budget_s of CPU work; the tile time is
-    scaled to all 5,440 tiles. Returns seconds per frame, a description and the threads."""
+    scaled to all tiles of the frame. Returns (seconds per frame extrapolated, a description,
+    the threads used, details: wall seconds spent, tiles blended, the oracle's per-Gaussian
+    state and the blended tiles' lists)."""
     import torch
 
     import oracle
     from paper_2503_16422_gb300 import scenes
-    cam = scenes.arc_camera(scenes.frame_theta(frame))
-    t = float(scenes.frame_times()[frame])
-    active = oracle.active_from_masks(masks, kt, t, scene.n)
-    P = oracle.Params.from_scene(scene)
-    t0 = time.perf_counter()
-    pre = oracle.preprocess(P, cam, t, active)
-    t1 = time.perf_counter()
-    gx, gy = pre["grid"]
-    order = np.random.default_rng(frame).permutation(gx * gy).tolist()
-    done = 0
-    while done < len(order) and (done < min_tiles or time.perf_counter() - t1 < budget_s):
-        chunk = order[done:done + 8]
-        oracle.render(P, cam, t, active, tiles=chunk, pre=pre)
-        done += len(chunk)
-    t2 = time.perf_counter()
+    old_threads = torch.get_num_threads()
+    if threads:
+        torch.set_num_threads(threads)
+    try:
+        cam = scenes.arc_camera(scenes.frame_theta(frame))
+        # the oracle gets the float32 time and key times the GPU receives
+        t = float(np.float32(scenes.frame_times()[frame]))
+        kt32 = [float(np.float32(k)) for k in kt]
+        active = oracle.active_from_masks(masks, kt32, t, scene.n) if masks is not None else None
+        P = oracle.Params.from_scene(scene)
+        t0 = time.perf_counter()
+        pre = oracle.preprocess(P, cam, t, active)
+        t1 = time.perf_counter()
+        gx, gy = pre["grid"]
+        order = np.random.default_rng(frame).permutation(gx * gy).tolist()
+        done = 0
+        lists = {}
+        while done < len(order) and (done < min_tiles or time.perf_counter() - t1 < budget_s):
+            chunk = order[done:done + 8]
+            out = oracle.render(P, cam, t, active, tiles=chunk, pre=pre)
+            lists.update(out["lists"])
+            done += len(chunk)
+        t2 = time.perf_counter()
+        used = torch.get_num_threads()
+    finally:
+        torch.set_num_threads(old_threads)
     frame_s = (t1 - t0) + (t2 - t1) * (gx * gy) / done
-    desc = (f"1 frame (k={frame}): per-Gaussian stage of all {scene.n} Gaussians + blend of "
-            f"{done}/{gx * gy} random tiles scaled to the frame ({t2 - t0:.1f} s of CPU work)")
-    return frame_s, desc, torch.get_num_threads()
+    desc = (f"1 frame (k={frame}): per-Gaussian stage of all {scene.n} Gaussians "
+            f"({t1 - t0:.1f} s) + blend of {done}/{gx * gy} random tiles ({t2 - t1:.1f} s), "
+            f"the tile time scaled to the frame; {t2 - t0:.1f} s of CPU work")
+    return frame_s, desc, used, dict(wall_s=t2 - t0, tiles=done, tiles_total=gx * gy,
+                                     pre=pre, lists=lists, cam=cam, t=t, active=active)
+
+
+def bench_frame_parity(sc, scene, det):
+    """The oracle's per-Gaussian decisions and the sampled tiles' lists of the CPU-baseline
+    frame against a GPU render of the same frame (the float32 exemptions of the parity
+    tests): counts only, for the bench line."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import parity
+    cam, t, pre = det["cam"], det["t"], det["pre"]
+    _, fr = sc.render(cam, t, use_mask=True, keep_frame=True)
+    ex_ = fr.export()
+    fr.release()
+    flags = ex_["flags"].cpu().numpy()
+    rec = ex_["records"].cpu().numpy().astype(np.float64)
+    ranges = ex_["tile_ranges"].cpu().numpy()
+    ids = ex_["tile_ids"].cpu().numpy()
+    ex, why = parity.exempt_gaussians(pre, cam, scene.mean4, detail=True)
+    nbad, nex, _, nex_diff = parity.compare_flags(flags, pre, ex)
+    b = parity.f32_bounds(pre, cam, scene.mean4)
+    vis = (flags & parity.FLAG_VISIBLE) > 0
+    depth = np.where(vis, rec[:, 9], np.nan)
+    lists = parity.compare_tile_lists(ranges, ids, det["lists"], pre, ex, depth, b["z"])
+    return dict(frame_gaussians=int(scene.n), active=int(pre["pass_mask"].sum()),
+                visible=int(pre["visible"].sum()), exempt_gaussians=nex,
+                exempt_by_reason=why, exempt_with_flag_difference=nex_diff,
+                flag_mismatches_outside_exemptions=nbad, tiles_checked=lists["tiles"],
+                keys_checked=lists["keys"], tiles_with_list_mismatch=len(lists["bad_tiles"]),
+                depth_tie_pairs=lists["tie_pairs"])
 
 
 # ---- helpers for our implementation ------------------------------------------------------
@@ -268,6 +353,63 @@ def roofline(stage_ms, counts, bytes_mean):
     ach = bytes_mean[dom] / (stage_ms[dom] / 1e3) / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
             "frac": ach / pk["hbm"], "traffic": None, "peak_src": pk["src"] + " copy GB/s"}
+
+
+def batch_stage_roofline(bst, bc, n, deg, nreq, masked, cams, alpha_evals, blend_s_total,
+                         steps):
+    """Every stage of the batched pipeline against its roofline: the HBM-bound stages in
+    GB/s of algorithmic DRAM bytes (each input read once per batch, each output written
+    once; re-reads from L2 are not counted) against the measured copy bandwidth, the depth
+    sort also in keys/s, the blend in FP32 TFLOP/s. Stage times are the in-graph
+    %globaltimer stamps averaged over the timed steps; counts are the last batch's."""
+    pk = peaks()
+    V = bc["n_visible"]
+    E = bc["n_block_entries"]
+    K = bc["n_keys"]
+    sh = (deg + 1) ** 2 * 3 * 4
+    words = [math.ceil(V / max(nreq, 1) / 32)] * nreq
+    bl = [((math.ceil(c.width / 16) + 3) // 4, (math.ceil(c.height / 16) + 3) // 4) for c in cams]
+    mask_bytes = sum((bx + by) * w * 4 for (bx, by), w in zip(bl, words))
+    passes = 5
+    stages = {
+        "preprocess": (n * (68 + sh + 80) + (nreq * 2 * math.ceil(n / 32) * 4 if masked else 0)
+                       + V * (48 + 8 + 8),
+                       "attributes (68 B + SH) and the per-batch conditional factors (80 B) once "
+                       "per Gaussian, the mask words of the two key-frames per request, and per "
+                       "visible (request, Gaussian) a 48 B record, an 8 B rectangle and an 8 B "
+                       "key"),
+        "depth_sort": (V * 8 * (1 + 2 * passes) + V * 16,
+                       f"segment compaction (8 B read + 8 B written per visible key), histogram "
+                       f"read and {passes} onesweep passes (8 B read + 8 B written per key)"),
+        "gather": (V * (8 + 8 + 4 + 8) + mask_bytes,
+                   "per visible slot its key and rectangle read, record index and rectangle "
+                   "written; the block-row and block-column coverage words written"),
+        "lists": (E * (8 + 4 + 6) + mask_bytes,
+                  "the coverage words read once, per block-list entry its rectangle and record "
+                  "index read and 6 B written"),
+    }
+    out = {}
+    for k, (b, what) in stages.items():
+        ms = bst.get(k, 0.0) + (bst.get("tile_scan", 0.0) if k == "lists" else 0.0)
+        if ms <= 0:
+            continue
+        ach = b / (ms / 1e3) / 1e9
+        out[k] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
+                  "frac": ach / pk["hbm"], "ms_per_batch": ms, "bytes_per_batch": b,
+                  "bytes": what, "peak_src": pk["src"] + " copy GB/s"}
+    if "depth_sort" in out:
+        out["depth_sort"]["keys_per_s"] = V / (bst["depth_sort"] / 1e3)
+    if "lists" in out:
+        out["lists"]["tile_keys_per_s"] = K / ((bst["lists"] + bst["tile_scan"]) / 1e3)
+        out["lists"]["ms_per_batch_note"] = "block counts, tile scan and block lists"
+    flop = alpha_evals * EVAL_FLOP
+    ach = flop / blend_s_total / 1e12
+    peak = fp32_peak_tflops(pk["sm_mhz"])
+    out["blend"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "ms_per_batch": blend_s_total * 1e3 / steps,
+                    "work": "evaluations reaching alpha >= 1/255 at a pixel still compositing "
+                            "x 20 FLOP"}
+    return out
 
 
 def timed_batches(sc, cams_list, ts_list, outs_list, masked, flush, stream, stages=None):
@@ -430,13 +572,14 @@ def run_ours(args):
         pk = peaks()
         ach = ep * EVAL_FLOP / blend_s / 1e12
         peak = fp32_peak_tflops(pk["sm_mhz"])
+        prof, prof_src = profiled_blend_counters()
         res["roofline"] = {
             "bound": "alu", "kernel": "k_blend_persist", "achieved": ach, "peak": peak,
             "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": BLEND_PERSIST_DRAM_BYTES_PER_FRAME * B,
-            "traffic_src": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 8-frame "
-                           "launch (profiles/k_blend_persist_batched_1352x1014.md), per frame "
-                           f"x {B} frames per launch",
+            "traffic": prof["dram_bytes_per_frame"] * B if prof else None,
+            "traffic_src": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                            f"{prof['frames']}-frame launch, per frame x {B} frames per launch: "
+                            + prof_src) if prof else prof_src,
             "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {pk['sm_mhz']:.0f} MHz",
             "work": "(Gaussian, pixel) evaluations reaching alpha >= 1/255 at a pixel still "
                     "compositing (the evaluations every blend order makes) x 20 FLOP, counted "
@@ -445,10 +588,10 @@ def run_ours(args):
             "blend_ms_per_batch": blend_s * 1e3 / len(steps),
             "evals_per_frame": ev / frames_done, "tests_per_frame": te / frames_done,
             "alpha_pass_evals_per_frame": ep / frames_done,
-            "issue_active": BLEND_PERSIST_ISSUE_ACTIVE,
-            "issue_src": "ncu smsp__issue_active of k_blend_persist<8, 4> on an 8-frame batch "
-                         "(profiles/k_blend_persist_batched_1352x1014.md): the kernel is "
-                         "bound by instruction issue, not by the FP32 pipes"}
+            "issue_active": prof["issue_active"] if prof else None,
+            "warp_instructions_per_frame": prof.get("warp_instructions_per_frame") if prof
+            else None,
+            "issue_src": prof_src}
         res["batch_stages_ms"] = bst
         # per-kernel profile on single renders of the same frames
         out1 = outs[0]
@@ -468,6 +611,8 @@ def run_ours(args):
         # sort (with its segment scan and compaction) and the list build in keys/s, the
         # blend in Gaussian-pixel evaluations/s
         bc = sc.batch_counts()
+        res["per_kernel_roofline"] = batch_stage_roofline(
+            bst, bc, scene.n, scene.sh_degree, B, True, steps[0][0], ep, blend_s, len(steps))
         res["batch_rates"] = {
             "preprocess_gbs": B * bytes_mean["preprocess"] / (bst["preprocess"] / 1e3) / 1e9,
             "depth_sort_keys_per_s": bc["n_visible"] / (bst["depth_sort"] / 1e3),
@@ -488,24 +633,42 @@ def comparisons(sc, cams, times, flush, stream):
     res = {}
     fr = frame_list(24, 3)
 
-    def single(scene_obj, masked, frames, tight=False, flush_buf=flush):
+    def single(scene_obj, masked, frames, tight=False, flush_buf=flush, temporal_cull=True,
+               counts=False):
+        kw = dict(use_mask=masked, out=out, tight=tight, temporal_cull=temporal_cull)
         # warm-up over every timed frame, so no workspace grows inside the timed renders
         for k in frames:
-            scene_obj.render(cams[k], float(times[k]), use_mask=masked, out=out, tight=tight)
+            scene_obj.render(cams[k], float(times[k]), **kw)
         ms = []
         for k in frames:
             _flush(flush_buf)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            scene_obj.render(cams[k], float(times[k]), use_mask=masked, out=out, tight=tight)
+            scene_obj.render(cams[k], float(times[k]), **kw)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        return dict(fps=len(frames) / (sum(ms) / 1e3), ms_per_frame=sum(ms) / len(frames))
+        r = dict(fps=len(frames) / (sum(ms) / 1e3), ms_per_frame=sum(ms) / len(frames))
+        if counts:
+            # per frame: Gaussians through the mask gate, visible ones, tile-list entries
+            st = []
+            for k in frames[:6]:
+                _, f_ = scene_obj.render(cams[k], float(times[k]), keep_frame=True, **kw)
+                st.append(f_.stats())
+                f_.release()
+            for f_ in ("n_active", "n_visible", "n_keys"):
+                r[f_ + "_per_frame"] = float(np.mean([x[f_] for x in st]))
+            r["active_fraction"] = r["n_active_per_frame"] / scene_obj.n
+        return r
 
-    res["single_masked"] = single(sc, True, fr)
-    res["single_unmasked"] = single(sc, False, fr)
+    # the filter (masks) and the exact temporal cull, each on and off (the paper's Table 3
+    # rows: masked = filter on; unmasked = filter off; no temporal cull = a renderer without
+    # the a < 1/255 cull, as vanilla 4DGS renders)
+    res["single_masked"] = single(sc, True, fr, counts=True)
+    res["single_unmasked"] = single(sc, False, fr, counts=True)
+    res["single_unmasked_no_temporal_cull"] = single(sc, False, fr, temporal_cull=False,
+                                                     counts=True)
     # the same frames with the alpha-tight tile sets (same images, shorter lists)
     res["single_masked_tight"] = single(sc, True, fr, tight=True)
     res["single_unmasked_tight"] = single(sc, False, fr, tight=True)
@@ -558,8 +721,17 @@ def comparisons(sc, cams, times, flush, stream):
     kt = scenes.keyframe_times()
     sc2 = fdgs.Scene.from_host(big)
     sc2.set_active_mask(torch.as_tensor(scenes.keyframe_masks(big, kt)).cuda(), kt)
-    res["unpruned_masked"] = dict(single(sc2, True, fr[:12]), n_gaussians=big.n)
-    res["unpruned_unmasked"] = dict(single(sc2, False, fr[:12]), n_gaussians=big.n)
+    res["unpruned_masked"] = dict(single(sc2, True, fr[:12], counts=True), n_gaussians=big.n)
+    res["unpruned_unmasked"] = dict(single(sc2, False, fr[:12], counts=True), n_gaussians=big.n)
+    res["unpruned_unmasked_no_temporal_cull"] = dict(
+        single(sc2, False, fr[:12], temporal_cull=False, counts=True), n_gaussians=big.n)
+    res["speedups"] = {
+        "pruned_masked_vs_unpruned_no_cull_single": res["single_masked"]["fps"]
+        / res["unpruned_unmasked_no_temporal_cull"]["fps"],
+        "unpruned_masked_vs_unpruned_no_cull_single": res["unpruned_masked"]["fps"]
+        / res["unpruned_unmasked_no_temporal_cull"]["fps"],
+        "note": "context for the paper's 9x raster speed-up of 4DGS-1K over 4DGS (Sec. 1, "
+                "Table 3 rows a and e), on synthetic scenes of the same sizes"}
     # the same scene in batches of 64 frames (the headline's frame walk)
     B = 64
     outs = [torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device="cuda")
@@ -703,6 +875,10 @@ def finetune_timing(iters=1000, prune_ratio=0.9, lr_scale=0.3):
 
 
 def backward_timing(sc, cams, times, flush, stream, n_frames=6, tight=False):
+    """Forward + backward of the L1 loss against a render of the scene with its means moved
+    by N(0, 0.01): forward and backward ms per frame (CUDA events), the backward split into
+    the reverse replay (k_blend_bwd) and the per-Gaussian chain (stage events), then one
+    counting pass over the same frames for the replay's evaluations and atomics."""
     import torch
 
     from paper_2503_16422_gb300 import fdgs
@@ -713,16 +889,19 @@ def backward_timing(sc, cams, times, flush, stream, n_frames=6, tight=False):
     target_scene = fdgs.Scene(fdgs.SceneTensors(pert, p.logscale4, p.q_left, p.q_right,
                                                 p.opacity_logit, p.sh, p.sh_degree))
     grads = fdgs.SceneTensors(*[torch.zeros_like(x) for x in p.list()], p.sh_degree)
-    fwd_ms, bwd_ms = [], []
-    for k in frame_list(n_frames, 40):
+    frames = frame_list(n_frames, 40)
+    targets = {k: target_scene.render(cams[k], float(times[k]), use_mask=False) for k in frames}
+    target_scene.close()
+    fwd_ms, bwd_ms, rep_ms, gau_ms = [], [], [], []
+    sc.profile(1)
+    for k in frames:
         cam, t = cams[k], float(times[k])
-        target = target_scene.render(cam, t, use_mask=False)
         _flush(flush)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         img, fr = sc.render(cam, t, use_mask=False, keep_frame=True, tight=tight)
         e1.record(stream)
-        dL = torch.sign(img - target) / img.numel()
+        dL = torch.sign(img - targets[k]) / img.numel()
         e1b = torch.cuda.Event(enable_timing=True)
         e1b.record(stream)
         sc.render_backward(fr, dL, grads=grads)
@@ -730,11 +909,43 @@ def backward_timing(sc, cams, times, flush, stream, n_frames=6, tight=False):
         e2.synchronize()
         fwd_ms.append(e0.elapsed_time(e1))
         bwd_ms.append(e1b.elapsed_time(e2))
+        st = sc.profile_read()[0]
+        rep_ms.append(st["backward_blend"])
+        gau_ms.append(st["backward_gauss"])
         fr.release()
-    target_scene.close()
+    # counting pass (a slower kernel variant, untimed)
+    sc.profile(2)
+    ev = [0, 0, 0]
+    for k in frames:
+        cam, t = cams[k], float(times[k])
+        img, fr = sc.render(cam, t, use_mask=False, keep_frame=True, tight=tight)
+        dL = torch.sign(img - targets[k]) / img.numel()
+        sc.render_backward(fr, dL, grads=grads)
+        c = sc.blend_counts()
+        ev = [a + b for a, b in zip(ev, c)]
+        fr.release()
+    sc.profile(0)
+    pk = peaks()
+    rep_s = sum(rep_ms) / 1e3
+    valid = ev[1]
+    peak = fp32_peak_tflops(pk["sm_mhz"])
+    ach = valid * BWD_EVAL_FLOP / rep_s / 1e12 if rep_s > 0 else None
     return dict(frames=n_frames, scene="pruned 200k, unmasked, 1352x1014",
                 tile_sets="alpha-tight" if tight else "3-sigma squares",
-                forward_ms=float(np.mean(fwd_ms)), backward_ms=float(np.mean(bwd_ms)))
+                forward_ms=float(np.mean(fwd_ms)), backward_ms=float(np.mean(bwd_ms)),
+                reverse_replay_ms=float(np.mean(rep_ms)),
+                per_gaussian_chain_ms=float(np.mean(gau_ms)),
+                replay_evals_per_frame=ev[0] / n_frames,
+                replay_blended_evals_per_frame=valid / n_frames,
+                replay_atomics_per_frame=ev[2] / n_frames,
+                replay_blended_evals_per_s=valid / rep_s if rep_s > 0 else None,
+                replay_atomics_per_s=ev[2] / rep_s if rep_s > 0 else None,
+                roofline={"bound": "alu", "kernel": "k_blend_bwd", "achieved": ach,
+                          "peak": peak, "unit": "TFLOP/s",
+                          "frac": ach / peak if ach is not None else None,
+                          "work": f"blended (Gaussian, pixel) entries of the replay x "
+                                  f"{BWD_EVAL_FLOP} FP32 FLOP; time = stage events around "
+                                  "the replay"})
 
 
 def score_timing(stream):
@@ -761,15 +972,6 @@ def score_timing(stream):
     return dict(n_gaussians=s.n, renders=n, resolution="1352x1014", batch=8,
                 wall_s=walls[8], ms_per_render=walls[8] * 1e3 / n, kept=kept,
                 per_frame_path_wall_s=walls[1])
-
-
-# DRAM bytes the persistent blend moves per frame of a batch at 1352x1014 on the 200k pruned
-# scene, from one ncu capture of an 8-frame launch of k_blend_persist<8, 4> (42.9 MB read +
-# 76.9 MB written); to be re-captured whenever the blend kernel changes.
-BLEND_PERSIST_DRAM_BYTES_PER_FRAME = (42894848 + 76912896) / 8
-# Fraction of cycles the persistent blend issues an instruction (ncu smsp__issue_active, same
-# capture).
-BLEND_PERSIST_ISSUE_ACTIVE = 0.879
 
 
 def launches_per_batch():
@@ -824,6 +1026,91 @@ def run_only(args):
     print(json.dumps({"only": args.only, "impl": "ours", "data": "synthetic", **res}))
 
 
+def active_fraction(masks, kt, frames, n):
+    """Mean fraction of the Gaussians the key-frame filter lets through at the given frames
+    (the union of the two nearest key-frames' rows, as the renderer reads them)."""
+    from paper_2503_16422_gb300 import scenes
+    times = scenes.frame_times()
+    kt = np.asarray(kt, np.float64)
+    rows = np.unpackbits(np.asarray(masks, np.uint8), axis=1, bitorder="little")[:, :n] > 0
+    fr = []
+    for k in frames:
+        t = float(times[k])
+        l = max([i for i in range(len(kt)) if kt[i] <= t] or [0])
+        r = min(l + 1, len(kt) - 1)
+        fr.append(float((rows[l] | rows[r]).mean()))
+    return float(np.mean(fr))
+
+
+def reference_arm(args):
+    """The oracle timed on the host cores (the reference arm of this benchmark): each step is
+    a bounded sample of one frame of the headline workload (the per-Gaussian stage of every
+    Gaussian, then randomly chosen tiles for about 3 s), extrapolated to the whole frame.
+    ms_per_step is the wall time a step actually took; value is the extrapolated FPS."""
+    scene, kt, masks = pruned_masked()
+    for w in range(args.warmup):
+        cpu_oracle_frame(scene, kt, masks, frame=frame_list(1, 200 + w)[0], budget_s=0.5,
+                         min_tiles=8)
+    secs, walls, tiles = [], [], []
+    cores = None
+    for i in range(max(args.steps, 1)):
+        s_, desc, cores, det = cpu_oracle_frame(scene, kt, masks, frame=frame_list(1, i)[0],
+                                                budget_s=3.0)
+        secs.append(s_)
+        walls.append(det["wall_s"])
+        tiles.append(det["tiles"])
+    fps = len(secs) / sum(secs)
+    line = {"metric": METRIC, "value": fps, "unit": "FPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(walls) / len(walls),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": workload_config(scene, kt, args.batch), "impl": "reference",
+            "extrapolated": {
+                "what": "value = frames per second of the whole frame, extrapolated from each "
+                        "step's sample: the per-Gaussian stage of all Gaussians plus a random "
+                        "sample of tiles, the tile time scaled by tiles per frame / tiles "
+                        "blended",
+                "tiles_blended_per_step": float(np.mean(tiles)), "tiles_per_frame":
+                    det["tiles_total"], "extrapolated_ms_per_frame": 1e3 * float(np.mean(secs)),
+                "wall_ms_per_step": 1e3 * float(np.mean(walls)),
+                "frames": len(secs), "step": "one frame of the workload, sampled"},
+            "cpu_baseline": {"value": fps, "unit": "FPS", "cores": cores, "kind": "oracle",
+                             "sample": "per step: " + desc},
+            "e2e": {"value": fps, "unit": "FPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baselines(scene, kt, masks, sc):
+    """The oracle on the host cores: the headline frame on all cores (with the parity counts
+    of that frame against the GPU), on one core, and a frame of the unpruned 3M scene."""
+    import torch
+
+    from paper_2503_16422_gb300 import scenes
+    s_, desc, cores, det = cpu_oracle_frame(scene, kt, masks)
+    out = {"value": 1.0 / s_, "unit": "FPS", "cores": cores, "kind": "oracle", "sample": desc}
+    try:
+        out_par = bench_frame_parity(sc, scene, det)
+    except Exception as e:  # noqa: BLE001
+        out_par = {"error": repr(e)}
+    s1, d1, c1, _ = cpu_oracle_frame(scene, kt, masks, frame=150, budget_s=6.0, threads=1)
+    out["one_core"] = {"value": 1.0 / s1, "unit": "FPS", "cores": c1, "sample": d1}
+    try:
+        big = scenes.unpruned_scene()
+        bkt = scenes.keyframe_times()
+        bm = scenes.keyframe_masks(big, bkt)
+        s3, d3, c3, _ = cpu_oracle_frame(big, bkt, bm, frame=150, budget_s=6.0)
+        out["unpruned_3M"] = {"value": 1.0 / s3, "unit": "FPS", "cores": c3, "sample": d3,
+                              "extrapolation": "one sampled frame of the 300-frame sequence "
+                                               "stands for every frame"}
+        del big, bm
+    except Exception as e:  # noqa: BLE001
+        out["unpruned_3M"] = {"error": repr(e)}
+    torch.set_num_threads(cores)
+    return out, out_par
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -832,43 +1119,27 @@ def main():
             run_only(args)
         return
     if args.impl == "reference":
-        if rank != 0:
-            return
-        scene, kt, masks = pruned_masked()
-        for w in range(args.warmup):
-            cpu_oracle_frame(scene, kt, masks, frame=frame_list(1, 200 + w)[0], budget_s=1.0)
-        secs = []
-        for i in range(max(args.steps, 1)):
-            s_, desc, cores = cpu_oracle_frame(scene, kt, masks, frame=frame_list(1, i)[0],
-                                               budget_s=4.0)
-            secs.append(s_)
-        fps = len(secs) / sum(secs)
-        line = {"metric": METRIC, "value": fps, "unit": "FPS", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / fps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic",
-                "config": workload_config(scene, kt, args.batch), "impl": "reference",
-                "cpu_baseline": {"value": fps, "unit": "FPS", "cores": cores, "kind": "oracle",
-                                 "sample": "per step: one frame of the batched workload, "
-                                           + desc},
-                "e2e": {"value": fps, "unit": "FPS", "h2d_bytes_per_step": 0,
-                        "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        if rank == 0:
+            reference_arm(args)
         return
     value, ms, res, scene, kt, masks, world, rank = run_ours(args)
     if rank != 0:
         return
     lat = res["lat"]
+    cfg = workload_config(scene, kt, args.batch)
+    cfg["active_fraction"] = active_fraction(
+        masks, kt, [k for st in rank_requests(0, args.steps, args.batch) for k in st], scene.n)
     line = {"metric": METRIC, "value": value, "unit": "FPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config(scene, kt, args.batch),
+            "data": "synthetic", "config": cfg,
             "roofline": res["roofline"], "clocks": res["clocks"], "e2e": res["e2e"],
             "gpu_launches": launches_per_batch() * args.steps,
             "latency_ms": {"p50": float(np.percentile(lat, 50)),
                            "p99": float(np.percentile(lat, 99))},
             "batch_shape": {k: v for k, v in res["batch_shape"].items() if k != "latency_ms"},
             "batch_stages_ms": res["batch_stages_ms"],
+            "per_kernel_roofline": res["per_kernel_roofline"],
             "batch_rates": res["batch_rates"],
             "single_frame_stages_ms": res["stage_ms"], "stage_gbs": res["stage_gbs"],
             "stage_rates": res["stage_rates"],
@@ -879,9 +1150,12 @@ def main():
     if "comparisons" in res:
         line["comparisons"] = res["comparisons"]
     if not args.no_cpu_baseline:
-        s_, desc, cores = cpu_oracle_frame(scene, kt, masks)
-        line["cpu_baseline"] = {"value": 1.0 / s_, "unit": "FPS", "cores": cores,
-                                "kind": "oracle", "sample": desc}
+        from paper_2503_16422_gb300 import fdgs
+        import torch
+        sc = fdgs.Scene.from_host(scene)
+        sc.set_active_mask(torch.as_tensor(masks).cuda(), kt)
+        line["cpu_baseline"], line["parity_exempt"] = cpu_baselines(scene, kt, masks, sc)
+        sc.close()
     print(json.dumps(line))
 
 

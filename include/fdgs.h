@@ -257,11 +257,13 @@ int fdgs_set_sh_codebook(fdgs_scene *scene, const float *codebook_dev, int n_cod
 int fdgs_set_batch_list_capacity(fdgs_scene *scene, uint64_t entries);
 
 /* Last batch: visible Gaussians and (tile, Gaussian) pairs summed over its requests (the
- * entries the tiles composite from their block lists). The batched lists use, per Gaussian,
- * the 3-sigma tile square intersected with the tiles its alpha >= 1/255 ellipse can reach,
- * so n_keys is at most the per-request renders' total (images are identical). Either pointer may be NULL. FDGS_ERR_STATE if no batch was
- * rendered. */
-int fdgs_batch_counts(fdgs_scene *scene, uint64_t *n_visible, uint64_t *n_keys);
+ * entries the tiles composite from their block lists), and the block-list entries the lists
+ * hold (one per (Gaussian, 4x4 tile block) pair). The batched lists use, per Gaussian, the
+ * 3-sigma tile square intersected with the tiles its alpha >= 1/255 ellipse can reach, so
+ * n_keys is at most the per-request renders' total (images are identical). Any pointer may
+ * be NULL. FDGS_ERR_STATE if no batch was rendered. */
+int fdgs_batch_counts(fdgs_scene *scene, uint64_t *n_visible, uint64_t *n_keys,
+                      uint64_t *n_block_entries);
 
 /* Last batch, request req (for tests and tools; synchronises the device): its tile lists in
  * the layout of fdgs_frame_export, copied to HOST buffers.
@@ -287,6 +289,32 @@ int fdgs_batch_tile_lists(fdgs_scene *scene, int req, uint32_t *tile_ranges_host
 int fdgs_variation_score(fdgs_scene *scene, const fdgs_camera *cams, int n_cam,
                          const float *ts, int n_t, int batch, float *score_out_dev,
                          fdgs_stream stream);
+
+/*
+ * The scores of the ablation of the Spatial-Temporal Variation Score (Table 4; their formulas
+ * are in the supplement's "Variant Settings"), each in the per-t reading of Eq. 7, with w_i,
+ * f_i(t) and gamma_i as in fdgs_variation_score:
+ *   FDGS_SCORE_FULL             (f, the paper's score)  sum_{t,cam} w_i f_i(t) gamma_i
+ *   FDGS_SCORE_SPATIAL          (b, spatial only)       sum_{t,cam} w_i
+ *   FDGS_SCORE_TEMPORAL         (c, temporal only)      sum_t f_i(t) gamma_i  (nothing is
+ *                                                       rendered; the cameras are ignored)
+ *   FDGS_SCORE_FIRST_DERIVATIVE (d)                     sum_{t,cam} w_i f1_i(t) gamma_i, f1 with
+ *                               p'_i(t) = -(t - mu_t) / Sigma_t p_i(t) in place of p''_i(t)
+ *   FDGS_SCORE_SIGMA_T          (e)                     sum_{t,cam} w_i Sigma_t,i gamma_i
+ */
+enum {
+  FDGS_SCORE_FULL = 0,
+  FDGS_SCORE_SPATIAL = 1,
+  FDGS_SCORE_TEMPORAL = 2,
+  FDGS_SCORE_FIRST_DERIVATIVE = 3,
+  FDGS_SCORE_SIGMA_T = 4
+};
+
+/* fdgs_variation_score for one of the FDGS_SCORE_* variants (same arguments, same output
+ * layout; score_out_dev is OVERWRITTEN). FDGS_ERR_INVALID for an unknown variant. */
+int fdgs_variation_score_variant(fdgs_scene *scene, const fdgs_camera *cams, int n_cam,
+                                 const float *ts, int n_t, int batch, int variant,
+                                 float *score_out_dev, fdgs_stream stream);
 
 /*
  * Pruning keep-set (Sec. 4.2.1 "Pruning"): ranks the n scores by ascending (score, index)
@@ -323,22 +351,26 @@ int fdgs_select_keep_noalloc(const float *score_dev, int64_t n, float prune_rati
                              uint8_t *keep_out_dev, fdgs_stream stream);
 
 /*
- * Stage profiling of the scene's subsequent fdgs_render calls. flags bit0: record CUDA
- * events on the render stream between the stages (FDGS_PROFILE_STAGES of them, in order:
- * preprocess, depth_sort, gather_scan, host_sync (the one mid-frame wait for the key count),
- * tile_scan (tile ranges and the blend's longest-first tile order), emit, tile_sort,
- * blend); bit1: count the
- * (Gaussian, pixel) evaluations of the blend (a slower kernel variant; use it in an
- * untimed pass). 0 turns profiling off.
+ * Stage profiling of the scene's subsequent fdgs_render and fdgs_render_backward calls.
+ * flags bit0: record CUDA events on the stream between the stages (FDGS_PROFILE_STAGES of
+ * them, in order: preprocess, depth_sort, gather_scan, host_sync (the one mid-frame wait for
+ * the key count), tile_scan (tile ranges and the blend's longest-first tile order), emit,
+ * tile_sort, blend, written by fdgs_render; then backward_blend (the reverse replay) and
+ * backward_gauss (the chain to the 4D parameters), written by fdgs_render_backward);
+ * bit1: count the (Gaussian, pixel) evaluations of the blend or of the reverse replay (slower
+ * kernel variants; use them in an untimed pass). 0 turns profiling off.
  */
-#define FDGS_PROFILE_STAGES 8
+#define FDGS_PROFILE_STAGES 10
 int fdgs_profile_enable(fdgs_scene *scene, int flags);
 
 /* Stage times in milliseconds of the last profiled render, and blend_counts[3] of the last
  * counted render or batch: (Gaussian, pixel) evaluations executed, footprint culling tests
  * executed, and evaluations that reached alpha >= 1/255 at a pixel still compositing (the
  * blended ones and the ones that stopped a pixel: the evaluations any blend order must
- * make, whatever its culling). Either pointer may be NULL. Synchronises the device. */
+ * make, whatever its culling). After a counted fdgs_render_backward, blend_counts holds the
+ * reverse replay's counts instead: entry evaluations at pixels whose replay reached them
+ * (list position below n_contrib), the blended ones among them, and the gradient atomics
+ * issued. Either pointer may be NULL. Synchronises the device. */
 int fdgs_profile_read(fdgs_scene *scene, float *stage_ms, uint64_t *blend_counts);
 
 /* How single-frame renders (fdgs_render) build the per-tile lists, process-wide. 1: emit one (tile, depth-rank) key

@@ -22,6 +22,10 @@ Parity status per function (what pins each one is in tests/test_oracle_pins.py):
   gradients ............................... pinned (float64 central finite differences)
   variation_scores, keep_set .............. pinned (weight identity, factor range, gamma
                                             range, permutation invariance, R1 = R2 at one t)
+  score variants of the ablation (Table 4) . pinned (each rendered variant against the spatial
+  temporal_first_derivative                 score, Sigma_t = exp(2 l_t) at identity rotations,
+                                            the temporal-only score's independence of the
+                                            views, finite differences for p^(1))
 tests/test_oracle_mutations.py plants plausible mistakes in these functions and checks that
 the pins catch each one.
 No values printed in the paper can pin any of them: the paper gives no worked example, so
@@ -31,5 +35,6 @@ from .fdgs_oracle import *  # noqa: F401,F403
 from .fdgs_oracle import (ALPHA_MAX, ALPHA_MIN, T_STOP, TILE, Params, active_from_masks,  # noqa
                           blend_tile, condition_on_time, covariance_4d, gradients, keep_set,
                           keyframe_pair, preprocess, render, render_image, rotation_4d,
-                          sh_basis, temporal_second_derivative, tile_list, tile_lists,
-                          variation_factor, variation_scores, volume_gamma)
+                          sh_basis, temporal_first_derivative, temporal_second_derivative,
+                          tile_list, tile_lists, variation_factor, variation_scores,
+                          volume_gamma, SCORE_VARIANTS)

@@ -480,10 +480,24 @@ def temporal_second_derivative(mean4, cov4, t):
     return (dt * dt / (s_tt * s_tt) - 1.0 / s_tt) * p
 
 
-def variation_factor(mean4, cov4, t):
-    """Per-timestamp term of S^TV (Eq. 6): 1 / (0.5 tanh(|p^(2)(t)|) + 0.5), in (1, 2]."""
-    p2 = temporal_second_derivative(mean4, cov4, t)
-    return 1.0 / (0.5 * torch.tanh(torch.abs(p2)) + 0.5)
+def temporal_first_derivative(mean4, cov4, t):
+    """p^(1)(t) = -((t - mu_t) / Sigma_t) p(t), the time derivative of Eq. 3's p(t): the
+    quantity that replaces p^(2) in variant (d) of the score ablation (Table 4 and the
+    supplement's variant settings)."""
+    s_tt = cov4[..., 3, 3]
+    dt = t - mean4[..., 3]
+    p = torch.exp(-0.5 * dt * dt / s_tt)
+    return -(dt / s_tt) * p
+
+
+def variation_factor(mean4, cov4, t, derivative=2):
+    """Per-timestamp term of S^TV (Eq. 6): 1 / (0.5 tanh(|p^(2)(t)|) + 0.5), in (1, 2];
+    ``derivative=1`` puts p^(1) in place of p^(2) (score variant (d))."""
+    if derivative == 1:
+        pk = temporal_first_derivative(mean4, cov4, t)
+    else:
+        pk = temporal_second_derivative(mean4, cov4, t)
+    return 1.0 / (0.5 * torch.tanh(torch.abs(pk)) + 0.5)
 
 
 def volume_gamma(logscale4, beta=0.1, q=0.9):
@@ -498,7 +512,10 @@ def volume_gamma(logscale4, beta=0.1, q=0.9):
     return torch.clamp(V / p90, 0.0, 1.0) ** beta
 
 
-def variation_scores(scene, cams, ts, reading="R1", return_parts=False):
+SCORE_VARIANTS = ("full", "spatial", "temporal", "first_derivative", "sigma_t")
+
+
+def variation_scores(scene, cams, ts, reading="R1", return_parts=False, variant="full"):
     """Spatial-Temporal Variation Score over renders at timestamps ``ts`` from cameras
     ``cams`` (no temporal filter: scoring precedes it).
 
@@ -506,7 +523,17 @@ def variation_scores(scene, cams, ts, reading="R1", return_parts=False):
     (Eq. 6); gamma_i (Sec. 4.2.1). Reading R1 (the per-t product of Eq. 7):
     S_i = sum_{t,v} S^S_i(t,v) f_i(t) gamma_i. Reading R2 (S^T already summed over t):
     S_i = (gamma_i sum_t f_i(t)) (sum_{t,v} S^S_i(t,v)). The two agree for a single t.
+
+    ``variant`` selects the score of one row of the ablation (Table 4; definitions in the
+    supplement's "Variant Settings"), each in the per-t reading R1:
+      "full"             (f, ours)  sum_{t,v} S^S_i(t,v) f_i(t) gamma_i
+      "spatial"          (b)        sum_{t,v} S^S_i(t,v)
+      "temporal"         (c)        sum_t f_i(t) gamma_i            (no render needed)
+      "first_derivative" (d)        sum_{t,v} S^S_i(t,v) f1_i(t) gamma_i, f1 with p^(1)
+      "sigma_t"          (e)        sum_{t,v} S^S_i(t,v) Sigma_t,i gamma_i
     """
+    if variant not in SCORE_VARIANTS:
+        raise ValueError(f"variant must be one of {SCORE_VARIANTS}")
     P = Params.from_scene(scene)
     with torch.no_grad():
         cov4 = covariance_4d(P.logscale4, P.q_left, P.q_right)
@@ -517,11 +544,22 @@ def variation_scores(scene, cams, ts, reading="R1", return_parts=False):
         for t in ts:
             f = variation_factor(P.mean4, cov4, float(t))
             FT += f
+            if variant == "temporal":
+                S += f * gamma
+                continue
+            if variant == "spatial":
+                g_t = torch.ones_like(f)
+            elif variant == "first_derivative":
+                g_t = variation_factor(P.mean4, cov4, float(t), derivative=1) * gamma
+            elif variant == "sigma_t":
+                g_t = cov4[:, 3, 3] * gamma
+            else:
+                g_t = f * gamma
             for cam in cams:
                 w = render(P, cam, float(t), None, weights=True)["w_sum"]
-                S += w * f * gamma
+                S += w * g_t
                 SS += w
-        if reading == "R2":
+        if reading == "R2" and variant == "full":
             S = gamma * FT * SS
     if return_parts:
         return S.numpy(), dict(gamma=gamma.numpy(), spatial=SS.numpy(), ftsum=FT.numpy())

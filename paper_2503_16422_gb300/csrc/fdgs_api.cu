@@ -138,7 +138,9 @@ struct BatchPlan {
   const uint64_t *vis_sorted = nullptr;    // sorted depth keys of the last batch (device)
   bool weighted = false;                   // next runs: a weighted pass (eager, no graph)
   float *score_out = nullptr;              // score pass: accumulate into this (else null)
+  int score_variant = 0;                   // score pass: fdgs_score_variant
   const float *gamma = nullptr;
+  const double *sig_t = nullptr;           // score pass: temporal variances (FP64)
   bool mark = false;                       // mask pass: requests carry mark_row
   Buf wsum, stop;                          // weighted passes: per-slot weights, stop flags
   const float *sh_cb = nullptr;            // codebook pointers captured in the graph
@@ -196,7 +198,8 @@ struct fdgs_scene {
   Buf aux[6];     // score pass / keep-set buffers: 0 keys, 1 gamma, 2 sort scratch,
                   // 3 device scalar, 4 score-pass image, 5 key-frame mask word row
   int prof = 0;   // profiling flags (fdgs_profile_enable)
-  cudaEvent_t ev[FDGS_PROFILE_STAGES + 1] = {};
+  // stage events: [0..8] bound the forward's eight stages, [9..11] the backward's two
+  cudaEvent_t ev[FDGS_PROFILE_STAGES + 2] = {};
   Buf evals;      // u64[3] blend evaluations, culling tests, alpha >= 1/255 evaluations
   const float *sh_cb = nullptr;        // borrowed SH codebook (fdgs_set_sh_codebook) or null
   const uint16_t *sh_code = nullptr;
@@ -684,7 +687,9 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.w_sum = p.weighted ? p.wsum.as<float>() : nullptr;
   b.stop_mark = p.weighted ? p.stop.as<uint32_t>() : nullptr;
   b.gamma = p.gamma;
+  b.sig_t = p.sig_t;
   b.score = p.score_out;
+  b.score_variant = p.score_variant;
   b.mark = p.mark ? 1 : 0;
   L.wsum_len = p.rn;
   L.diff_bytes = p.diff_ints * 4;
@@ -704,7 +709,9 @@ int plan_capture(fdgs_scene *s, BatchPlan &p) {
   b.w_sum = nullptr;   // a graph never holds a weighted pass (they run eagerly)
   b.stop_mark = nullptr;
   b.gamma = nullptr;
+  b.sig_t = nullptr;
   b.score = nullptr;
+  b.score_variant = 0;
   b.mark = 0;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeRelaxed));
@@ -977,11 +984,18 @@ int fdgs_render_backward(fdgs_scene *s, fdgs_frame *f, const float *dL_drgb_dev,
   ba.n_contrib = ws.nc.as<uint32_t>();
   ba.g2d = ws.g2d.as<float>();
   ba.order = ws.order.as<uint32_t>();   // the forward's longest-first tile order
+  if ((s->prof & 2) && s->evals.p) {
+    CK(cudaMemsetAsync(s->evals.p, 0, 24, st));
+    ba.evals = s->evals.as<unsigned long long>();
+  }
   const uint32_t rmask = (uint32_t)((1ull << m.rb) - 1);
+  const bool prof = (s->prof & 1) && s->ev[0];
+  if (prof) CK(cudaEventRecord(s->ev[9], st));
   if (m.key64)
     launch_blend_bwd<uint64_t>(ba, (const uint64_t *)m.keys, rmask, st);
   else
     launch_blend_bwd<uint32_t>(ba, (const uint32_t *)m.keys, rmask, st);
+  if (prof) CK(cudaEventRecord(s->ev[10], st));
   PreBwdArgs pa;
   pa.mean4 = (const float4 *)s->d.mean4;
   pa.ls4 = (const float4 *)s->d.logscale4;
@@ -1003,6 +1017,7 @@ int fdgs_render_backward(fdgs_scene *s, fdgs_frame *f, const float *dL_drgb_dev,
   pa.g_op = g_opacity_logit;
   pa.g_sh = g_sh;
   launch_preprocess_bwd(pa, st);
+  if (prof) CK(cudaEventRecord(s->ev[11], st));
   CK(cudaGetLastError());
   return FDGS_OK;
 }
@@ -1217,12 +1232,16 @@ int fdgs_set_batch_list_capacity(fdgs_scene *s, uint64_t entries) {
   return FDGS_OK;
 }
 
-int fdgs_batch_counts(fdgs_scene *s, uint64_t *n_visible, uint64_t *n_keys) {
+int fdgs_batch_counts(fdgs_scene *s, uint64_t *n_visible, uint64_t *n_keys,
+                      uint64_t *n_block_entries) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   if (!s->plan) return fail(FDGS_ERR_STATE, "no batch has been rendered");
   const BatchPlan &p = *s->plan;
   if (n_visible) *n_visible = p.h_ctr[BC_NVIS];
   if (n_keys) *n_keys = (uint64_t)p.h_ctr[BC_NKEYS_LO] | ((uint64_t)p.h_ctr[BC_NKEYS_HI] << 32);
+  if (n_block_entries)
+    *n_block_entries =
+        (uint64_t)p.h_ctr[BC_NBKEYS_LO] | ((uint64_t)p.h_ctr[BC_NBKEYS_HI] << 32);
   return FDGS_OK;
 }
 
@@ -1289,17 +1308,27 @@ int fdgs_batch_tile_lists(fdgs_scene *s, int req, uint32_t *tile_ranges_host,
 
 int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, const float *ts,
                          int n_t, int batch, float *score_out_dev, fdgs_stream stream) {
+  return fdgs_variation_score_variant(s, cams, n_cam, ts, n_t, batch, FDGS_SCORE_FULL,
+                                      score_out_dev, stream);
+}
+
+int fdgs_variation_score_variant(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
+                                 const float *ts, int n_t, int batch, int variant,
+                                 float *score_out_dev, fdgs_stream stream) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   if (n_cam < 0 || n_t < 0 || batch < 1 || !score_out_dev ||
       (n_cam > 0 && !cams) || (n_t > 0 && !ts))
     return fail(FDGS_ERR_INVALID, "bad score arguments");
+  if (variant < FDGS_SCORE_FULL || variant > FDGS_SCORE_SIGMA_T)
+    return fail(FDGS_ERR_INVALID, "unknown score variant %d", variant);
   cudaStream_t st = (cudaStream_t)stream;
   const uint32_t N = (uint32_t)s->d.n;
   CK(cudaMemsetAsync(score_out_dev, 0, (size_t)N * 4, st));
   if (N == 0) return FDGS_OK;
   // gamma = clamp(V / V_p90, 0, 1)^0.1, V_p90 the nearest-rank 90th percentile
   TRY(grow(s->aux[0], (size_t)N * 4 * 2 + 16));   // volume bits, ping-pong
-  TRY(grow(s->aux[1], (size_t)N * 4));            // gamma
+  const size_t goff = ((size_t)N * 4 + 255) & ~(size_t)255;
+  TRY(grow(s->aux[1], goff + (size_t)N * 8));     // gamma, then Sigma_t (FP64)
   TRY(grow(s->aux[2], sort_scratch_bytes(N, 32)));
   TRY(grow(s->aux[3], 16));
   uint32_t *vb = s->aux[0].as<uint32_t>();
@@ -1308,7 +1337,18 @@ int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, cons
   uint32_t *vs = radix_sort<uint32_t>(vb, vb + N, s->aux[3].as<uint32_t>(), N, 0, 32,
                                       s->aux[2].p, st, s->status.as<uint32_t>());
   const uint32_t k = (uint32_t)std::max<int64_t>(1, (int64_t)ceil(0.9 * (double)N)) - 1;
-  launch_gamma((const float4 *)s->d.logscale4, N, vs, k, s->aux[1].as<float>(), st);
+  float *gamma = s->aux[1].as<float>();
+  double *sig_t = (double *)((char *)s->aux[1].p + goff);
+  launch_score_consts((const float4 *)s->d.logscale4, (const float4 *)s->d.q_left,
+                      (const float4 *)s->d.q_right, N, vs, k, gamma, sig_t, st);
+  if (variant == FDGS_SCORE_TEMPORAL) {
+    // no render: S_i = sum over t of f_i(t) gamma_i
+    for (int it = 0; it < n_t; ++it)
+      launch_score_temporal((const float4 *)s->d.mean4, sig_t, gamma, N, ts[it],
+                            score_out_dev, st);
+    CK(cudaGetLastError());
+    return FDGS_OK;
+  }
   fdgs_render_opts o{};
   o.use_mask = 0;
   o.tile_sets = 1;   // same weights as the 3-sigma squares, shorter lists
@@ -1345,11 +1385,15 @@ int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, cons
       TRY(grow(p.stop, std::max<uint64_t>(p.rn, 1) * 4));
       p.weighted = true;
       p.score_out = score_out_dev;
-      p.gamma = s->aux[1].as<float>();
+      p.score_variant = variant;
+      p.gamma = gamma;
+      p.sig_t = sig_t;
       const int rc = plan_run(s, p, st);
       p.weighted = false;
       p.score_out = nullptr;
+      p.score_variant = 0;
       p.gamma = nullptr;
+      p.sig_t = nullptr;
       TRY(rc);
     }
     return FDGS_OK;
@@ -1363,9 +1407,8 @@ int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, cons
       TRY(render_impl(s, ws, &cams[ic], ts[it], &o, s->aux[4].as<float>(), false, true, false,
                       m, st));
       launch_score_accumulate(m.sorted, ws.ctr.as<uint32_t>() + C_NVIS, m.nv, ws.wsum.as<float>(),
-                              (const float4 *)s->d.mean4, (const float4 *)s->d.logscale4,
-                              (const float4 *)s->d.q_left, (const float4 *)s->d.q_right,
-                              s->aux[1].as<float>(), ts[it], score_out_dev, st);
+                              (const float4 *)s->d.mean4, sig_t, gamma, ts[it], score_out_dev,
+                              variant, st);
       if (++done % batch == 0) CK(cudaGetLastError());
     }
   CK(cudaGetLastError());
@@ -1423,9 +1466,16 @@ int fdgs_profile_read(fdgs_scene *s, float *stage_ms, uint64_t *blend_counts) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   CK(cudaDeviceSynchronize());
   if (stage_ms) {
+    // forward stages from events 0..8, backward stages from events 9..11; zeros for a stage
+    // whose events were never recorded
     for (int i = 0; i < FDGS_PROFILE_STAGES; ++i) {
-      stage_ms[i] = 0.f;   // zeros when stage profiling was never enabled
-      if (s->ev[0]) CK(cudaEventElapsedTime(&stage_ms[i], s->ev[i], s->ev[i + 1]));
+      stage_ms[i] = 0.f;
+      if (!s->ev[0]) continue;
+      const int a = i < 8 ? i : i + 1;
+      if (cudaEventElapsedTime(&stage_ms[i], s->ev[a], s->ev[a + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        stage_ms[i] = 0.f;
+      }
     }
   }
   if (blend_counts) {

@@ -68,7 +68,9 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int &fi)
 // lane owns PX pixels of one footprint row, FW / PX apart, and sums their gradient terms
 // before the warp reduction. As in the forward, the evaluation has no branches: an entry a
 // pixel did not blend takes alpha = 0 and leaves its state unchanged.
-template <typename K, int FW, int PX>
+// kCount: also count (into a.evals) the entry evaluations at pixels whose replay has reached
+// them (list position below n_contrib), the ones that were blended, and the atomics issued.
+template <typename K, int FW, int PX, bool kCount = false>
 __global__ void __launch_bounds__(256 / PX)
 k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
   constexpr int NT = 256 / PX;
@@ -120,6 +122,7 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
     bg_dot[p] = a.bg[0] * dL0[p] + a.bg[1] * dL1[p] + a.bg[2] * dL2[p];
     acc0[p] = acc1[p] = acc2[p] = last_a[p] = lc0[p] = lc1[p] = lc2[p] = 0.f;
   }
+  uint32_t n_eval = 0, n_valid = 0, n_atomic = 0;
   const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, lane_nc);
   if (lane == 0) atomicMax(&s_max, warp_nc);
   const float fpy = (float)py;
@@ -172,15 +175,18 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
         // the exponent as in the forward, with the row terms shared by the lane's pixels
         const float dy = __fsub_rn(e0.y, fpy);
         const float b2dy = __fmul_rn(e0.w, dy);
-        const float c2dy2 = __fmul_rn(__fmul_rn(e1.x, dy), dy);
+        const float c2l = __fmaf_rn(__fmul_rn(e1.x, dy), dy, e1.y);
         float G[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         bool any = false;
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
           const float dx = __fsub_rn(e0.x, (float)(px0 + p * HW));
-          const float q = __fmaf_rn(dx, __fmaf_rn(e0.z, dx, b2dy), c2dy2);
-          const float e = __fadd_rn(q, e1.y);
-          const bool valid = pos < nc[p] && q <= 0.f && e >= kLog2AlphaMin;
+          const float e = __fmaf_rn(dx, __fmaf_rn(e0.z, dx, b2dy), c2l);
+          const bool valid = pos < nc[p] && e >= kLog2AlphaMin;
+          if (kCount) {
+            n_eval += pos < nc[p] ? 1u : 0u;
+            n_valid += valid ? 1u : 0u;
+          }
           any = any || valid;
           const float raw = ex2_approx(e);
           const float alpha = valid ? fminf(kAlphaMax, raw) : 0.f;
@@ -219,10 +225,17 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
           const float s9 = warp_sum(G[8]);
           if ((lane & 3) == 0 && s8 != 0.f) atomicAdd(&dst[fi], s8);
           if (lane == 4 && s9 != 0.f) atomicAdd(&dst[8], s9);
+          if (kCount) n_atomic += ((lane & 3) == 0 && s8 != 0.f) + (lane == 4 && s9 != 0.f);
         }
       }
       __syncwarp();                    // the list is rewritten by the next group
     }
+  }
+  if (kCount) {
+    const uint32_t e = warp_sum(n_eval), v = warp_sum(n_valid), t = warp_sum(n_atomic);
+    if (lane == 0 && e) atomicAdd(&a.evals[0], (unsigned long long)e);
+    if (lane == 0 && v) atomicAdd(&a.evals[1], (unsigned long long)v);
+    if (lane == 0 && t) atomicAdd(&a.evals[2], (unsigned long long)t);
   }
 }
 
@@ -252,7 +265,10 @@ void launch_blend_bwd(const BlendBwdArgs &a, const K *keys, uint32_t rmask, cuda
   // 8x16 warp footprints, four pixels per lane (0.66 vs 0.95 ms for one pixel per lane with
   // branches, alpha-tight frames of the 200k scene at 1352x1014, including the per-Gaussian
   // backward)
-  k_blend_bwd<K, 8, 4><<<tiles, 64, 0, st>>>(a, keys, rmask);
+  if (a.evals)
+    k_blend_bwd<K, 8, 4, true><<<tiles, 64, 0, st>>>(a, keys, rmask);
+  else
+    k_blend_bwd<K, 8, 4><<<tiles, 64, 0, st>>>(a, keys, rmask);
 }
 
 template void launch_blend<uint32_t>(const BlendArgs &, const uint32_t *, uint32_t, cudaStream_t);

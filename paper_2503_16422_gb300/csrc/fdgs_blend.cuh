@@ -20,6 +20,15 @@
 // already stopped, takes alpha = 0, and T - 0 T, fma(c, 0, C) leave its transmittance and
 // colour sums bit-for-bit unchanged. So the arithmetic of every pixel, and every result, is
 // the same for every footprint, every PX and the one-pixel-per-branch formulation.
+//
+// The plain colour blend of the batched path (kTz) with an even PX evaluates the lane's pixels
+// in pairs with the paired FP32 instructions of sm_100-class GPUs (one fma.rn.f32x2 does the
+// two IEEE fmas of a pixel pair): the exponent, the weight, the transmittance step and the
+// colour sums of two pixels take one instruction each. Its tests become multiplications by
+// 0 or 1 (set.ge gives 1.0f or 0.0f), which pair too; every value is the one of the scalar
+// form bit for bit (x * 1 = x, a finite x * 0 = 0). The colour sums are kept negated
+// (fma(c, -w, -C) = -fma(c, w, C) exactly under round-to-nearest), so the weight's sign
+// needs no extra instruction per hit.
 #pragma once
 #include <type_traits>
 
@@ -40,6 +49,13 @@ inline void with_blend_shape(int shape, F &&f) {
     case 5: f(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{}); break;
     default: f(std::integral_constant<int, 8>{}, std::integral_constant<int, 1>{}); break;
   }
+}
+
+// 1.0f if a >= b, else 0.0f (one FSET; a multiplier that pairs with f32x2 instructions).
+__device__ __forceinline__ float set_ge(float a, float b) {
+  float r;
+  asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -140,6 +156,19 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     lane_done = lane_done && done[p];
   }
   uint32_t nevals = 0, ntests = 0, npass = 0;
+  // the paired form (kTz, even PX): pixel pairs (2q, 2q + 1) of the lane, the negated pixel
+  // x coordinates (dx = u + (-px) is u - px exactly)
+  constexpr bool kPair = kTz && PX % 2 == 0;
+  constexpr int PH = PX / 2 > 0 ? PX / 2 : 1;
+  float2 T2[PH], C02[PH], C12[PH], C22[PH], npx2[PH];
+  if constexpr (kPair) {
+#pragma unroll
+    for (int q = 0; q < PH; ++q) {
+      T2[q] = make_float2(T[2 * q], T[2 * q + 1]);
+      C02[q] = C12[q] = C22[q] = make_float2(0.f, 0.f);
+      npx2[q] = make_float2(-(float)(px0 + 2 * q * HW), -(float)(px0 + (2 * q + 1) * HW));
+    }
+  }
   bool warp_done = __all_sync(0xffffffffu, lane_done);
 
   constexpr K kNone = ~(K)0;     // block lists: the entry does not cover this tile
@@ -230,6 +259,40 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
       }
       __syncwarp();
       const int nh = __popc(m);
+      if constexpr (kPair) {
+        for (int k = 0; k < nh; ++k) {
+          const float4 h0 = sm.h0[warp][k];
+          const float4 h1 = sm.h1[warp][k];
+          const float2 h2 = sm.h2[warp][k];
+          // row terms (shared by the lane's pixels), log2 opacity folded into the constant term
+          const float dy = __fsub_rn(h0.y, fpy);
+          const float b2dy = __fmul_rn(h0.w, dy);
+          const float c2l = __fmaf_rn(__fmul_rn(h1.x, dy), dy, h1.y);
+          const float2 uu = make_float2(h0.x, h0.x), aa = make_float2(h0.z, h0.z);
+          const float2 bd = make_float2(b2dy, b2dy), cl = make_float2(c2l, c2l);
+          const float2 cr = make_float2(h1.z, h1.z), cg = make_float2(h1.w, h1.w);
+          const float2 cb = make_float2(h2.x, h2.x);
+#pragma unroll
+          for (int q = 0; q < PH; ++q) {
+            const float2 dx = __fadd2_rn(uu, npx2[q]);
+            const float2 e = __ffma2_rn(dx, __ffma2_rn(aa, dx, bd), cl);
+            // -alpha = -min(0.99, 2^e) where e >= log2(1/255), else -0
+            const float2 ok = make_float2(set_ge(e.x, kLog2AlphaMin), set_ge(e.y, kLog2AlphaMin));
+            const float2 na = __fmul2_rn(make_float2(fmaxf(-kAlphaMax, -ex2_approx(e.x)),
+                                                     fmaxf(-kAlphaMax, -ex2_approx(e.y))), ok);
+            const float2 nw = __fmul2_rn(na, T2[q]);          // -alpha T
+            const float2 nT = __fadd2_rn(T2[q], nw);          // T - alpha T
+            // a pixel stops (T = 0, no colour) at the entry that takes T below 1e-4, and a
+            // stopped pixel stops again at every later entry
+            const float2 kp = make_float2(set_ge(nT.x, kTStop), set_ge(nT.y, kTStop));
+            const float2 nwi = __fmul2_rn(nw, kp);            // -(blend weight)
+            C02[q] = __ffma2_rn(cr, nwi, C02[q]);     // the negated colour sums
+            C12[q] = __ffma2_rn(cg, nwi, C12[q]);
+            C22[q] = __ffma2_rn(cb, nwi, C22[q]);
+            T2[q] = __fmul2_rn(nT, kp);
+          }
+        }
+      } else
       for (int k = 0; k < nh; ++k) {
         const float4 h0 = sm.h0[warp][k];
         const float4 h1 = sm.h1[warp][k];
@@ -237,15 +300,14 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
         // the row terms of the exponent are shared by the lane's pixels
         const float dy = __fsub_rn(h0.y, fpy);
         const float b2dy = __fmul_rn(h0.w, dy);
-        const float c2dy2 = __fmul_rn(__fmul_rn(h1.x, dy), dy);
+        const float c2l = __fmaf_rn(__fmul_rn(h1.x, dy), dy, h1.y);
         float w = 0.f;
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
           const float dx = __fsub_rn(h0.x, (float)(px0 + p * HW));
-          const float q = __fmaf_rn(dx, __fmaf_rn(h0.z, dx, b2dy), c2dy2);
-          const float e = __fadd_rn(q, h1.y);
+          const float e = __fmaf_rn(dx, __fmaf_rn(h0.z, dx, b2dy), c2l);
           if constexpr (kTz) {
-            const bool valid = q <= 0.f && e >= kLog2AlphaMin;
+            const bool valid = e >= kLog2AlphaMin;
             const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
             const float wa = alpha * T[p];
             const float nT = T[p] - wa;
@@ -258,7 +320,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
             T[p] = stop ? 0.f : nT;
             continue;
           }
-          const bool valid = !done[p] && q <= 0.f && e >= kLog2AlphaMin;
+          const bool valid = !done[p] && e >= kLog2AlphaMin;
           if (kCount && !done[p]) ++nevals;
           if (kCount && valid) ++npass;
           const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
@@ -290,7 +352,12 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
       __syncwarp();                    // the list is rewritten by the next round
       lane_done = true;
 #pragma unroll
-      for (int p = 0; p < PX; ++p) lane_done = lane_done && (kTz ? T[p] == 0.f : done[p]);
+      for (int p = 0; p < PX; ++p) {
+        if constexpr (kPair)
+          lane_done = lane_done && ((p & 1) ? T2[p >> 1].y : T2[p >> 1].x) == 0.f;
+        else
+          lane_done = lane_done && (kTz ? T[p] == 0.f : done[p]);
+      }
       warp_done = __all_sync(0xffffffffu, lane_done);
     }
     if (__syncthreads_and(warp_done)) {
@@ -303,6 +370,19 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     if (lane == 0 && ws) atomicAdd(&bt.evals[0], (unsigned long long)ws);
     if (lane == 0 && wt) atomicAdd(&bt.evals[1], (unsigned long long)wt);
     if (lane == 0 && wp) atomicAdd(&bt.evals[2], (unsigned long long)wp);
+  }
+  if constexpr (kPair) {
+#pragma unroll
+    for (int q = 0; q < PH; ++q) {
+      T[2 * q] = T2[q].x;
+      T[2 * q + 1] = T2[q].y;
+      C0[2 * q] = -C02[q].x;
+      C0[2 * q + 1] = -C02[q].y;
+      C1[2 * q] = -C12[q].x;
+      C1[2 * q + 1] = -C12[q].y;
+      C2[2 * q] = -C22[q].x;
+      C2[2 * q + 1] = -C22[q].y;
+    }
   }
   const size_t hw = (size_t)bt.W * bt.H;
 #pragma unroll

@@ -244,11 +244,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // The exponent of one (Gaussian, pixel) pair from the blend-ready record. The forward blend
 // (blend_tile) and the backward replay (k_blend_bwd) evaluate it with the same explicit
 // rounding, so both take the same decisions bit for bit:
-//   dy = v - py, b2dy = b2 dy, c2dy2 = (c2 dy) dy        (row terms, once per pixel row)
-//   dx = u - px, q = fma(dx, fma(a2, dx, b2dy), c2dy2), e = q + log2(a)
-// with d = mean2D - pixel and q = log2(e) * power, power = -1/2 (A dx^2 + 2 B dx dy + C dy^2).
-// The pair is skipped when power > 0 or when e puts a * exp(power) below 1/255; otherwise
-// alpha = min(0.99, 2^e). (Written out in both kernels: factored into helper functions the
-// same arithmetic compiled 12% slower in the persistent blend.)
+//   dy = v - py, b2dy = b2 dy, c2l = fma(c2 dy, dy, log2(a))   (row terms, once per pixel row)
+//   dx = u - px, e = fma(dx, fma(a2, dx, b2dy), c2l)
+// with d = mean2D - pixel and e = log2(a exp(power)), power = -1/2 (A dx^2 + 2 B dx dy +
+// C dy^2). The pair is skipped when e puts a exp(power) below 1/255; otherwise alpha =
+// min(0.99, 2^e). The renderer's "power > 0 is skipped" rule needs no test: the conic is the
+// inverse of J Sigma J^T + 0.3 I, positive definite by construction, so power <= 0 exactly,
+// and a float32 power that rounds above 0 belongs to an exact power within rounding of 0,
+// which the reference rule would blend (alpha = a to within that rounding). (Written out in
+// both kernels: factored into helper functions the same arithmetic compiled 12% slower in the
+// persistent blend.)
 
 }  // namespace fdgs

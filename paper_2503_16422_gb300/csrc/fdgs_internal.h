@@ -101,6 +101,7 @@ struct BlendBwdArgs {
   const uint32_t *n_contrib;
   float *g2d;          // [nv][9] per rank: u, v, A, B, C, a, r, g, b
   const uint32_t *order = nullptr;  // optional [tiles] launch order (the forward's)
+  unsigned long long *evals = nullptr;  // optional counters [3] (profiling; see k_blend_bwd)
 };
 template <typename K>
 void launch_blend_bwd(const BlendBwdArgs &a, const K *keys, uint32_t rmask, cudaStream_t st);
@@ -126,14 +127,20 @@ void launch_export_records(const uint64_t *sorted, uint32_t nv, const float *rec
                            float *out, cudaStream_t st);
 // V_i = prod of the four scales, as float bits (positive floats sort as unsigned ints)
 void launch_volume_bits(const float4 *ls4, uint32_t n, uint32_t *vbits, cudaStream_t st);
-// gamma_i = clamp(V_i / V_sorted[k], 0, 1)^0.1 with V_sorted the ascending volumes
-void launch_gamma(const float4 *ls4, uint32_t n, const uint32_t *vsorted, uint32_t k,
-                  float *gamma, cudaStream_t st);
-// score[id] += w_sum[rank] * f_id(t) * gamma[id] for every visible rank
+// per Gaussian: gamma_i = clamp(V_i / V_sorted[k], 0, 1)^0.1 with V_sorted the ascending
+// volumes, and the temporal variance Sigma_t,i in FP64
+void launch_score_consts(const float4 *ls4, const float4 *ql, const float4 *qr, uint32_t n,
+                         const uint32_t *vsorted, uint32_t k, float *gamma, double *sig_t,
+                         cudaStream_t st);
+// score[id] += w_sum[rank] * factor_id(t) for every visible rank, the factor of the score
+// variant (fdgs_score_variant; 0: f_id(t) gamma[id], the score of Eq. 7)
 void launch_score_accumulate(const uint64_t *sorted, const uint32_t *nv_dev, uint32_t nv_cap,
-                             const float *w_sum, const float4 *mean4, const float4 *ls4,
-                             const float4 *ql, const float4 *qr, const float *gamma, float t,
-                             float *score, cudaStream_t st);
+                             const float *w_sum, const float4 *mean4, const double *sig_t,
+                             const float *gamma, float t, float *score, int variant,
+                             cudaStream_t st);
+// the temporal-only score variant: score[i] += f_i(t) gamma[i] for every Gaussian
+void launch_score_temporal(const float4 *mean4, const double *sig_t, const float *gamma,
+                           uint32_t n, float t, float *score, cudaStream_t st);
 void launch_score_keys(const float *score, uint32_t n, uint64_t *keys, cudaStream_t st);
 // key-frame masks: row[id / 32] |= bit id % 32 for visible ranks blended somewhere
 // (w_sum > 0) or that stopped a pixel (stop_mark); rows packed into LSB-first bytes
@@ -206,7 +213,9 @@ struct BatchDev {
   float *w_sum;
   uint32_t *stop_mark;
   const float *gamma;
+  const double *sig_t;               // [n] temporal variances (score pass)
   float *score;
+  int score_variant;                 // fdgs_score_variant of the score pass
   int mark;
   unsigned long long *stamps;        // [kBatchStages + 1] %globaltimer at stage boundaries
 };

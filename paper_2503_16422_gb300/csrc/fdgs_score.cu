@@ -38,62 +38,106 @@ __global__ void k_volume_bits(const float4 *__restrict__ ls4, uint32_t n, uint32
   }
 }
 
-__global__ void k_gamma(const float4 *__restrict__ ls4, uint32_t n,
-                        const uint32_t *__restrict__ vsorted, uint32_t k, float *gamma) {
+// Per-Gaussian constants of the score pass, once per pass: gamma_i = clamp(V_i / V_p90, 0,
+// 1)^0.1 (V_p90 = vsorted[k]) and the temporal variance Sigma_t,i = |row t of R diag(s)|^2 in
+// FP64. f_i(t) (Eqs. 5-6) takes the difference (t - mu_t)^2 / Sigma_t - 1, which cancels at
+// the inflection points of p(t): there a float32 Sigma_t (a sum of four products after two
+// quaternion normalisations and four exponentials, a few ulps off) would move f by up to 1e-3
+// relative for short-lived Gaussians (Sigma_t ~ 3e-4), so Sigma_t is formed in FP64 from the
+// float32 attributes, once per Gaussian.
+__global__ void k_score_consts(const float4 *__restrict__ ls4, const float4 *__restrict__ ql,
+                               const float4 *__restrict__ qr, uint32_t n,
+                               const uint32_t *__restrict__ vsorted, uint32_t k, float *gamma,
+                               double *sig_t) {
   const float vref = __uint_as_float(vsorted[k]);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float4 l = ls4[i];
     const float v = expf(l.x + l.y + l.z + l.w);
     const float x = fminf(fmaxf(v / vref, 0.f), 1.f);
     gamma[i] = powf(x, 0.1f);
+    const float4 a4 = ql[i], b4 = qr[i];
+    const double na = rsqrt((double)a4.x * a4.x + (double)a4.y * a4.y + (double)a4.z * a4.z +
+                            (double)a4.w * a4.w);
+    const double nb = rsqrt((double)b4.x * b4.x + (double)b4.y * b4.y + (double)b4.z * b4.z +
+                            (double)b4.w * b4.w);
+    // row t of the left-multiplication matrix of q_l = (a, b, c, d): (d, -c, b, a)
+    const double L3[4] = {a4.w * na, -a4.z * na, a4.y * na, a4.x * na};
+    // the right-multiplication matrix of q_r = (p, x, r, s), row-major
+    const double p_ = b4.x * nb, x_ = b4.y * nb, r_ = b4.z * nb, s_ = b4.w * nb;
+    const double R[16] = {p_, -x_, -r_, -s_, x_, p_, s_, -r_, r_, -s_, p_, x_, s_, r_, -x_, p_};
+    const double sc[4] = {exp((double)l.x), exp((double)l.y), exp((double)l.z),
+                          exp((double)l.w)};
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      double e = 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e = fma(L3[j], R[j * 4 + m], e);
+      e *= sc[m];
+      acc = fma(e, e, acc);
+    }
+    sig_t[i] = acc;
   }
 }
 
-// Temporal variance Sigma_t = |row t of R diag(s)|^2 of one Gaussian.
-__device__ __forceinline__ float temporal_variance(float4 ls, float4 ql, float4 qr) {
-  float qn_l[4], qn_r[4], il, ir, L[16], Rr[16];
-  quat_unit(ql, qn_l, il);
-  quat_unit(qr, qn_r, ir);
-  left_mat(qn_l, L);
-  right_mat(qn_r, Rr);
-  const float s[4] = {expf(ls.x), expf(ls.y), expf(ls.z), expf(ls.w)};
-  float v = 0.f;
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    float r = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r = fmaf(L[12 + k], Rr[k * 4 + m], r);
-    const float e = r * s[m];
-    v = fmaf(e, e, v);
-  }
-  return v;
-}
-
-// f_i(t) of Eqs. 5-6: the second time derivative of the temporal opacity p_i(t) mapped
-// through tanh into [1, 2] (its reciprocal half-plus-half form).
-__device__ __forceinline__ float variation_factor(float t, float4 m4, float4 ls, float4 ql,
-                                                  float4 qr) {
-  const float st = temporal_variance(ls, ql, qr);
-  const float dt = t - m4.w;
-  const float p = expf(-0.5f * dt * dt / st);
-  const float p2 = (dt * dt / (st * st) - 1.f / st) * p;
+// f_i(t) of Eqs. 5-6: the second time derivative of the temporal opacity p_i(t) =
+// exp(-(t - mu_t)^2 / (2 Sigma_t)), p'' = ((t - mu_t)^2 / Sigma_t - 1) / Sigma_t p, mapped
+// through tanh into [1, 2] (its reciprocal half-plus-half form). The difference is taken in
+// FP64 (t - mu_t is exact there); p and tanh are float32.
+__device__ __forceinline__ float variation_factor(float t, float mu_t, double st) {
+  const double dt = (double)t - (double)mu_t;
+  const double inv = 1.0 / st;
+  const double x = dt * dt * inv;
+  const float p = expf(-0.5f * (float)x);
+  const float p2 = (float)((x - 1.0) * inv) * p;
   return 1.f / (0.5f * tanhf(fabsf(p2)) + 0.5f);
+}
+
+// The factor of score variant (d) of the ablation (Table 4): p^(1)(t) = -(t - mu_t) / Sigma_t
+// p(t) in place of p^(2) in Eq. 6.
+__device__ __forceinline__ float variation_factor_d1(float t, float mu_t, double st) {
+  const double dt = (double)t - (double)mu_t;
+  const float p = expf(-0.5f * (float)(dt * dt / st));
+  const float p1 = -(float)(dt / st) * p;
+  return 1.f / (0.5f * tanhf(fabsf(p1)) + 0.5f);
+}
+
+// The per-(Gaussian, t) factor that multiplies the blend weight w_i(t, view) in each rendered
+// score variant (fdgs_score_variant): f gamma (Eq. 7, ours), 1 (spatial only), f1 gamma
+// (p^(1) in place of p^(2)), Sigma_t gamma (Sigma_t in place of S^TV).
+__device__ __forceinline__ float score_factor(int variant, float t, float mu_t, double st,
+                                              float gamma) {
+  switch (variant) {
+    case 1: return 1.f;
+    case 3: return variation_factor_d1(t, mu_t, st) * gamma;
+    case 4: return (float)st * gamma;
+    default: return variation_factor(t, mu_t, st) * gamma;
+  }
 }
 
 __global__ void k_score_accumulate(const uint64_t *__restrict__ sorted,
                                    const uint32_t *__restrict__ nv_dev,
                                    const float *__restrict__ w_sum,
-                                   const float4 *__restrict__ mean4, const float4 *__restrict__ ls4,
-                                   const float4 *__restrict__ ql, const float4 *__restrict__ qr,
-                                   const float *__restrict__ gamma, float t, float *score) {
+                                   const float4 *__restrict__ mean4,
+                                   const double *__restrict__ sig_t,
+                                   const float *__restrict__ gamma, float t, float *score,
+                                   int variant) {
   const uint32_t nv = *nv_dev;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
     const float w = w_sum[r];
     if (w == 0.f) continue;
     const uint32_t id = (uint32_t)sorted[r];
-    const float f = variation_factor(t, mean4[id], ls4[id], ql[id], qr[id]);
-    score[id] += w * f * gamma[id];
+    score[id] += w * score_factor(variant, t, mean4[id].w, sig_t[id], gamma[id]);
   }
+}
+
+// Temporal-only score (variant (c) of Table 4): S_i += f_i(t) gamma_i for one t, no render.
+__global__ void k_score_temporal(const float4 *__restrict__ mean4,
+                                 const double *__restrict__ sig_t,
+                                 const float *__restrict__ gamma, uint32_t n, float t,
+                                 float *score) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    score[i] += variation_factor(t, mean4[i].w, sig_t[i]) * gamma[i];
 }
 
 // The batched score pass: the weight of Gaussian i over the pixels of request r sits at
@@ -106,8 +150,8 @@ __global__ void k_score_batch(BatchDev b) {
     const float w = b.w_sum[ri];
     if (w == 0.f) continue;
     const uint32_t r = (uint32_t)(ri / b.n), id = (uint32_t)(ri % b.n);
-    const float f = variation_factor(b.reqs[r].t, b.mean4[id], b.ls4[id], b.ql[id], b.qr[id]);
-    atomicAdd(&b.score[id], w * f * b.gamma[id]);
+    atomicAdd(&b.score[id], w * score_factor(b.score_variant, b.reqs[r].t, b.mean4[id].w,
+                                             b.sig_t[id], b.gamma[id]));
   }
 }
 
@@ -185,10 +229,11 @@ void launch_volume_bits(const float4 *ls4, uint32_t n, uint32_t *vbits, cudaStre
   k_volume_bits<<<grid_for(n), kB, 0, st>>>(ls4, n, vbits);
 }
 
-void launch_gamma(const float4 *ls4, uint32_t n, const uint32_t *vsorted, uint32_t k,
-                  float *gamma, cudaStream_t st) {
+void launch_score_consts(const float4 *ls4, const float4 *ql, const float4 *qr, uint32_t n,
+                         const uint32_t *vsorted, uint32_t k, float *gamma, double *sig_t,
+                         cudaStream_t st) {
   if (n == 0) return;
-  k_gamma<<<grid_for(n), kB, 0, st>>>(ls4, n, vsorted, k, gamma);
+  k_score_consts<<<grid_for(n), kB, 0, st>>>(ls4, ql, qr, n, vsorted, k, gamma, sig_t);
 }
 
 void launch_score_batch(const BatchDev &b, cudaStream_t st) {
@@ -200,12 +245,18 @@ void launch_mark_batch(const BatchDev &b, cudaStream_t st) {
 }
 
 void launch_score_accumulate(const uint64_t *sorted, const uint32_t *nv_dev, uint32_t nv_cap,
-                             const float *w_sum, const float4 *mean4, const float4 *ls4,
-                             const float4 *ql, const float4 *qr, const float *gamma, float t,
-                             float *score, cudaStream_t st) {
+                             const float *w_sum, const float4 *mean4, const double *sig_t,
+                             const float *gamma, float t, float *score, int variant,
+                             cudaStream_t st) {
   if (nv_cap == 0) return;
-  k_score_accumulate<<<grid_for(nv_cap), kB, 0, st>>>(sorted, nv_dev, w_sum, mean4, ls4, ql, qr,
-                                                      gamma, t, score);
+  k_score_accumulate<<<grid_for(nv_cap), kB, 0, st>>>(sorted, nv_dev, w_sum, mean4, sig_t, gamma,
+                                                      t, score, variant);
+}
+
+void launch_score_temporal(const float4 *mean4, const double *sig_t, const float *gamma,
+                           uint32_t n, float t, float *score, cudaStream_t st) {
+  if (n == 0) return;
+  k_score_temporal<<<grid_for(n), kB, 0, st>>>(mean4, sig_t, gamma, n, t, score);
 }
 
 void launch_mark_contributors(const uint64_t *sorted, const uint32_t *nv_dev, uint32_t nv_cap,

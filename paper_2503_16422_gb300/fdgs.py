@@ -70,6 +70,9 @@ _SIGNATURES = {
                           ctypes.POINTER(_P), _P],
     "fdgs_variation_score": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
                              ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int, _P, _P],
+    "fdgs_variation_score_variant": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, _P, _P],
     "fdgs_select_keep": [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P],
     "fdgs_select_keep_noalloc": [_P, ctypes.c_int64, ctypes.c_float, _P, _P],
     "fdgs_status_sync": [_P],
@@ -83,7 +86,8 @@ _SIGNATURES = {
                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                         ctypes.POINTER(ctypes.c_float)],
     "fdgs_profile_read": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)],
-    "fdgs_batch_counts": [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
+    "fdgs_batch_counts": [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                          ctypes.POINTER(ctypes.c_uint64)],
     "fdgs_set_batch_list_capacity": [_P, ctypes.c_uint64],
     "fdgs_batch_tile_lists": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32),
                               ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint64,
@@ -93,10 +97,12 @@ _SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P, _P],
     "fdgs_debug_inject": [ctypes.c_int, ctypes.c_int64],
 }
+# score variants of fdgs_variation_score_variant (Table 4 of the paper: f, b, c, d, e)
+SCORE_VARIANTS = {"full": 0, "spatial": 1, "temporal": 2, "first_derivative": 3, "sigma_t": 4}
 # fdgs_debug_inject kinds
 INJECT_NONE, INJECT_SPIN_LIMIT, INJECT_WITHHOLD_PUBLISH, INJECT_FAIL_ALLOCS = 0, 1, 2, 3
 PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "tile_scan", "emit",
-                  "tile_sort", "blend")
+                  "tile_sort", "blend", "backward_blend", "backward_gauss")
 BATCH_STAGES = ("preprocess", "depth_sort", "gather", "tile_scan", "lists", "queue_sort",
                 "blend")
 
@@ -427,10 +433,12 @@ class Scene:
         return out
 
     def batch_counts(self):
-        """Visible Gaussians and tile-list entries of the last batch, over all requests."""
-        nv, nk = ctypes.c_uint64(), ctypes.c_uint64()
-        check(lib().fdgs_batch_counts(self.handle, ctypes.byref(nv), ctypes.byref(nk)))
-        return dict(n_visible=nv.value, n_keys=nk.value)
+        """Visible Gaussians, tile-list entries and block-list entries of the last batch,
+        over all requests."""
+        nv, nk, nb = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib().fdgs_batch_counts(self.handle, ctypes.byref(nv), ctypes.byref(nk),
+                                      ctypes.byref(nb)))
+        return dict(n_visible=nv.value, n_keys=nk.value, n_block_entries=nb.value)
 
     def set_batch_list_capacity(self, entries):
         """Block-list capacity batches start with (0: default); see the C header."""
@@ -451,13 +459,20 @@ class Scene:
                                           ctypes.byref(nt), ctypes.byref(n)))
         return ranges, ids[: n.value]
 
-    def variation_score(self, cams, ts, batch=8, out=None, stream=None):
+    def variation_score(self, cams, ts, batch=8, out=None, stream=None, variant="full"):
+        """Spatial-temporal variation score [n] over the (t, camera) renders; ``variant``
+        selects a score of the paper's ablation (SCORE_VARIANTS; "full" is the paper's)."""
         _ca, carr = make_cameras(cams)
         tarr = (ctypes.c_float * max(len(ts), 1))(*[float(t) for t in ts])
         if out is None:
             out = torch.empty((self.n,), dtype=torch.float32, device=self.device)
-        check(lib().fdgs_variation_score(self.handle, carr, len(cams), tarr, len(ts),
-                                         int(batch), _ptr(out), _stream(stream)))
+        if variant == "full":
+            check(lib().fdgs_variation_score(self.handle, carr, len(cams), tarr, len(ts),
+                                             int(batch), _ptr(out), _stream(stream)))
+        else:
+            check(lib().fdgs_variation_score_variant(
+                self.handle, carr, len(cams), tarr, len(ts), int(batch), SCORE_VARIANTS[variant],
+                _ptr(out), _stream(stream)))
         return out
 
     def select_keep(self, scores, prune_ratio=0.8, stream=None):

@@ -218,13 +218,15 @@ def test_bench_batch_configuration_matches_oracle_on_sampled_tiles(fd):
     P = oracle.Params.from_scene(s)
     rng = np.random.default_rng(5)
     for i in (0, 31, 63):
-        active = oracle.active_from_masks(masks, kt, tt[i], s.n)
-        pre = oracle.preprocess(P, cams[i], tt[i], active)
+        ti = parity.f32(tt[i])
+        active = oracle.active_from_masks(masks, [parity.f32(k) for k in kt], ti, s.n)
+        pre = oracle.preprocess(P, cams[i], ti, active)
         gx, gy = pre["grid"]
         tiles = sorted(set([0, gx - 1, gx * gy - 1, (gy // 2) * gx + gx // 2] +
                            rng.choice(gx * gy, 3, replace=False).tolist()))
-        ref = oracle.render(P, cams[i], tt[i], active, tiles=tiles, pre=pre)
+        ref = oracle.render(P, cams[i], ti, active, tiles=tiles, pre=pre)
         im = parity.image_metrics(outs[i].cpu().numpy(), ref["image"].numpy())
         assert im["n"] >= 3 * 48 * len(tiles)     # every sampled tile has at least 8x6 pixels
         assert im["frac_bad"] <= 1e-4 and im["psnr"] >= 60.0, (frames[i], im)
+        parity.report(f"batch bench configuration frame {frames[i]}", tiles=len(tiles), **im)
     sc.close()

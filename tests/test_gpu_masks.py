@@ -36,9 +36,10 @@ def test_keyframe_masks_match_oracle(fd):
     ex = np.zeros_like(gpu)
     for k, t in enumerate(kt):
         for cam in cams:
-            m, e = parity.contribution_exempt(P, cam, float(t))
+            m, e = parity.contribution_exempt(P, cam, parity.f32(t))
             want[k] |= m
-            ex[k] |= e | parity.exempt_gaussians(oracle.preprocess(P, cam, float(t)), cam)
+            ex[k] |= e | parity.exempt_gaussians(oracle.preprocess(P, cam, parity.f32(t)), cam,
+                                                   s.mean4)
     bad = (gpu != want) & ~ex
     print(f"marked {int(want.sum())}, exempt {int(ex.sum())}, mismatches {int((gpu != want).sum())}")
     assert not bad.any(), np.argwhere(bad)[:10]

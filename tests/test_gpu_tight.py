@@ -35,10 +35,17 @@ def test_tight_lists_match_oracle_and_images_equal_square(fd, wh):
     P = oracle.Params.from_scene(s)
     ref = oracle.render(P, cam, 0.5, tile_sets="tight")
     pre = ref["pre"]
-    exempt = parity.exempt_gaussians(pre, cam)
+    exempt, why = parity.exempt_gaussians(pre, cam, s.mean4, detail=True)
+    b = parity.f32_bounds(pre, cam, s.mean4)
+    vis = (ex["flags"] & parity.FLAG_VISIBLE) > 0
+    depth = np.where(vis, ex["records"][:, 9].astype(np.float64), np.nan)
     lists = parity.compare_tile_lists(ex["tile_ranges"], ex["tile_ids"], ref["lists"], pre,
-                                      exempt)
+                                      exempt, depth, b["z"])
     assert not lists["bad_tiles"], lists["bad_tiles"][:10]
+    assert int(exempt.sum()) <= 0.02 * s.n + 5
+    parity.report(f"tight lists {wh[0]}x{wh[1]}", exempt_gaussians=int(exempt.sum()),
+                  exempt_by_reason=why, keys_checked=lists["keys"],
+                  depth_tie_pairs=lists["tie_pairs"])
     n_sq = sum(len(v) for v in oracle.render(P, cam, 0.5)["lists"].values())
     assert ex["stats"]["n_keys"] < n_sq
     sc.close()

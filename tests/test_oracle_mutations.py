@@ -60,9 +60,28 @@ MUTATIONS = {
         ["test_positive_power_is_skipped"]),
     "variation factor without the 1/2 on tanh (Eq. 6)": (
         "variation_factor",
-        "return 1.0 / (0.5 * torch.tanh(torch.abs(p2)) + 0.5)",
-        "return 1.0 / (torch.tanh(torch.abs(p2)) + 0.5)",
+        "return 1.0 / (0.5 * torch.tanh(torch.abs(pk)) + 0.5)",
+        "return 1.0 / (torch.tanh(torch.abs(pk)) + 0.5)",
         ["test_variation_factor_range_and_fixed_points"]),
+    "first derivative of p(t) without its 1/Sigma_t (score variant d, Table 4)": (
+        "temporal_first_derivative",
+        "return -(dt / s_tt) * p",
+        "return -dt * p",
+        ["test_first_derivative_by_finite_differences_and_its_factor_range"]),
+    "temporal-only score variant summed over the views (Table 4 c)": (
+        "variation_scores",
+        """            if variant == "temporal":
+                S += f * gamma
+                continue""",
+        """            if variant == "temporal":
+                S += f * gamma * max(len(cams), 1)
+                continue""",
+        ["test_score_variants_against_the_spatial_score_and_each_other"]),
+    "Sigma_t variant with the temporal scale instead of its variance (Table 4 e)": (
+        "variation_scores",
+        "g_t = cov4[:, 3, 3] * gamma",
+        "g_t = torch.sqrt(cov4[:, 3, 3]) * gamma",
+        ["test_score_variants_against_the_spatial_score_and_each_other"]),
     "volume normalisation not clamped": (
         "volume_gamma",
         "return torch.clamp(V / p90, 0.0, 1.0) ** beta",

@@ -436,6 +436,59 @@ def test_gradients_match_central_finite_differences():
     assert checked > 50
 
 
+def test_gradients_match_finite_differences_at_the_backward_workload_size():
+    """The backward workload's check: 500 Gaussians (the densest in view of the pruned
+    scene's draw, degree-3 SH) at 64x64, central differences with h = 1e-6 of
+    L = sum(dL * image) with dL the L1-loss gradient against a target rendered from means
+    perturbed by N(0, 0.01). Components whose +-h moves a decision (visibility, rectangle,
+    n_contrib, SH clamp) are skipped and counted; a sample of every parameter tensor is
+    checked."""
+    full = scenes.pruned_scene(20_000, 5)
+    idx = np.argsort(np.abs(full.mean4[:, 0]) + np.abs(full.mean4[:, 1]))[:500]
+    s = full.subset(np.sort(idx))
+    s = _scene64(s.mean4, s.logscale4, s.q_left, s.q_right, s.opacity_logit, s.sh, 3)
+    cam = scenes.arc_camera(3.0, 64, 64)
+    t = 0.45
+    rng = np.random.default_rng(55)
+    m = s.mean4.copy()
+    m[:, :3] += rng.normal(0, 0.01, (s.n, 3))
+    target = oracle.render(oracle.Params.from_scene(scenes.Scene(**{**s.arrays(), "mean4": m},
+                                                                 sh_degree=3)), cam, t)["image"]
+    img0 = oracle.render(oracle.Params.from_scene(s), cam, t)["image"].numpy()
+    g = np.sign(img0 - target.numpy()) / img0.size
+    grads, _ = oracle.gradients(s, cam, t, g)
+    base = _decisions(oracle.Params.from_scene(s), cam, t)
+    names = ["mean4", "logscale4", "q_left", "q_right", "opacity_logit", "sh"]
+    h = 1e-6
+    pick = np.random.default_rng(6)
+    checked = skipped = 0
+    for name, gr in zip(names, grads):
+        arr = getattr(s, name)
+        # sample among components with a non-zero gradient (Gaussians that reach the image)
+        nz = np.flatnonzero(np.abs(gr.reshape(-1)) > 0)
+        for flat in pick.choice(nz, size=min(len(nz), 24 if name == "sh" else 12),
+                                replace=False):
+            vals = []
+            same = True
+            for sgn in (1, -1):
+                a2 = arr.copy().reshape(-1)
+                a2[flat] += sgn * h
+                s2 = scenes.Scene(**{**s.arrays(), name: a2.reshape(arr.shape)}, sh_degree=3)
+                P2 = oracle.Params.from_scene(s2)
+                img, _ = oracle.render_image(P2, cam, t)
+                vals.append(float((img.numpy() * g).sum()))
+                same &= all(np.array_equal(x, y) for x, y in zip(base, _decisions(P2, cam, t)))
+            if not same:
+                skipped += 1
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = gr.reshape(-1)[flat]
+            scale = np.abs(gr).max()
+            assert abs(fd - an) <= 1e-6 * abs(an) + 1e-7 * scale, (name, flat, fd, an)
+            checked += 1
+    assert checked >= 70 and skipped <= 10, (checked, skipped)
+
+
 # ---- Sec. 4.2.1: spatial-temporal variation score ------------------------------------------
 
 def test_blend_weights_sum_to_one_minus_final_transmittance():
@@ -493,6 +546,75 @@ def test_scores_permutation_invariant_and_readings_agree_at_one_t():
     assert np.allclose(Sp, S1[perm], rtol=1e-10, atol=1e-14)
     Sm = oracle.variation_scores(s, cams, [0.2, 0.5, 0.9], "R1")
     assert np.all(Sm >= S1 - 1e-15) and Sm.max() > 0
+
+
+def test_first_derivative_by_finite_differences_and_its_factor_range():
+    """p^(1)(t) of score variant (d) (Table 4) is the time derivative of Eq. 3's p(t): central
+    differences of the oracle's own marginal; the factor with p^(1) lies in (1, 2] and is
+    exactly 2 at t = mu_t, where p^(1) = 0."""
+    mean4, ls, ql, qr = _rand_params(16, 15)
+    cov = oracle.covariance_4d(torch.tensor(ls), torch.tensor(ql), torch.tensor(qr))
+    m4 = torch.tensor(mean4)
+    t, h = 0.37, 1e-6
+
+    def p(tt):
+        return oracle.condition_on_time(m4, cov, tt)[3].numpy()
+    fd1 = (p(t + h) - p(t - h)) / (2 * h)
+    p1 = oracle.temporal_first_derivative(m4, cov, t).numpy()
+    assert np.allclose(p1, fd1, rtol=1e-6, atol=1e-8)
+    for tt in np.linspace(-0.5, 1.5, 9):
+        f1 = oracle.variation_factor(m4, cov, float(tt), derivative=1).numpy()
+        assert np.all(f1 >= 1.0) and np.all(f1 <= 2.0)
+    for i in range(6):
+        f1 = oracle.variation_factor(m4[i:i + 1], cov[i:i + 1], float(m4[i, 3]), derivative=1)
+        assert float(f1) == 2.0
+
+
+def _variant_scene():
+    s = scenes.make_scene(120, 41, sh_degree=0, lxyz=(-2.2, 0.4), lt_long=(-1.2, 0.3))
+    # identity quaternions for every fourth Gaussian: its 4D covariance is diag(s^2), so
+    # Sigma_t = exp(2 l_t)
+    ql, qr = s.q_left.copy(), s.q_right.copy()
+    ql[::4] = (1.0, 0.0, 0.0, 0.0)
+    qr[::4] = (1.0, 0.0, 0.0, 0.0)
+    return scenes.Scene(**{**s.arrays(), "q_left": ql, "q_right": qr}, sh_degree=0)
+
+
+def test_score_variants_against_the_spatial_score_and_each_other():
+    """The score ablation's variants (Table 4; supplement "Variant Settings"), at one (t, view):
+    every rendered variant is the spatial score S^S (variant b, the blend weights of Eq. 4)
+    times its own per-Gaussian factor: f gamma (ours), f1 gamma (d), Sigma_t gamma (e), with
+    Sigma_t = exp(2 l_t) where the rotation is the identity; the temporal-only score (c)
+    needs no render, so it is the same for any views and adds up over disjoint time sets."""
+    s = _variant_scene()
+    cams = [scenes.look_at_camera((0.3, 0.1, 4.0), 40, 32)]
+    t = 0.45
+    P = oracle.Params.from_scene(s)
+    w = oracle.render(P, cams[0], t, weights=True)["w_sum"].numpy()
+    cov = oracle.covariance_4d(P.logscale4, P.q_left, P.q_right)
+    gamma = oracle.volume_gamma(P.logscale4).numpy()
+    f2 = oracle.variation_factor(P.mean4, cov, t).numpy()
+    f1 = oracle.variation_factor(P.mean4, cov, t, derivative=1).numpy()
+    sc = {v: oracle.variation_scores(s, cams, [t], variant=v) for v in oracle.SCORE_VARIANTS}
+    assert np.array_equal(sc["spatial"], w) and int((w > 0).sum()) > 20
+    assert np.allclose(sc["full"], w * f2 * gamma, rtol=1e-12, atol=0)
+    assert np.allclose(sc["first_derivative"], w * f1 * gamma, rtol=1e-12, atol=0)
+    idq = np.zeros(s.n, bool)
+    idq[::4] = True
+    sig_t = np.exp(2.0 * s.logscale4[:, 3].astype(np.float64))
+    assert np.allclose(sc["sigma_t"][idq], (w * sig_t * gamma)[idq], rtol=1e-12, atol=0)
+    assert np.allclose(sc["temporal"], f2 * gamma, rtol=1e-12, atol=0)
+    # temporal only: the same with other views or none, additive over time sets
+    other = [scenes.look_at_camera((-1.0, 0.0, 3.8), 24, 24)] * 3
+    assert np.array_equal(oracle.variation_scores(s, other, [t], variant="temporal"),
+                          sc["temporal"])
+    assert np.array_equal(oracle.variation_scores(s, [], [t], variant="temporal"),
+                          sc["temporal"])
+    a = oracle.variation_scores(s, cams, [0.1, 0.9], variant="temporal")
+    b = oracle.variation_scores(s, cams, [0.1, 0.9, t], variant="temporal")
+    assert np.allclose(b, a + sc["temporal"], rtol=1e-12, atol=0)
+    with pytest.raises(ValueError):
+        oracle.variation_scores(s, cams, [t], variant="other")
 
 
 def test_keep_set_ties_broken_by_id():
