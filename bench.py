@@ -704,6 +704,8 @@ def comparisons(sc, cams, times, flush, stream):
         sequential_p50_ms=float(np.percentile(seq_lat, 50)),
         sequential_p99_ms=float(np.percentile(seq_lat, 99)),
         shape=sc.batch_info(64))
+    # record staging of the batched blend: per-thread cp.async against TMA gather4
+    res["blend_staging"] = staging_ab(sc, cams, times, flush, stream)
     # backward (fine-tuning step): L1 loss against a render of the scene with means perturbed
     # by N(0, 0.01); render with a frame, then the reverse replay + per-Gaussian chain
     res["backward"] = backward_timing(sc, cams, times, flush, stream)
@@ -751,6 +753,35 @@ def comparisons(sc, cams, times, flush, stream):
     del big
     torch.cuda.empty_cache()
     return res
+
+
+def staging_ab(sc, cams, times, flush, stream, B=64):
+    """The headline's batches (64 masked frames at 1352x1014, the autotuned launch shape)
+    under each record staging of the batched blend: per-thread cp.async copies, or TMA
+    cp.async.bulk.tensor tile::gather4 into mbarrier-completed buffers. Batch and blend ms
+    (medians of six L2-flushed batches each; the images are the same)."""
+    import torch
+
+    from paper_2503_16422_gb300 import fdgs
+    outs = [torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device="cuda")
+            for _ in range(B)]
+    steps = [frame_list(B, 7 * B), frame_list(B, 9 * B), frame_list(B, 11 * B)]
+    bargs = [([cams[k] for k in f], [float(times[k]) for k in f]) for f in steps]
+    out = {"shape": sc.batch_info(B)}
+    for name, mode in (("cp_async", fdgs.STAGING_CP_ASYNC), ("tma_gather4", fdgs.STAGING_TMA),
+                       ("cp_async_again", fdgs.STAGING_CP_ASYNC)):
+        fdgs.set_batch_staging(mode)
+        for a, b_ in bargs[:2]:                       # re-capture, warm up
+            sc.render_batch(a, b_, use_mask=True, outs=outs)
+        stages = []
+        ms, _ = timed_batches(sc, [a for a, _ in bargs] * 2, [b_ for _, b_ in bargs] * 2,
+                              [outs] * 6, True, flush, stream, stages)
+        out[name] = dict(ms_per_batch=statistics.median(ms),
+                         fps=B / (statistics.median(ms) / 1e3),
+                         blend_ms=statistics.median([x["blend"] for x in stages]))
+    fdgs.set_batch_staging(fdgs.DEFAULT_BATCH_STAGING)
+    del outs
+    return out
 
 
 def keyframe_mask_timing(sc, cams, times, flush, stream, B=64):

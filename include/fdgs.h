@@ -388,6 +388,18 @@ int fdgs_set_list_builder(int mode);
  * other values. */
 int fdgs_set_blend_shape(int footprint);
 
+/* How the batched blend (fdgs_render_batch and the batched score and mask passes) stages the
+ * blend-ready records of each tile's list entries in shared memory, process-wide; batch graphs
+ * are re-captured at their next run after a change. 0 (default): per-thread 16-byte cp.async
+ * copies, three per record. 1: TMA, one cp.async.bulk.tensor tile::gather4 copy of four
+ * 48-byte records per instruction, completing on a transaction-counting mbarrier (four-pixel
+ * blend shapes and the weighted passes; the others, or a driver without the tensor-map
+ * encoder, fall back to 0). Results are identical either way; a stage wait that exceeds its
+ * spin limit sets FDGS_ERR_TIMEOUT. Returns FDGS_ERR_INVALID for other values. This is the
+ * staging of Sec. 3's tile rasterisation (Eq. 2), which the paper leaves to the inherited
+ * renderer. */
+int fdgs_set_batch_staging(int mode);
+
 /* Reads and clears the scene's device status word (synchronises the device): FDGS_OK, or
  * FDGS_ERR_CAPACITY / FDGS_ERR_TIMEOUT raised by a kernel since the last read. */
 int fdgs_status_sync(fdgs_scene *scene);

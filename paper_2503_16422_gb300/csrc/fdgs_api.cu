@@ -157,6 +157,7 @@ struct BatchPlan {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   int footprint = 5, ctas = 0;
+  int staging = -1;                            // record staging the graph was captured with
   bool tuned = false;
   std::vector<float> lat_ms;
   Buf stamps;                                  // u64[kBatchStages + 1] %globaltimer
@@ -696,6 +697,9 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   L.sort_scratch = p.scratch.p;
   L.footprint = p.footprint;
   L.blend_ctas_per_sm = p.ctas;
+  L.staging = g_batch_staging;
+  b.rec_map_ok = 0;
+  if (g_batch_staging == 1) encode_record_map(b, p.rn);   // cp.async staging if it fails
 }
 
 int plan_capture(fdgs_scene *s, BatchPlan &p) {
@@ -713,6 +717,7 @@ int plan_capture(fdgs_scene *s, BatchPlan &p) {
   b.score = nullptr;
   b.score_variant = 0;
   b.mark = 0;
+  p.staging = g_batch_staging;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeRelaxed));
   cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice, p.cap);
@@ -735,6 +740,7 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
   // a counting profile (fdgs_profile_enable bit1) runs the batch eagerly with the counting
   // blend variant, so that fdgs_profile_read returns its evaluation and test counts
   const bool count = (s->prof & 2) && s->evals.p;
+  if (p.exec && p.staging != g_batch_staging) TRY(plan_capture(s, p));
   for (int attempt = 0; attempt < 4; ++attempt) {
     if (p.exec && !count && !p.weighted) {
       CK(cudaGraphLaunch(p.exec, st));
@@ -797,6 +803,7 @@ int batch_args_ok(fdgs_scene *s, const fdgs_camera *cams, const float *ts, int n
 
 void fdgs::set_error_message(const char *msg) { g_err = msg ? msg : ""; }
 int fdgs::g_list_mode = 0;
+int fdgs::g_batch_staging = 0;
 
 extern "C" {
 
@@ -1442,6 +1449,13 @@ int fdgs_set_list_builder(int mode) {
   if (mode < 0 || mode > 2)
     return fail(FDGS_ERR_INVALID, "mode must be 0 (auto), 1 (sort) or 2 (bitmask)");
   g_list_mode = mode;
+  return FDGS_OK;
+}
+
+int fdgs_set_batch_staging(int mode) {
+  if (mode < 0 || mode > 1)
+    return fail(FDGS_ERR_INVALID, "staging must be 0 (cp.async) or 1 (TMA gather4)");
+  g_batch_staging = mode;
   return FDGS_OK;
 }
 

@@ -515,13 +515,26 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
 // The minimum resident CTAs cap the registers at 69 (four pixels a lane) so that 14 CTAs fit
 // an SM (measured: 9.42 ms per 64 frames at 14 CTAs against 9.88 ms at the compiler's own 80
 // registers, 12 CTAs).
-template <int FW, int PX, bool kCount, bool kWeights = false>
+// kTma: records staged by TMA gather4 through b.rec_map (the map lives in the kernel's
+// parameter space, hence __grid_constant__); a stage wait that gives up ends the CTA's work
+// with kErrTimeout set.
+template <int FW, int PX, bool kCount, bool kWeights = false, bool kTma = false>
 __global__ void __launch_bounds__(256 / PX, PX == 4 ? 14 : (PX == 2 ? 7 : 4))
-    k_blend_persist(BatchDev b) {
-  __shared__ BlendSmem<256 / PX> sm;
+    k_blend_persist(const __grid_constant__ BatchDev b) {
+  constexpr int NT = 256 / PX;
+  __shared__ BlendSmem<NT, kTma> sm;
   __shared__ uint32_t s_q;
   __shared__ uint32_t s_tile_base[kMaxReq];
-  for (int r = threadIdx.x; r < b.nreq; r += 256 / PX) s_tile_base[r] = b.reqs[r].tile_base;
+  for (int r = threadIdx.x; r < b.nreq; r += NT) s_tile_base[r] = b.reqs[r].tile_base;
+  uint32_t tma_ph = 0;
+  if constexpr (kTma) {
+    if (threadIdx.x == 0) {
+      mbar_init((uint32_t)__cvta_generic_to_shared(&sm.stage.bar[0]), NT / 4);
+      mbar_init((uint32_t)__cvta_generic_to_shared(&sm.stage.bar[1]), NT / 4);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
   for (;;) {
     if (threadIdx.x == 0) s_q = atomicAdd(&b.ctr[BC_QUEUE], 1u);
     __syncthreads();
@@ -556,11 +569,16 @@ __global__ void __launch_bounds__(256 / PX, PX == 4 ? 14 : (PX == 2 ? 7 : 4))
     bt.w_sum = kWeights ? b.w_sum : nullptr;
     bt.stop_mark = kWeights ? b.stop_mark : nullptr;
     bt.evals = b.evals;
+    bt.tmap = &b.rec_map;
+    bt.err = b.err;
+    bool ok;
     if (!kWeights && !kCount && q.bg[0] == 0.f && q.bg[1] == 0.f && q.bg[2] == 0.f)
-      blend_tile<uint32_t, FW, PX, false, false, false, true, true>(bt, b.lists, 0xFFFFFFFFu,
-                                                                    sm);
+      ok = blend_tile<uint32_t, FW, PX, false, false, false, true, true, kTma>(
+          bt, b.lists, 0xFFFFFFFFu, sm, tma_ph);
     else
-      blend_tile<uint32_t, FW, PX, kWeights, kCount, false, true>(bt, b.lists, 0xFFFFFFFFu, sm);
+      ok = blend_tile<uint32_t, FW, PX, kWeights, kCount, false, true, false, kTma>(
+          bt, b.lists, 0xFFFFFFFFu, sm, tma_ph);
+    if (!ok) break;                              // uniform over the CTA
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(&b.done_ns[r], (unsigned long long)global_timer_ns());
   }
@@ -647,12 +665,26 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
                                                     64, 0);
       per_sm = std::max(1, per_sm);
     }
-    k_blend_persist<8, 4, false, true><<<per_sm * num_sms(), 64, 0, st>>>(b2);
+    if (L.staging == 1 && b.rec_map_ok)
+      k_blend_persist<8, 4, false, true, true><<<per_sm * num_sms(), 64, 0, st>>>(b2);
+    else
+      k_blend_persist<8, 4, false, true><<<per_sm * num_sms(), 64, 0, st>>>(b2);
     if (b.score) launch_score_batch(b2, st);
     if (b.mark) launch_mark_batch(b2, st);
   } else {
+    const bool tma = L.staging == 1 && b.rec_map_ok;
     with_blend_shape(L.footprint, [&](auto fw, auto px) {
       constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
+      if constexpr (PX == 4) {
+        // the gather4 staging is built for the four-pixels-a-lane shapes
+        if (tma) {
+          if (b.evals)
+            k_blend_persist<FW, PX, true, false, true><<<grid, 256 / PX, 0, st>>>(b2);
+          else
+            k_blend_persist<FW, PX, false, false, true><<<grid, 256 / PX, 0, st>>>(b2);
+          return;
+        }
+      }
       if (b.evals)
         k_blend_persist<FW, PX, true><<<grid, 256 / PX, 0, st>>>(b2);
       else
@@ -660,6 +692,38 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
     });
   }
   mark(7);
+}
+
+bool encode_record_map(BatchDev &b, uint64_t rows) {
+  using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  // the driver's encoder, fetched once (no link against the driver library)
+  static const Encode enc = []() -> Encode {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                         cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<Encode>(fn);
+  }();
+  b.rec_map_ok = 0;
+  // gather4 row coordinates are 32-bit signed; the base must be 16-byte aligned
+  if (!enc || !b.rec || rows == 0 || rows >= (1ull << 31) || ((uintptr_t)b.rec & 15)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)kRec, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kRec * sizeof(float)};   // 48 B rows
+  const cuuint32_t box[2] = {(cuuint32_t)kRec, 1};                      // one row high
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&b.rec_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)b.rec, dims, strides, box,
+          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  b.rec_map_ok = 1;
+  return true;
 }
 
 int batch_blend_max_ctas_per_sm(int shape) {

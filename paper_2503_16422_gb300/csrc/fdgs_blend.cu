@@ -29,7 +29,8 @@ k_blend(BlendArgs a, const K *__restrict__ keys, uint32_t rmask) {
   bt.w_sum = a.w_sum;
   bt.stop_mark = a.stop_mark;
   bt.evals = a.evals;
-  blend_tile<K, FW, PX, kWeights, kCount, true>(bt, keys, rmask, sm);
+  uint32_t no_tma = 0;
+  blend_tile<K, FW, PX, kWeights, kCount, true>(bt, keys, rmask, sm, no_tma);
 }
 
 // Sums of eight per-lane values over the warp by a transposed butterfly: at offsets 16, 8

@@ -79,11 +79,26 @@ __device__ __forceinline__ bool may_hit_rect(float4 g0, float c2, float lga, flo
   return qmax + lga >= kLog2AlphaMin - kCullMargin;
 }
 
+// The staged records of a batch of NT list entries, double-buffered. cp.async (per thread,
+// 16 bytes at a time) fills three structure-of-arrays planes; TMA (tile::gather4, four
+// 48-byte rows of the record tensor per instruction) fills rows, four to a 256-byte chunk
+// whose start is 128-byte aligned as tensor copies require, with one transaction-counting
+// mbarrier per buffer.
 template <int NT>
-struct BlendSmem {
+struct StageSoa {
   float4 g0[2][NT];            // u, v, a2, b2
   float4 g1[2][NT];            // c2, lga, r, g
   float4 g2[2][NT];            // b, kx, ky, radius
+};
+template <int NT>
+struct StageRows {
+  alignas(128) unsigned char c[2][NT / 4][256];
+  unsigned long long bar[2];
+};
+
+template <int NT, bool kTma = false>
+struct BlendSmem {
+  typename std::conditional<kTma, StageRows<NT>, StageSoa<NT>>::type stage;
   uint32_t rk[2][NT];          // rank (score weights)
   uint16_t idx[NT];            // compacted survivors of the tile test
   uint32_t wcnt[NT / 32];
@@ -94,6 +109,37 @@ struct BlendSmem {
   float4 h1[NT / 32][32];
   float2 h2[NT / 32][32];
 };
+
+// mbarrier and TMA helpers of the gather4 staging (shared-window addresses).
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_arrive(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Four rows (r0..r3) of a 2D float tensor, columns [0, box width), into dst.
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void *tmap, uint32_t bar,
+                                            uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(tmap), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+      : "memory");
+}
+// Spin limit of a stage wait (each try_wait may itself suspend for a while): far above any
+// legitimate copy time, so it only ends a broken protocol.
+constexpr uint32_t kTmaSpin = 1u << 20;
 
 // Where one tile's inputs and outputs live.
 struct BlendTile {
@@ -111,6 +157,8 @@ struct BlendTile {
   uint32_t *stop_mark;         // per-rank flag: the entry stopped a pixel (with w_sum)
   unsigned long long *evals;   // [3] evaluations, culling tests, alpha >= 1/255 evaluations
                                // (profiling) or null
+  const void *tmap = nullptr;  // kTma: tensor map of the 12-float records (kBlk)
+  uint32_t *err = nullptr;     // kTma: error word (kErrTimeout when a stage wait gives up)
 };
 
 // kAux: also write the final transmittance and 1 + the list position of the last blended
@@ -123,16 +171,22 @@ struct BlendTile {
 // marked by T = 0 instead of a flag. Every later entry then gives alpha T = 0, so its colour
 // sums stay bit-for-bit the same, and the final C + T bg equals the flag form's C + T_stop bg
 // for bg = 0; the loop keeps no per-pixel flags.
+// kTma (block lists only): records are staged by TMA gather4 (four per instruction, issued by
+// every fourth thread for its own entry and the next three) instead of per-thread cp.async;
+// tma_ph carries the two buffers' mbarrier phases across the tiles of a persistent CTA.
+// Returns false when a stage wait gave up (kErrTimeout set; nothing is in flight).
 template <typename K, int FW, int PX, bool kWeights, bool kCount, bool kAux, bool kBlk = false,
-          bool kTz = false>
-__device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restrict__ keys,
-                                           uint32_t rmask, BlendSmem<256 / PX> &sm) {
+          bool kTz = false, bool kTma = false>
+__device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restrict__ keys,
+                                           uint32_t rmask, BlendSmem<256 / PX, kTma> &sm,
+                                           uint32_t &tma_ph) {
   constexpr int NT = 256 / PX;   // threads = records staged per batch
   constexpr int FH = 32 * PX / FW;
   constexpr int HW = FW / PX;    // lanes per footprint row
   constexpr int WX = kTile / FW;
   static_assert(FW % PX == 0 && FW <= kTile && FH * (NT / 32) == kTile * WX, "shape");
   static_assert(!kTz || (!kWeights && !kCount && !kAux), "kTz: plain colour blend only");
+  static_assert(!kTma || (kBlk && NT % 4 == 0), "kTma: block lists, whole chunks");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int fx0 = bt.tx * kTile + (warp % WX) * FW, fy0 = bt.ty * kTile + (warp / WX) * FH;
   const int px0 = fx0 + lane % HW, py = fy0 + lane / HW;
@@ -178,21 +232,67 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     kr = i < n ? keys[bt.range.x + i] : (K)0;
     if (kBlk && i < n && !((bt.tmask[bt.range.x + i] >> bt.tbit) & 1u)) kr = kNone;
   };
+  uint32_t none_bits = 0;        // kTma: bit st set when this thread's entry of buffer st
+                                 // does not cover the tile (its record is staged anyway)
   auto issue = [&](int b) {
     const int st = b & 1;
     const uint32_t i = (uint32_t)b * NT + tid;
-    if (kBlk && i < n && kr == kNone) sm.g1[st][tid].y = -INFINITY;
-    if (i < n && (!kBlk || kr != kNone)) {
-      const uint32_t r = (uint32_t)(kr & (K)rmask);
-      // block lists index the batch's 12-float records by (request, id); tile lists the
-      // per-frame 16-float records by depth rank
-      const float *rp = bt.rec_sorted + (size_t)r * (kBlk ? kRec : kRecS);
-      cp_async16(&sm.g0[st][tid], rp);
-      cp_async16(&sm.g1[st][tid], rp + 4);
-      cp_async16(&sm.g2[st][tid], rp + 8);
+    if constexpr (kTma) {
+      const bool mine = i < n && kr != kNone;
+      const uint32_t r = mine ? (uint32_t)(kr & (K)rmask) : 0u;   // row 0 fills the tail
+      none_bits = (none_bits & ~(1u << st)) | (mine ? 0u : (1u << st));
       if (kWeights) sm.rk[st][tid] = r;
+      const uint32_t r1 = __shfl_down_sync(0xffffffffu, r, 1);
+      const uint32_t r2 = __shfl_down_sync(0xffffffffu, r, 2);
+      const uint32_t r3 = __shfl_down_sync(0xffffffffu, r, 3);
+      if ((tid & 3) == 0) {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&sm.stage.bar[st]);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&sm.stage.c[st][tid >> 2][0]);
+        // the buffer was last read through the generic proxy (ordered by the CTA barrier)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_arrive(bar, 4u * kRec * 4u);
+        tma_gather4(dst, bt.tmap, bar, r, r1, r2, r3);
+      }
+    } else {
+      if (kBlk && i < n && kr == kNone) sm.stage.g1[st][tid].y = -INFINITY;
+      if (i < n && (!kBlk || kr != kNone)) {
+        const uint32_t r = (uint32_t)(kr & (K)rmask);
+        // block lists index the batch's 12-float records by (request, id); tile lists the
+        // per-frame 16-float records by depth rank
+        const float *rp = bt.rec_sorted + (size_t)r * (kBlk ? kRec : kRecS);
+        cp_async16(&sm.stage.g0[st][tid], rp);
+        cp_async16(&sm.stage.g1[st][tid], rp + 4);
+        cp_async16(&sm.stage.g2[st][tid], rp + 8);
+        if (kWeights) sm.rk[st][tid] = r;
+      }
+      cp_async_commit();
     }
-    cp_async_commit();
+  };
+  // kTma: waits for buffer st's copies (bounded); false when the wait gave up
+  auto wait_buf = [&](int st) -> bool {
+    if constexpr (kTma) {
+      const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&sm.stage.bar[st]);
+      const uint32_t ph = (tma_ph >> st) & 1u;
+      bool ok = false;
+      for (uint32_t it = 0; it < kTmaSpin && !ok; ++it) ok = mbar_try_wait(bar, ph);
+      tma_ph ^= 1u << st;
+      return ok;
+    } else {
+      return true;
+    }
+  };
+  // the three float4 of staged record j of buffer st
+  auto staged = [&](int st, int j, float4 &a, float4 &b4, float4 &c) {
+    if constexpr (kTma) {
+      const float4 *q = reinterpret_cast<const float4 *>(&sm.stage.c[st][j >> 2][(j & 3) * 48]);
+      a = q[0];
+      b4 = q[1];
+      c = q[2];
+    } else {
+      a = sm.stage.g0[st][j];
+      b4 = sm.stage.g1[st][j];
+      c = sm.stage.g2[st][j];
+    }
   };
 
   if (nb > 0) {
@@ -204,21 +304,31 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
     if (b + 1 < nb) {
       issue(b + 1);
       if (b + 2 < nb) load_key(b + 2);
-      cp_async_wait<1>();
+      if constexpr (!kTma) cp_async_wait<1>();
     } else {
-      cp_async_wait<0>();
+      if constexpr (!kTma) cp_async_wait<0>();
     }
-    __syncthreads();
+    if constexpr (kTma) {
+      // every thread waits for the buffer's copies; a wait that gives up ends the tile (and
+      // the CTA's work) after the other buffer's copies, if any are in flight, are waited for
+      const bool ok = wait_buf(b & 1);
+      if (__syncthreads_or(!ok)) {
+        if (b + 1 < nb) wait_buf((b + 1) & 1);
+        if (tid == 0) atomicOr(bt.err, kErrTimeout);
+        return false;
+      }
+    } else {
+      __syncthreads();
+    }
     const int st = b & 1;
     const int cnt = (int)min((uint32_t)NT, n - (uint32_t)b * NT);
     const uint32_t pos1 = (uint32_t)b * NT + 1;
     // 1. tile-level test of the thread's own staged Gaussian, block compaction
     bool keep = false;
     if (kCount && tid < cnt) ++ntests;
-    if (tid < cnt) {
-      const float4 g0 = sm.g0[st][tid];
-      const float2 g1 = *reinterpret_cast<const float2 *>(&sm.g1[st][tid]);
-      const float4 g2 = sm.g2[st][tid];
+    if (tid < cnt && !(kTma && ((none_bits >> st) & 1u))) {
+      float4 g0, g1, g2;
+      staged(st, tid, g0, g1, g2);
       keep = may_hit_rect(g0, g1.x, g1.y, g2.y, g2.z, tx0, tx0 + (kTile - 1), ty0,
                           ty0 + (kTile - 1));
     }
@@ -245,9 +355,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
       if (kCount && c0 + lane < ncomp) ++ntests;
       if (c0 + lane < ncomp) {
         j = sm.idx[c0 + lane];
-        g0 = sm.g0[st][j];
-        g1 = sm.g1[st][j];
-        g2 = sm.g2[st][j];
+        staged(st, j, g0, g1, g2);
         hit = may_hit_rect(g0, g1.x, g1.y, g2.y, g2.z, fxl, fxh, fyl, fyh);
       }
       const uint32_t m = __ballot_sync(0xffffffffu, hit);
@@ -361,7 +469,15 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
       warp_done = __all_sync(0xffffffffu, lane_done);
     }
     if (__syncthreads_and(warp_done)) {
-      cp_async_wait<0>();
+      if constexpr (kTma) {
+        // the next buffer's copies are in flight: consume its phase before leaving
+        if (b + 1 < nb && !wait_buf((b + 1) & 1)) {
+          if (tid == 0) atomicOr(bt.err, kErrTimeout);
+          return false;
+        }
+      } else {
+        cp_async_wait<0>();
+      }
       break;
     }
   }
@@ -399,6 +515,7 @@ __device__ __forceinline__ void blend_tile(const BlendTile &bt, const K *__restr
       }
     }
   }
+  return true;
 }
 
 }  // namespace fdgs

@@ -1,5 +1,6 @@
 // Internal host-side interfaces between the C ABI and the kernel files.
 #pragma once
+#include <cuda.h>            // CUtensorMap (types only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -218,6 +219,10 @@ struct BatchDev {
   int score_variant;                 // fdgs_score_variant of the score pass
   int mark;
   unsigned long long *stamps;        // [kBatchStages + 1] %globaltimer at stage boundaries
+  // TMA descriptor of rec as a 2D tensor (12 floats x nreq n rows, 48-byte rows, box 12 x 1)
+  // for the blend's gather4 staging; valid when rec_map_ok
+  alignas(64) CUtensorMap rec_map;
+  int rec_map_ok;
 };
 struct BatchLaunch {
   size_t diff_bytes;
@@ -226,7 +231,13 @@ struct BatchLaunch {
   int blend_ctas_per_sm;             // persistent blend grid = this x SMs
   const uint64_t *vis_sorted;        // out: the buffer that holds the sorted depth keys
   uint64_t wsum_len;                 // entries of the weighted passes' buffers (nreq x n)
+  int staging;                       // blend record staging: 0 cp.async, 1 TMA gather4
 };
+// Encodes b.rec_map over b.rec with the given row count (nreq x n); false (and
+// b.rec_map_ok = 0) when the driver offers no tensor-map encoder or rejects the layout.
+bool encode_record_map(BatchDev &b, uint64_t rows);
+// Record staging of the batched blend for plans captured from now on (fdgs_set_batch_staging).
+extern int g_batch_staging;
 // Gaussian id bits at the bottom of the batched depth keys (request | depth | id).
 constexpr int kBatchIdBits = 25;
 // Stages timed by the device stamps: preprocess, depth_sort (bases, compaction, sort),

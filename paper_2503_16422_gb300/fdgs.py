@@ -96,6 +96,7 @@ _SIGNATURES = {
     "fdgs_build_keyframe_masks": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P, _P],
     "fdgs_debug_inject": [ctypes.c_int, ctypes.c_int64],
+    "fdgs_set_batch_staging": [ctypes.c_int],
 }
 # score variants of fdgs_variation_score_variant (Table 4 of the paper: f, b, c, d, e)
 SCORE_VARIANTS = {"full": 0, "spatial": 1, "temporal": 2, "first_derivative": 3, "sigma_t": 4}
@@ -550,6 +551,16 @@ def version():
 def set_list_builder(mode):
     """Tile-list builder (0: auto, 1: emit + radix sort, 2: coverage bitmasks), process-wide."""
     check(lib().fdgs_set_list_builder(int(mode)))
+
+
+STAGING_CP_ASYNC, STAGING_TMA = 0, 1
+DEFAULT_BATCH_STAGING = STAGING_CP_ASYNC    # the library's default (fdgs_set_batch_staging)
+
+
+def set_batch_staging(mode):
+    """Record staging of the batched blend, process-wide (0: per-thread cp.async, 1: TMA
+    tile::gather4); results do not depend on it."""
+    check(lib().fdgs_set_batch_staging(int(mode)))
 
 
 # launch shape of the forward blend when none is set (8x8 warp footprint, two pixels a lane)
