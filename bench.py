@@ -892,9 +892,25 @@ def finetune_timing(iters=1000, prune_ratio=0.9, lr_scale=0.3):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ls = losses.cpu().numpy()
+    # the GPU work of an iteration: the forward's and the reverse replay's stage events (the
+    # host synchronisation inside the forward excluded; the loss and Adam kernels, elementwise
+    # over the image and the attributes, are not staged), on a further 48 iterations
+    student.profile(1)
+    dev = []
+    scratch = torch.zeros(1, device="cuda")
+    for it in range(48):
+        c, t_, tgt = train[it % len(train)]
+        ft.step(c, t_, tgt, loss_accum=scratch)
+        st_ = student.profile_read()[0]
+        dev.append(sum(v for k, v in st_.items() if k != "host_sync"))
+    student.profile(0)
     out = dict(teacher_gaussians=tsc.n, kept=student.n, prune_ratio=prune_ratio,
                lr_scale=lr_scale, train_views=len(train), iterations=iters,
                ms_per_iteration=wall * 1e3 / iters,
+               gpu_stage_ms_per_iteration=float(np.median(dev)),
+               wall_over_gpu=wall * 1e3 / iters / float(np.median(dev)),
+               loop="one fdgs_finetune_step call per iteration (render through the filter, L1, "
+                    "reverse replay, Adam in place)",
                l1_first50=float(ls[:50].mean()), l1_last50=float(ls[-50:].mean()),
                train_psnr_before=train0, train_psnr_after=psnr_of(train),
                held_out_psnr_before=held0, held_out_psnr_after=psnr_of(held))

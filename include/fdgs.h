@@ -388,6 +388,30 @@ int fdgs_set_list_builder(int mode);
  * other values. */
 int fdgs_set_blend_shape(int footprint);
 
+/*
+ * Post-pruning fine-tuning (Sec. 4.2.1 "Pruning": the Gaussians the score keeps are optimised
+ * further; Sec. 4.2.2: through the key-frame filter when opts->use_mask is set), one iteration
+ * in one call. In stream order: render view cam at t with opts (a frame kept for the reverse
+ * replay) into a scene-owned image; the L1 loss against target_dev [3][H][W] (device,
+ * float32), added to *loss_accum_dev as mean |image - target| (one device float; NULL: not
+ * reported); its image gradient sign(image - target) / (3 H W); the reverse replay into
+ * scene-owned gradient buffers; and one Adam step (Kingma and Ba, in PyTorch's formulation
+ * with bias corrections) that updates the scene's attribute arrays IN PLACE, so they must be
+ * writable device memory. lr[7] are the rates of mean4, logscale4, q_left, q_right,
+ * opacity_logit, the SH DC plane and the higher SH bands. The scene keeps Adam's moments and
+ * step count; fdgs_finetune_reset clears them (and a change of the scene's size does). The
+ * call synchronises the stream once (the render sizes its tile lists). FDGS_ERR_INVALID for
+ * null arguments, a bad camera or betas outside [0, 1).
+ */
+typedef struct {
+  float lr[7];
+  float beta1, beta2, eps;
+} fdgs_adam_opts;
+int fdgs_finetune_step(fdgs_scene *scene, const fdgs_camera *cam, float t,
+                       const fdgs_render_opts *opts, const float *target_dev,
+                       const fdgs_adam_opts *adam, float *loss_accum_dev, fdgs_stream stream);
+int fdgs_finetune_reset(fdgs_scene *scene);
+
 /* How the batched blend (fdgs_render_batch and the batched score and mask passes) stages the
  * blend-ready records of each tile's list entries in shared memory, process-wide; batch graphs
  * are re-captured at their next run after a change. 0 (default): per-thread 16-byte cp.async

@@ -205,6 +205,11 @@ struct fdgs_scene {
   const float *sh_cb = nullptr;        // borrowed SH codebook (fdgs_set_sh_codebook) or null
   const uint16_t *sh_code = nullptr;
   int n_code = 0;
+  // fine-tuning (fdgs_finetune_step): image, its gradient, the concatenated gradients and
+  // Adam moments of every attribute array, the loss scratch, Adam's step count
+  Buf ft_img, ft_dL, ft_grad, ft_m, ft_v, ft_loss;
+  uint64_t ft_total = 0;
+  int ft_step = 0;
 };
 
 struct fdgs_frame {
@@ -1449,6 +1454,87 @@ int fdgs_set_list_builder(int mode) {
   if (mode < 0 || mode > 2)
     return fail(FDGS_ERR_INVALID, "mode must be 0 (auto), 1 (sort) or 2 (bitmask)");
   g_list_mode = mode;
+  return FDGS_OK;
+}
+
+int fdgs_finetune_reset(fdgs_scene *s) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  s->ft_step = 0;
+  s->ft_total = 0;     // the next step zeroes the moments
+  return FDGS_OK;
+}
+
+int fdgs_finetune_step(fdgs_scene *s, const fdgs_camera *cam, float t,
+                       const fdgs_render_opts *opts, const float *target_dev,
+                       const fdgs_adam_opts *adam, float *loss_accum_dev, fdgs_stream stream) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (!cam || !target_dev || !adam) return fail(FDGS_ERR_INVALID, "null argument");
+  if (!(adam->beta1 >= 0.f && adam->beta1 < 1.f && adam->beta2 >= 0.f && adam->beta2 < 1.f &&
+        adam->eps >= 0.f))
+    return fail(FDGS_ERR_INVALID, "Adam needs 0 <= beta < 1 and eps >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t N = (uint64_t)s->d.n;
+  if (N == 0) return FDGS_OK;
+  const uint64_t K = (uint64_t)(s->d.sh_degree + 1) * (s->d.sh_degree + 1);
+  // the attribute arrays as one parameter space: mean4, logscale4, q_left, q_right, opacity,
+  // the SH DC plane and the higher SH bands (the SH array is [K][3][N], DC plane first)
+  const uint64_t len[7] = {4 * N, 4 * N, 4 * N, 4 * N, N, 3 * N, 3 * N * (K - 1)};
+  float *par[7] = {const_cast<float *>(s->d.mean4), const_cast<float *>(s->d.logscale4),
+                   const_cast<float *>(s->d.q_left), const_cast<float *>(s->d.q_right),
+                   const_cast<float *>(s->d.opacity_logit), const_cast<float *>(s->d.sh),
+                   const_cast<float *>(s->d.sh) + 3 * N};
+  uint64_t off[8] = {0};
+  for (int i = 0; i < 7; ++i) off[i + 1] = off[i] + len[i];
+  const uint64_t total = off[7];
+  TRY(grow(s->ft_grad, total * 4));
+  TRY(grow(s->ft_m, total * 4));
+  TRY(grow(s->ft_v, total * 4));
+  TRY(grow(s->ft_loss, 16));
+  if (s->ft_total != total) {
+    CK(cudaMemsetAsync(s->ft_m.p, 0, total * 4, st));
+    CK(cudaMemsetAsync(s->ft_v.p, 0, total * 4, st));
+    s->ft_total = total;
+    s->ft_step = 0;
+  }
+  const uint64_t pix = (uint64_t)cam->width * cam->height;
+  if (cam->width <= 0 || cam->height <= 0) return fail(FDGS_ERR_INVALID, "bad camera size");
+  TRY(grow(s->ft_img, pix * 12));
+  TRY(grow(s->ft_dL, pix * 12));
+  // forward with a frame kept for the reverse replay
+  fdgs_frame *f = nullptr;
+  TRY(fdgs_render(s, cam, t, opts, s->ft_img.as<float>(), &f, stream));
+  float *loss = loss_accum_dev ? loss_accum_dev : s->ft_loss.as<float>();
+  launch_l1_grad(s->ft_img.as<float>(), target_dev, (uint32_t)(3 * pix), s->ft_dL.as<float>(),
+                 loss, st);
+  float *g = s->ft_grad.as<float>();
+  CK(cudaMemsetAsync(g, 0, total * 4, st));
+  const int rc = fdgs_render_backward(s, f, s->ft_dL.as<float>(), g + off[0], g + off[1],
+                                      g + off[2], g + off[3], g + off[4], g + off[5], stream);
+  fdgs_frame_release(f);
+  TRY(rc);
+  // Adam with PyTorch's bias corrections
+  ++s->ft_step;
+  const double bc1 = 1.0 - pow((double)adam->beta1, (double)s->ft_step);
+  const double bc2 = 1.0 - pow((double)adam->beta2, (double)s->ft_step);
+  AdamArgs a{};
+  a.nseg = 0;
+  for (int i = 0; i < 7; ++i) {
+    if (len[i] == 0) continue;
+    a.off[a.nseg] = off[i];
+    a.param[a.nseg] = par[i];
+    a.step_size[a.nseg] = (float)(adam->lr[i] / bc1);
+    ++a.nseg;
+  }
+  a.off[a.nseg] = total;
+  a.grad = g;
+  a.m = s->ft_m.as<float>();
+  a.v = s->ft_v.as<float>();
+  a.b1 = adam->beta1;
+  a.b2 = adam->beta2;
+  a.eps = adam->eps;
+  a.sqrt_bc2 = (float)sqrt(bc2);
+  launch_adam(a, st);
+  CK(cudaGetLastError());
   return FDGS_OK;
 }
 

@@ -164,9 +164,9 @@ struct BlendTile {
 // kAux: also write the final transmittance and 1 + the list position of the last blended
 // entry per pixel (what the reverse replay of the backward starts from).
 // kBlk: keys[range] is the list of the tile's block of tiles, entries (indices of 12-float
-// records) in rank order with a mask of the block's tiles each covers; only entries with bit tbit are staged (the others
-// get log2 opacity -inf, so the tile test drops them), and the tile composites exactly its
-// own list.
+// records) in rank order with a mask of the block's tiles each covers; only entries with bit
+// tbit are staged and tested (the others are flagged per thread and skip the tile test), and
+// the tile composites exactly its own list.
 // kTz (black background, no weights, counts or side outputs): a pixel that has stopped is
 // marked by T = 0 instead of a flag. Every later entry then gives alpha T = 0, so its colour
 // sums stay bit-for-bit the same, and the final C + T bg equals the flag form's C + T_stop bg
@@ -232,8 +232,9 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
     kr = i < n ? keys[bt.range.x + i] : (K)0;
     if (kBlk && i < n && !((bt.tmask[bt.range.x + i] >> bt.tbit) & 1u)) kr = kNone;
   };
-  uint32_t none_bits = 0;        // kTma: bit st set when this thread's entry of buffer st
-                                 // does not cover the tile (its record is staged anyway)
+  uint32_t none_bits = 0;        // kBlk: bit st set when this thread's entry of buffer st
+                                 // does not cover the tile (nothing is staged for it with
+                                 // cp.async; TMA stages its record anyway); it skips the tests
   auto issue = [&](int b) {
     const int st = b & 1;
     const uint32_t i = (uint32_t)b * NT + tid;
@@ -254,7 +255,7 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
         tma_gather4(dst, bt.tmap, bar, r, r1, r2, r3);
       }
     } else {
-      if (kBlk && i < n && kr == kNone) sm.stage.g1[st][tid].y = -INFINITY;
+      if (kBlk) none_bits = (none_bits & ~(1u << st)) | ((i < n && kr == kNone) ? (1u << st) : 0u);
       if (i < n && (!kBlk || kr != kNone)) {
         const uint32_t r = (uint32_t)(kr & (K)rmask);
         // block lists index the batch's 12-float records by (request, id); tile lists the
@@ -326,7 +327,7 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
     // 1. tile-level test of the thread's own staged Gaussian, block compaction
     bool keep = false;
     if (kCount && tid < cnt) ++ntests;
-    if (tid < cnt && !(kTma && ((none_bits >> st) & 1u))) {
+    if (tid < cnt && !(kBlk && ((none_bits >> st) & 1u))) {
       float4 g0, g1, g2;
       staged(st, tid, g0, g1, g2);
       keep = may_hit_rect(g0, g1.x, g1.y, g2.y, g2.z, tx0, tx0 + (kTile - 1), ty0,

@@ -233,6 +233,24 @@ struct BatchLaunch {
   uint64_t wsum_len;                 // entries of the weighted passes' buffers (nreq x n)
   int staging;                       // blend record staging: 0 cp.async, 1 TMA gather4
 };
+// ---- post-pruning fine-tuning (fdgs_finetune.cu) ----------------------------------------
+// dL = sign(img - target) / n, loss += mean |img - target| (n floats)
+void launch_l1_grad(const float *img, const float *target, uint32_t n, float *dL, float *loss,
+                    cudaStream_t st);
+// One Adam step over nseg segments of a concatenated parameter space: segment s is
+// [off[s], off[s + 1]) of grad, m and v, and updates param[s] in place with its step size
+// lr_s / (1 - b1^step); sqrt_bc2 = sqrt(1 - b2^step).
+struct AdamArgs {
+  int nseg;
+  uint64_t off[9];
+  float *param[8];
+  float step_size[8];
+  const float *grad;
+  float *m, *v;
+  float b1, b2, eps, sqrt_bc2;
+};
+void launch_adam(const AdamArgs &a, cudaStream_t st);
+
 // Encodes b.rec_map over b.rec with the given row count (nreq x n); false (and
 // b.rec_map_ok = 0) when the driver offers no tensor-map encoder or rejects the layout.
 bool encode_record_map(BatchDev &b, uint64_t rows);

@@ -40,6 +40,11 @@ class fdgs_camera(ctypes.Structure):
                 ("width", ctypes.c_int), ("height", ctypes.c_int), ("znear", ctypes.c_float)]
 
 
+class fdgs_adam_opts(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 7), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
 class fdgs_render_opts(ctypes.Structure):
     _fields_ = [("use_mask", ctypes.c_int), ("bg", ctypes.c_float * 3), ("tile_sets", ctypes.c_int),
                 ("no_temporal_cull", ctypes.c_int)]
@@ -97,6 +102,10 @@ _SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P, _P],
     "fdgs_debug_inject": [ctypes.c_int, ctypes.c_int64],
     "fdgs_set_batch_staging": [ctypes.c_int],
+    "fdgs_finetune_step": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_float,
+                           ctypes.POINTER(fdgs_render_opts), _P, ctypes.POINTER(fdgs_adam_opts),
+                           _P, _P],
+    "fdgs_finetune_reset": [_P],
 }
 # score variants of fdgs_variation_score_variant (Table 4 of the paper: f, b, c, d, e)
 SCORE_VARIANTS = {"full": 0, "spatial": 1, "temporal": 2, "first_derivative": 3, "sigma_t": 4}
@@ -347,6 +356,29 @@ class Scene:
         if keep_frame:
             return out, Frame(self, fh)
         return out
+
+    def finetune_step(self, cam, t, target, lr, betas=(0.9, 0.999), eps=1e-15, use_mask=True,
+                      tight=True, loss_accum=None, stream=None):
+        """One fine-tuning iteration in libfdgs (fdgs_finetune_step): render, L1 loss against
+        ``target`` [3,H,W], reverse replay and an Adam step on the scene's own attribute
+        tensors in place. ``lr``: the seven rates (mean4, logscale4, q_left, q_right,
+        opacity_logit, SH DC, higher SH bands). The loss is added to ``loss_accum`` (a device
+        float tensor) when given."""
+        c = make_camera(cam)
+        o = _opts(use_mask, (0.0, 0.0, 0.0), tight)
+        a = fdgs_adam_opts()
+        for i, v in enumerate(lr):
+            a.lr[i] = float(v)
+        a.beta1, a.beta2, a.eps = float(betas[0]), float(betas[1]), float(eps)
+        tgt = target.contiguous()
+        check(lib().fdgs_finetune_step(self.handle, ctypes.byref(c), float(t), ctypes.byref(o),
+                                       _ptr(tgt), ctypes.byref(a),
+                                       _ptr(loss_accum) if loss_accum is not None else None,
+                                       _stream(stream)))
+
+    def finetune_reset(self):
+        """Clears the Adam moments and step count of fdgs_finetune_step."""
+        check(lib().fdgs_finetune_reset(self.handle))
 
     def render_backward(self, frame: Frame, dL_drgb, grads=None, stream=None):
         """Adds the gradients of L (given dL/drgb [3,H,W]) into ``grads`` (a SceneTensors of

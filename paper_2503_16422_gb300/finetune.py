@@ -3,8 +3,8 @@ kept by the spatial-temporal variation score, rendered through the key-frame fil
 optimised against target images for a number of iterations to recover what pruning and the
 filter lost.
 
-Every render and gradient runs in libfdgs (``fdgs.render``: the forward rasterizer and the
-hand-written reverse replay); PyTorch provides the device tensors and the Adam update.
+Every step runs in libfdgs (``fdgs_finetune_step``: the forward rasterizer, the L1 loss, the
+hand-written reverse replay and the Adam update); PyTorch provides the device tensors.
 """
 from __future__ import annotations
 
@@ -41,48 +41,34 @@ def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:
     return float("inf") if mse == 0 else -10.0 * math.log10(mse)
 
 
+LR_ORDER = ("mean4", "logscale4", "q_left", "q_right", "opacity_logit", "sh_dc", "sh_rest")
+
+
 class FineTuner:
-    """Adam over the scene's own parameter tensors (the scene borrows them, so each in-place
-    update is what the next render sees)."""
+    """Adam over the scene's own attribute tensors, one libfdgs call per iteration
+    (fdgs_finetune_step: render through the filter, L1 loss, reverse replay, Adam step in
+    place; the scene borrows the tensors, so the next render sees the update). The SH DC
+    plane and the higher bands take their own rates."""
 
     def __init__(self, scene: fdgs.Scene, lr=None):
         self.scene = scene
-        p = scene.params
         lr = dict(DEFAULT_LR, **(lr or {}))
-        for x in p.list():
-            x.requires_grad_(True)
-        # the SH tensor is one leaf; its DC plane and the higher bands take different rates by
-        # scaling the gradient of the higher bands before the update
-        self.sh_rest_scale = lr["sh_rest"] / lr["sh_dc"]
-        self.opt = torch.optim.Adam([
-            dict(params=[p.mean4], lr=lr["mean4"]),
-            dict(params=[p.logscale4], lr=lr["logscale4"]),
-            dict(params=[p.q_left], lr=lr["q_left"]),
-            dict(params=[p.q_right], lr=lr["q_right"]),
-            dict(params=[p.opacity_logit], lr=lr["opacity_logit"]),
-            dict(params=[p.sh], lr=lr["sh_dc"]),
-        ], eps=1e-15)
+        self.lr = [lr[k] for k in LR_ORDER]
+        scene.finetune_reset()
 
-    def step(self, cam, t, target, use_mask=True):
-        """One iteration: L1 loss of the render against ``target``; returns the loss."""
-        img = fdgs.render(self.scene, cam, t, use_mask=use_mask, tight=True)
-        loss = torch.mean(torch.abs(img - target))
-        self.opt.zero_grad(set_to_none=False)
-        loss.backward()
-        sh = self.scene.params.sh
-        if sh.grad is not None and sh.shape[0] > 1:
-            sh.grad[1:].mul_(self.sh_rest_scale)
-        with torch.no_grad():
-            self.opt.step()
-        return loss.detach()
+    def step(self, cam, t, target, use_mask=True, loss_accum=None):
+        """One iteration against ``target``; adds the L1 loss to ``loss_accum`` (a device
+        float tensor) when given."""
+        self.scene.finetune_step(cam, t, target, self.lr, eps=1e-15, use_mask=use_mask,
+                                 tight=True, loss_accum=loss_accum)
 
     def run(self, views, iters, use_mask=True, log_every=0):
         """``views``: list of (camera, t, target image). Cycles through them in order for
         ``iters`` iterations; returns the per-iteration losses (a device tensor)."""
-        losses = torch.empty(iters, device=self.scene.device)
+        losses = torch.zeros(iters, device=self.scene.device)
         for it in range(iters):
             cam, t, target = views[it % len(views)]
-            losses[it] = self.step(cam, t, target, use_mask)
+            self.step(cam, t, target, use_mask, loss_accum=losses[it:it + 1])
             if log_every and (it + 1) % log_every == 0:
                 print(f"iter {it + 1}: L1 {float(losses[it]):.5f}")
         return losses
