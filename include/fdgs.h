@@ -383,9 +383,10 @@ int fdgs_set_list_builder(int mode);
 /* Launch shape of the forward blend, process-wide: the pixel footprint of one warp inside a
  * 16x16 tile and the pixels each lane composites (one CTA of 256 / pixels-per-lane threads per
  * tile): 0: 16x2, 1: 8x4, 2: 4x8 (one pixel per lane), 3: 8x8 (two, the default), 4: 16x8,
- * 5: 8x16 (four). Each warp culls, by ballot, the Gaussians that cannot reach alpha >= 1/255
- * anywhere in its footprint; results do not depend on the shape. Returns FDGS_ERR_INVALID for
- * other values. */
+ * 5: 8x16 (four), 6: 16x16 (eight: one warp per tile). Each warp culls, by ballot, the
+ * Gaussians that cannot reach alpha >= 1/255 anywhere in its footprint; results do not depend
+ * on the shape. The batch autotuner (fdgs_batch_autotune) searches the same shapes for the
+ * batched blend. Returns FDGS_ERR_INVALID for other values. */
 int fdgs_set_blend_shape(int footprint);
 
 /*
@@ -411,6 +412,15 @@ int fdgs_finetune_step(fdgs_scene *scene, const fdgs_camera *cam, float t,
                        const fdgs_render_opts *opts, const float *target_dev,
                        const fdgs_adam_opts *adam, float *loss_accum_dev, fdgs_stream stream);
 int fdgs_finetune_reset(fdgs_scene *scene);
+
+/* Launch shape of the scene's batched blend (fdgs_render_batch): a blend shape as in
+ * fdgs_set_blend_shape and the persistent CTAs per SM (0: the occupancy limit). It applies to
+ * the current batch plan (whose next batch runs eagerly and re-captures its graph) and to the
+ * plans of new batch geometries, until fdgs_batch_autotune picks a shape for a plan. The
+ * default is shape 6 (16x16 warp footprint, eight pixels a lane) at the occupancy limit.
+ * Results do not depend on it. FDGS_ERR_INVALID for a shape outside [0, 7) or CTAs outside
+ * [0, 64]. */
+int fdgs_set_batch_shape(fdgs_scene *scene, int footprint, int ctas_per_sm);
 
 /* How the batched blend (fdgs_render_batch and the batched score and mask passes) stages the
  * blend-ready records of each tile's list entries in shared memory, process-wide; batch graphs
@@ -442,6 +452,12 @@ int fdgs_status_sync(fdgs_scene *scene);
  *     look-back, so its successors wait until the spin limit. One-shot.
  *   FDGS_INJECT_FAIL_ALLOCS (value = count): the next `value` device-buffer growths fail with
  *     FDGS_ERR_OOM, as a refused cudaMalloc would.
+ *   FDGS_INJECT_TMA_MISSING_ARRIVAL (value ignored): the next batch run with TMA record
+ *     staging (fdgs_set_batch_staging(1)) runs eagerly, and in it the first issuing thread of
+ *     every CTA neither arrives on its stage barriers nor issues its copy, so no stage
+ *     completes; the stage waits give up after 4096 polls, the blend supplies the missing
+ *     arrival, waits (bounded) for the copies in flight, sets FDGS_ERR_TIMEOUT and the call
+ *     returns it. One-shot.
  *   FDGS_INJECT_NONE: clears all of the above.
  * Returns FDGS_ERR_INVALID for an unknown kind or a value out of range. Not thread-safe.
  */
@@ -449,7 +465,8 @@ enum {
   FDGS_INJECT_NONE = 0,
   FDGS_INJECT_SPIN_LIMIT = 1,
   FDGS_INJECT_WITHHOLD_PUBLISH = 2,
-  FDGS_INJECT_FAIL_ALLOCS = 3
+  FDGS_INJECT_FAIL_ALLOCS = 3,
+  FDGS_INJECT_TMA_MISSING_ARRIVAL = 4
 };
 int fdgs_debug_inject(int kind, int64_t value);
 

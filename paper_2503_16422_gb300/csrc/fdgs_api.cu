@@ -156,8 +156,10 @@ struct BatchPlan {
   unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int footprint = 5, ctas = 0;
+  int footprint = 6, ctas = 0;
   int staging = -1;                            // record staging the graph was captured with
+  int black = 1;                               // this call's requests have black backgrounds
+  int cap_black = -1;                          // ... and those the graph was captured for
   bool tuned = false;
   std::vector<float> lat_ms;
   Buf stamps;                                  // u64[kBatchStages + 1] %globaltimer
@@ -210,6 +212,9 @@ struct fdgs_scene {
   Buf ft_img, ft_dL, ft_grad, ft_m, ft_v, ft_loss;
   uint64_t ft_total = 0;
   int ft_step = 0;
+  // launch shape of new batch plans (fdgs_set_batch_shape): blend shape, CTAs per SM (0: the
+  // occupancy limit)
+  int batch_footprint = 6, batch_ctas = 0;
 };
 
 struct fdgs_frame {
@@ -602,7 +607,8 @@ int plan_build(fdgs_scene *s, BatchPlan &p, const fdgs_camera *cams, int n, bool
   CK(cudaStreamCreateWithFlags(&p.cap, cudaStreamNonBlocking));
   TRY(grow(p.stamps, (kBatchStages + 1) * 8));
   CK(cudaMallocHost(&p.h_stamps, (kBatchStages + 1) * 8));
-  p.ctas = batch_blend_max_ctas_per_sm(p.footprint);
+  p.footprint = s->batch_footprint;
+  p.ctas = s->batch_ctas ? s->batch_ctas : batch_blend_max_ctas_per_sm(p.footprint);
   return FDGS_OK;
 }
 
@@ -616,6 +622,7 @@ int plan_fill(fdgs_scene *s, BatchPlan &p, const fdgs_camera *cams, const float 
     q.t = ts[i];
     q.rgb = rgb[i];
     for (int c = 0; c < 3; ++c) q.bg[c] = opts ? opts->bg[c] : 0.f;
+    if (i == 0) p.black = q.bg[0] == 0.f && q.bg[1] == 0.f && q.bg[2] == 0.f;
     q.mask_l = q.mask_r = nullptr;
     if (p.masked) {
       int l, r;
@@ -703,6 +710,9 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   L.footprint = p.footprint;
   L.blend_ctas_per_sm = p.ctas;
   L.staging = g_batch_staging;
+  L.black = p.black;
+  b.tma_skip = g_debug_tma_skip;
+  b.tma_spin = g_debug_tma_skip ? 4096u : 0u;
   b.rec_map_ok = 0;
   if (g_batch_staging == 1) encode_record_map(b, p.rn);   // cp.async staging if it fails
 }
@@ -722,7 +732,10 @@ int plan_capture(fdgs_scene *s, BatchPlan &p) {
   b.score = nullptr;
   b.score_variant = 0;
   b.mark = 0;
+  b.tma_skip = 0;      // injections never enter a captured graph
+  b.tma_spin = 0;
   p.staging = g_batch_staging;
+  p.cap_black = p.black;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeRelaxed));
   cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice, p.cap);
@@ -745,9 +758,12 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
   // a counting profile (fdgs_profile_enable bit1) runs the batch eagerly with the counting
   // blend variant, so that fdgs_profile_read returns its evaluation and test counts
   const bool count = (s->prof & 2) && s->evals.p;
-  if (p.exec && p.staging != g_batch_staging) TRY(plan_capture(s, p));
+  if (p.exec && (p.staging != g_batch_staging || p.cap_black != p.black))
+    TRY(plan_capture(s, p));
+  // an injected stage-barrier failure runs the batch eagerly, once
+  const bool inject = g_debug_tma_skip != 0 && g_batch_staging == 1;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    if (p.exec && !count && !p.weighted) {
+    if (p.exec && !count && !p.weighted && !inject) {
       CK(cudaGraphLaunch(p.exec, st));
     } else {
       BatchDev b;
@@ -758,6 +774,7 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
                          st));
       launch_batch(b, L, st);
       p.vis_sorted = L.vis_sorted;
+      if (inject) g_debug_tma_skip = 0;
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(p.h_ctr, p.ctr.p, BC_COUNT * 4, cudaMemcpyDeviceToHost, st));
@@ -809,6 +826,7 @@ int batch_args_ok(fdgs_scene *s, const fdgs_camera *cams, const float *ts, int n
 void fdgs::set_error_message(const char *msg) { g_err = msg ? msg : ""; }
 int fdgs::g_list_mode = 0;
 int fdgs::g_batch_staging = 0;
+uint32_t fdgs::g_debug_tma_skip = 0;
 
 extern "C" {
 
@@ -1075,7 +1093,7 @@ int fdgs_batch_autotune(fdgs_scene *s, const fdgs_camera *cams, const float *ts,
   int best_f = p.footprint, best_c = p.ctas;
   for (int f = 0; f < kBlendShapes; ++f) {
     // resident CTAs per SM: the occupancy limit and half of it
-    const int maxc = batch_blend_max_ctas_per_sm(f);
+    const int maxc = batch_blend_max_ctas_per_sm(f, p.black != 0);
     std::vector<int> ctas = {std::max(1, maxc / 2), maxc};
     ctas.erase(std::unique(ctas.begin(), ctas.end()), ctas.end());
     for (int c : ctas) {
@@ -1538,6 +1556,27 @@ int fdgs_finetune_step(fdgs_scene *s, const fdgs_camera *cam, float t,
   return FDGS_OK;
 }
 
+int fdgs_set_batch_shape(fdgs_scene *s, int footprint, int ctas_per_sm) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (footprint < 0 || footprint >= kBlendShapes)
+    return fail(FDGS_ERR_INVALID, "blend shape must be in [0, %d)", kBlendShapes);
+  if (ctas_per_sm < 0 || ctas_per_sm > 64)
+    return fail(FDGS_ERR_INVALID, "CTAs per SM must be in [0, 64]");
+  s->batch_footprint = footprint;
+  s->batch_ctas = ctas_per_sm;
+  if (s->plan) {
+    BatchPlan &p = *s->plan;
+    p.footprint = footprint;
+    p.ctas = ctas_per_sm ? ctas_per_sm : batch_blend_max_ctas_per_sm(footprint);
+    p.tuned = false;
+    if (p.exec) {            // the next batch runs eagerly and captures the new shape
+      cudaGraphExecDestroy(p.exec);
+      p.exec = nullptr;
+    }
+  }
+  return FDGS_OK;
+}
+
 int fdgs_set_batch_staging(int mode) {
   if (mode < 0 || mode > 1)
     return fail(FDGS_ERR_INVALID, "staging must be 0 (cp.async) or 1 (TMA gather4)");
@@ -1590,6 +1629,7 @@ int fdgs_debug_inject(int kind, int64_t value) {
     case FDGS_INJECT_NONE:
       fdgs::g_debug_spin_limit = 0;
       fdgs::g_debug_withhold = ~0u;
+      fdgs::g_debug_tma_skip = 0;
       g_fail_allocs = 0;
       return FDGS_OK;
     case FDGS_INJECT_SPIN_LIMIT:
@@ -1605,6 +1645,9 @@ int fdgs_debug_inject(int kind, int64_t value) {
     case FDGS_INJECT_FAIL_ALLOCS:
       if (value < 0 || value > (1 << 20)) return fail(FDGS_ERR_INVALID, "bad allocation count");
       g_fail_allocs = (int)value;
+      return FDGS_OK;
+    case FDGS_INJECT_TMA_MISSING_ARRIVAL:
+      fdgs::g_debug_tma_skip = 1;
       return FDGS_OK;
     default:
       return fail(FDGS_ERR_INVALID, "unknown injection kind %d", kind);

@@ -518,8 +518,11 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
 // kTma: records staged by TMA gather4 through b.rec_map (the map lives in the kernel's
 // parameter space, hence __grid_constant__); a stage wait that gives up ends the CTA's work
 // with kErrTimeout set.
-template <int FW, int PX, bool kCount, bool kWeights = false, bool kTma = false>
-__global__ void __launch_bounds__(256 / PX, PX == 4 ? 14 : (PX == 2 ? 7 : 4))
+// kBlack: every request of the batch has a black background, so only the T = 0 colour blend
+// is compiled in (fewer registers: 64 against 71 for four pixels a lane).
+template <int FW, int PX, bool kCount, bool kWeights = false, bool kTma = false,
+          bool kBlack = false>
+__global__ void __launch_bounds__(256 / PX, PX == 8 ? 24 : (PX == 4 ? 14 : (PX == 2 ? 7 : 4)))
     k_blend_persist(const __grid_constant__ BatchDev b) {
   constexpr int NT = 256 / PX;
   __shared__ BlendSmem<NT, kTma> sm;
@@ -571,8 +574,14 @@ __global__ void __launch_bounds__(256 / PX, PX == 4 ? 14 : (PX == 2 ? 7 : 4))
     bt.evals = b.evals;
     bt.tmap = &b.rec_map;
     bt.err = b.err;
+    bt.tma_skip = b.tma_skip;
+    bt.tma_spin = b.tma_spin;
+    static_assert(!kBlack || (!kWeights && !kCount), "kBlack: plain colour blend only");
     bool ok;
-    if (!kWeights && !kCount && q.bg[0] == 0.f && q.bg[1] == 0.f && q.bg[2] == 0.f)
+    if constexpr (kBlack)
+      ok = blend_tile<uint32_t, FW, PX, false, false, false, true, true, kTma>(
+          bt, b.lists, 0xFFFFFFFFu, sm, tma_ph);
+    else if (!kWeights && !kCount && q.bg[0] == 0.f && q.bg[1] == 0.f && q.bg[2] == 0.f)
       ok = blend_tile<uint32_t, FW, PX, false, false, false, true, true, kTma>(
           bt, b.lists, 0xFFFFFFFFu, sm, tma_ph);
     else
@@ -673,6 +682,7 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
     if (b.mark) launch_mark_batch(b2, st);
   } else {
     const bool tma = L.staging == 1 && b.rec_map_ok;
+    const bool black = L.black != 0;
     with_blend_shape(L.footprint, [&](auto fw, auto px) {
       constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
       if constexpr (PX == 4) {
@@ -680,6 +690,8 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
         if (tma) {
           if (b.evals)
             k_blend_persist<FW, PX, true, false, true><<<grid, 256 / PX, 0, st>>>(b2);
+          else if (black)
+            k_blend_persist<FW, PX, false, false, true, true><<<grid, 256 / PX, 0, st>>>(b2);
           else
             k_blend_persist<FW, PX, false, false, true><<<grid, 256 / PX, 0, st>>>(b2);
           return;
@@ -687,6 +699,8 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
       }
       if (b.evals)
         k_blend_persist<FW, PX, true><<<grid, 256 / PX, 0, st>>>(b2);
+      else if (black)
+        k_blend_persist<FW, PX, false, false, false, true><<<grid, 256 / PX, 0, st>>>(b2);
       else
         k_blend_persist<FW, PX, false><<<grid, 256 / PX, 0, st>>>(b2);
     });
@@ -726,12 +740,16 @@ bool encode_record_map(BatchDev &b, uint64_t rows) {
   return true;
 }
 
-int batch_blend_max_ctas_per_sm(int shape) {
+int batch_blend_max_ctas_per_sm(int shape, bool black) {
   int per_sm = 0;
   with_blend_shape(shape, [&](auto fw, auto px) {
     constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_persist<FW, PX, false>,
-                                                  256 / PX, 0);
+    if (black)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, k_blend_persist<FW, PX, false, false, false, true>, 256 / PX, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_persist<FW, PX, false>,
+                                                    256 / PX, 0);
   });
   return std::max(1, per_sm);
 }

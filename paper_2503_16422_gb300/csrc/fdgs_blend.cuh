@@ -9,10 +9,12 @@
 // both exact for the concave exponent and conservative by a margin, so no per-pixel decision
 // changes:
 //   1. staging: each thread tests its staged Gaussian against the whole tile; survivors are
-//      compacted (block ballot + prefix) into an index list that keeps list order;
+//      compacted per warp (ballot) into index segments that, read in turn, keep list order;
 //   2. warps: lanes test 32 survivors at a time against the warp's footprint and
 //      __ballot_sync the hits; each hitting lane writes its record to the warp's hit list, and
-//      the warp evaluates the list in order, one Gaussian at a time, for 32 PX pixels.
+//      the warp evaluates the list in order, one Gaussian at a time, for 32 PX pixels. With
+//      eight pixels a lane one warp covers the tile: the CTA is that warp, its barriers are
+//      warp-level, and the footprint test is the tile test already made.
 // A culled Gaussian has alpha < 1/255 at every pixel it is culled for, so it would have been
 // skipped pixel by pixel anyway: results equal evaluating every entry at every pixel.
 //
@@ -38,7 +40,8 @@ namespace fdgs {
 
 // Launch shapes of the forward blend (kBlendShapes of them): warp footprint FW x (32 PX / FW)
 // pixels, PX pixels per lane.
-//   0: 16x2, 1: 8x4, 2: 4x8 (one pixel per lane), 3: 8x8 (two), 4: 16x8, 5: 8x16 (four)
+//   0: 16x2, 1: 8x4, 2: 4x8 (one pixel per lane), 3: 8x8 (two), 4: 16x8, 5: 8x16 (four),
+//   6: 16x16 (eight; one warp per tile, so the tile test is the footprint test)
 template <class F>
 inline void with_blend_shape(int shape, F &&f) {
   switch (shape) {
@@ -47,6 +50,7 @@ inline void with_blend_shape(int shape, F &&f) {
     case 3: f(std::integral_constant<int, 8>{}, std::integral_constant<int, 2>{}); break;
     case 4: f(std::integral_constant<int, 16>{}, std::integral_constant<int, 4>{}); break;
     case 5: f(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{}); break;
+    case 6: f(std::integral_constant<int, 16>{}, std::integral_constant<int, 8>{}); break;
     default: f(std::integral_constant<int, 8>{}, std::integral_constant<int, 1>{}); break;
   }
 }
@@ -102,7 +106,6 @@ struct BlendSmem {
   uint32_t rk[2][NT];          // rank (score weights)
   uint16_t idx[NT];            // compacted survivors of the tile test
   uint32_t wcnt[NT / 32];
-  uint32_t ncomp;
   // per warp, the records of the footprint-test hits in hit order, written by the lanes that
   // tested them: u, v, a2, b2 | c2, lga, r, g | b, stage index
   float4 h0[NT / 32][32];
@@ -159,6 +162,8 @@ struct BlendTile {
                                // (profiling) or null
   const void *tmap = nullptr;  // kTma: tensor map of the 12-float records (kBlk)
   uint32_t *err = nullptr;     // kTma: error word (kErrTimeout when a stage wait gives up)
+  uint32_t tma_skip = 0;       // kTma: failure injection, thread 0 withholds its arrivals
+  uint32_t tma_spin = 0;       // kTma: stage-wait poll limit (0: kTmaSpin)
 };
 
 // kAux: also write the final transmittance and 1 + the list position of the last blended
@@ -187,6 +192,18 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
   static_assert(FW % PX == 0 && FW <= kTile && FH * (NT / 32) == kTile * WX, "shape");
   static_assert(!kTz || (!kWeights && !kCount && !kAux), "kTz: plain colour blend only");
   static_assert(!kTma || (kBlk && NT % 4 == 0), "kTma: block lists, whole chunks");
+  // one warp covers the whole tile: a survivor of the tile test is a hit of the warp
+  constexpr bool kWholeTile = FW == kTile && FH == kTile;
+  // CTA barriers; a one-warp CTA needs only warp-level ones
+  auto cta_sync = [] {
+    if constexpr (NT == 32) __syncwarp(); else __syncthreads();
+  };
+  auto cta_and = [](bool v) -> bool {
+    if constexpr (NT == 32) return __all_sync(0xffffffffu, v); else return __syncthreads_and(v);
+  };
+  auto cta_or = [](bool v) -> bool {
+    if constexpr (NT == 32) return __any_sync(0xffffffffu, v); else return __syncthreads_or(v);
+  };
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int fx0 = bt.tx * kTile + (warp % WX) * FW, fy0 = bt.ty * kTile + (warp / WX) * FH;
   const int px0 = fx0 + lane % HW, py = fy0 + lane / HW;
@@ -246,7 +263,7 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
       const uint32_t r1 = __shfl_down_sync(0xffffffffu, r, 1);
       const uint32_t r2 = __shfl_down_sync(0xffffffffu, r, 2);
       const uint32_t r3 = __shfl_down_sync(0xffffffffu, r, 3);
-      if ((tid & 3) == 0) {
+      if ((tid & 3) == 0 && !(bt.tma_skip && tid == 0)) {
         const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&sm.stage.bar[st]);
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&sm.stage.c[st][tid >> 2][0]);
         // the buffer was last read through the generic proxy (ordered by the CTA barrier)
@@ -270,16 +287,40 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
     }
   };
   // kTma: waits for buffer st's copies (bounded); false when the wait gave up
-  auto wait_buf = [&](int st) -> bool {
+  auto wait_parity = [&](int st, uint32_t ph) -> bool {
     if constexpr (kTma) {
       const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&sm.stage.bar[st]);
-      const uint32_t ph = (tma_ph >> st) & 1u;
+      const uint32_t limit = bt.tma_spin ? bt.tma_spin : kTmaSpin;
       bool ok = false;
-      for (uint32_t it = 0; it < kTmaSpin && !ok; ++it) ok = mbar_try_wait(bar, ph);
-      tma_ph ^= 1u << st;
+      for (uint32_t it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, ph);
       return ok;
     } else {
       return true;
+    }
+  };
+  auto wait_buf = [&](int st) -> bool {
+    const bool ok = wait_parity(st, (tma_ph >> st) & 1u);
+    tma_ph ^= 1u << st;
+    return ok;
+  };
+  // kTma: a stage wait gave up. Records kErrTimeout and settles the buffers whose copies may
+  // be in flight (the one that timed out and, with in_flight, the other one): every thread
+  // waits again (bounded) before the CTA leaves. Under the injected failure, whose phases lack
+  // exactly thread 0's arrival, thread 0 supplies it first, so they complete once the copies
+  // issued have landed and none is left in flight.
+  auto give_up = [&](int st, bool in_flight) {
+    if constexpr (kTma) {
+      if (tid == 0) atomicOr(bt.err, kErrTimeout);
+      for (int k = 0; k < (in_flight ? 2 : 1); ++k) {
+        const int sb = k == 0 ? st : (st ^ 1);
+        const uint32_t ph = ((tma_ph >> sb) & 1u) ^ 1u;   // the phase waited on (bit flipped)
+        if (tid == 0 && bt.tma_skip)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                           (uint32_t)__cvta_generic_to_shared(&sm.stage.bar[sb]))
+                       : "memory");
+        wait_parity(sb, ph);
+      }
+      cta_sync();
     }
   };
   // the three float4 of staged record j of buffer st
@@ -313,13 +354,13 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
       // every thread waits for the buffer's copies; a wait that gives up ends the tile (and
       // the CTA's work) after the other buffer's copies, if any are in flight, are waited for
       const bool ok = wait_buf(b & 1);
-      if (__syncthreads_or(!ok)) {
-        if (b + 1 < nb) wait_buf((b + 1) & 1);
-        if (tid == 0) atomicOr(bt.err, kErrTimeout);
+      if (cta_or(!ok)) {
+        if (b + 1 < nb) tma_ph ^= 1u << ((b + 1) & 1);   // its phase is settled below
+        give_up(b & 1, b + 1 < nb);
         return false;
       }
     } else {
-      __syncthreads();
+      cta_sync();
     }
     const int st = b & 1;
     const int cnt = (int)min((uint32_t)NT, n - (uint32_t)b * NT);
@@ -333,31 +374,33 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
       keep = may_hit_rect(g0, g1.x, g1.y, g2.y, g2.z, tx0, tx0 + (kTile - 1), ty0,
                           ty0 + (kTile - 1));
     }
+    // survivors are compacted per warp: warp w's in idx[32 w, 32 w + wcnt[w]), so one barrier
+    // publishes them; the list of all survivors in rank order is the warps' segments in turn
     const uint32_t kb = __ballot_sync(0xffffffffu, keep);
+    if (keep) sm.idx[warp * 32 + __popc(kb & lanemask_lt())] = (uint16_t)tid;
     if (lane == 0) sm.wcnt[warp] = __popc(kb);
-    __syncthreads();
-    if (keep) {
-      uint32_t off = __popc(kb & lanemask_lt());
-      for (int w = 0; w < warp; ++w) off += sm.wcnt[w];
-      sm.idx[off] = (uint16_t)tid;
+    cta_sync();
+    int seg0[NT / 32];               // first survivor position of each warp's segment
+    int ncomp = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+      seg0[w] = ncomp;
+      ncomp += (int)sm.wcnt[w];
     }
-    if (tid == 0) {
-      uint32_t tot = 0;
-      for (int w = 0; w < NT / 32; ++w) tot += sm.wcnt[w];
-      sm.ncomp = tot;
-    }
-    __syncthreads();
-    const int ncomp = (int)sm.ncomp;
     // 2. warp footprint tests on the survivors, evaluation of the hits
     for (int c0 = 0; c0 < ncomp && !warp_done; c0 += 32) {
       bool hit = false;
       int j = 0;
       float4 g0, g1, g2;
-      if (kCount && c0 + lane < ncomp) ++ntests;
+      if (kCount && !kWholeTile && c0 + lane < ncomp) ++ntests;
       if (c0 + lane < ncomp) {
-        j = sm.idx[c0 + lane];
+        const int pos = c0 + lane;
+        int slot = pos;                // in warp 0's segment, else in the last one it reaches
+#pragma unroll
+        for (int v = 1; v < NT / 32; ++v) slot = pos >= seg0[v] ? v * 32 + pos - seg0[v] : slot;
+        j = sm.idx[slot];
         staged(st, j, g0, g1, g2);
-        hit = may_hit_rect(g0, g1.x, g1.y, g2.y, g2.z, fxl, fxh, fyl, fyh);
+        hit = kWholeTile || may_hit_rect(g0, g1.x, g1.y, g2.y, g2.z, fxl, fxh, fyl, fyh);
       }
       const uint32_t m = __ballot_sync(0xffffffffu, hit);
       if (hit) {                       // hand the record to the warp's hit list
@@ -469,11 +512,11 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
       }
       warp_done = __all_sync(0xffffffffu, lane_done);
     }
-    if (__syncthreads_and(warp_done)) {
+    if (cta_and(warp_done)) {
       if constexpr (kTma) {
         // the next buffer's copies are in flight: consume its phase before leaving
-        if (b + 1 < nb && !wait_buf((b + 1) & 1)) {
-          if (tid == 0) atomicOr(bt.err, kErrTimeout);
+        if (b + 1 < nb && cta_or(!wait_buf((b + 1) & 1))) {
+          give_up((b + 1) & 1, false);
           return false;
         }
       } else {

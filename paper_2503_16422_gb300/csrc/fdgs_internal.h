@@ -223,6 +223,8 @@ struct BatchDev {
   // for the blend's gather4 staging; valid when rec_map_ok
   alignas(64) CUtensorMap rec_map;
   int rec_map_ok;
+  uint32_t tma_skip;                 // failure injection: thread 0 skips its stage arrivals
+  uint32_t tma_spin;                 // stage-wait poll limit (0: kTmaSpin)
 };
 struct BatchLaunch {
   size_t diff_bytes;
@@ -232,6 +234,7 @@ struct BatchLaunch {
   const uint64_t *vis_sorted;        // out: the buffer that holds the sorted depth keys
   uint64_t wsum_len;                 // entries of the weighted passes' buffers (nreq x n)
   int staging;                       // blend record staging: 0 cp.async, 1 TMA gather4
+  int black;                         // every request's background is black
 };
 // ---- post-pruning fine-tuning (fdgs_finetune.cu) ----------------------------------------
 // dL = sign(img - target) / n, loss += mean |img - target| (n floats)
@@ -256,6 +259,9 @@ void launch_adam(const AdamArgs &a, cudaStream_t st);
 bool encode_record_map(BatchDev &b, uint64_t rows);
 // Record staging of the batched blend for plans captured from now on (fdgs_set_batch_staging).
 extern int g_batch_staging;
+// Failure injection (fdgs_debug_inject): the next eager TMA-staged batch withholds one arrival
+// (and its copy) on every stage barrier.
+extern uint32_t g_debug_tma_skip;
 // Gaussian id bits at the bottom of the batched depth keys (request | depth | id).
 constexpr int kBatchIdBits = 25;
 // Stages timed by the device stamps: preprocess, depth_sort (bases, compaction, sort),
@@ -268,11 +274,13 @@ void launch_score_batch(const BatchDev &b, cudaStream_t st);
 // Mask pass of a batch: sets bit id of request r's mark_row for every Gaussian that was
 // blended somewhere in r (weight > 0) or stopped one of its pixels.
 void launch_mark_batch(const BatchDev &b, cudaStream_t st);
-int batch_blend_max_ctas_per_sm(int shape);
+// Resident CTAs per SM of the persistent blend of a launch shape (black: the variant for
+// batches whose requests all have a black background).
+int batch_blend_max_ctas_per_sm(int shape, bool black = false);
 
 int num_sms();
 extern int g_blend_shape;   // launch shape of the forward blend (with_blend_shape)
-constexpr int kBlendShapes = 6;
+constexpr int kBlendShapes = 7;
 
 // Sets the message returned by fdgs_last_error() on this thread.
 void set_error_message(const char *msg);

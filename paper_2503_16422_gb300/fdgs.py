@@ -102,6 +102,7 @@ _SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P, _P],
     "fdgs_debug_inject": [ctypes.c_int, ctypes.c_int64],
     "fdgs_set_batch_staging": [ctypes.c_int],
+    "fdgs_set_batch_shape": [_P, ctypes.c_int, ctypes.c_int],
     "fdgs_finetune_step": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_float,
                            ctypes.POINTER(fdgs_render_opts), _P, ctypes.POINTER(fdgs_adam_opts),
                            _P, _P],
@@ -111,6 +112,7 @@ _SIGNATURES = {
 SCORE_VARIANTS = {"full": 0, "spatial": 1, "temporal": 2, "first_derivative": 3, "sigma_t": 4}
 # fdgs_debug_inject kinds
 INJECT_NONE, INJECT_SPIN_LIMIT, INJECT_WITHHOLD_PUBLISH, INJECT_FAIL_ALLOCS = 0, 1, 2, 3
+INJECT_TMA_MISSING_ARRIVAL = 4
 PROFILE_STAGES = ("preprocess", "depth_sort", "gather_scan", "host_sync", "tile_scan", "emit",
                   "tile_sort", "blend", "backward_blend", "backward_gauss")
 BATCH_STAGES = ("preprocess", "depth_sort", "gather", "tile_scan", "lists", "queue_sort",
@@ -376,6 +378,10 @@ class Scene:
                                        _ptr(loss_accum) if loss_accum is not None else None,
                                        _stream(stream)))
 
+    def set_batch_shape(self, footprint, ctas_per_sm=0):
+        """Launch shape of this scene's batched blend (fdgs_set_batch_shape)."""
+        check(lib().fdgs_set_batch_shape(self.handle, int(footprint), int(ctas_per_sm)))
+
     def finetune_reset(self):
         """Clears the Adam moments and step count of fdgs_finetune_step."""
         check(lib().fdgs_finetune_reset(self.handle))
@@ -602,7 +608,7 @@ DEFAULT_BLEND_SHAPE = 3
 def set_blend_shape(footprint):
     """Forward-blend launch shape, process-wide: the warp footprint and pixels per lane (0:
     16x2, 1: 8x4, 2: 4x8 with one pixel a lane; 3: 8x8 with two; 4: 16x8, 5: 8x16 with
-    four). Results do not depend on it."""
+    four; 6: 16x16 with eight, one warp per tile). Results do not depend on it."""
     check(lib().fdgs_set_blend_shape(int(footprint)))
 
 

@@ -62,11 +62,39 @@ def test_batch_autotune_and_background(fd):
     bg = (0.1, 0.2, 0.3)
     outs = sc.batch_autotune(cams, ts, bg=bg)
     info = sc.batch_info(5)
-    assert info["footprint"] in (0, 1, 2) and info["ctas_per_sm"] >= 1
+    assert info["footprint"] in range(7) and info["ctas_per_sm"] >= 1
     outs2 = sc.render_batch(cams, ts, bg=bg)
     for i, (c, t) in enumerate(zip(cams, ts)):
         ref = sc.render(c, t, bg=bg)
         assert torch.equal(outs[i], ref) and torch.equal(outs2[i], ref), i
+    sc.close()
+
+
+def test_every_batch_shape_gives_the_per_request_images(fd):
+    """Each of the seven launch shapes of the batched blend (fdgs_set_batch_shape), at the
+    occupancy limit and at a quarter of it, with a black background (the black-only kernel)
+    and a coloured one: the images equal the per-request renders, eagerly and on graph
+    replay."""
+    _, sc = _scene_gpu(fd, True, n=8000, seed=49)
+    res = [(200, 150), (33, 17), (96, 96)]
+    cams, ts = _requests(14, len(res), res)
+    try:
+        for bg in ((0.0, 0.0, 0.0), (0.1, 0.2, 0.3)):
+            want = [sc.render(c, t, bg=bg).clone() for c, t in zip(cams, ts)]
+            for shape in range(7):
+                for quarter in (False, True):
+                    ctas = 0
+                    if quarter:
+                        sc.set_batch_shape(shape, 0)
+                        sc.render_batch(cams, ts, bg=bg)
+                        ctas = max(1, sc.batch_info(len(cams))["ctas_per_sm"] // 4)
+                    sc.set_batch_shape(shape, ctas)
+                    for call in range(2):        # eager run and capture, then replay
+                        outs = sc.render_batch(cams, ts, bg=bg)
+                        for i in range(len(cams)):
+                            assert torch.equal(outs[i], want[i]), (bg, shape, ctas, call, i)
+    finally:
+        sc.set_batch_shape(6, 0)
     sc.close()
 
 

@@ -76,3 +76,31 @@ def test_refused_allocation_returns_oom_and_the_next_render_works(fd):
     for c, t, o in zip(cams, [0.3, 0.5], outs):
         assert torch.equal(o, sc.render(c, t, use_mask=False))
     sc.close()
+
+
+def test_tma_stage_wait_timeout_is_reported_and_the_next_batch_works(fd):
+    """TMA record staging with one arrival withheld on every stage barrier of one batch: the
+    blend's stage waits give up after their poll limit, the missing arrival is supplied so the
+    copies in flight land before the CTAs leave, the call reports FDGS_ERR_TIMEOUT, and the
+    next batch (graph replay) renders the same images as before the failure."""
+    s = scenes.make_scene(6000, 53, sh_degree=1, lt_short=(-3.0, 0.5), lt_long=(-1.0, 0.5),
+                          short_frac=0.5)
+    sc = fd.Scene.from_host(s)
+    cams = [scenes.arc_camera(th, 96, 72) for th in (-5.0, 2.0, 8.0)]
+    ts = [0.2, 0.5, 0.8]
+    try:
+        fd.set_batch_staging(fd.STAGING_TMA)
+        sc.set_batch_shape(5, 0)            # a four-pixels-a-lane shape: TMA staging applies
+        want = [o.clone() for o in sc.render_batch(cams, ts, use_mask=False)]
+        fd.debug_inject(fd.INJECT_TMA_MISSING_ARRIVAL, 0)
+        with pytest.raises(fd.FdgsError) as ei:
+            sc.render_batch(cams, ts, use_mask=False)
+        assert ei.value.code == -5
+        got = sc.render_batch(cams, ts, use_mask=False)
+        sc.status_sync()
+        for i in range(len(cams)):
+            assert torch.equal(got[i], want[i]), i
+    finally:
+        fd.set_batch_staging(fd.STAGING_CP_ASYNC)
+        fd.debug_inject(fd.INJECT_NONE)
+    sc.close()

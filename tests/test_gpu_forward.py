@@ -205,11 +205,11 @@ def test_background_colour(fd):
     sc.close()
 
 
-@pytest.mark.parametrize("builder,shape", [(1, 0), (1, 2), (1, 3), (1, 4), (1, 5), (2, 0),
-                                           (2, 1), (2, 2), (2, 3)])
+@pytest.mark.parametrize("builder,shape", [(1, 0), (1, 2), (1, 3), (1, 4), (1, 5), (1, 6),
+                                           (2, 0), (2, 1), (2, 2), (2, 3), (2, 6)])
 def test_list_builders_and_blend_shapes_give_identical_frames(fd, builder, shape):
-    """Bitmask vs sort tile lists, and the six launch shapes of the blend (warp footprints
-    with their ballot culling, one, two or four pixels per lane), must all give the same lists
+    """Bitmask vs sort tile lists, and the seven launch shapes of the blend (warp footprints
+    with their ballot culling, one, two, four or eight pixels per lane), must all give the same lists
     and bit-identical images, transmittances and n_contrib."""
     s = scenes.make_scene(6000, 17, sh_degree=1, lt_long=(-1.0, 0.5))
     cam = scenes.arc_camera(4.0, 200, 150)

@@ -36,6 +36,7 @@ def _masked_scene(fd, n, seed):
     s = scenes.make_scene(n, seed, sh_degree=3, lt_short=(-3.0, 0.5), lt_long=(-1.0, 0.5),
                           short_frac=0.5)
     sc = fd.Scene.from_host(s)
+    sc.set_batch_shape(5, 0)     # the gather4 staging is built for four pixels a lane
     kt = scenes.keyframe_times(300, 6)
     sc.set_active_mask(torch.as_tensor(scenes.keyframe_masks(s, kt)).cuda(), kt)
     return s, sc
@@ -56,25 +57,28 @@ def test_gather4_staging_equals_cp_async_and_per_request_renders(fd):
     _, sc = _masked_scene(fd, 20_000, 51)
     res = [(512, 512), (200, 150), (1352, 1014), (37, 61), (800, 800), (16, 16)]
     cams, ts = _requests(5, len(res), res)
-    for bg in ((0.0, 0.0, 0.0), (0.2, 0.1, 0.05)):
-        want = _batch(fd, sc, fd.STAGING_CP_ASYNC, cams, ts, bg=bg)
-        for call in range(2):
-            got = _batch(fd, sc, fd.STAGING_TMA, cams, ts, bg=bg)
-            for i in range(len(cams)):
-                assert torch.equal(got[i], want[i]), (bg, call, i)
+    for shape in (4, 5):
+        sc.set_batch_shape(shape, 0)
+        for bg in ((0.0, 0.0, 0.0), (0.2, 0.1, 0.05)):
+            want = _batch(fd, sc, fd.STAGING_CP_ASYNC, cams, ts, bg=bg)
+            for call in range(2):
+                got = _batch(fd, sc, fd.STAGING_TMA, cams, ts, bg=bg)
+                for i in range(len(cams)):
+                    assert torch.equal(got[i], want[i]), (shape, bg, call, i)
         for i, (c, t) in enumerate(zip(cams, ts)):
             assert torch.equal(want[i], sc.render(c, t, bg=bg)), (bg, i)
     sc.status_sync()
     sc.close()
 
 
-def test_gather4_staging_on_the_full_size_scene_and_both_four_pixel_shapes(fd):
+def test_gather4_staging_on_the_full_size_scene(fd):
     """The 200k pruned scene at 1352x1014 (thousands of entries per tile, many stages per
-    tile, early exits of saturated tiles with a stage in flight), four frames, through the
-    autotuned shape and through the default one; the counting variant of the kernel gives
-    the same evaluation counts under either staging."""
+    tile, early exits of saturated tiles with a stage in flight), four frames, through shape 5
+    and through the autotuned shape (which may be one without TMA staging); the counting
+    variant of the kernel gives the same evaluation counts under either staging."""
     s = scenes.pruned_scene()
     sc = fd.Scene.from_host(s)
+    sc.set_batch_shape(5, 0)
     kt = scenes.keyframe_times(300, 6)
     sc.set_active_mask(torch.as_tensor(scenes.keyframe_masks(s, kt)).cuda(), kt)
     ft = scenes.frame_times()
