@@ -385,8 +385,11 @@ int fdgs_set_list_builder(int mode);
  * tile): 0: 16x2, 1: 8x4, 2: 4x8 (one pixel per lane), 3: 8x8 (two, the default), 4: 16x8,
  * 5: 8x16 (four), 6: 16x16 (eight: one warp per tile). Each warp culls, by ballot, the
  * Gaussians that cannot reach alpha >= 1/255 anywhere in its footprint; results do not depend
- * on the shape. The batch autotuner (fdgs_batch_autotune) searches the same shapes for the
- * batched blend. Returns FDGS_ERR_INVALID for other values. */
+ * on the shape. A render that keeps no frame, on a black background, uses the forward-only
+ * blend (no transmittance or n_contrib, the paired FP32 evaluation), whose shape starts at 5
+ * and is set by this call too; -1 restores both defaults (3 and 5). The batch autotuner
+ * (fdgs_batch_autotune) searches the same shapes for the batched blend. Returns
+ * FDGS_ERR_INVALID for other values. */
 int fdgs_set_blend_shape(int footprint);
 
 /*

@@ -430,8 +430,12 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   ba.W = W; ba.H = H; ba.gx = gx; ba.gy = gy;
   for (int c = 0; c < 3; ++c) ba.bg[c] = opts ? opts->bg[c] : 0.f;
   ba.rgb = rgb;
-  ba.T_final = ws.Tf.as<float>();
-  ba.n_contrib = ws.nc.as<uint32_t>();
+  // a render that keeps no frame, uncounted, on a black background needs no transmittance or
+  // n_contrib: the forward-only blend (launch_blend takes it exactly when T_final is null)
+  const bool fwd_only = !want_flags && !want_wsum && !count && ba.bg[0] == 0.f &&
+                        ba.bg[1] == 0.f && ba.bg[2] == 0.f;
+  ba.T_final = fwd_only ? nullptr : ws.Tf.as<float>();
+  ba.n_contrib = fwd_only ? nullptr : ws.nc.as<uint32_t>();
   ba.w_sum = want_wsum ? ws.wsum.as<float>() : nullptr;
   ba.stop_mark = want_wsum ? ws.stopmark.as<uint32_t>() : nullptr;
   ba.evals = count ? s->evals.as<unsigned long long>() : nullptr;
@@ -1585,10 +1589,11 @@ int fdgs_set_batch_staging(int mode) {
 }
 
 int fdgs_set_blend_shape(int footprint) {
-  if (footprint < 0 || footprint >= kBlendShapes)
-    return fail(FDGS_ERR_INVALID,
-                "blend shape must be 0 (16x2), 1 (8x4), 2 (4x8), 3 (8x8), 4 (16x8) or 5 (8x16)");
-  g_blend_shape = footprint;
+  if (footprint < -1 || footprint >= kBlendShapes)
+    return fail(FDGS_ERR_INVALID, "blend shape must be -1 (the defaults), 0 (16x2), 1 (8x4), "
+                "2 (4x8), 3 (8x8), 4 (16x8), 5 (8x16) or 6 (16x16)");
+  g_blend_shape = footprint < 0 ? kBlendShapeDefault : footprint;
+  g_blend_shape_fwd = footprint < 0 ? kBlendShapeFwdDefault : footprint;
   return FDGS_OK;
 }
 

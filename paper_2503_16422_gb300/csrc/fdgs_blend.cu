@@ -33,6 +33,33 @@ k_blend(BlendArgs a, const K *__restrict__ keys, uint32_t rmask) {
   blend_tile<K, FW, PX, kWeights, kCount, true>(bt, keys, rmask, sm, no_tma);
 }
 
+// The forward-only blend of a single render on a black background (no frame kept, so no
+// transmittance or n_contrib is written): the T = 0 stop encoding and, with an even number of
+// pixels a lane, the paired FP32 evaluation of the batched blend; images are bit-identical to
+// the flag form's.
+template <typename K, int FW, int PX>
+__global__ void __launch_bounds__(256 / PX)
+k_blend_fwd(BlendArgs a, const K *__restrict__ keys, uint32_t rmask) {
+  __shared__ BlendSmem<256 / PX> sm;
+  const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
+  BlendTile bt;
+  bt.tx = tile % a.gx;
+  bt.ty = tile / a.gx;
+  bt.W = a.W;
+  bt.H = a.H;
+  bt.range = a.ranges[tile];
+  bt.rec_sorted = a.rec_sorted;
+  bt.rgb = a.rgb;
+  bt.T_final = nullptr;
+  bt.n_contrib = nullptr;
+  bt.bg0 = bt.bg1 = bt.bg2 = 0.f;
+  bt.w_sum = nullptr;
+  bt.stop_mark = nullptr;
+  bt.evals = nullptr;
+  uint32_t no_tma = 0;
+  blend_tile<K, FW, PX, false, false, false, false, true>(bt, keys, rmask, sm, no_tma);
+}
+
 // Sums of eight per-lane values over the warp by a transposed butterfly: at offsets 16, 8
 // and 4 each lane keeps half of its partial sums and adds its partner's copy of them (7
 // shuffles for 8 values instead of 40), then offsets 2 and 1 finish one sum per lane. Lane L
@@ -242,12 +269,22 @@ k_blend_bwd(BlendBwdArgs a, const K *__restrict__ keys, uint32_t rmask) {
 
 }  // namespace
 
-int g_blend_shape = 3;   // launch shape of the forward blend (see with_blend_shape)
+int g_blend_shape = kBlendShapeDefault;
+int g_blend_shape_fwd = kBlendShapeFwdDefault;
 
 template <typename K>
 void launch_blend(const BlendArgs &a, const K *keys, uint32_t rmask, cudaStream_t st) {
   const int tiles = a.gx * a.gy;
   if (tiles == 0) return;
+  // no transmittance to write: the forward-only blend (the caller passes a null T_final only
+  // for an uncounted, unweighted render on a black background)
+  if (!a.T_final) {
+    with_blend_shape(g_blend_shape_fwd, [&](auto fw, auto px) {
+      constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
+      k_blend_fwd<K, FW, PX><<<tiles, 256 / PX, 0, st>>>(a, keys, rmask);
+    });
+    return;
+  }
   with_blend_shape(g_blend_shape, [&](auto fw, auto px) {
     constexpr int FW = decltype(fw)::value, PX = decltype(px)::value;
     if (a.w_sum)

@@ -82,7 +82,7 @@ struct BlendArgs {
   int W, H, gx, gy;
   float bg[3];
   float *rgb;          // [3][H][W]
-  float *T_final;      // [H][W]
+  float *T_final;      // [H][W], or null for a forward-only render (then n_contrib too)
   uint32_t *n_contrib; // [H][W]
   float *w_sum;        // optional [nv] per-rank blend-weight sums (score pass)
   uint32_t *stop_mark; // with w_sum: [nv] per-rank flag, set where the entry stopped a pixel
@@ -280,7 +280,12 @@ int batch_blend_max_ctas_per_sm(int shape, bool black = false);
 
 int num_sms();
 extern int g_blend_shape;   // launch shape of the forward blend (with_blend_shape)
+extern int g_blend_shape_fwd;   // ... of the forward-only blend on black backgrounds
 constexpr int kBlendShapes = 7;
+// 8x8 footprint, two pixels a lane, for the blend that writes transmittance; 8x16, four
+// pixels a lane, for the forward-only blend (0.430 against 0.436 ms for 16x16 and 0.447 for
+// 8x8, masked 200k-Gaussian frames at 1352x1014)
+constexpr int kBlendShapeDefault = 3, kBlendShapeFwdDefault = 5;
 
 // Sets the message returned by fdgs_last_error() on this thread.
 void set_error_message(const char *msg);

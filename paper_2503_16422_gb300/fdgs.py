@@ -601,15 +601,19 @@ def set_batch_staging(mode):
     check(lib().fdgs_set_batch_staging(int(mode)))
 
 
-# launch shape of the forward blend when none is set (8x8 warp footprint, two pixels a lane)
+# launch shapes when none is set: the blend that writes transmittance (8x8 warp footprint,
+# two pixels a lane) and the forward-only blend (8x16, four pixels a lane)
 DEFAULT_BLEND_SHAPE = 3
+DEFAULT_BLEND_SHAPE_FWD = 5
 
 
 def set_blend_shape(footprint):
     """Forward-blend launch shape, process-wide: the warp footprint and pixels per lane (0:
     16x2, 1: 8x4, 2: 4x8 with one pixel a lane; 3: 8x8 with two; 4: 16x8, 5: 8x16 with
-    four; 6: 16x16 with eight, one warp per tile). Results do not depend on it."""
-    check(lib().fdgs_set_blend_shape(int(footprint)))
+    four; 6: 16x16 with eight, one warp per tile), for both the blend that writes
+    transmittance and the forward-only one; None restores the defaults of each. Results do
+    not depend on it."""
+    check(lib().fdgs_set_blend_shape(-1 if footprint is None else int(footprint)))
 
 
 def debug_inject(kind, value=0):

@@ -222,10 +222,30 @@ def test_list_builders_and_blend_shapes_give_identical_frames(fd, builder, shape
         g = _run(fd, s, cam, 0.4)
     finally:
         fd.set_list_builder(0)
-        fd.set_blend_shape(fd.DEFAULT_BLEND_SHAPE)
+        fd.set_blend_shape(None)
     assert ref["stats"]["list_builder"] == 1 and g["stats"]["list_builder"] == builder
     for k in ("image", "T_final", "n_contrib", "tile_ranges", "tile_ids"):
         assert np.array_equal(g[k], ref[k]), k
+
+
+def test_forward_only_blend_equals_the_frame_render(fd):
+    """A render that keeps no frame (black background) runs the forward-only blend (T = 0
+    stop encoding, paired FP32 evaluation, no transmittance or n_contrib written): for every
+    launch shape its image equals, bit for bit, the render that keeps a frame."""
+    s = scenes.make_scene(6000, 18, sh_degree=3, lt_long=(-1.0, 0.5))
+    sc = fd.Scene.from_host(s)
+    try:
+        for cam in (scenes.arc_camera(3.0, 200, 150), scenes.tiny_camera(37, 61)):
+            ref, fr = sc.render(cam, 0.45, keep_frame=True)
+            ref = ref.clone()
+            fr.release()
+            for shape in range(7):
+                fd.set_blend_shape(shape)
+                got = sc.render(cam, 0.45)
+                assert torch.equal(got, ref), (cam.width, shape)
+    finally:
+        fd.set_blend_shape(None)
+    sc.close()
 
 
 @pytest.mark.slow
