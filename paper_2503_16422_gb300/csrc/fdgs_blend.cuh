@@ -435,13 +435,14 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
             const float2 nw = __fmul2_rn(na, T2[q]);          // -alpha T
             const float2 nT = __fadd2_rn(T2[q], nw);          // T - alpha T
             // a pixel stops (T = 0, no colour) at the entry that takes T below 1e-4, and a
-            // stopped pixel stops again at every later entry
-            const float2 kp = make_float2(set_ge(nT.x, kTStop), set_ge(nT.y, kTStop));
-            const float2 nwi = __fmul2_rn(nw, kp);            // -(blend weight)
+            // stopped pixel stops again at every later entry; selects on the stop test keep
+            // these two products off the FMA pipe (0 * x and x * 1 give the same values)
+            const bool k0 = nT.x >= kTStop, k1 = nT.y >= kTStop;
+            const float2 nwi = make_float2(k0 ? nw.x : 0.f, k1 ? nw.y : 0.f);   // -(weight)
             C02[q] = __ffma2_rn(cr, nwi, C02[q]);     // the negated colour sums
             C12[q] = __ffma2_rn(cg, nwi, C12[q]);
             C22[q] = __ffma2_rn(cb, nwi, C22[q]);
-            T2[q] = __fmul2_rn(nT, kp);
+            T2[q] = make_float2(k0 ? nT.x : 0.f, k1 ? nT.y : 0.f);
           }
         }
       } else
