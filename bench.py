@@ -685,10 +685,51 @@ def comparisons(sc, cams, times, flush, stream):
             r["active_fraction"] = r["n_active_per_frame"] / scene_obj.n
         return r
 
+    def single_no_sync(scene_obj, frames):
+        """The same masked single renders through fdgs_render_async (no host synchronisation
+        inside a render): each frame timed alone (L2 flushed before it), then all frames
+        queued back to back (L2 flushed between them) under one event pair."""
+        for k in frames:
+            scene_obj.render_async(cams[k], float(times[k]), out=out)
+        scene_obj.status_sync()
+        ms = []
+        for k in frames:
+            _flush(flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            scene_obj.render_async(cams[k], float(times[k]), out=out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        # the flushes alone, then the flushes with the renders queued between them
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in frames:
+            _flush(flush)
+        e1.record(stream)
+        e1.synchronize()
+        fl = e0.elapsed_time(e1)
+        e0.record(stream)
+        for k in frames:
+            _flush(flush)
+            scene_obj.render_async(cams[k], float(times[k]), out=out)
+        e1.record(stream)
+        e1.synchronize()
+        q = e0.elapsed_time(e1) - fl
+        scene_obj.status_sync()
+        return dict(fps=len(frames) / (sum(ms) / 1e3), ms_per_frame=sum(ms) / len(frames),
+                    queued_fps=len(frames) / (q / 1e3), queued_ms_per_frame=q / len(frames),
+                    queued="frames enqueued back to back, L2 flushed between them; the "
+                           "flushes' own time (timed alone) subtracted")
+
     # the filter (masks) and the exact temporal cull, each on and off (the paper's Table 3
     # rows: masked = filter on; unmasked = filter off; no temporal cull = a renderer without
     # the a < 1/255 cull, as vanilla 4DGS renders)
     res["single_masked"] = single(sc, True, fr, counts=True)
+    res["single_masked_no_host_sync"] = single_no_sync(sc, fr)
     res["single_unmasked"] = single(sc, False, fr, counts=True)
     res["single_unmasked_no_temporal_cull"] = single(sc, False, fr, temporal_cull=False,
                                                      counts=True)

@@ -149,6 +149,31 @@ int fdgs_render(fdgs_scene *scene, const fdgs_camera *cam, float t,
                 fdgs_stream stream);
 
 /*
+ * fdgs_render without any host synchronisation (the same render, Sec. 3, Eqs. 1-3, mask gate
+ * Sec. 4.2.2; the paper has no counterpart of the call itself): every stage is enqueued on
+ * the stream and the call returns, so renders queue back to back and can be captured in a
+ * CUDA graph. Keeps no frame. The tile lists are the coverage-bitmask lists (identical to the
+ * other builder's), built into a list capacity fixed before the launch, in buffers of the
+ * scene that no other call reallocates. The first call on a scene sizes that capacity with
+ * one synchronised render (twice that frame's lists, plus 65536 entries; or set it with
+ * fdgs_reserve_render_lists); make it, at the largest image size to be used, before any stream
+ * capture (a later call that needs larger per-pixel or per-Gaussian buffers allocates them).
+ * A frame whose lists exceed the capacity composites no Gaussian (its image is the background
+ * only) and sets FDGS_ERR_CAPACITY in the status word: fdgs_status_sync (or the next call
+ * that synchronises) returns it and grows the capacity to fit that frame, after which the
+ * render can be repeated (a graph holding it must then be captured again).
+ * Errors: as fdgs_render; FDGS_ERR_INVALID when the coverage-bitmask builder is unavailable
+ * (fdgs_set_list_builder(1), or (tiles_x + tiles_y) * ceil(n / 256) * 32 B above 512 MiB).
+ */
+int fdgs_render_async(fdgs_scene *scene, const fdgs_camera *cam, float t,
+                      const fdgs_render_opts *opts, float *rgb_out_dev, fdgs_stream stream);
+
+/* List capacity (tile-list entries) of fdgs_render_async; 0 makes its next call size the
+ * capacity again. Allocates: call it outside stream capture. FDGS_ERR_INVALID above 2^30 - 1
+ * entries. */
+int fdgs_reserve_render_lists(fdgs_scene *scene, uint64_t entries);
+
+/*
  * Reverse of fdgs_render for the frame (reverse-order per-tile replay that recovers
  * transmittance by division, then the chain to the 4D parameters). dL_drgb_dev is
  * [3][height][width]. Gradients are ADDED (+=) into the caller's buffers, laid out like the
@@ -438,7 +463,9 @@ int fdgs_set_batch_shape(fdgs_scene *scene, int footprint, int ctas_per_sm);
 int fdgs_set_batch_staging(int mode);
 
 /* Reads and clears the scene's device status word (synchronises the device): FDGS_OK, or
- * FDGS_ERR_CAPACITY / FDGS_ERR_TIMEOUT raised by a kernel since the last read. */
+ * FDGS_ERR_CAPACITY / FDGS_ERR_TIMEOUT raised by a kernel since the last read. After a
+ * capacity overflow of fdgs_render_async it also grows that call's list capacity to fit the
+ * longest overflowing frame. */
 int fdgs_status_sync(fdgs_scene *scene);
 
 /*

@@ -102,10 +102,15 @@ struct Workspace {
   Buf stopmark;                  // u32[n] per-rank "stopped a pixel" flags (with wsum)
   Buf diff;                      // i32[gy + 1][gx + 1] tile-coverage difference array
   Buf rowmask, colmask;          // u32 coverage bitmasks by depth rank per tile row / column
+  // renders without a host synchronisation (fdgs_render_async): the tile-list capacity in
+  // entries (0 until the first, sizing call) and the u64 list length an overflowing render
+  // needed (atomicMax on the device, read and cleared by fdgs_status_sync)
+  uint64_t key_cap = 0;
+  Buf need;
   ~Workspace() {
     Buf *all[] = {&ctr, &pre_status, &scan_status, &rec, &rec_sorted, &vis[0], &vis[1],
                   &offsets, &flags, &keys[0], &keys[1], &ranges, &order, &Tf, &nc, &scratch, &g2d,
-                  &wsum, &stopmark, &diff, &rowmask, &colmask};
+                  &wsum, &stopmark, &diff, &rowmask, &colmask, &need};
     for (Buf *b : all) b->release();
     if (hctr) cudaFreeHost(hctr);
   }
@@ -195,6 +200,7 @@ struct fdgs_scene {
   int n_key = 0;
   std::vector<float> key_times;
   Workspace main;
+  Workspace nosync;   // fdgs_render_async's own buffers (no other call reallocates them)
   std::vector<Workspace *> pool;
   std::set<fdgs_frame *> live;
   Buf status;     // u32 device error bits
@@ -274,6 +280,20 @@ int check_device_errors(fdgs_scene *s, cudaStream_t st) {
   CK(cudaMemcpyAsync(&e, s->status.p, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (e) {
+    // a render without host synchronisation that overflowed its list capacity recorded the
+    // length it needed: the capacity grows to fit it (the buffer is allocated here, outside
+    // any stream capture), so that the render can be repeated
+    Workspace &ws = s->nosync;
+    if ((e & kErrCapacity) && ws.need.p) {
+      unsigned long long need = 0;
+      CK(cudaMemcpyAsync(&need, ws.need.p, 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (need > ws.key_cap) {
+        ws.key_cap = need + need / 4;
+        TRY(grow(ws.keys[0], ws.key_cap * 4));
+      }
+      CK(cudaMemsetAsync(ws.need.p, 0, 8, st));
+    }
     CK(cudaMemsetAsync(s->status.p, 0, 4, st));
     if (e & kErrTimeout) return fail(FDGS_ERR_TIMEOUT, "device spin-wait limit reached");
     return fail(FDGS_ERR_CAPACITY, "device capacity exceeded");
@@ -300,9 +320,12 @@ K *emit_and_sort(Workspace &ws, uint32_t nv, uint64_t nkeys, int gx, int gy, int
 
 // One render into workspace ws. want_flags: also write per-Gaussian decision flags.
 // wsum: per-rank blend weights are accumulated (score pass); the buffer is zeroed here.
+// no_sync: nothing waits for the device (fdgs_render_async): the coverage-bitmask lists are
+// built into the workspace's fixed capacity ws.key_cap from device-side counts; lists that do
+// not fit empty the frame's ranges and are reported through the status word.
 int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
                 const fdgs_render_opts *opts, float *rgb, bool want_flags, bool want_wsum,
-                bool use_mask_override, FrameMeta &m, cudaStream_t st) {
+                bool use_mask_override, FrameMeta &m, cudaStream_t st, bool no_sync = false) {
   DevCam dc;
   TRY(make_cam(cam, dc));
   if (!rgb) return fail(FDGS_ERR_INVALID, "null output image");
@@ -324,6 +347,11 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   const uint32_t mask_words = (uint32_t)((N + 255) / 256 * 8);
   const uint64_t mask_bytes = (uint64_t)(gx + gy) * mask_words * 4;
   const bool want_masks = g_list_mode != 1 && N > 0 && mask_bytes <= (512ull << 20);
+  if (no_sync && ((N > 0 && !want_masks) || want_flags || want_wsum))
+    return fail(FDGS_ERR_INVALID,
+                "a render without host synchronisation needs the coverage-bitmask list builder "
+                "(list mode 0 or 2, (tiles_x + tiles_y) * ceil(n / 256) * 32 B <= 512 MiB) and "
+                "keeps no frame");
   if (want_masks) {
     TRY(grow(ws.rowmask, (uint64_t)gy * mask_words * 4));
     TRY(grow(ws.colmask, (uint64_t)gx * mask_words * 4));
@@ -394,31 +422,43 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
                      want_masks ? ws.colmask.as<uint32_t>() : nullptr, mask_words, tight, st);
   if (prof) CK(cudaEventRecord(s->ev[3], st));
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(ws.hctr, ctr, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
-  TRY(check_device_errors(s, st));   // synchronises the stream
-
-  const uint32_t nv = ws.hctr[C_NVIS];
-  const uint64_t nkeys = (uint64_t)ws.hctr[C_NKEYS_LO] | ((uint64_t)ws.hctr[C_NKEYS_HI] << 32);
-  if (nkeys > kSortMaxKeys)
-    return fail(FDGS_ERR_CAPACITY, "%llu tile keys exceed the sort limit",
-                (unsigned long long)nkeys);
+  uint32_t nv = 0;
+  uint64_t nkeys = 0;
   const int tb = ceil_log2(std::max<uint64_t>(tiles, 2));
-  // List builder: coverage bitmasks read tiles x ceil(nv/32) word pairs from L2; emit + sort
-  // move the keys through DRAM (1 write + 2 per pass). Bitmasks win when coverage is dense.
-  const uint64_t words = (nv + 31) / 32;
-  const int rb_sort = ceil_log2(std::max<uint32_t>(nv, 2));
-  const uint64_t kb_sort = (rb_sort + tb) > 32 ? 8 : 4;
-  const bool use_masks =
-      want_masks && nkeys > 0 &&
-      (g_list_mode == 2 ||
-       tiles * words * 8 < 2 * nkeys * kb_sort * (1 + 2 * (uint64_t)sort_passes(tb)));
-  const int rb = use_masks ? 32 : rb_sort;
-  const int key64 = use_masks ? 0 : (rb + tb) > 32;
-  const size_t kb = key64 ? 8 : 4;
-  const uint64_t k1 = std::max<uint64_t>(nkeys, 1);
-  TRY(grow(ws.keys[0], k1 * kb));
-  if (!use_masks) TRY(grow(ws.keys[1], k1 * kb));
-  TRY(grow(ws.scratch, std::max(sort_scratch_bytes(n1, 32), sort_scratch_bytes(k1, tb))));
+  bool use_masks = true;
+  int rb = 32, key64 = 0;
+  if (no_sync) {
+    // lists into the fixed capacity, counts left on the device
+    TRY(grow(ws.keys[0], std::max<uint64_t>(ws.key_cap, 1) * 4));
+    if (!ws.need.p) {
+      TRY(grow(ws.need, 8));
+      CK(cudaMemsetAsync(ws.need.p, 0, 8, st));
+    }
+  } else {
+    CK(cudaMemcpyAsync(ws.hctr, ctr, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
+    TRY(check_device_errors(s, st));   // synchronises the stream
+
+    nv = ws.hctr[C_NVIS];
+    nkeys = (uint64_t)ws.hctr[C_NKEYS_LO] | ((uint64_t)ws.hctr[C_NKEYS_HI] << 32);
+    if (nkeys > kSortMaxKeys)
+      return fail(FDGS_ERR_CAPACITY, "%llu tile keys exceed the sort limit",
+                  (unsigned long long)nkeys);
+    // List builder: coverage bitmasks read tiles x ceil(nv/32) word pairs from L2; emit + sort
+    // move the keys through DRAM (1 write + 2 per pass). Bitmasks win when coverage is dense.
+    const uint64_t words = (nv + 31) / 32;
+    const int rb_sort = ceil_log2(std::max<uint32_t>(nv, 2));
+    const uint64_t kb_sort = (rb_sort + tb) > 32 ? 8 : 4;
+    use_masks = want_masks && nkeys > 0 &&
+                (g_list_mode == 2 ||
+                 tiles * words * 8 < 2 * nkeys * kb_sort * (1 + 2 * (uint64_t)sort_passes(tb)));
+    rb = use_masks ? 32 : rb_sort;
+    key64 = use_masks ? 0 : (rb + tb) > 32;
+    const size_t kb = key64 ? 8 : 4;
+    const uint64_t k1 = std::max<uint64_t>(nkeys, 1);
+    TRY(grow(ws.keys[0], k1 * kb));
+    if (!use_masks) TRY(grow(ws.keys[1], k1 * kb));
+    TRY(grow(ws.scratch, std::max(sort_scratch_bytes(n1, 32), sort_scratch_bytes(k1, tb))));
+  }
   if (want_wsum) {
     CK(cudaMemsetAsync(ws.wsum.p, 0, n1 * 4, st));
     CK(cudaMemsetAsync(ws.stopmark.p, 0, n1 * 4, st));
@@ -443,14 +483,16 @@ int render_impl(fdgs_scene *s, Workspace &ws, const fdgs_camera *cam, float t,
   // tile ranges and the tile sort's digit offsets, straight from the coverage counts
   launch_tile_scan(ws.diff.as<int>(), gx, gy, use_masks ? 0 : sort_passes(tb),
                    sort_digit_bits(tb), ws.ranges.as<uint2>(), sort_hist(ws.scratch.p),
-                   ws.order.as<uint32_t>(), st);
+                   ws.order.as<uint32_t>(), st, no_sync ? std::max<uint64_t>(ws.key_cap, 1) : 0,
+                   no_sync ? ws.need.as<unsigned long long>() : nullptr, err);
   ba.order = ws.order.as<uint32_t>();
   if (prof) CK(cudaEventRecord(s->ev[5], st));
   void *skeys;
   if (use_masks) {
     // lists of plain ranks straight in tile-major, depth order (the "emit" stage; no sort)
     launch_tile_lists(ws.rowmask.as<uint32_t>(), ws.colmask.as<uint32_t>(), mask_words, nv, gx,
-                      gy, ws.ranges.as<uint2>(), ws.keys[0].as<uint32_t>(), st);
+                      gy, ws.ranges.as<uint2>(), ws.keys[0].as<uint32_t>(), st,
+                      no_sync ? ctr + C_NVIS : nullptr);
     if (prof) CK(cudaEventRecord(s->ev[6], st));
     if (prof) CK(cudaEventRecord(s->ev[7], st));
     skeys = ws.keys[0].p;
@@ -933,6 +975,49 @@ int fdgs_render(fdgs_scene *s, const fdgs_camera *cam, float t, const fdgs_rende
   }
   s->live.insert(f);
   *frame_out = f;
+  return FDGS_OK;
+}
+
+int fdgs_render_async(fdgs_scene *s, const fdgs_camera *cam, float t,
+                      const fdgs_render_opts *opts, float *rgb_out_dev, fdgs_stream stream) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  cudaStream_t st = (cudaStream_t)stream;
+  DevCam dc;
+  TRY(make_cam(cam, dc));
+  const uint64_t mask_bytes = (uint64_t)(dc.gx + dc.gy) * (((uint64_t)s->d.n + 255) / 256 * 8) * 4;
+  if (g_list_mode == 1 || mask_bytes > (512ull << 20))
+    return fail(FDGS_ERR_INVALID,
+                "fdgs_render_async needs the coverage-bitmask list builder (list mode 0 or 2, "
+                "(tiles_x + tiles_y) * ceil(n / 256) * 32 B <= 512 MiB)");
+  Workspace &ws = s->nosync;
+  FrameMeta m;
+  if (ws.key_cap == 0) {
+    // the first call sizes the list capacity with one synchronised render: twice its lists
+    // (4 bytes an entry), room for the other frames of a sequence
+    TRY(render_impl(s, ws, cam, t, opts, rgb_out_dev, false, false, true, m, st));
+    ws.key_cap = 2 * m.nkeys + 65536;
+    TRY(grow(ws.keys[0], ws.key_cap * 4));
+    if (!ws.need.p) {
+      TRY(grow(ws.need, 8));
+      CK(cudaMemsetAsync(ws.need.p, 0, 8, st));
+    }
+    return FDGS_OK;
+  }
+  return render_impl(s, ws, cam, t, opts, rgb_out_dev, false, false, true, m, st, true);
+}
+
+int fdgs_reserve_render_lists(fdgs_scene *s, uint64_t entries) {
+  if (!s) return fail(FDGS_ERR_INVALID, "null scene");
+  if (entries > kSortMaxKeys) return fail(FDGS_ERR_INVALID, "entries above the list limit");
+  Workspace &ws = s->nosync;
+  ws.key_cap = entries;
+  if (entries) {
+    TRY(grow(ws.keys[0], entries * 4));
+    if (!ws.need.p) {
+      TRY(grow(ws.need, 8));
+      CK(cudaMemset(ws.need.p, 0, 8));
+    }
+  }
   return FDGS_OK;
 }
 

@@ -60,17 +60,21 @@ void launch_gather_scan(const uint64_t *sorted, const uint32_t *ctr_nvis, uint32
                         int tight, cudaStream_t st);
 // Tile lists by coverage bitmasks (rowmask/colmask written by the gather when non-null,
 // [gy or gx][mask_words] words): lists[ranges[t].x ..] = ranks covering tile t, ascending.
+// nv_dev (optional): the visible count on the device, read by the kernel instead of nv.
+// Tiles whose range is empty are skipped.
 void launch_tile_lists(const uint32_t *rowmask, const uint32_t *colmask, uint32_t mask_words,
                        uint32_t nv, int gx, int gy, const uint2 *ranges, uint32_t *lists,
-                       cudaStream_t st);
+                       cudaStream_t st, const uint32_t *nv_dev = nullptr);
 // Tile-list builder: 0 auto (cost model), 1 emit + radix sort, 2 coverage bitmasks.
 extern int g_list_mode;
 // Integrates diff into per-tile counts; writes tile ranges and the tile sort's digit offsets.
 // order (optional): tile ids by descending list length, in buckets of 16 entries (order
 // within a bucket unspecified), so that the one-CTA-per-tile blend starts its longest tiles
-// first.
+// first. cap (0: none): the list capacity; longer lists set kErrCapacity in err, raise
+// *need to their total length and empty every range.
 void launch_tile_scan(int *diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
-                      uint32_t *hist, uint32_t *order, cudaStream_t st);
+                      uint32_t *hist, uint32_t *order, cudaStream_t st, uint64_t cap = 0,
+                      unsigned long long *need = nullptr, uint32_t *err = nullptr);
 
 template <typename K>
 void launch_emit(const float *rec_sorted, const uint32_t *offsets, uint32_t nv, int gx, int gy,

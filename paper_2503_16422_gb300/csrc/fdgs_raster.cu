@@ -216,7 +216,8 @@ __device__ __forceinline__ uint32_t order_bucket(uint32_t len) {
 }
 __global__ void __launch_bounds__(kScanBlock)
 k_tile_scan(int *__restrict__ diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
-            uint32_t *__restrict__ hist, uint32_t *__restrict__ order) {
+            uint32_t *__restrict__ hist, uint32_t *__restrict__ order, uint64_t cap,
+            unsigned long long *need, uint32_t *err) {
   __shared__ uint32_t s_hist[4 * 256];
   __shared__ uint32_t s_ord[kOrderBuckets];
   __shared__ uint32_t s_wsum[kScanBlock / 32];
@@ -275,6 +276,21 @@ k_tile_scan(int *__restrict__ diff, int gx, int gy, int npass, int dbits, uint2 
     if (tid == kScanBlock - 1) s_carry = start + c;
     __syncthreads();
   }
+  // a list capacity fixed before the launch (renders sized without a host synchronisation):
+  // when the lists do not fit, every range is emptied (nothing is written or read beyond the
+  // capacity, the frame composites no Gaussian) and the length needed is recorded
+  if (cap && (uint64_t)s_carry > cap) {
+    if (tid == 0) {
+      atomicOr(err, kErrCapacity);
+      atomicMax(need, (unsigned long long)s_carry);
+    }
+    for (uint32_t t = tid; t < tiles; t += kScanBlock) ranges[t] = make_uint2(0u, 0u);
+    // the length buckets of the tile order were counted with the lengths before: now every
+    // tile is in the bucket of empty lists (else the order's slots would run past its end)
+    for (int i = tid; i < kOrderBuckets; i += kScanBlock)
+      s_ord[i] = i == kOrderBuckets - 1 ? tiles : 0u;
+    __syncthreads();
+  }
   // exclusive digit offsets per pass (threads 0..255 = warps 0..7 hold the 256 digits)
   for (int p = 0; p < npass; ++p) {
     uint32_t v = 0, inc = 0;
@@ -325,16 +341,20 @@ k_tile_scan(int *__restrict__ diff, int gx, int gy, int npass, int dbits, uint2 
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock)
 k_tile_lists(const uint32_t *__restrict__ rowmask, const uint32_t *__restrict__ colmask,
-             uint32_t mask_words, uint32_t words, int gx, int gy,
-             const uint2 *__restrict__ ranges, uint32_t *__restrict__ lists) {
+             uint32_t mask_words, uint32_t words, const uint32_t *__restrict__ nv_dev,
+             int gx, int gy, const uint2 *__restrict__ ranges, uint32_t *__restrict__ lists) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tiles = (uint32_t)gx * gy;
+  // the visible count from the device when the host did not read it
+  if (nv_dev) words = (*nv_dev + 31) / 32;
   for (uint32_t t = blockIdx.x * kWarps + warp; t < tiles; t += gridDim.x * kWarps) {
     const uint32_t *rows = rowmask + (size_t)(t / gx) * mask_words;
     const uint32_t *cols = colmask + (size_t)(t % gx) * mask_words;
     // one word per lane per step: a frame has one wave of tile warps, so the shorter steps
     // (and lower register count) win here; the batched builder reads four words per lane
-    uint32_t off = ranges[t].x;
+    const uint2 rg = ranges[t];
+    if (rg.y == rg.x) continue;   // no entries (or ranges emptied by a capacity overflow)
+    uint32_t off = rg.x;
     // the words of group g+2 are loading while group g is written out
     uint32_t nr0 = lane < words ? __ldg(&rows[lane]) : 0u;
     uint32_t nc0 = lane < words ? __ldg(&cols[lane]) : 0u;
@@ -483,19 +503,21 @@ void launch_gather_scan(const uint64_t *sorted, const uint32_t *ctr_nvis, uint32
 }
 
 void launch_tile_scan(int *diff, int gx, int gy, int npass, int dbits, uint2 *ranges,
-                      uint32_t *hist, uint32_t *order, cudaStream_t st) {
-  k_tile_scan<<<1, kScanBlock, 0, st>>>(diff, gx, gy, npass, dbits, ranges, hist, order);
+                      uint32_t *hist, uint32_t *order, cudaStream_t st, uint64_t cap,
+                      unsigned long long *need, uint32_t *err) {
+  k_tile_scan<<<1, kScanBlock, 0, st>>>(diff, gx, gy, npass, dbits, ranges, hist, order, cap,
+                                        need, err);
 }
 
 void launch_tile_lists(const uint32_t *rowmask, const uint32_t *colmask, uint32_t mask_words,
                        uint32_t nv, int gx, int gy, const uint2 *ranges, uint32_t *lists,
-                       cudaStream_t st) {
+                       cudaStream_t st, const uint32_t *nv_dev) {
   const uint64_t tiles = (uint64_t)gx * gy;
-  if (tiles == 0 || nv == 0) return;
+  if (tiles == 0 || (nv == 0 && !nv_dev)) return;
   const int grid = (int)std::min<uint64_t>((tiles + kWarps - 1) / kWarps,
                                            (uint64_t)num_sms() * 8);
-  k_tile_lists<<<grid, kBlock, 0, st>>>(rowmask, colmask, mask_words, (nv + 31) / 32, gx, gy,
-                                        ranges, lists);
+  k_tile_lists<<<grid, kBlock, 0, st>>>(rowmask, colmask, mask_words, (nv + 31) / 32, nv_dev,
+                                        gx, gy, ranges, lists);
 }
 
 template <typename K>

@@ -66,6 +66,9 @@ _SIGNATURES = {
     "fdgs_set_active_mask": [_P, _P, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _P],
     "fdgs_render": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_float,
                     ctypes.POINTER(fdgs_render_opts), _P, ctypes.POINTER(_P), _P],
+    "fdgs_render_async": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_float,
+                          ctypes.POINTER(fdgs_render_opts), _P, _P],
+    "fdgs_reserve_render_lists": [_P, ctypes.c_uint64],
     "fdgs_render_backward": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "fdgs_frame_release": [_P],
     "fdgs_frame_get_stats": [_P, ctypes.POINTER(fdgs_frame_stats)],
@@ -358,6 +361,23 @@ class Scene:
         if keep_frame:
             return out, Frame(self, fh)
         return out
+
+    def render_async(self, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0), out=None, stream=None):
+        """Render [3,H,W] float32 without any host synchronisation (fdgs_render_async): the
+        call only enqueues work on the stream, so it can be captured in a CUDA graph after a
+        first, sizing call. A list-capacity overflow leaves the image at the background and
+        is reported by the next status_sync(), which grows the capacity."""
+        c = make_camera(cam)
+        if out is None:
+            out = torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.device)
+        o = _opts(use_mask, bg)
+        check(lib().fdgs_render_async(self.handle, ctypes.byref(c), float(t), ctypes.byref(o),
+                                      _ptr(out), _stream(stream)))
+        return out
+
+    def reserve_render_lists(self, entries):
+        """List capacity of render_async in tile-list entries (0: size it at the next call)."""
+        check(lib().fdgs_reserve_render_lists(self.handle, int(entries)))
 
     def finetune_step(self, cam, t, target, lr, betas=(0.9, 0.999), eps=1e-15, use_mask=True,
                       tight=True, loss_accum=None, stream=None):
