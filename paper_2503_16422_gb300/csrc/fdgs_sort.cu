@@ -68,8 +68,12 @@ __global__ void __launch_bounds__(kRadix) k_hist_scan(uint32_t *hist) {
 // [0, n); the keys are then wrong but no access is out of bounds. withhold: a partition
 // whose index equals it publishes nothing (failure injection on the host's request; ~0u
 // otherwise).
+// Three CTAs an SM (registers capped at 80): 0.55 -> 0.49 ms for the 64-frame batch's depth
+// sort against two CTAs at the compiler's 128 registers (four CTAs, 64 registers and spills:
+// 0.53 ms). The pass waits on shared memory (the warp ranking and the scatter into s_keys),
+// so more resident warps hide more of it.
 template <typename K>
-__global__ void __launch_bounds__(kSortBlock)
+__global__ void __launch_bounds__(kSortBlock, 3)
 k_onesweep(const K *__restrict__ in, K *__restrict__ out, const uint32_t *__restrict__ n_dev,
            int shift, int dbits, const uint32_t *__restrict__ goff, uint32_t *status,
            uint32_t *part_ctr, uint32_t *err, uint32_t *abort_word, uint32_t spin_limit,
