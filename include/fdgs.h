@@ -503,6 +503,15 @@ int fdgs_debug_inject(int kind, int64_t value);
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char *fdgs_last_error(void);
 
+/* FP32 fma throughput of the current device, measured (the paper has no counterpart; this
+ * is the denominator of the blend's FP32 roofline). Every thread of a grid of 8 x 256-thread
+ * CTAs per SM runs 16 independent fma chains, as scalar fma.rn.f32 (paired = 0) or as
+ * fma.rn.f32x2 on pairs (paired = 1), 2^16 steps each; *tflops_out = 2 FLOP per lane fma /
+ * the fastest of three launches timed with events on the stream (after one untimed launch).
+ * Allocates a small buffer and synchronises. Errors: FDGS_ERR_INVALID (null output, paired
+ * not 0 or 1), FDGS_ERR_CUDA. */
+int fdgs_measure_fp32_peak(int paired, double *tflops_out, fdgs_stream stream);
+
 /* Library version string. */
 const char *fdgs_version(void);
 

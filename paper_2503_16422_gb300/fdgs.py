@@ -110,6 +110,7 @@ _SIGNATURES = {
                            ctypes.POINTER(fdgs_render_opts), _P, ctypes.POINTER(fdgs_adam_opts),
                            _P, _P],
     "fdgs_finetune_reset": [_P],
+    "fdgs_measure_fp32_peak": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P],
 }
 # score variants of fdgs_variation_score_variant (Table 4 of the paper: f, b, c, d, e)
 SCORE_VARIANTS = {"full": 0, "spatial": 1, "temporal": 2, "first_derivative": 3, "sigma_t": 4}
@@ -362,15 +363,17 @@ class Scene:
             return out, Frame(self, fh)
         return out
 
-    def render_async(self, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0), out=None, stream=None):
+    def render_async(self, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0), out=None, stream=None,
+                     tight=False):
         """Render [3,H,W] float32 without any host synchronisation (fdgs_render_async): the
         call only enqueues work on the stream, so it can be captured in a CUDA graph after a
         first, sizing call. A list-capacity overflow leaves the image at the background and
-        is reported by the next status_sync(), which grows the capacity."""
+        is reported by the next status_sync(), which grows the capacity. tight: the
+        alpha-tight tile sets (same image, shorter lists)."""
         c = make_camera(cam)
         if out is None:
             out = torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.device)
-        o = _opts(use_mask, bg)
+        o = _opts(use_mask, bg, tight)
         check(lib().fdgs_render_async(self.handle, ctypes.byref(c), float(t), ctypes.byref(o),
                                       _ptr(out), _stream(stream)))
         return out
@@ -604,6 +607,14 @@ def render(scene: Scene, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0), tight=False)
 
 def version():
     return lib().fdgs_version().decode()
+
+
+def measure_fp32_peak(paired=False, stream=None):
+    """Measured FP32 fma throughput of the current device in TFLOP/s (fdgs_measure_fp32_peak):
+    scalar fma.rn.f32, or fma.rn.f32x2 on pairs when ``paired``."""
+    v = ctypes.c_double()
+    check(lib().fdgs_measure_fp32_peak(1 if paired else 0, ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def set_list_builder(mode):

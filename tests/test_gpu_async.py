@@ -58,14 +58,16 @@ def fit(fd, sc, frames, **kw):
     raise AssertionError("the list capacity kept overflowing")
 
 
-@pytest.mark.parametrize("use_mask,bg", [(True, (0.0, 0.0, 0.0)), (False, (0.0, 0.0, 0.0)),
-                                         (True, (0.2, 0.5, 1.0))])
-def test_async_renders_equal_synchronised_renders(fd, masked_scene, use_mask, bg):
+@pytest.mark.parametrize("use_mask,bg,tight", [(True, (0.0, 0.0, 0.0), False),
+                                               (False, (0.0, 0.0, 0.0), False),
+                                               (True, (0.2, 0.5, 1.0), False),
+                                               (True, (0.0, 0.0, 0.0), True)])
+def test_async_renders_equal_synchronised_renders(fd, masked_scene, use_mask, bg, tight):
     sc, frames = masked_scene
-    want = [sc.render(c, t, use_mask=use_mask, bg=bg).clone() for c, t in frames]
-    fit(fd, sc, frames, use_mask=use_mask, bg=bg)
+    want = [sc.render(c, t, use_mask=use_mask, bg=bg, tight=tight).clone() for c, t in frames]
+    fit(fd, sc, frames, use_mask=use_mask, bg=bg, tight=tight)
     # queued back to back on one stream, no host synchronisation between them
-    outs = [sc.render_async(c, t, use_mask=use_mask, bg=bg) for c, t in frames]
+    outs = [sc.render_async(c, t, use_mask=use_mask, bg=bg, tight=tight) for c, t in frames]
     sc.status_sync()
     for k, (o, w) in enumerate(zip(outs, want)):
         assert torch.equal(o, w), f"frame {k}: async render differs"
