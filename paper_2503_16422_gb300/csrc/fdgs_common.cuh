@@ -84,36 +84,55 @@ __device__ __forceinline__ void st_volatile_u32(uint32_t *p, uint32_t v) {
 // Status word of a single-value decoupled look-back: 2-bit flag in the top bits.
 constexpr uint64_t kLbAgg = 1ull << 62, kLbPrefix = 2ull << 62, kLbValue = (1ull << 62) - 1;
 
-// Thread-0 look-back of partition `part` with aggregate `agg`. Publishes the aggregate,
-// walks back over predecessors until an inclusive prefix is found (bounded spin), publishes
-// the inclusive prefix and returns the exclusive one. On timeout sets kErrTimeout and
-// returns the partial sum so that every waiting successor still terminates.
-__device__ __forceinline__ uint64_t lookback_single(uint64_t *status, uint32_t part,
-                                                    uint64_t agg, uint32_t *err) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v);
+
+// Look-back of partition `part` with aggregate `agg`, walked by a whole warp (all 32 lanes
+// call it; every decision is uniform over the warp). Lane 0 publishes the aggregate; the
+// lanes read the status words of 32 predecessors at once (partitions j, j - 1, ..., j - 31),
+// so the walk back to the nearest inclusive prefix takes one L2 round trip per 32 of them;
+// a predecessor that has not published yet is waited for (bounded spin). Lane 0 publishes
+// the inclusive prefix; every lane returns the exclusive one. On timeout sets kErrTimeout and
+// returns the partial sum, so that every waiting successor still terminates.
+__device__ __forceinline__ uint64_t lookback_warp(uint64_t *status, uint32_t part,
+                                                  uint64_t agg, uint32_t *err) {
+  const uint32_t lane = lane_id();
   if (part == 0) {
-    st_volatile_u64(&status[0], kLbPrefix | agg);
+    if (lane == 0) st_volatile_u64(&status[0], kLbPrefix | agg);
     return 0;
   }
-  st_volatile_u64(&status[part], kLbAgg | agg);
+  if (lane == 0) st_volatile_u64(&status[part], kLbAgg | agg);
   uint64_t excl = 0;
-  int64_t j = (int64_t)part - 1;
+  int64_t j = (int64_t)part - 1;   // the nearest predecessor not summed yet
   uint32_t spins = 0;
-  while (j >= 0) {
-    uint64_t s = ld_volatile_u64(&status[j]);
-    uint64_t f = s & ~kLbValue;
-    if (f == 0) {
-      if (++spins > kSpinLimit || ((spins & 255) == 0 && (ld_volatile_u32(err) & kErrTimeout))) {
-        atomicOr(err, kErrTimeout);
+  for (;;) {
+    const int64_t jj = j - (int64_t)lane;
+    // before partition 0 the prefix is 0
+    const uint64_t s = jj >= 0 ? ld_volatile_u64(&status[jj]) : kLbPrefix;
+    const uint64_t f = s & ~kLbValue;
+    const uint32_t nr = __ballot_sync(0xffffffffu, f == 0);
+    const uint32_t pf = __ballot_sync(0xffffffffu, f == kLbPrefix);
+    const int first_nr = nr ? __ffs(nr) - 1 : 32;
+    const int first_pf = pf ? __ffs(pf) - 1 : 32;
+    if (first_pf < first_nr) {
+      // aggregates up to the nearest inclusive prefix, which ends the walk
+      excl += warp_sum<uint64_t>((int)lane <= first_pf ? (s & kLbValue) : 0ull);
+      break;
+    }
+    // the aggregates before the nearest partition that has not published yet
+    excl += warp_sum<uint64_t>((int)lane < first_nr ? (s & kLbValue) : 0ull);
+    j -= first_nr;
+    if (first_nr < 32) {
+      const bool give_up =
+          ++spins > kSpinLimit || ((spins & 255) == 0 && (ld_volatile_u32(err) & kErrTimeout));
+      if (__any_sync(0xffffffffu, give_up)) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
         break;
       }
       nanosleep_ns(32);
-      continue;
     }
-    excl += s & kLbValue;
-    if (f == kLbPrefix) break;
-    --j;
   }
-  st_volatile_u64(&status[part], kLbPrefix | (excl + agg));
+  if (lane == 0) st_volatile_u64(&status[part], kLbPrefix | (excl + agg));
   return excl;
 }
 

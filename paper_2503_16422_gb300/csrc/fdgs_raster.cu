@@ -105,16 +105,20 @@ __global__ void __launch_bounds__(kBlock) k_preprocess(PreArgs a) {
       if (ab) atomicAdd(&a.ctr[C_NACTIVE], (uint32_t)__popc(ab));
     }
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
       uint32_t tot = 0;
-      for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_wcnt[w];
-        s_wcnt[w] = tot;
-        tot += c;
+      if (lane == 0)
+        for (int w = 0; w < kWarps; ++w) {
+          const uint32_t c = s_wcnt[w];
+          s_wcnt[w] = tot;
+          tot += c;
+        }
+      tot = __shfl_sync(0xffffffffu, tot, 0);
+      const uint64_t base = lookback_warp(a.status, part, tot, a.err);
+      if (lane == 0) {
+        s_base = base;
+        if (part == nparts - 1) a.ctr[C_NVIS] = (uint32_t)(base + tot);
       }
-      const uint64_t base = lookback_single(a.status, part, tot, a.err);
-      s_base = base;
-      if (part == nparts - 1) a.ctr[C_NVIS] = (uint32_t)(base + tot);
     }
     __syncthreads();
     if (vis) a.vis_keys[s_base + s_wcnt[warp] + __popc(vb & lanemask_lt())] = key;
@@ -181,19 +185,23 @@ k_gather_scan(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ 
     const uint32_t inc = warp_incl_scan(cnt);
     if (lane == 31) s_wtot[warp] = inc;
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
       uint32_t tot = 0;
-      for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_wtot[w];
-        s_wtot[w] = tot;
-        tot += c;
-      }
-      const uint64_t base = lookback_single(status, part, tot, err);
-      s_base = base;
-      if (part == nparts - 1) {
-        const uint64_t total = base + tot;
-        ctr[C_NKEYS_LO] = (uint32_t)total;
-        ctr[C_NKEYS_HI] = (uint32_t)(total >> 32);
+      if (lane == 0)
+        for (int w = 0; w < kWarps; ++w) {
+          const uint32_t c = s_wtot[w];
+          s_wtot[w] = tot;
+          tot += c;
+        }
+      tot = __shfl_sync(0xffffffffu, tot, 0);
+      const uint64_t base = lookback_warp(status, part, tot, err);
+      if (lane == 0) {
+        s_base = base;
+        if (part == nparts - 1) {
+          const uint64_t total = base + tot;
+          ctr[C_NKEYS_LO] = (uint32_t)total;
+          ctr[C_NKEYS_HI] = (uint32_t)(total >> 32);
+        }
       }
     }
     __syncthreads();

@@ -23,6 +23,7 @@ constexpr int kMaxPasses = 8;                    // digit passes supported (64 b
 constexpr int kAbortWord = 32;                   // index of the abort word after the counters
 
 // Per-digit status word of the onesweep look-back: 2-bit flag | 30-bit count.
+constexpr int kLookWin = 4;   // predecessors read per look-back step
 constexpr uint32_t kStAgg = 1u << 30, kStPrefix = 2u << 30, kStValue = (1u << 30) - 1;
 
 template <typename K>
@@ -147,12 +148,30 @@ k_onesweep(const K *__restrict__ in, K *__restrict__ out, const uint32_t *__rest
         if (publish) st_volatile_u32(st, kStPrefix | cnt);
       } else {
         if (publish) st_volatile_u32(st, kStAgg | cnt);
+        // the digit's status words of kLookWin predecessors are read at once, so the walk
+        // back to the nearest inclusive prefix takes one L2 round trip per kLookWin of them
         int64_t j = (int64_t)part - 1;
         uint32_t spins = 0;
         while (j >= 0) {
-          const uint32_t s = ld_volatile_u32(status + (size_t)j * kRadix + tid);
-          const uint32_t f = s & ~kStValue;
-          if (f == 0) {
+          uint32_t sv[kLookWin];
+#pragma unroll
+          for (int w = 0; w < kLookWin; ++w)   // before partition 0 the prefix is 0
+            sv[w] = j - w >= 0 ? ld_volatile_u32(status + (size_t)(j - w) * kRadix + tid)
+                               : kStPrefix;
+          int used = 0;         // entries summed; a word not yet published stops the window
+          bool done = false;
+#pragma unroll
+          for (int w = 0; w < kLookWin; ++w) {
+            if (done || used < w) continue;
+            const uint32_t f = sv[w] & ~kStValue;
+            if (f == 0) continue;
+            excl += sv[w] & kStValue;
+            used = w + 1;
+            if (f == kStPrefix) done = true;
+          }
+          if (done) break;
+          j -= used;
+          if (used < kLookWin) {   // partition j has not published: wait for it
             if (++spins > spin_limit ||
                 ((spins & 255) == 0 && ld_volatile_u32(abort_word))) {
               atomicOr(err, kErrTimeout);
@@ -160,11 +179,7 @@ k_onesweep(const K *__restrict__ in, K *__restrict__ out, const uint32_t *__rest
               break;
             }
             __nanosleep(20);
-            continue;
           }
-          excl += s & kStValue;
-          if (f == kStPrefix) break;
-          --j;
         }
         if (publish) st_volatile_u32(st, kStPrefix | ((excl + cnt) & kStValue));
       }
