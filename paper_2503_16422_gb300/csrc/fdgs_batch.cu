@@ -62,90 +62,125 @@ __global__ void __launch_bounds__(kB) k_cond_batch(BatchDev b) {
   }
 }
 
+// Requests served by one item of the batched preprocess: the item's partition of 256
+// Gaussians has its SH coefficients staged in shared memory and its conditional factors held
+// in registers once for all of them (they do not depend on the request), instead of being
+// read from L2 once per request.
+constexpr int kPreGroup = 16;
+// Dynamic shared memory of k_pre_batch: the staged SH planes of one partition.
+inline size_t pre_smem_bytes(int deg, bool vq) {
+  return (size_t)(vq ? 3 : (deg + 1) * (deg + 1) * 3) * kB * sizeof(float);
+}
+
+// Four CTAs an SM (registers capped at 64; the staged coefficients take 48 KB a CTA at degree
+// 3): 0.63 ms per 64 requests for the one-request-per-item kernel, 0.50 with groups of 8 at 80
+// registers, 0.44 with groups of 16 at 64.
 template <bool kVQ>
-__global__ void __launch_bounds__(kB) k_pre_batch(BatchDev b) {
+__global__ void __launch_bounds__(kB, 4) k_pre_batch(BatchDev b) {
   __shared__ uint32_t s_item;
   __shared__ uint32_t s_wcnt[kW];
+  extern __shared__ float s_sh[];   // [planes][kB]: plane k * 3 + c of the partition
   const uint32_t P = (b.n + kB - 1) / kB;
-  const uint32_t items = P * b.nreq;
+  const uint32_t G = (b.nreq + kPreGroup - 1) / kPreGroup;
+  const uint32_t items = P * G;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = (b.deg + 1) * (b.deg + 1);
+  const int planes = kVQ ? 3 : K * 3;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(&b.ctr[BC_PRE_ITEM], 1u);
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= items) break;
-    // request-major order, or partition-major (the requests of one partition back to back,
+    // request-group-major, or partition-major (the groups of one partition back to back,
     // sharing its attributes in L2) for scenes too large for L2; segments and counts are
     // stored request-major (si)
-    const uint32_t r = b.part_major ? item % b.nreq : item / P;
-    const uint32_t part = b.part_major ? item / b.nreq : item % P;
-    const uint32_t si = r * P + part;
-    const ReqDesc &q = b.reqs[r];
+    const uint32_t grp = b.part_major ? item % G : item / P;
+    const uint32_t part = b.part_major ? item / G : item % P;
     const uint32_t i = part * kB + tid;
-    bool active = false, vis = false;
-    uint64_t key = 0;
-    if (i < b.n) {
-      active = true;
-      if (q.mask_l) {
-        const uint32_t w = __ldg(&q.mask_l[i >> 5]) | __ldg(&q.mask_r[i >> 5]);
-        active = (w >> (i & 31)) & 1u;
-      }
-      if (active) {
-        GaussState g;
-        float inv_nt;
-        cond_load(b.cond + (size_t)i * kCond4, g, inv_nt);
-        const uint8_t fl = gauss_forward_tail(q.cam, q.t, __ldg(&b.mean4[i]), inv_nt, g);
-        if (fl & kFlagDet) {
-          const float half = 0.5f * (g.c00 - g.c11);
-          const float disc = half * half + g.c01 * g.c01;
-          const float mid = 0.5f * (g.c00 + g.c11);
-          const float lam = mid + sqrtf(fmaxf(kRadiusFloor, disc));
-          const float rad = ceilf(3.f * sqrtf(lam));
-          const float u = fmaf(q.cam.fx, g.xr, q.cam.cx);
-          const float v = fmaf(q.cam.fy, g.yr, q.cam.cy);
-          int x0, y0, x1, y1;
-          tile_rect(u, v, rad, q.cam.gx, q.cam.gy, x0, y0, x1, y1);
-          if (x1 > x0 && y1 > y0) {
-            vis = true;
-            float rgb[3];
-            gauss_colour<kVQ>(q.cam, b.sh, b.sh_cb, b.sh_code, b.deg, b.n, i, g, rgb);
-            // the blend-ready record by (request, id), and the alpha-tight tile rectangle:
-            // the arithmetic of the per-frame record and gather, so records and lists equal
-            // those of fdgs_render
-            const float idet = 1.f / g.det;
-            const float A = g.c11 * idet, B = -g.c01 * idet, C = g.c00 * idet;
-            const float qa = -0.5f * kLog2e * A, qb = -kLog2e * B, qc = -0.5f * kLog2e * C;
-            const size_t ri = (size_t)r * b.n + i;
-            float4 *rp = reinterpret_cast<float4 *>(b.rec + ri * kRec);
-            rp[0] = make_float4(u, v, qa, qb);
-            rp[1] = make_float4(qc, log2f(g.a), rgb[0], rgb[1]);
-            rp[2] = make_float4(rgb[2], -qb / (2.f * qa), -qb / (2.f * qc), rad);
-            tighten_rect(u, v, A, B, C, g.a, x0, y0, x1, y1);
-            if (!(x1 > x0 && y1 > y0)) x0 = y0 = x1 = y1 = 0;
-            b.rect_id[ri] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16),
-                                       (uint32_t)y0 | ((uint32_t)y1 << 16));
-            key = ((uint64_t)r << 57) | ((uint64_t)__float_as_uint(g.xc[2]) << kIdBits) |
-                  (uint64_t)i;
+    const bool in = i < b.n;
+    for (int pl = 0; pl < planes; ++pl)
+      s_sh[pl * kB + tid] = in ? __ldg(&b.sh[(size_t)pl * b.n + i]) : 0.f;
+    GaussState g0;
+    float inv_nt = 0.f;
+    float4 mean = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (in) {
+      cond_load(b.cond + (size_t)i * kCond4, g0, inv_nt);
+      mean = __ldg(&b.mean4[i]);
+    }
+    // the codebook row (vector-quantised SH): bands k >= 1
+    const float *row = kVQ && in ? b.sh_cb + (size_t)__ldg(&b.sh_code[i]) * (size_t)(K - 1) * 3
+                                 : nullptr;
+    __syncthreads();   // the staged coefficients
+    const uint32_t r_end = min((grp + 1) * (uint32_t)kPreGroup, (uint32_t)b.nreq);
+    for (uint32_t r = grp * kPreGroup; r < r_end; ++r) {
+      const uint32_t si = r * P + part;
+      const ReqDesc &q = b.reqs[r];
+      bool active = false, vis = false;
+      uint64_t key = 0;
+      if (in) {
+        active = true;
+        if (q.mask_l) {
+          const uint32_t w = __ldg(&q.mask_l[i >> 5]) | __ldg(&q.mask_r[i >> 5]);
+          active = (w >> (i & 31)) & 1u;
+        }
+        if (active) {
+          GaussState g = g0;
+          const uint8_t fl = gauss_forward_tail(q.cam, q.t, mean, inv_nt, g);
+          if (fl & kFlagDet) {
+            const float half = 0.5f * (g.c00 - g.c11);
+            const float disc = half * half + g.c01 * g.c01;
+            const float mid = 0.5f * (g.c00 + g.c11);
+            const float lam = mid + sqrtf(fmaxf(kRadiusFloor, disc));
+            const float rad = ceilf(3.f * sqrtf(lam));
+            const float u = fmaf(q.cam.fx, g.xr, q.cam.cx);
+            const float v = fmaf(q.cam.fy, g.yr, q.cam.cy);
+            int x0, y0, x1, y1;
+            tile_rect(u, v, rad, q.cam.gx, q.cam.gy, x0, y0, x1, y1);
+            if (x1 > x0 && y1 > y0) {
+              vis = true;
+              float rgb[3];
+              gauss_colour_from(q.cam, b.deg, g, rgb, [&](int k, int c) {
+                return (kVQ && k > 0) ? __ldg(&row[(k - 1) * 3 + c])
+                                      : s_sh[(k * 3 + c) * kB + tid];
+              });
+              // the blend-ready record by (request, id), and the alpha-tight tile rectangle:
+              // the arithmetic of the per-frame record and gather, so records and lists equal
+              // those of fdgs_render
+              const float idet = 1.f / g.det;
+              const float A = g.c11 * idet, B = -g.c01 * idet, C = g.c00 * idet;
+              const float qa = -0.5f * kLog2e * A, qb = -kLog2e * B, qc = -0.5f * kLog2e * C;
+              const size_t ri = (size_t)r * b.n + i;
+              float4 *rp = reinterpret_cast<float4 *>(b.rec + ri * kRec);
+              rp[0] = make_float4(u, v, qa, qb);
+              rp[1] = make_float4(qc, log2f(g.a), rgb[0], rgb[1]);
+              rp[2] = make_float4(rgb[2], -qb / (2.f * qa), -qb / (2.f * qc), rad);
+              tighten_rect(u, v, A, B, C, g.a, x0, y0, x1, y1);
+              if (!(x1 > x0 && y1 > y0)) x0 = y0 = x1 = y1 = 0;
+              b.rect_id[ri] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16),
+                                         (uint32_t)y0 | ((uint32_t)y1 << 16));
+              key = ((uint64_t)r << 57) | ((uint64_t)__float_as_uint(g.xc[2]) << kIdBits) |
+                    (uint64_t)i;
+            }
           }
         }
       }
-    }
-    const uint32_t vb = __ballot_sync(0xffffffffu, vis);
-    if (lane == 0) s_wcnt[warp] = __popc(vb);
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t tot = 0;
-      for (int w = 0; w < kW; ++w) {
-        const uint32_t c = s_wcnt[w];
-        s_wcnt[w] = tot;
-        tot += c;
+      const uint32_t vb = __ballot_sync(0xffffffffu, vis);
+      if (lane == 0) s_wcnt[warp] = __popc(vb);
+      __syncthreads();
+      if (tid == 0) {
+        uint32_t tot = 0;
+        for (int w = 0; w < kW; ++w) {
+          const uint32_t c = s_wcnt[w];
+          s_wcnt[w] = tot;
+          tot += c;
+        }
+        b.part[si].x = tot;
       }
-      b.part[si].x = tot;
+      __syncthreads();
+      // the item's own 256-key segment, in id order; placed by k_seg_compact
+      if (vis) b.vis_seg[(size_t)si * kB + s_wcnt[warp] + __popc(vb & lanemask_lt())] = key;
+      __syncthreads();
     }
-    __syncthreads();
-    // the item's own 256-key segment, in id order; placed by k_seg_compact
-    if (vis) b.vis_seg[(size_t)si * kB + s_wcnt[warp] + __popc(vb & lanemask_lt())] = key;
-    __syncthreads();
   }
 }
 
@@ -599,9 +634,9 @@ __global__ void k_batch_start(BatchDev b) {
 
 __global__ void k_stamp(unsigned long long *stamps, int i) { stamps[i] = global_timer_ns(); }
 
-int grid_of(const void *kernel, int threads, int per_sm_cap) {
+int grid_of(const void *kernel, int threads, int per_sm_cap, size_t smem = 0) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   per_sm = std::max(1, std::min(per_sm, per_sm_cap));
   return per_sm * num_sms();
 }
@@ -629,18 +664,29 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
   static int g_pre = 0, g_gather = 0;
   k_cond_batch<<<(int)std::min<uint64_t>((b.n + kB - 1) / kB, (uint64_t)num_sms() * 8), kB, 0,
                  st>>>(b);
-  if (!g_pre) g_pre = grid_of((const void *)k_pre_batch<false>, kB, 64);
+  const size_t pre_smem = pre_smem_bytes(b.deg, b.sh_cb != nullptr);
+  static size_t pre_smem_set = 0;
+  if (pre_smem > pre_smem_set) {   // above 48 KB the kernels must opt in
+    cudaFuncSetAttribute(k_pre_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pre_smem);
+    cudaFuncSetAttribute(k_pre_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pre_smem);
+    pre_smem_set = pre_smem;
+    g_pre = 0;
+  }
+  if (!g_pre) g_pre = grid_of((const void *)k_pre_batch<false>, kB, 64, pre_smem);
   if (!g_gather) g_gather = grid_of((const void *)k_gather_batch, kB, 64);
-  const uint64_t pre_items = (uint64_t)((b.n + kB - 1) / kB) * b.nreq;
+  const uint64_t pre_items = (uint64_t)((b.n + kB - 1) / kB) *
+                             (uint64_t)((b.nreq + kPreGroup - 1) / kPreGroup);
   if (b.sh_cb)
-    k_pre_batch<true><<<(int)std::min<uint64_t>(pre_items, g_pre), kB, 0, st>>>(b);
+    k_pre_batch<true><<<(int)std::min<uint64_t>(pre_items, g_pre), kB, pre_smem, st>>>(b);
   else
-    k_pre_batch<false><<<(int)std::min<uint64_t>(pre_items, g_pre), kB, 0, st>>>(b);
+    k_pre_batch<false><<<(int)std::min<uint64_t>(pre_items, g_pre), kB, pre_smem, st>>>(b);
   mark(1);
   k_part_scan<<<b.nreq, kPS, 0, st>>>(b);
   k_batch_bases<<<1, 32, 0, st>>>(b);
   const uint64_t rn = (uint64_t)b.nreq * b.n;
-  const uint64_t segs = (pre_items * kB + kB - 1) / kB;
+  const uint64_t segs = (uint64_t)((b.n + kB - 1) / kB) * b.nreq;   // (request, partition)
   k_seg_compact<<<(int)std::min<uint64_t>(segs, (uint64_t)num_sms() * 16), kB, 0, st>>>(b);
   uint64_t *srt = radix_sort<uint64_t>(b.vis, b.vis_alt, b.ctr + BC_NVIS, rn, kIdBits,
                                        64 - kIdBits, L.sort_scratch, st, b.err);

@@ -242,16 +242,12 @@ __device__ __forceinline__ void cond_load(const float4 *__restrict__ src, GaussS
   g.nt2 = e.x; g.sig = e.y;
 }
 
-// Colour of a Gaussian that reached the projection (state has mu3). sh is [K][3][n].
-// SH coefficients are read from sh [K][3][n], or, with kVQ, the DC plane from sh and bands
-// k >= 1 from cb[code[i]][k - 1][c] (vector-quantised SH). kVQ is a template parameter so
-// that the full-coefficient kernels carry none of the codebook path.
-template <bool kVQ = false>
-__device__ __forceinline__ void gauss_colour(const DevCam &cam, const float *__restrict__ sh,
-                                             const float *__restrict__ cb,
-                                             const uint16_t *__restrict__ code, int deg,
-                                             int64_t n, int64_t i, GaussState &g,
-                                             float rgb[3]) {
+// Colour of a Gaussian that reached the projection (state has mu3), from its SH coefficients
+// coef(k, c) (band-major k = 0 .. (deg+1)^2 - 1, channel c): the view direction from the
+// camera centre to the conditional mean, the real SH basis, max(0, sum + 0.5).
+template <typename Coef>
+__device__ __forceinline__ void gauss_colour_from(const DevCam &cam, int deg, GaussState &g,
+                                                  float rgb[3], Coef &&coef) {
   float d0 = g.mu3[0] - cam.eye[0], d1 = g.mu3[1] - cam.eye[1], d2 = g.mu3[2] - cam.eye[2];
   g.dlen = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
   const float il = 1.f / g.dlen;
@@ -259,18 +255,30 @@ __device__ __forceinline__ void gauss_colour(const DevCam &cam, const float *__r
   float Y[16];
   sh_eval(deg, g.dn[0], g.dn[1], g.dn[2], Y);
   const int K = (deg + 1) * (deg + 1);
-  const float *row = kVQ ? cb + (size_t)__ldg(&code[i]) * (size_t)(K - 1) * 3 : nullptr;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float acc = 0.5f;
-    for (int k = 0; k < K; ++k) {
-      const float f = (kVQ && k > 0) ? __ldg(&row[(k - 1) * 3 + c])
-                                     : __ldg(&sh[((int64_t)k * 3 + c) * n + i]);
-      acc = fmaf(Y[k], f, acc);
-    }
+    for (int k = 0; k < K; ++k) acc = fmaf(Y[k], coef(k, c), acc);
     g.raw[c] = acc;
     rgb[c] = fmaxf(acc, 0.f);
   }
+}
+
+// The colour with the coefficients read from sh [K][3][n], or, with kVQ, the DC plane from sh
+// and bands k >= 1 from cb[code[i]][k - 1][c] (vector-quantised SH). kVQ is a template
+// parameter so that the full-coefficient kernels carry none of the codebook path.
+template <bool kVQ = false>
+__device__ __forceinline__ void gauss_colour(const DevCam &cam, const float *__restrict__ sh,
+                                             const float *__restrict__ cb,
+                                             const uint16_t *__restrict__ code, int deg,
+                                             int64_t n, int64_t i, GaussState &g,
+                                             float rgb[3]) {
+  const int K = (deg + 1) * (deg + 1);
+  const float *row = kVQ ? cb + (size_t)__ldg(&code[i]) * (size_t)(K - 1) * 3 : nullptr;
+  gauss_colour_from(cam, deg, g, rgb, [&](int k, int c) {
+    return (kVQ && k > 0) ? __ldg(&row[(k - 1) * 3 + c])
+                          : __ldg(&sh[((int64_t)k * 3 + c) * n + i]);
+  });
 }
 
 // Gradients of one Gaussian's parameters from the gradients of its 2D record:
