@@ -151,14 +151,19 @@ struct BatchPlan {
   const float *sh_cb = nullptr;            // codebook pointers captured in the graph
   const uint16_t *sh_code = nullptr;
   uint32_t ntiles = 0, nblocks = 0, mask_words = 0;
-  uint64_t key_cap = 0, rn = 0, slot_cap = 0, diff_ints = 0, mask_total = 0;
+  uint64_t key_cap = 0, rn = 0, slot_cap = 0, mask_total = 0;
   std::vector<ReqDesc> tmpl;
   Buf reqs, ctr, part, rec, vis_seg, vis, vis_alt, nv, vis_base, slot_base, key_cnt,
-      rect_id, ridx, rect, diff, masks, ranges, branges, bcount, bkey_cnt, qkeys, qkeys_alt,
+      rect_id, ridx, rect, masks, ranges, branges, bcount, bkey_cnt, qkeys, qkeys_alt,
       lists, ltm, done, t0, scratch, cond;
+  // pinned host memory that the GPU also addresses (mapped; d_* are the device pointers)
   ReqDesc *h_reqs = nullptr;
   uint32_t *h_ctr = nullptr;
   unsigned long long *h_done = nullptr;   // [nreq] completion, then t0
+  uint32_t *h_status = nullptr;           // the status word, read back with the counters
+  ReqDesc *d_h_reqs = nullptr;
+  uint32_t *d_h_ctr = nullptr, *d_h_status = nullptr;
+  unsigned long long *d_h_done = nullptr, *d_h_stamps = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   int footprint = 6, ctas = 0;
@@ -176,13 +181,14 @@ struct BatchPlan {
     stop.release();
     if (h_stamps) cudaFreeHost(h_stamps);
     Buf *all[] = {&reqs, &ctr, &part, &rec, &vis_seg, &vis, &vis_alt, &nv, &vis_base,
-                  &slot_base, &key_cnt, &rect_id, &ridx, &rect, &diff, &masks, &ranges, &branges,
+                  &slot_base, &key_cnt, &rect_id, &ridx, &rect, &masks, &ranges, &branges,
                   &bcount, &bkey_cnt, &qkeys, &qkeys_alt, &lists, &ltm, &done, &t0, &scratch,
                   &cond};
     for (Buf *b : all) b->release();
     if (h_reqs) cudaFreeHost(h_reqs);
     if (h_ctr) cudaFreeHost(h_ctr);
     if (h_done) cudaFreeHost(h_done);
+    if (h_status) cudaFreeHost(h_status);
     if (exec) cudaGraphExecDestroy(exec);
     if (cap) cudaStreamDestroy(cap);
   }
@@ -587,7 +593,7 @@ int plan_build(fdgs_scene *s, BatchPlan &p, const fdgs_camera *cams, int n, bool
   const uint32_t N = (uint32_t)s->d.n;
   p.mask_words = (N + 255) / 256 * 8;
   p.tmpl.resize(n);
-  uint64_t tiles = 0, blocks = 0, diff = 0, mask = 0;
+  uint64_t tiles = 0, blocks = 0, mask = 0;
   for (int i = 0; i < n; ++i) {
     DevCam dc;
     TRY(make_cam(&cams[i], dc));
@@ -596,21 +602,18 @@ int plan_build(fdgs_scene *s, BatchPlan &p, const fdgs_camera *cams, int n, bool
     ReqDesc &q = p.tmpl[i];
     memset(&q, 0, sizeof q);
     q.tile_base = (uint32_t)tiles;
-    q.diff_base = (uint32_t)diff;
     q.mask_base = mask;
     q.block_base = (uint32_t)blocks;
     const uint64_t bgx = (dc.gx + kListBlock - 1) / kListBlock;
     const uint64_t bgy = (dc.gy + kListBlock - 1) / kListBlock;
     blocks += bgx * bgy;
     tiles += (uint64_t)dc.gx * dc.gy;
-    diff += (uint64_t)(dc.gx + 1) * (dc.gy + 1);
     mask += (bgx + bgy) * p.mask_words;
   }
-  if (tiles >= (1ull << 32) || diff >= (1ull << 31))
+  if (tiles >= (1ull << 32))
     return fail(FDGS_ERR_INVALID, "batch too large");
   p.ntiles = (uint32_t)tiles;
   p.nblocks = (uint32_t)blocks;
-  p.diff_ints = diff;
   p.mask_total = mask;
   p.rn = (uint64_t)n * N;
   p.slot_cap = p.rn + (uint64_t)n * 256;
@@ -634,7 +637,6 @@ int plan_build(fdgs_scene *s, BatchPlan &p, const fdgs_camera *cams, int n, bool
   TRY(grow(p.ridx, p.slot_cap * 4));
   TRY(grow(p.rect, p.slot_cap * 8));
   TRY(grow(p.cond, std::max<uint64_t>(N, 1) * 80));
-  TRY(grow(p.diff, diff * 4));
   TRY(grow(p.masks, std::max<uint64_t>(mask, 1) * 4));
   TRY(grow(p.ranges, tiles * 8));
   TRY(grow(p.branges, std::max<uint64_t>(blocks, 1) * 8));
@@ -647,12 +649,18 @@ int plan_build(fdgs_scene *s, BatchPlan &p, const fdgs_camera *cams, int n, bool
   TRY(grow(p.scratch, std::max(sort_scratch_bytes(std::max<uint64_t>(p.rn, 1), 39),
                                sort_scratch_bytes(tiles, 24))));
   TRY(plan_alloc_lists(p));
-  CK(cudaMallocHost(&p.h_reqs, n * sizeof(ReqDesc)));
-  CK(cudaMallocHost(&p.h_ctr, BC_COUNT * 4));
-  CK(cudaMallocHost(&p.h_done, (n + 1) * 8));
+  CK(cudaHostAlloc(&p.h_reqs, n * sizeof(ReqDesc), cudaHostAllocMapped));
+  CK(cudaHostAlloc(&p.h_ctr, BC_COUNT * 4, cudaHostAllocMapped));
+  CK(cudaHostAlloc(&p.h_done, (n + 1) * 8, cudaHostAllocMapped));
+  CK(cudaHostAlloc(&p.h_status, 4, cudaHostAllocMapped));
   CK(cudaStreamCreateWithFlags(&p.cap, cudaStreamNonBlocking));
   TRY(grow(p.stamps, (kBatchStages + 1) * 8));
-  CK(cudaMallocHost(&p.h_stamps, (kBatchStages + 1) * 8));
+  CK(cudaHostAlloc(&p.h_stamps, (kBatchStages + 1) * 8, cudaHostAllocMapped));
+  CK(cudaHostGetDevicePointer((void **)&p.d_h_reqs, p.h_reqs, 0));
+  CK(cudaHostGetDevicePointer((void **)&p.d_h_ctr, p.h_ctr, 0));
+  CK(cudaHostGetDevicePointer((void **)&p.d_h_done, p.h_done, 0));
+  CK(cudaHostGetDevicePointer((void **)&p.d_h_status, p.h_status, 0));
+  CK(cudaHostGetDevicePointer((void **)&p.d_h_stamps, p.h_stamps, 0));
   p.footprint = s->batch_footprint;
   p.ctas = s->batch_ctas ? s->batch_ctas : batch_blend_max_ctas_per_sm(p.footprint);
   return FDGS_OK;
@@ -728,7 +736,6 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.ridx = p.ridx.as<uint32_t>();
   b.cond = p.cond.as<float4>();
   b.rect = p.rect.as<uint2>();
-  b.diff = p.diff.as<int>();
   b.masks = p.masks.as<uint32_t>();
   b.ranges = p.ranges.as<uint2>();
   b.branges = p.branges.as<uint2>();
@@ -751,7 +758,6 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.score_variant = p.score_variant;
   b.mark = p.mark ? 1 : 0;
   L.wsum_len = p.rn;
-  L.diff_bytes = p.diff_ints * 4;
   L.sort_scratch = p.scratch.p;
   L.footprint = p.footprint;
   L.blend_ctas_per_sm = p.ctas;
@@ -761,6 +767,17 @@ void plan_dev(const fdgs_scene *s, BatchPlan &p, BatchDev &b, BatchLaunch &L) {
   b.tma_spin = g_debug_tma_skip ? 4096u : 0u;
   b.rec_map_ok = 0;
   if (g_batch_staging == 1) encode_record_map(b, p.rn);   // cp.async staging if it fails
+}
+
+// The request descriptors from the mapped host array to the device, by a kernel.
+static_assert(sizeof(ReqDesc) % 4 == 0, "descriptors are copied as 32-bit words");
+void upload_reqs(BatchPlan &p, cudaStream_t st) {
+  WordJobs j{};
+  j.src[0] = reinterpret_cast<const uint32_t *>(p.d_h_reqs);
+  j.dst[0] = static_cast<uint32_t *>(p.reqs.p);
+  j.n[0] = (uint32_t)(p.nreq * sizeof(ReqDesc) / 4);
+  j.count = 1;
+  launch_copy_words(j, st);
 }
 
 int plan_capture(fdgs_scene *s, BatchPlan &p) {
@@ -784,7 +801,7 @@ int plan_capture(fdgs_scene *s, BatchPlan &p) {
   p.cap_black = p.black;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeRelaxed));
-  cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice, p.cap);
+  upload_reqs(p, p.cap);
   launch_batch(b, L, p.cap);
   p.vis_sorted = L.vis_sorted;
   const cudaError_t e = cudaStreamEndCapture(p.cap, &g);
@@ -816,21 +833,29 @@ int plan_run(fdgs_scene *s, BatchPlan &p, cudaStream_t st) {
       BatchLaunch L;
       plan_dev(s, p, b, L);
       if (count) b.evals = s->evals.as<unsigned long long>();
-      CK(cudaMemcpyAsync(p.reqs.p, p.h_reqs, p.nreq * sizeof(ReqDesc), cudaMemcpyHostToDevice,
-                         st));
+      upload_reqs(p, st);
       launch_batch(b, L, st);
       p.vis_sorted = L.vis_sorted;
       if (inject) g_debug_tma_skip = 0;
     }
+    // counters, completion times, stage stamps and the status word, written by the GPU
+    // straight into pinned host memory
+    WordJobs j{};
+    auto job = [&](const void *src, void *dst, size_t bytes) {
+      j.src[j.count] = static_cast<const uint32_t *>(src);
+      j.dst[j.count] = static_cast<uint32_t *>(dst);
+      j.n[j.count] = (uint32_t)(bytes / 4);
+      ++j.count;
+    };
+    job(p.ctr.p, p.d_h_ctr, BC_COUNT * 4);
+    job(p.done.p, p.d_h_done, p.nreq * 8);
+    job(p.t0.p, p.d_h_done + p.nreq, 8);
+    job(p.stamps.p, p.d_h_stamps, (kBatchStages + 1) * 8);
+    job(s->status.p, p.d_h_status, 4);
+    launch_copy_words(j, st);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(p.h_ctr, p.ctr.p, BC_COUNT * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(p.h_done, p.done.p, p.nreq * 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(p.h_done + p.nreq, p.t0.p, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(p.h_stamps, p.stamps.p, (kBatchStages + 1) * 8, cudaMemcpyDeviceToHost,
-                       st));
-    uint32_t e = 0;
-    CK(cudaMemcpyAsync(&e, s->status.p, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    const uint32_t e = *(volatile uint32_t *)p.h_status;
     if (e & kErrTimeout) {
       CK(cudaMemset(s->status.p, 0, 4));
       return fail(FDGS_ERR_TIMEOUT, "device spin-wait limit reached");
@@ -1377,15 +1402,21 @@ int fdgs_batch_tile_lists(fdgs_scene *s, int req, uint32_t *tile_ranges_host,
   std::vector<uint2> rg(tiles);
   CK(cudaMemcpy(rg.data(), p.ranges.as<uint2>() + q.tile_base, tiles * 8,
                 cudaMemcpyDeviceToHost));
-  // a request's lists are laid out tile-major from its first tile's start
-  const uint32_t lo = tiles ? rg[0].x : 0, hi = tiles ? rg[tiles - 1].y : 0;
-  const uint64_t n = hi >= lo ? hi - lo : 0;
+  // the device holds each tile's list length as [0, length); laid out tile-major, the
+  // request's lists start where the previous tile's end
+  uint64_t n = 0;
+  for (size_t t = 0; t < tiles; ++t) {
+    const uint32_t len = rg[t].y - rg[t].x;
+    rg[t] = make_uint2((uint32_t)n, (uint32_t)(n + len));
+    n += len;
+  }
+  const uint32_t lo = 0;
   if (n_tiles) *n_tiles = tiles;
   if (n_ids) *n_ids = n;
   if (tile_ranges_host)
     for (size_t t = 0; t < tiles; ++t) {
-      tile_ranges_host[2 * t] = rg[t].x - lo;
-      tile_ranges_host[2 * t + 1] = rg[t].y - lo;
+      tile_ranges_host[2 * t] = rg[t].x;
+      tile_ranges_host[2 * t + 1] = rg[t].y;
     }
   if (!tile_ids_host || n == 0) return FDGS_OK;
   if (ids_cap < n) return fail(FDGS_ERR_INVALID, "tile_ids buffer holds %llu of %llu ids",

@@ -277,15 +277,7 @@ __global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
       x1 = (int)(rc.x >> 16);
       y0 = (int)(rc.y & 0xFFFFu);
       y1 = (int)(rc.y >> 16);
-      if (x1 > x0 && y1 > y0) {
-        cnt = (uint32_t)((x1 - x0) * (y1 - y0));
-        int *diff = b.diff + q.diff_base;
-        const int W1 = q.cam.gx + 1;
-        atomicAdd(&diff[y0 * W1 + x0], 1);
-        atomicAdd(&diff[y0 * W1 + x1], -1);
-        atomicAdd(&diff[y1 * W1 + x0], -1);
-        atomicAdd(&diff[y1 * W1 + x1], 1);
-      }
+      if (x1 > x0 && y1 > y0) cnt = (uint32_t)((x1 - x0) * (y1 - y0));
     }
     // block-row and block-column coverage bitmasks of the request (a block row holds
     // kListBlock tile rows); the warp owns local word l / 32
@@ -305,51 +297,22 @@ __global__ void __launch_bounds__(kB, 4) k_gather_batch(BatchDev b) {
   }
 }
 
-// One CTA per request: coverage counts -> global tile ranges (or empty ranges if the lists
-// would overflow the capacity) and the longest-first queue keys; block coverage counts ->
-// the block lists' ranges.
+// One CTA per request: the request's list totals, the capacity check (empty block ranges if
+// the lists would overflow it), and the block lists' ranges from the block coverage counts.
 constexpr int kTS = 1024;
 
-// In place, the 2-D inclusive prefix of a (h + 1) x (w + 1) coverage difference array (rows,
-// then columns): afterwards d[y][x] is the coverage count of cell (x, y).
-__device__ void prefix_2d(int *d, int w, int h) {
-  const int W1 = w + 1;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int y = warp; y < h; y += kTS / 32) {
-    int carry = 0;
-    for (int x0 = 0; x0 < w; x0 += 32) {
-      const int x = x0 + lane;
-      int v = x < w ? d[y * W1 + x] : 0;
-      v = warp_incl_scan(v) + carry;
-      if (x < w) d[y * W1 + x] = v;
-      carry = __shfl_sync(0xffffffffu, v, 31);
-    }
-  }
-  __syncthreads();
-  for (int x = tid; x < w; x += kTS) {
-    int acc = 0;
-    for (int y = 0; y < h; ++y) {
-      acc += d[y * W1 + x];
-      d[y * W1 + x] = acc;
-    }
-  }
-  __syncthreads();
-}
-
-// Exclusive scan, in cell order, of the counts of a w x h grid: d[y][x] of a coverage
-// difference array after prefix_2d (row stride w + 1), or a plain count array (kPlain, row
-// stride w); emit(cell, start, count) for every cell.
-template <bool kPlain = false, class Cnt, class F>
+// Exclusive scan, in cell order, of the counts of a w x h grid (row stride w); emit(cell,
+// start, count) for every cell.
+template <class Cnt, class F>
 __device__ void scan_cells(const Cnt *d, int w, int h, uint32_t *s_wsum, uint32_t &s_carry,
                            F &&emit) {
-  const int W1 = kPlain ? w : w + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t cells = (uint32_t)w * h;
   if (tid == 0) s_carry = 0;
   __syncthreads();
   for (uint32_t c0 = 0; c0 < cells; c0 += kTS) {
     const uint32_t t = c0 + tid;
-    const uint32_t c = t < cells ? (uint32_t)d[(t / w) * W1 + (t % w)] : 0u;
+    const uint32_t c = t < cells ? (uint32_t)d[t] : 0u;
     const uint32_t inc = warp_incl_scan(c);
     if (lane == 31) s_wsum[warp] = inc;
     __syncthreads();
@@ -371,19 +334,13 @@ __global__ void __launch_bounds__(kTS) k_tile_scan_batch(BatchDev b) {
   __shared__ uint32_t s_carry;
   const int r = blockIdx.x;
   const ReqDesc &q = b.reqs[r];
-  const int gx = q.cam.gx, gy = q.cam.gy;
-  const int bgx = (gx + kListBlock - 1) / kListBlock, bgy = (gy + kListBlock - 1) / kListBlock;
-  int *diff = b.diff + q.diff_base;
-  prefix_2d(diff, gx, gy);
-  // the request's first tile key and first block-list entry: the counts of the requests
-  // before it
-  uint64_t base = 0, nkeys = 0, bbase = 0, nbkeys = 0;
+  const int bgx = (q.cam.gx + kListBlock - 1) / kListBlock;
+  const int bgy = (q.cam.gy + kListBlock - 1) / kListBlock;
+  // the request's first block-list entry: the counts of the requests before it
+  uint64_t nkeys = 0, bbase = 0, nbkeys = 0;
   for (int i = 0; i < b.nreq; ++i) {
     const uint64_t c = b.key_cnt[i], cb = b.bkey_cnt[i];
-    if (i < r) {
-      base += c;
-      bbase += cb;
-    }
+    if (i < r) bbase += cb;
     nkeys += c;
     nbkeys += cb;
   }
@@ -395,16 +352,7 @@ __global__ void __launch_bounds__(kTS) k_tile_scan_batch(BatchDev b) {
   }
   const bool overflow = nbkeys > b.key_cap;
   if (overflow && threadIdx.x == 0) atomicOr(b.err, kErrCapacity);
-  // tile ranges in the request's tile-key order (the lengths order the queue; the entries
-  // themselves live in the block lists)
-  scan_cells(diff, gx, gy, s_wsum, s_carry, [&](uint32_t t, uint32_t start, uint32_t c) {
-    const uint32_t gt = q.tile_base + t;
-    const uint32_t st = (uint32_t)(base + start);
-    b.ranges[gt] = overflow ? make_uint2(0, 0) : make_uint2(st, st + c);
-    const uint32_t len = overflow ? 0u : min(c, 0xFFFFFFu);
-    b.qkeys[gt] = ((uint64_t)(0xFFFFFFu - len) << 32) | gt;
-  });
-  scan_cells<true>(b.bcount + q.block_base, bgx, bgy, s_wsum, s_carry,
+  scan_cells(b.bcount + q.block_base, bgx, bgy, s_wsum, s_carry,
              [&](uint32_t k, uint32_t start, uint32_t c) {
                const uint32_t st = (uint32_t)(bbase + start);
                b.branges[q.block_base + k] = overflow ? make_uint2(0, 0) : make_uint2(st, st + c);
@@ -423,6 +371,33 @@ __global__ void __launch_bounds__(kTS) k_tile_scan_batch(BatchDev b) {
 constexpr int kLW = 4;                          // warps per CTA
 constexpr uint32_t kLQ = 288;                   // queue entries per warp
 static_assert(kListBlock == 4, "the tile masks below hold 4 x 4 tiles in 16 bits");
+
+// Per-tile entry counts of a block list, kept by each lane for the entries it handles: the
+// 16-bit tile mask of an entry is spread four bits to a word of byte fields (bit j of a nibble
+// to bit 8 j) and added to four lane-local words; tile_counts_flush sums those words over the
+// warp into lane t < 16's count of tile t and clears them. A field grows by at most one per
+// entry, so a lane flushes at least every 255 entries.
+__device__ __forceinline__ void tile_counts_add(uint32_t tm, uint32_t acc[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k] += (((tm >> (4 * k)) & 0xFu) * 0x204081u) & 0x01010101u;
+}
+__device__ __forceinline__ void tile_counts_flush(uint32_t acc[4], uint32_t lane,
+                                                  uint32_t &tcnt) {
+  uint32_t red[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    // per byte field: sum over the warp without carries between fields (each field of a
+    // lane is at most 255, so the four fields are summed as separate 16-bit halves)
+    const uint32_t lo = __reduce_add_sync(0xffffffffu, acc[k] & 0x00FF00FFu);
+    const uint32_t hi = __reduce_add_sync(0xffffffffu, (acc[k] >> 8) & 0x00FF00FFu);
+    red[k] = lane < 16 ? ((lane & 1) ? hi : lo) : 0u;
+    acc[k] = 0u;
+  }
+  const uint32_t k = lane >> 2;
+  const uint32_t w = k == 0 ? red[0] : k == 1 ? red[1] : k == 2 ? red[2] : red[3];
+  // field f = lane & 3 of the word: bytes 0 and 2 went to lo (halves), 1 and 3 to hi
+  if (lane < 16) tcnt += (w >> (16 * ((lane & 3) >> 1))) & 0xFFFFu;
+}
 
 // Entries of every block list: per block (a warp), the popcount of the AND of its row and
 // column bitmasks, and the request's total.
@@ -476,7 +451,6 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
   const int nreq = b.nreq;
   for (uint32_t gb = blockIdx.x * kLW + warp; gb < b.nblocks; gb += gridDim.x * kLW) {
     const uint2 brg = b.branges[gb];
-    if (brg.y == brg.x) continue;
     const int r = find_segment(s_block_base, nreq, gb);
     const ReqDesc &q = b.reqs[r];
     const int gx = q.cam.gx, gy = q.cam.gy;
@@ -488,12 +462,14 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
     const uint32_t *rows = masks + q.mask_base + (size_t)(by0 / kListBlock) * mw;
     const uint32_t *cols = masks + q.mask_base + (size_t)bgy * mw + (size_t)(bx0 / kListBlock) * mw;
     uint32_t out = brg.x;                        // next list position (warp-uniform)
+    uint32_t tcnt = 0;                           // lane t < 16: entries of the block's tile t
+    uint32_t tacc[4] = {0u, 0u, 0u, 0u}, tn = 0;  // lane-local counts, entries since a flush
     // two words per lane per round (64-bit loads; the masks are zero up to the request's
     // 256-slot boundary, so the pair of the last word is readable and empty); the words of
     // the next round are loaded while this round is processed
     const uint2 *rows2 = reinterpret_cast<const uint2 *>(rows);
     const uint2 *cols2 = reinterpret_cast<const uint2 *>(cols);
-    const uint32_t pairs = (words + 1) / 2;
+    const uint32_t pairs = brg.y > brg.x ? (words + 1) / 2 : 0u;   // an empty list: no pass
     uint2 nr = lane < pairs ? __ldg(&rows2[lane]) : make_uint2(0u, 0u);
     uint2 nc = lane < pairs ? __ldg(&cols2[lane]) : make_uint2(0u, 0u);
     for (uint32_t p0 = 0; p0 < pairs; p0 += 32) {
@@ -514,23 +490,33 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
         const uint32_t qn = min(tot, kLQ);
         __syncwarp();
         // tile masks from the rectangles (independent loads), coalesced stores
-        for (uint32_t e = lane; e < qn; e += 32) {
-          const uint32_t slot = qs[e];
-          const uint2 rc = __ldg(&rect[slot]);
-          const uint32_t ri = __ldg(&ridx[slot]);
-          const int rx0 = max((int)(rc.x & 0xFFFFu) - bx0, 0);
-          const int rx1 = min((int)(rc.x >> 16) - bx0, kListBlock);
-          const int ry0 = max((int)(rc.y & 0xFFFFu) - by0, 0);
-          const int ry1 = min((int)(rc.y >> 16) - by0, kListBlock);
+        for (uint32_t e0 = 0; e0 < qn; e0 += 32) {
+          const uint32_t e = e0 + lane;
           uint32_t tm = 0;
-          if (rx1 > rx0 && ry1 > ry0) {
-            const uint32_t xm = (1u << rx1) - (1u << rx0);
-            const uint32_t ym = (1u << (kListBlock * ry1)) - (1u << (kListBlock * ry0));
-            tm = (xm * 0x1111u) & ym;
+          if (e < qn) {
+            const uint32_t slot = qs[e];
+            const uint2 rc = __ldg(&rect[slot]);
+            const uint32_t ri = __ldg(&ridx[slot]);
+            const int rx0 = max((int)(rc.x & 0xFFFFu) - bx0, 0);
+            const int rx1 = min((int)(rc.x >> 16) - bx0, kListBlock);
+            const int ry0 = max((int)(rc.y & 0xFFFFu) - by0, 0);
+            const int ry1 = min((int)(rc.y >> 16) - by0, kListBlock);
+            if (rx1 > rx0 && ry1 > ry0) {
+              const uint32_t xm = (1u << rx1) - (1u << rx0);
+              const uint32_t ym = (1u << (kListBlock * ry1)) - (1u << (kListBlock * ry0));
+              tm = (xm * 0x1111u) & ym;
+            }
+            if (out + e < brg.y) {               // the block's range bounds every store
+              lists[out + e] = ri;
+              ltm[out + e] = (uint16_t)tm;
+            } else {
+              tm = 0;
+            }
           }
-          if (out + e < brg.y) {                 // the block's range bounds every store
-            lists[out + e] = ri;
-            ltm[out + e] = (uint16_t)tm;
+          tile_counts_add(tm, tacc);
+          if (++tn == 255u) {                     // uniform: every lane counts each step
+            tile_counts_flush(tacc, lane, tcnt);
+            tn = 0;
           }
         }
         out += qn;
@@ -539,6 +525,18 @@ __global__ void __launch_bounds__(kLW * 32) k_lists_blocks(BatchDev b) {
         pc = __popcll(m);                          // bits the full queue could not take
         inc = warp_incl_scan(pc);
         tot = __shfl_sync(0xffffffffu, inc, 31);
+      }
+    }
+    tile_counts_flush(tacc, lane, tcnt);
+    // the block's tiles: list lengths (as [0, length) ranges: the blend skips empty tiles)
+    // and the keys of the longest-first queue
+    if (lane < kListBlock * kListBlock) {
+      const int tx = bx0 + (int)(lane % kListBlock), ty = by0 + (int)(lane / kListBlock);
+      if (tx < gx && ty < gy) {
+        const uint32_t gt = q.tile_base + (uint32_t)(ty * gx + tx);
+        b.ranges[gt] = make_uint2(0u, tcnt);
+        const uint32_t len = min(tcnt, 0xFFFFFFu);
+        b.qkeys[gt] = ((uint64_t)(0xFFFFFFu - len) << 32) | gt;
       }
     }
   }
@@ -649,7 +647,6 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
   cudaMemsetAsync(b.ctr, 0, BC_COUNT * sizeof(uint32_t), st);
   cudaMemsetAsync(b.key_cnt, 0, b.nreq * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.bkey_cnt, 0, b.nreq * sizeof(unsigned long long), st);
-  cudaMemsetAsync(b.diff, 0, L.diff_bytes, st);
   cudaMemsetAsync(b.done_ns, 0, b.nreq * sizeof(unsigned long long), st);
   if (b.evals) cudaMemsetAsync(b.evals, 0, 3 * sizeof(unsigned long long), st);
   if (b.w_sum) {
@@ -752,6 +749,17 @@ void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st) {
     });
   }
   mark(7);
+}
+
+__global__ void k_copy_words(WordJobs j) {
+  for (int k = 0; k < j.count; ++k)
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < j.n[k];
+         i += gridDim.x * blockDim.x)
+      j.dst[k][i] = j.src[k][i];
+}
+
+void launch_copy_words(const WordJobs &j, cudaStream_t st) {
+  k_copy_words<<<4, 256, 0, st>>>(j);
 }
 
 bool encode_record_map(BatchDev &b, uint64_t rows) {

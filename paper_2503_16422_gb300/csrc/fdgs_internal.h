@@ -166,7 +166,6 @@ struct ReqDesc {
   float *rgb;                        // [3][H][W]
   uint32_t tile_base;                // first global tile id of the request
   uint32_t block_base;               // first global tile-block id (kListBlock^2 tiles each)
-  uint32_t diff_base;                // offset of its coverage difference array (ints)
   uint64_t mask_base;                // offset of its block-row and block-column bitmasks
   uint32_t *mark_row;                // mask pass: the key-frame word row it marks, or null
 };
@@ -199,9 +198,10 @@ struct BatchDev {
   uint32_t *nv, *vis_base, *slot_base;
   unsigned long long *key_cnt;       // [nreq] list entries per request
   uint2 *rect;                       // [slots] tile rectangle: x0 | x1 << 16, y0 | y1 << 16
-  int *diff;
   uint32_t *masks;
-  uint2 *ranges;                     // [ntiles] tile-key ranges (counts; lists are per block)
+  uint2 *ranges;                     // [ntiles] [0, list length) of each tile's list
+                                     // (written with the block lists; the entries live
+                                     // in the block lists)
   uint2 *branges;                    // [nblocks] [start, end) into lists / ltm
   uint32_t *bcount;                  // [nblocks] block-list entries
   unsigned long long *bkey_cnt;      // [nreq] block-list entries per request
@@ -231,7 +231,6 @@ struct BatchDev {
   uint32_t tma_spin;                 // stage-wait poll limit (0: kTmaSpin)
 };
 struct BatchLaunch {
-  size_t diff_bytes;
   void *sort_scratch;
   int footprint;                     // launch shape of the blend (with_blend_shape)
   int blend_ctas_per_sm;             // persistent blend grid = this x SMs
@@ -272,6 +271,18 @@ constexpr int kBatchIdBits = 25;
 // gather, tile_scan, lists, queue_sort, blend.
 constexpr int kBatchStages = 7;
 void launch_batch(const BatchDev &b, BatchLaunch &L, cudaStream_t st);
+// Word copies run by one small kernel (up to kWordJobs of them): the batch uploads its request
+// descriptors from, and reads its counters back into, pinned host memory that the GPU
+// addresses directly, so that no copy engine is involved and they never wait behind the
+// caller's own host copies on other streams.
+constexpr int kWordJobs = 6;
+struct WordJobs {
+  const uint32_t *src[kWordJobs];
+  uint32_t *dst[kWordJobs];
+  uint32_t n[kWordJobs];
+  int count;
+};
+void launch_copy_words(const WordJobs &j, cudaStream_t st);
 // Score pass of a batch: adds w_sum[r][i] * f_i(t_r) * gamma_i to score[i] for every request
 // r and Gaussian i (after the weighted blend of the batch).
 void launch_score_batch(const BatchDev &b, cudaStream_t st);
