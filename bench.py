@@ -461,6 +461,36 @@ def timed_batches(sc, cams_list, ts_list, outs_list, masked, flush, stream, stag
     return ms, lat
 
 
+RASTER_STAGES = ("depth_sort", "gather", "tile_scan", "lists", "queue_sort", "blend")
+
+
+def raster_fps(stage_ms, frames):
+    """Frames per second of the rasterisation stages alone (the paper's Raster FPS, Table 3:
+    sort, lists, tile ranges and blend; the per-Gaussian stage left out), from the batch's
+    in-graph stage stamps."""
+    ms = sum(stage_ms[k] for k in RASTER_STAGES if k in stage_ms)
+    return frames / (ms / 1e3) if ms > 0 else None
+
+
+def batched_table3(sc, cams, times, masked, flush, stream, B=64, walk=(7, 9, 11)):
+    """The headline's frame walk in batches of B, masked or not: FPS and Raster FPS (the
+    paper's Table 3 columns, with and without the key-frame filter), medians of three
+    L2-flushed batches."""
+    import torch
+    outs = [torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device="cuda")
+            for _ in range(B)]
+    bargs = [([cams[k] for k in frame_list(B, w * B)],
+              [float(times[k]) for k in frame_list(B, w * B)]) for w in walk]
+    sc.render_batch(*bargs[0], use_mask=masked, outs=outs)
+    stages = []
+    ms, _ = timed_batches(sc, [a for a, _ in bargs], [b_ for _, b_ in bargs],
+                          [outs] * len(bargs), masked, flush, stream, stages)
+    st = {k: statistics.median([x[k] for x in stages]) for k in stages[0]}
+    del outs
+    return dict(fps=B / (statistics.median(ms) / 1e3), raster_fps=raster_fps(st, B),
+                ms_per_batch=statistics.median(ms), batch=B, masked=masked, stage_ms=st)
+
+
 def batch_counts(sc, cams_list, ts_list, outs):
     """Blend evaluations and culling tests of the given batches (counting profile: eager
     runs with the counting blend variant; untimed)."""
@@ -644,6 +674,7 @@ def run_ours(args):
             else None,
             "issue_src": prof_src}
         res["batch_stages_ms"] = bst
+        res["raster_fps"] = raster_fps(bst, B) * world
         # per-kernel profile on single renders of the same frames
         out1 = outs[0]
         fr_prof = frame_list(24, 11)
@@ -803,6 +834,8 @@ def comparisons(sc, cams, times, flush, stream):
         sequential_p50_ms=float(np.percentile(seq_lat, 50)),
         sequential_p99_ms=float(np.percentile(seq_lat, 99)),
         shape=sc.batch_info(64))
+    # the pruned scene's batches without the key-frame filter (Table 3 columns)
+    res["pruned_unmasked_batched"] = batched_table3(sc, cams, times, False, flush, stream)
     # record staging of the batched blend: per-thread cp.async against TMA gather4
     res["blend_staging"] = staging_ab(sc, cams, times, flush, stream)
     # backward (fine-tuning step): L1 loss against a render of the scene with means perturbed
@@ -843,11 +876,14 @@ def comparisons(sc, cams, times, flush, stream):
     stages = []
     ms, _ = timed_batches(sc2, [a for a, _ in bargs], [b_ for _, b_ in bargs], [outs] * 3, True,
                           flush, stream, stages)
+    st2 = {k: statistics.median([x[k] for x in stages]) for k in stages[0]}
     res["unpruned_masked_batched"] = dict(
-        fps=B / (statistics.median(ms) / 1e3), ms_per_batch=statistics.median(ms), batch=B,
-        n_gaussians=big.n, stage_ms={k: statistics.median([x[k] for x in stages])
-                                     for k in stages[0]})
+        fps=B / (statistics.median(ms) / 1e3), raster_fps=raster_fps(st2, B),
+        ms_per_batch=statistics.median(ms), batch=B, n_gaussians=big.n, stage_ms=st2)
     del outs
+    # the paper's Table 3 columns (FPS, Raster FPS) without the key-frame filter, batched
+    res["unpruned_unmasked_batched"] = dict(
+        batched_table3(sc2, cams, times, False, flush, stream), n_gaussians=big.n)
     sc2.close()
     del big
     torch.cuda.empty_cache()
@@ -1291,6 +1327,7 @@ def main():
                            "p99": float(np.percentile(lat, 99))},
             "batch_shape": {k: v for k, v in res["batch_shape"].items() if k != "latency_ms"},
             "batch_stages_ms": res["batch_stages_ms"],
+            "raster_fps": res["raster_fps"],
             "per_kernel_roofline": res["per_kernel_roofline"],
             "batch_rates": res["batch_rates"],
             "single_frame_stages_ms": res["stage_ms"], "stage_gbs": res["stage_gbs"],
