@@ -341,6 +341,16 @@ int fdgs_variation_score_variant(fdgs_scene *scene, const fdgs_camera *cams, int
                                  const float *ts, int n_t, int batch, int variant,
                                  float *score_out_dev, fdgs_stream stream);
 
+/* fdgs_variation_score_variant that ADDS the pass's scores into score_inout_dev [n] instead of
+ * overwriting it (the paper has no counterpart of the call). A score pass split into parts over
+ * disjoint sets of (t, camera) renders then sums to the scores of the whole pass, up to the
+ * order of the float additions, so a long pass can be checkpointed (the partial scores and the
+ * parts done) and resumed after an interruption. Same arguments and errors as
+ * fdgs_variation_score_variant. */
+int fdgs_variation_score_add(fdgs_scene *scene, const fdgs_camera *cams, int n_cam,
+                             const float *ts, int n_t, int batch, int variant,
+                             float *score_inout_dev, fdgs_stream stream);
+
 /*
  * Pruning keep-set (Sec. 4.2.1 "Pruning"): ranks the n scores by ascending (score, index)
  * and clears the lowest floor(prune_ratio * n). keep_out_dev [n] uint8 gets 1 = keep,

@@ -1462,9 +1462,32 @@ int fdgs_variation_score(fdgs_scene *s, const fdgs_camera *cams, int n_cam, cons
                                       score_out_dev, stream);
 }
 
+}  // extern "C"
+namespace {
+int score_impl(fdgs_scene *s, const fdgs_camera *cams, int n_cam, const float *ts, int n_t,
+               int batch, int variant, float *score_out_dev, bool zero, fdgs_stream stream);
+}  // namespace
+extern "C" {
+
 int fdgs_variation_score_variant(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
                                  const float *ts, int n_t, int batch, int variant,
                                  float *score_out_dev, fdgs_stream stream) {
+  return score_impl(s, cams, n_cam, ts, n_t, batch, variant, score_out_dev, true, stream);
+}
+
+int fdgs_variation_score_add(fdgs_scene *s, const fdgs_camera *cams, int n_cam, const float *ts,
+                             int n_t, int batch, int variant, float *score_inout_dev,
+                             fdgs_stream stream) {
+  return score_impl(s, cams, n_cam, ts, n_t, batch, variant, score_inout_dev, false, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The score pass; zero: overwrite score_out_dev, else add to it (a pass split into parts).
+int score_impl(fdgs_scene *s, const fdgs_camera *cams, int n_cam, const float *ts, int n_t,
+               int batch, int variant, float *score_out_dev, bool zero, fdgs_stream stream) {
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   if (n_cam < 0 || n_t < 0 || batch < 1 || !score_out_dev ||
       (n_cam > 0 && !cams) || (n_t > 0 && !ts))
@@ -1473,7 +1496,7 @@ int fdgs_variation_score_variant(fdgs_scene *s, const fdgs_camera *cams, int n_c
     return fail(FDGS_ERR_INVALID, "unknown score variant %d", variant);
   cudaStream_t st = (cudaStream_t)stream;
   const uint32_t N = (uint32_t)s->d.n;
-  CK(cudaMemsetAsync(score_out_dev, 0, (size_t)N * 4, st));
+  if (zero) CK(cudaMemsetAsync(score_out_dev, 0, (size_t)N * 4, st));
   if (N == 0) return FDGS_OK;
   // gamma = clamp(V / V_p90, 0, 1)^0.1, V_p90 the nearest-rank 90th percentile
   TRY(grow(s->aux[0], (size_t)N * 4 * 2 + 16));   // volume bits, ping-pong
@@ -1564,6 +1587,10 @@ int fdgs_variation_score_variant(fdgs_scene *s, const fdgs_camera *cams, int n_c
   CK(cudaGetLastError());
   return FDGS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int fdgs_select_keep(fdgs_scene *s, const float *score_dev, int64_t n, float prune_ratio,
                      uint8_t *keep_out_dev, fdgs_stream stream) {

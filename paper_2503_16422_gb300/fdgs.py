@@ -81,6 +81,9 @@ _SIGNATURES = {
     "fdgs_variation_score_variant": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _P, _P],
+    "fdgs_variation_score_add": [_P, ctypes.POINTER(fdgs_camera), ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, _P, _P],
     "fdgs_select_keep": [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P],
     "fdgs_select_keep_noalloc": [_P, ctypes.c_int64, ctypes.c_float, _P, _P],
     "fdgs_status_sync": [_P],
@@ -521,11 +524,21 @@ class Scene:
                                           ctypes.byref(nt), ctypes.byref(n)))
         return ranges, ids[: n.value]
 
-    def variation_score(self, cams, ts, batch=8, out=None, stream=None, variant="full"):
+    def variation_score(self, cams, ts, batch=8, out=None, stream=None, variant="full",
+                        accumulate=False):
         """Spatial-temporal variation score [n] over the (t, camera) renders; ``variant``
-        selects a score of the paper's ablation (SCORE_VARIANTS; "full" is the paper's)."""
+        selects a score of the paper's ablation (SCORE_VARIANTS; "full" is the paper's).
+        accumulate=True adds the pass's scores into ``out`` (fdgs_variation_score_add), for a
+        pass split into parts."""
         _ca, carr = make_cameras(cams)
         tarr = (ctypes.c_float * max(len(ts), 1))(*[float(t) for t in ts])
+        if accumulate:
+            if out is None:
+                raise ValueError("accumulate=True adds into out, which must be given")
+            check(lib().fdgs_variation_score_add(
+                self.handle, carr, len(cams), tarr, len(ts), int(batch), SCORE_VARIANTS[variant],
+                _ptr(out), _stream(stream)))
+            return out
         if out is None:
             out = torch.empty((self.n,), dtype=torch.float32, device=self.device)
         if variant == "full":

@@ -249,3 +249,43 @@ def test_batched_score_equals_per_frame_score_and_leaves_renders_alone(fd):
         assert torch.equal(again[i], outs[i]), i
         assert torch.equal(again[i], sc.render(cams[i], ts[i], use_mask=False)), i
     sc.close()
+
+
+def test_score_pass_in_parts_and_resumed_equals_the_whole_pass(fd, tmp_path):
+    """fdgs_variation_score_add: a pass split into parts adds up to the whole pass; a pass
+    interrupted after its first part and resumed from its checkpoint gives the same scores
+    (up to the order of the float sums)."""
+    from paper_2503_16422_gb300 import checkpoint
+    s = scenes.make_scene(3000, 9, sh_degree=3, lt_short=(-4.0, 0.5), lt_long=(-2.0, 0.5),
+                          short_frac=0.7, name="ck")
+    sc = fd.Scene.from_host(s)
+    cams = [scenes.arc_camera(a, 96, 72) for a in (-8.0, 0.0, 8.0)]
+    ts = [0.05, 0.3, 0.55, 0.8, 0.95]
+    for batch in (1, 4):
+        want = sc.variation_score(cams, ts, batch=batch).cpu().numpy()
+        acc = torch.zeros(s.n, dtype=torch.float32, device="cuda")
+        for part in checkpoint.parts_of(ts, 2):
+            sc.variation_score(cams, part, batch=batch, out=acc, accumulate=True)
+        got = acc.cpu().numpy()
+        assert np.allclose(got, want, rtol=1e-5, atol=1e-7 * float(want.max()))
+    # interrupted after one part (the stand-in raises), then resumed by the library's pass
+    path = str(tmp_path / "score.npz")
+    parts = checkpoint.parts_of(ts, 2)
+    key = checkpoint.pass_key(s.n, cams, ts, "full", 4)
+
+    def first_only(i, scores):
+        if i > 0:
+            raise RuntimeError("interrupted")
+        acc = torch.as_tensor(scores).cuda()
+        sc.variation_score(cams, parts[i], batch=4, out=acc, accumulate=True)
+        return acc.cpu().numpy()
+    with pytest.raises(RuntimeError):
+        checkpoint.resumable_pass(path, key, s.n, parts, first_only)
+    assert checkpoint.describe(path)["done"] == 1
+    got = checkpoint.variation_score_resumable(sc, cams, ts, path, per_part=2, batch=4)
+    want = sc.variation_score(cams, ts, batch=4).cpu().numpy()
+    assert np.allclose(got.cpu().numpy(), want, rtol=1e-5, atol=1e-7 * float(want.max()))
+    assert checkpoint.describe(path)["done"] == len(parts)
+    with pytest.raises(ValueError):
+        sc.variation_score(cams, ts, accumulate=True)
+    sc.close()
