@@ -27,16 +27,21 @@ def _atomic_savez(path, **arrays):
     os.replace(tmp, path)
 
 
-def save_scene(path, scene) -> None:
+def _host(a):
+    if hasattr(a, "detach"):                # a torch tensor on any device
+        a = a.detach().cpu().numpy()
+    return np.asarray(a)
+
+
+def save_scene(path, scene, masks=None, key_times=None) -> None:
     """Write a scene's attribute arrays (host Scene, or device SceneTensors) to ``path``
-    (.npz)."""
-    arrays = {}
-    for f in SCENE_FIELDS:
-        a = getattr(scene, f)
-        if hasattr(a, "detach"):            # a torch tensor on any device
-            a = a.detach().cpu().numpy()
-        arrays[f] = np.ascontiguousarray(a, np.float32)
+    (.npz), with its key-frame active masks when given: the packed bits [n_key][ceil(n/8)]
+    (LSB-first, the layout of fdgs_set_active_mask) and the key-frame times."""
+    arrays = {f: np.ascontiguousarray(_host(getattr(scene, f)), np.float32) for f in SCENE_FIELDS}
     arrays["sh_degree"] = np.array(int(scene.sh_degree), np.int64)
+    if masks is not None:
+        arrays["mask_bits"] = np.ascontiguousarray(_host(masks), np.uint8)
+        arrays["key_times"] = np.ascontiguousarray(_host(key_times), np.float32)
     _atomic_savez(path, **arrays)
 
 
@@ -44,6 +49,14 @@ def load_scene(path, name="") -> Scene:
     """Read a scene written by save_scene (host arrays)."""
     with np.load(path) as z:
         return Scene(*(z[f].copy() for f in SCENE_FIELDS), int(z["sh_degree"]), name)
+
+
+def load_masks(path):
+    """The key-frame masks saved with a scene: (bits, key_times), or None if it has none."""
+    with np.load(path) as z:
+        if "mask_bits" not in z.files:
+            return None
+        return z["mask_bits"].copy(), z["key_times"].copy()
 
 
 def pass_key(n, cams, ts, variant, batch) -> str:

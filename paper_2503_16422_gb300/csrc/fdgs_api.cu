@@ -12,8 +12,16 @@
 
 #include "fdgs.h"
 #include "fdgs_internal.h"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace fdgs;
+
+// An NVTX range around each entry point's host work, for profilers that show them (ncu
+// --nvtx filters, Nsight Systems timelines); without a profiler attached it costs a call.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 namespace {
 
@@ -955,6 +963,7 @@ int fdgs_destroy_scene(fdgs_scene *s) {
 
 int fdgs_set_active_mask(fdgs_scene *s, const uint8_t *bits_dev, const float *key_times,
                          int n_key, fdgs_stream stream) {
+  NvtxRange nvtx_range_("fdgs_set_active_mask");
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   cudaStream_t st = (cudaStream_t)stream;
   if (n_key < 0) return fail(FDGS_ERR_INVALID, "n_key < 0");
@@ -983,6 +992,7 @@ int fdgs_set_active_mask(fdgs_scene *s, const uint8_t *bits_dev, const float *ke
 
 int fdgs_render(fdgs_scene *s, const fdgs_camera *cam, float t, const fdgs_render_opts *opts,
                 float *rgb_out_dev, fdgs_frame **frame_out, fdgs_stream stream) {
+  NvtxRange nvtx_range_("fdgs_render");
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   cudaStream_t st = (cudaStream_t)stream;
   if (frame_out) *frame_out = nullptr;
@@ -1005,6 +1015,7 @@ int fdgs_render(fdgs_scene *s, const fdgs_camera *cam, float t, const fdgs_rende
 
 int fdgs_render_async(fdgs_scene *s, const fdgs_camera *cam, float t,
                       const fdgs_render_opts *opts, float *rgb_out_dev, fdgs_stream stream) {
+  NvtxRange nvtx_range_("fdgs_render_async");
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   cudaStream_t st = (cudaStream_t)stream;
   DevCam dc;
@@ -1107,6 +1118,7 @@ int fdgs_frame_export(fdgs_frame *f, uint32_t *tile_ranges_dev, uint32_t *tile_i
 int fdgs_render_backward(fdgs_scene *s, fdgs_frame *f, const float *dL_drgb_dev,
                          float *g_mean4, float *g_logscale4, float *g_q_left, float *g_q_right,
                          float *g_opacity_logit, float *g_sh, fdgs_stream stream) {
+  NvtxRange nvtx_range_("fdgs_render_backward");
   if (!s || !f) return fail(FDGS_ERR_INVALID, "null argument");
   if (f->scene != s || !s->live.count(f)) return fail(FDGS_ERR_STATE, "frame not of this scene");
   if (!dL_drgb_dev) return fail(FDGS_ERR_INVALID, "null dL/drgb");
@@ -1169,6 +1181,7 @@ int fdgs_render_backward(fdgs_scene *s, fdgs_frame *f, const float *dL_drgb_dev,
 int fdgs_render_batch(fdgs_scene *s, const fdgs_camera *cams, const float *ts, int n_req,
                       const fdgs_render_opts *opts, float *const *rgb_out_dev,
                       fdgs_stream stream) {
+  NvtxRange nvtx_range_("fdgs_render_batch");
   TRY(batch_args_ok(s, cams, ts, n_req, rgb_out_dev));
   if (n_req == 0 || s->d.n == 0) {
     for (int i = 0; i < n_req; ++i) {   // empty scene: background only
@@ -1192,6 +1205,7 @@ int fdgs_render_batch(fdgs_scene *s, const fdgs_camera *cams, const float *ts, i
 int fdgs_batch_autotune(fdgs_scene *s, const fdgs_camera *cams, const float *ts, int n_req,
                         const fdgs_render_opts *opts, float *const *rgb_out_dev,
                         fdgs_stream stream) {
+  NvtxRange nvtx_range_("fdgs_batch_autotune");
   TRY(batch_args_ok(s, cams, ts, n_req, rgb_out_dev));
   if (n_req == 0 || s->d.n == 0) return FDGS_OK;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1258,6 +1272,7 @@ int fdgs_batch_info(fdgs_scene *s, float *latency_ms, int n, int *footprint,
 int fdgs_build_keyframe_masks(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
                               const float *key_times, int n_key, uint8_t *bits_out_dev,
                               fdgs_stream stream) {
+  NvtxRange nvtx_range_("fdgs_build_keyframe_masks");
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   if (n_cam < 0 || n_key < 0 || (n_key > 0 && (!key_times || !bits_out_dev)) ||
       (n_cam > 0 && !cams))
@@ -1468,6 +1483,7 @@ int score_impl(fdgs_scene *s, const fdgs_camera *cams, int n_cam, const float *t
                int batch, int variant, float *score_out_dev, bool zero, fdgs_stream stream);
 }  // namespace
 extern "C" {
+  NvtxRange nvtx_range_("fdgs_variation_score");
 
 int fdgs_variation_score_variant(fdgs_scene *s, const fdgs_camera *cams, int n_cam,
                                  const float *ts, int n_t, int batch, int variant,
@@ -1594,6 +1610,7 @@ extern "C" {
 
 int fdgs_select_keep(fdgs_scene *s, const float *score_dev, int64_t n, float prune_ratio,
                      uint8_t *keep_out_dev, fdgs_stream stream) {
+  NvtxRange nvtx_range_("fdgs_select_keep");
   if (!s || !score_dev || !keep_out_dev || n < 0 || n >= (1ll << 30))
     return fail(FDGS_ERR_INVALID, "bad keep-set arguments");
   if (!(prune_ratio >= 0.f && prune_ratio <= 1.f))
@@ -1632,6 +1649,7 @@ int fdgs_finetune_reset(fdgs_scene *s) {
 int fdgs_finetune_step(fdgs_scene *s, const fdgs_camera *cam, float t,
                        const fdgs_render_opts *opts, const float *target_dev,
                        const fdgs_adam_opts *adam, float *loss_accum_dev, fdgs_stream stream) {
+  NvtxRange nvtx_range_("fdgs_finetune_step");
   if (!s) return fail(FDGS_ERR_INVALID, "null scene");
   if (!cam || !target_dev || !adam) return fail(FDGS_ERR_INVALID, "null argument");
   if (!(adam->beta1 >= 0.f && adam->beta1 < 1.f && adam->beta2 >= 0.f && adam->beta2 < 1.f &&

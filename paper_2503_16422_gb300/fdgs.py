@@ -438,7 +438,27 @@ class Scene:
         return outs
 
     def batch_autotune(self, cams, ts, use_mask=True, bg=(0.0, 0.0, 0.0), outs=None,
-                       stream=None):
+                       stream=None, cache=None):
+        """fdgs_batch_autotune. With ``cache`` (a JSON file path) the launch shape is looked up
+        under the batch's key (autotune_key) first: on a hit it is set without a search and
+        the batch rendered once; on a miss the search runs and its pick is stored.
+        ``self.autotune_from_cache`` tells which happened."""
+        self.autotune_from_cache = False
+        key = None
+        if cache is not None:
+            key = autotune_key(cams, self.n, use_mask, bg, _device_name(self.device))
+            hit = read_autotune_cache(cache).get(key)
+            if hit is not None:
+                self.set_batch_shape(hit["footprint"], hit["ctas_per_sm"])
+                self.autotune_from_cache = True
+                return self.render_batch(cams, ts, use_mask, bg, outs, stream)
+        outs = self._batch_autotune(cams, ts, use_mask, bg, outs, stream)
+        if key is not None:
+            info = self.batch_info(0)
+            write_autotune_cache(cache, key, info["footprint"], info["ctas_per_sm"])
+        return outs
+
+    def _batch_autotune(self, cams, ts, use_mask, bg, outs, stream):
         n = len(cams)
         _ca, carr = make_cameras(cams)
         _ta, tarr = _times(ts)
@@ -616,6 +636,56 @@ def render(scene: Scene, cam, t, use_mask=True, bg=(0.0, 0.0, 0.0), tight=False)
     p = scene.params
     return _RenderFn.apply(scene, cam, float(t), use_mask, tuple(bg), bool(tight), p.mean4,
                            p.logscale4, p.q_left, p.q_right, p.opacity_logit, p.sh)
+
+
+def _device_name(device):
+    d = torch.device(device)
+    if d.type != "cuda":
+        return d.type
+    p = torch.cuda.get_device_properties(d)
+    return f"{p.name}/{p.multi_processor_count}sm"
+
+
+def autotune_key(cams, n_gauss, use_mask, bg, device_name) -> str:
+    """Key of a batch launch shape in the autotune cache: the GPU (name and SM count), the
+    request count, the multiset of tile-grid sizes of the requests (16x16 tiles, so images of
+    nearby sizes share an entry), the scene size rounded up to a power of two, the key-frame
+    filter and whether the background is black (the blend variant depends on it)."""
+    grids = sorted(((int(c.width) + 15) // 16, (int(c.height) + 15) // 16) for c in cams)
+    runs, prev, cnt = [], None, 0
+    for g in grids + [None]:
+        if g == prev:
+            cnt += 1
+            continue
+        if prev is not None:
+            runs.append(f"{prev[0]}x{prev[1]}*{cnt}")
+        prev, cnt = g, 1
+    n_pow2 = 1 << max(int(n_gauss) - 1, 0).bit_length()
+    black = all(float(v) == 0.0 for v in bg)
+    return "|".join([device_name, f"n_req={len(cams)}", "tiles=" + ",".join(runs),
+                     f"gauss<={n_pow2}", f"mask={int(bool(use_mask))}", f"black={int(black)}"])
+
+
+def read_autotune_cache(path) -> dict:
+    """The entries of an autotune cache file ({} if it does not exist or is unreadable)."""
+    import json
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    return d if isinstance(d, dict) else {}
+
+
+def write_autotune_cache(path, key, footprint, ctas_per_sm) -> None:
+    """Adds (or replaces) one entry; the file is rewritten atomically."""
+    import json
+    d = read_autotune_cache(path)
+    d[key] = {"footprint": int(footprint), "ctas_per_sm": int(ctas_per_sm)}
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 def version():

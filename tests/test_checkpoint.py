@@ -15,6 +15,13 @@ def test_scene_roundtrip(tmp_path):
     assert r.sh_degree == 3 and r.n == 500
     for f in checkpoint.SCENE_FIELDS:
         assert np.array_equal(getattr(r, f), getattr(s, f)), f
+    assert checkpoint.load_masks(path) is None
+    kt = scenes.keyframe_times()
+    bits = scenes.keyframe_masks(s, kt)
+    checkpoint.save_scene(path, s, masks=bits, key_times=kt)
+    got_bits, got_kt = checkpoint.load_masks(path)
+    assert np.array_equal(got_bits, bits) and np.array_equal(got_kt, kt.astype(np.float32))
+    assert np.array_equal(checkpoint.load_scene(path).sh, s.sh)
 
 
 def _part_adder(n, fail_at=None):

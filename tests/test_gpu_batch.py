@@ -70,6 +70,41 @@ def test_batch_autotune_and_background(fd):
     sc.close()
 
 
+def test_batch_autotune_cache(fd, tmp_path):
+    """The autotune cache: a miss searches and stores the pick under the batch's key; a hit
+    (another scene of a size in the same power-of-two bucket) sets that shape without a
+    search, and both give the per-request images."""
+    path = str(tmp_path / "shapes.json")
+    cams, ts = _requests(5, 4, [(320, 240), (250, 200)])
+    _, sc = _scene_gpu(fd, True, n=7000, seed=45)
+    try:
+        outs = sc.batch_autotune(cams, ts, cache=path)
+        assert not sc.autotune_from_cache
+        picked = sc.batch_info(4)
+        entries = fd.read_autotune_cache(path)
+        assert len(entries) == 1
+        (key, entry), = entries.items()
+        assert entry == {"footprint": picked["footprint"], "ctas_per_sm": picked["ctas_per_sm"]}
+        for i, (c, t) in enumerate(zip(cams, ts)):
+            assert torch.equal(outs[i], sc.render(c, t)), i
+        sc.close()
+        _, sc = _scene_gpu(fd, True, n=8000, seed=46)
+        sc.set_batch_shape(6 if entry["footprint"] != 6 else 5, 1)
+        outs = sc.batch_autotune(cams, ts, cache=path)
+        assert sc.autotune_from_cache
+        info = sc.batch_info(4)
+        assert (info["footprint"], info["ctas_per_sm"]) == (entry["footprint"],
+                                                            entry["ctas_per_sm"])
+        for i, (c, t) in enumerate(zip(cams, ts)):
+            assert torch.equal(outs[i], sc.render(c, t)), i
+        sc.batch_autotune(cams, ts, use_mask=False, cache=path)   # another key: a search
+        assert not sc.autotune_from_cache
+        assert len(fd.read_autotune_cache(path)) == 2
+    finally:
+        sc.set_batch_shape(6, 0)
+        sc.close()
+
+
 def test_every_batch_shape_gives_the_per_request_images(fd):
     """Each of the seven launch shapes of the batched blend (fdgs_set_batch_shape), at the
     occupancy limit and at a quarter of it, with a black background (the black-only kernel)
