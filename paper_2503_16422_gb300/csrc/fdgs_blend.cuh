@@ -26,11 +26,11 @@
 // The plain colour blend of the batched path (kTz) with an even PX evaluates the lane's pixels
 // in pairs with the paired FP32 instructions of sm_100-class GPUs (one fma.rn.f32x2 does the
 // two IEEE fmas of a pixel pair): the exponent, the weight, the transmittance step and the
-// colour sums of two pixels take one instruction each. Its tests become multiplications by
-// 0 or 1 (set.ge gives 1.0f or 0.0f), which pair too; every value is the one of the scalar
-// form bit for bit (x * 1 = x, a finite x * 0 = 0). The colour sums are kept negated
-// (fma(c, -w, -C) = -fma(c, w, C) exactly under round-to-nearest), so the weight's sign
-// needs no extra instruction per hit.
+// colour sums of two pixels take one instruction each. Its alpha floor becomes a
+// multiplication by 0 or 1 (set.ge gives 1.0f or 0.0f), which pairs too; every value is the
+// one of the scalar form bit for bit (x * 1 = x, a finite x * 0 = 0). The colour sums are
+// kept negated (fma(c, -w, -C) = -fma(c, w, C) exactly under round-to-nearest), so the
+// weight's sign needs no extra instruction per hit.
 #pragma once
 #include <type_traits>
 
@@ -111,6 +111,10 @@ struct BlendSmem {
   float4 h0[NT / 32][32];
   float4 h1[NT / 32][32];
   float2 h2[NT / 32][32];
+  // one-warp CTAs on block lists: the tile's entries (record indices) in list order, between
+  // the scan of the list and their staging (kRing of them, a power of two)
+  uint32_t ring[NT == 32 ? 256 : 1];
+  uint32_t cand[NT == 32 ? 128 : 1];   // ... and the entries of one scan with the tile's bit
 };
 
 // mbarrier and TMA helpers of the gather4 staging (shared-window addresses).
@@ -171,11 +175,17 @@ struct BlendTile {
 // kBlk: keys[range] is the list of the tile's block of tiles, entries (indices of 12-float
 // records) in rank order with a mask of the block's tiles each covers; only entries with bit
 // tbit are staged and tested (the others are flagged per thread and skip the tile test), and
-// the tile composites exactly its own list.
-// kTz (black background, no weights, counts or side outputs): a pixel that has stopped is
-// marked by T = 0 instead of a flag. Every later entry then gives alpha T = 0, so its colour
-// sums stay bit-for-bit the same, and the final C + T bg equals the flag form's C + T_stop bg
-// for bg = 0; the loop keeps no per-pixel flags.
+// the tile composites exactly its own list. One-warp CTAs (kCompact) stage only the tile's
+// hits, in full stages: the list is scanned 128 positions at a time; the entries with bit tbit
+// take the tile test on their records (read from global memory), and those that pass go to a
+// ring of record indices, from which every stage takes 32. The hits are then read straight
+// from the stage, with no test or hit list.
+// kTz (black background, no weights, counts or side outputs): the loop keeps no per-pixel
+// stop flags. T is updated at every entry, and an entry blends only when its T - alpha T is
+// at least 1e-4. T never grows, so the first entry that fails the test (the one that stops
+// the pixel) is followed only by entries that fail it too: the colour sums are those of the
+// flag form bit for bit, and the final T, which differs after a stop, is multiplied by the
+// black background. Pixels outside the image start at T = 0.
 // kTma (block lists only): records are staged by TMA gather4 (four per instruction, issued by
 // every fourth thread for its own entry and the next three) instead of per-thread cp.async;
 // tma_ph carries the two buffers' mbarrier phases across the tiles of a persistent CTA.
@@ -194,6 +204,9 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
   static_assert(!kTma || (kBlk && NT % 4 == 0), "kTma: block lists, whole chunks");
   // one warp covers the whole tile: a survivor of the tile test is a hit of the warp
   constexpr bool kWholeTile = FW == kTile && FH == kTile;
+  // one-warp CTAs on block lists with cp.async staging: compacted stages (see above)
+  constexpr bool kCompact = kBlk && !kTma && NT == 32;
+  static_assert(!kCompact || !kAux, "kCompact: no list positions");
   // CTA barriers; a one-warp CTA needs only warp-level ones
   auto cta_sync = [] {
     if constexpr (NT == 32) __syncwarp(); else __syncthreads();
@@ -337,6 +350,202 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
     }
   };
 
+  // Evaluation of nh hits of stage buffer st in list order: get(k, h0, h1, h2) reads hit k's
+  // record (h2.x the blue coefficient, h2.y the stage slot as an int); pos1 - 1 is the list
+  // position of the buffer's slot 0. The paired loop reads each next record one hit ahead.
+  auto run_hits = [&](int nh, int st, uint32_t pos1, auto get) {
+    if constexpr (kPair) {
+      float4 h0, h1;
+      float2 h2;
+      get(0, h0, h1, h2);
+      for (int k = 0; k < nh; ++k) {
+        float4 n0, n1;
+        float2 n2;
+        get(min(k + 1, 31), n0, n1, n2);
+        // row terms (shared by the lane's pixels), log2 opacity folded into the constant term
+        const float dy = __fsub_rn(h0.y, fpy);
+        const float b2dy = __fmul_rn(h0.w, dy);
+        const float c2l = __fmaf_rn(__fmul_rn(h1.x, dy), dy, h1.y);
+        const float2 uu = make_float2(h0.x, h0.x), aa = make_float2(h0.z, h0.z);
+        const float2 bd = make_float2(b2dy, b2dy), cl = make_float2(c2l, c2l);
+        const float2 cr = make_float2(h1.z, h1.z), cg = make_float2(h1.w, h1.w);
+        const float2 cb = make_float2(h2.x, h2.x);
+#pragma unroll
+        for (int q = 0; q < PH; ++q) {
+          const float2 dx = __fadd2_rn(uu, npx2[q]);
+          const float2 e = __ffma2_rn(dx, __ffma2_rn(aa, dx, bd), cl);
+          // -alpha = -min(0.99, 2^e) where e >= log2(1/255), else -0
+          const float2 ok = make_float2(set_ge(e.x, kLog2AlphaMin), set_ge(e.y, kLog2AlphaMin));
+          const float2 na = __fmul2_rn(make_float2(fmaxf(-kAlphaMax, -ex2_approx(e.x)),
+                                                   fmaxf(-kAlphaMax, -ex2_approx(e.y))), ok);
+          const float2 nw = __fmul2_rn(na, T2[q]);          // -alpha T
+          const float2 nT = __fadd2_rn(T2[q], nw);          // T - alpha T
+          // the entry that takes T below 1e-4 stops the pixel and blends nothing. T never
+          // grows (T - alpha T <= T), so it keeps being updated: every later entry finds
+          // T - alpha T below 1e-4 as well and blends nothing, as a stopped pixel must. A
+          // select on the test keeps the colour weight's product off the FMA pipe.
+          const bool k0 = nT.x >= kTStop, k1 = nT.y >= kTStop;
+          const float2 nwi = make_float2(k0 ? nw.x : 0.f, k1 ? nw.y : 0.f);   // -(weight)
+          C02[q] = __ffma2_rn(cr, nwi, C02[q]);     // the negated colour sums
+          C12[q] = __ffma2_rn(cg, nwi, C12[q]);
+          C22[q] = __ffma2_rn(cb, nwi, C22[q]);
+          T2[q] = nT;
+        }
+        h0 = n0;
+        h1 = n1;
+        h2 = n2;
+      }
+    } else {
+      for (int k = 0; k < nh; ++k) {
+        float4 h0, h1;
+        float2 h2;
+        get(k, h0, h1, h2);
+        // the row terms of the exponent are shared by the lane's pixels
+        const float dy = __fsub_rn(h0.y, fpy);
+        const float b2dy = __fmul_rn(h0.w, dy);
+        const float c2l = __fmaf_rn(__fmul_rn(h1.x, dy), dy, h1.y);
+        float w = 0.f;
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+          const float dx = __fsub_rn(h0.x, (float)(px0 + p * HW));
+          const float e = __fmaf_rn(dx, __fmaf_rn(h0.z, dx, b2dy), c2l);
+          if constexpr (kTz) {
+            const bool valid = e >= kLog2AlphaMin;
+            const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
+            const float wa = alpha * T[p];
+            const float nT = T[p] - wa;
+            // T keeps being updated after the stop: it never grows, so every later entry
+            // fails the test too and blends nothing
+            const bool stop = nT < kTStop;
+            const float wi = stop ? 0.f : wa;
+            C0[p] = fmaf(h1.z, wi, C0[p]);
+            C1[p] = fmaf(h1.w, wi, C1[p]);
+            C2[p] = fmaf(h2.x, wi, C2[p]);
+            T[p] = nT;
+            continue;
+          }
+          const bool valid = !done[p] && e >= kLog2AlphaMin;
+          if (kCount && !done[p]) ++nevals;
+          if (kCount && valid) ++npass;
+          const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
+          // Eq. 2's transmittance step T (1 - alpha), taken as T - alpha T: the weight alpha T
+          // is needed anyway, so this saves the subtraction 1 - alpha
+          const float wa = alpha * T[p];
+          const float nT = T[p] - wa;
+          // only a valid entry can stop a pixel: an unfinished pixel has T >= kTStop
+          const bool stop = nT < kTStop;
+          // the entry that ends this pixel's list: the key-frame masks keep it
+          if (kWeights && stop) bt.stop_mark[sm.rk[st][__float_as_int(h2.y)]] = 1u;
+          done[p] = done[p] || stop;
+          const bool use = valid && !stop;
+          const float wi = stop ? 0.f : wa;
+          C0[p] = fmaf(h1.z, wi, C0[p]);
+          C1[p] = fmaf(h1.w, wi, C1[p]);
+          C2[p] = fmaf(h2.x, wi, C2[p]);
+          T[p] = use ? nT : T[p];
+          if (kAux) last[p] = use ? pos1 + (uint32_t)__float_as_int(h2.y) : last[p];
+          if (kWeights) w += wi;
+        }
+        if (kWeights) {
+          if (__any_sync(0xffffffffu, w != 0.f)) {
+            const float s = warp_sum(w);
+            if (lane == 0) atomicAdd(&bt.w_sum[sm.rk[st][__float_as_int(h2.y)]], s);
+          }
+        }
+      }
+    }
+  };
+  auto check_done = [&] {
+    lane_done = true;
+#pragma unroll
+    for (int p = 0; p < PX; ++p) {
+      if constexpr (kPair)
+        lane_done = lane_done && ((p & 1) ? T2[p >> 1].y : T2[p >> 1].x) < kTStop;
+      else
+        lane_done = lane_done && (kTz ? T[p] < kTStop : done[p]);
+    }
+    warp_done = __all_sync(0xffffffffu, lane_done);
+  };
+
+  if constexpr (kCompact) {
+    // ring of the tile's hits, filled 128 list positions at a time while fewer than 32 wait:
+    // at most 159 are held, so a slot is rewritten only after its stage has read it
+    constexpr uint32_t kRing = 256;
+    uint32_t sp = 0, rh = 0, rt = 0;   // list positions scanned; ring entries read, written
+    auto refill = [&] {
+      while (rt - rh < 32u && sp < n) {
+        uint32_t kk[4], tw[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const uint32_t i = sp + (uint32_t)(32 * g) + (uint32_t)lane;
+          kk[g] = i < n ? keys[bt.range.x + i] : (K)0;
+          tw[g] = i < n ? bt.tmask[bt.range.x + i] : 0u;
+        }
+        // the entries with the tile's bit, in list order
+        uint32_t nc = 0;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const bool cv = (tw[g] >> bt.tbit) & 1u;
+          const uint32_t bm = __ballot_sync(0xffffffffu, cv);
+          if (cv) sm.cand[nc + __popc(bm & lanemask_lt())] = (uint32_t)(kk[g] & (K)rmask);
+          nc += __popc(bm);
+        }
+        sp += 128;
+        __syncwarp();
+        // their tile tests, 32 at a time; the hits go to the ring in order
+        for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
+          bool hit = false;
+          uint32_t r = 0;
+          if (c0 + (uint32_t)lane < nc) {
+            if (kCount) ++ntests;
+            r = sm.cand[c0 + lane];
+            const float4 *rp = reinterpret_cast<const float4 *>(bt.rec_sorted + (size_t)r * kRec);
+            const float4 g0 = __ldg(rp), g1 = __ldg(rp + 1), g2 = __ldg(rp + 2);
+            hit = may_hit_rect(g0, g1.x, g1.y, g2.y, g2.z, tx0, tx0 + (kTile - 1), ty0,
+                               ty0 + (kTile - 1));
+          }
+          const uint32_t bm = __ballot_sync(0xffffffffu, hit);
+          if (hit) sm.ring[(rt + __popc(bm & lanemask_lt())) & (kRing - 1)] = r;
+          rt += __popc(bm);
+        }
+        __syncwarp();                    // the candidates are rewritten by the next scan
+      }
+    };
+    // stages the next (up to) 32 ring entries into buffer st; one commit group each call
+    auto issue_c = [&](int st) -> int {
+      const uint32_t c = min(32u, rt - rh);
+      if ((uint32_t)lane < c) {
+        const uint32_t r = sm.ring[(rh + lane) & (kRing - 1)];
+        const float *rp = bt.rec_sorted + (size_t)r * kRec;
+        cp_async16(&sm.stage.g0[st][lane], rp);
+        cp_async16(&sm.stage.g1[st][lane], rp + 4);
+        cp_async16(&sm.stage.g2[st][lane], rp + 8);
+        if (kWeights) sm.rk[st][lane] = r;
+      }
+      cp_async_commit();
+      rh += c;
+      return (int)c;
+    };
+    refill();
+    int cnt = issue_c(0);
+    refill();
+    for (int b = 0; cnt > 0 && !warp_done; ++b) {
+      const int st = b & 1;
+      const int cnt_next = issue_c(st ^ 1);
+      refill();                          // the entries of the stage after it
+      cp_async_wait<1>();
+      __syncwarp();
+      run_hits(cnt, st, 0u, [&](int k, float4 &a, float4 &b4, float2 &c) {
+        a = sm.stage.g0[st][k];
+        b4 = sm.stage.g1[st][k];
+        c = make_float2(sm.stage.g2[st][k].x, __int_as_float(k));
+      });
+      check_done();
+      __syncwarp();                      // buffer st is staged into again by the next call
+      cnt = cnt_next;
+    }
+    cp_async_wait<0>();
+  } else {
   if (nb > 0) {
     load_key(0);
     issue(0);
@@ -411,107 +620,13 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
       }
       __syncwarp();
       const int nh = __popc(m);
-      if constexpr (kPair) {
-        for (int k = 0; k < nh; ++k) {
-          const float4 h0 = sm.h0[warp][k];
-          const float4 h1 = sm.h1[warp][k];
-          const float2 h2 = sm.h2[warp][k];
-          // row terms (shared by the lane's pixels), log2 opacity folded into the constant term
-          const float dy = __fsub_rn(h0.y, fpy);
-          const float b2dy = __fmul_rn(h0.w, dy);
-          const float c2l = __fmaf_rn(__fmul_rn(h1.x, dy), dy, h1.y);
-          const float2 uu = make_float2(h0.x, h0.x), aa = make_float2(h0.z, h0.z);
-          const float2 bd = make_float2(b2dy, b2dy), cl = make_float2(c2l, c2l);
-          const float2 cr = make_float2(h1.z, h1.z), cg = make_float2(h1.w, h1.w);
-          const float2 cb = make_float2(h2.x, h2.x);
-#pragma unroll
-          for (int q = 0; q < PH; ++q) {
-            const float2 dx = __fadd2_rn(uu, npx2[q]);
-            const float2 e = __ffma2_rn(dx, __ffma2_rn(aa, dx, bd), cl);
-            // -alpha = -min(0.99, 2^e) where e >= log2(1/255), else -0
-            const float2 ok = make_float2(set_ge(e.x, kLog2AlphaMin), set_ge(e.y, kLog2AlphaMin));
-            const float2 na = __fmul2_rn(make_float2(fmaxf(-kAlphaMax, -ex2_approx(e.x)),
-                                                     fmaxf(-kAlphaMax, -ex2_approx(e.y))), ok);
-            const float2 nw = __fmul2_rn(na, T2[q]);          // -alpha T
-            const float2 nT = __fadd2_rn(T2[q], nw);          // T - alpha T
-            // a pixel stops (T = 0, no colour) at the entry that takes T below 1e-4, and a
-            // stopped pixel stops again at every later entry; selects on the stop test keep
-            // these two products off the FMA pipe (0 * x and x * 1 give the same values)
-            const bool k0 = nT.x >= kTStop, k1 = nT.y >= kTStop;
-            const float2 nwi = make_float2(k0 ? nw.x : 0.f, k1 ? nw.y : 0.f);   // -(weight)
-            C02[q] = __ffma2_rn(cr, nwi, C02[q]);     // the negated colour sums
-            C12[q] = __ffma2_rn(cg, nwi, C12[q]);
-            C22[q] = __ffma2_rn(cb, nwi, C22[q]);
-            T2[q] = make_float2(k0 ? nT.x : 0.f, k1 ? nT.y : 0.f);
-          }
-        }
-      } else
-      for (int k = 0; k < nh; ++k) {
-        const float4 h0 = sm.h0[warp][k];
-        const float4 h1 = sm.h1[warp][k];
-        const float2 h2 = sm.h2[warp][k];
-        // the row terms of the exponent are shared by the lane's pixels
-        const float dy = __fsub_rn(h0.y, fpy);
-        const float b2dy = __fmul_rn(h0.w, dy);
-        const float c2l = __fmaf_rn(__fmul_rn(h1.x, dy), dy, h1.y);
-        float w = 0.f;
-#pragma unroll
-        for (int p = 0; p < PX; ++p) {
-          const float dx = __fsub_rn(h0.x, (float)(px0 + p * HW));
-          const float e = __fmaf_rn(dx, __fmaf_rn(h0.z, dx, b2dy), c2l);
-          if constexpr (kTz) {
-            const bool valid = e >= kLog2AlphaMin;
-            const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
-            const float wa = alpha * T[p];
-            const float nT = T[p] - wa;
-            // a stopped pixel (T = 0) stops again at every entry and blends nothing
-            const bool stop = nT < kTStop;
-            const float wi = stop ? 0.f : wa;
-            C0[p] = fmaf(h1.z, wi, C0[p]);
-            C1[p] = fmaf(h1.w, wi, C1[p]);
-            C2[p] = fmaf(h2.x, wi, C2[p]);
-            T[p] = stop ? 0.f : nT;
-            continue;
-          }
-          const bool valid = !done[p] && e >= kLog2AlphaMin;
-          if (kCount && !done[p]) ++nevals;
-          if (kCount && valid) ++npass;
-          const float alpha = valid ? fminf(kAlphaMax, ex2_approx(e)) : 0.f;
-          // Eq. 2's transmittance step T (1 - alpha), taken as T - alpha T: the weight alpha T
-          // is needed anyway, so this saves the subtraction 1 - alpha
-          const float wa = alpha * T[p];
-          const float nT = T[p] - wa;
-          // only a valid entry can stop a pixel: an unfinished pixel has T >= kTStop
-          const bool stop = nT < kTStop;
-          // the entry that ends this pixel's list: the key-frame masks keep it
-          if (kWeights && stop) bt.stop_mark[sm.rk[st][__float_as_int(h2.y)]] = 1u;
-          done[p] = done[p] || stop;
-          const bool use = valid && !stop;
-          const float wi = stop ? 0.f : wa;
-          C0[p] = fmaf(h1.z, wi, C0[p]);
-          C1[p] = fmaf(h1.w, wi, C1[p]);
-          C2[p] = fmaf(h2.x, wi, C2[p]);
-          T[p] = use ? nT : T[p];
-          if (kAux) last[p] = use ? pos1 + (uint32_t)__float_as_int(h2.y) : last[p];
-          if (kWeights) w += wi;
-        }
-        if (kWeights) {
-          if (__any_sync(0xffffffffu, w != 0.f)) {
-            const float s = warp_sum(w);
-            if (lane == 0) atomicAdd(&bt.w_sum[sm.rk[st][__float_as_int(h2.y)]], s);
-          }
-        }
-      }
+      run_hits(nh, st, pos1, [&](int k, float4 &a, float4 &b4, float2 &c) {
+        a = sm.h0[warp][k];
+        b4 = sm.h1[warp][k];
+        c = sm.h2[warp][k];
+      });
       __syncwarp();                    // the list is rewritten by the next round
-      lane_done = true;
-#pragma unroll
-      for (int p = 0; p < PX; ++p) {
-        if constexpr (kPair)
-          lane_done = lane_done && ((p & 1) ? T2[p >> 1].y : T2[p >> 1].x) == 0.f;
-        else
-          lane_done = lane_done && (kTz ? T[p] == 0.f : done[p]);
-      }
-      warp_done = __all_sync(0xffffffffu, lane_done);
+      check_done();
     }
     if (cta_and(warp_done)) {
       if constexpr (kTma) {
@@ -525,6 +640,7 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
       }
       break;
     }
+  }
   }
   if (kCount) {
     const uint32_t ws = warp_sum(nevals), wt = warp_sum(ntests), wp = warp_sum(npass);
