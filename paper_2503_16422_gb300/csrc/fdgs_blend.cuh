@@ -26,11 +26,9 @@
 // The plain colour blend of the batched path (kTz) with an even PX evaluates the lane's pixels
 // in pairs with the paired FP32 instructions of sm_100-class GPUs (one fma.rn.f32x2 does the
 // two IEEE fmas of a pixel pair): the exponent, the weight, the transmittance step and the
-// colour sums of two pixels take one instruction each. Its alpha floor becomes a
-// multiplication by 0 or 1 (set.ge gives 1.0f or 0.0f), which pairs too; every value is the
-// one of the scalar form bit for bit (x * 1 = x, a finite x * 0 = 0). The colour sums are
-// kept negated (fma(c, -w, -C) = -fma(c, w, C) exactly under round-to-nearest), so the
-// weight's sign needs no extra instruction per hit.
+// colour sums of two pixels take one instruction each; every value is the one of the scalar
+// form bit for bit. The colour sums are kept negated (fma(c, -w, -C) = -fma(c, w, C) exactly
+// under round-to-nearest), so the weight's sign needs no extra instruction per hit.
 #pragma once
 #include <type_traits>
 
@@ -53,13 +51,6 @@ inline void with_blend_shape(int shape, F &&f) {
     case 6: f(std::integral_constant<int, 16>{}, std::integral_constant<int, 8>{}); break;
     default: f(std::integral_constant<int, 8>{}, std::integral_constant<int, 1>{}); break;
   }
-}
-
-// 1.0f if a >= b, else 0.0f (one FSET; a multiplier that pairs with f32x2 instructions).
-__device__ __forceinline__ float set_ge(float a, float b) {
-  float r;
-  asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
-  return r;
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -374,10 +365,11 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
         for (int q = 0; q < PH; ++q) {
           const float2 dx = __fadd2_rn(uu, npx2[q]);
           const float2 e = __ffma2_rn(dx, __ffma2_rn(aa, dx, bd), cl);
-          // -alpha = -min(0.99, 2^e) where e >= log2(1/255), else -0
-          const float2 ok = make_float2(set_ge(e.x, kLog2AlphaMin), set_ge(e.y, kLog2AlphaMin));
-          const float2 na = __fmul2_rn(make_float2(fmaxf(-kAlphaMax, -ex2_approx(e.x)),
-                                                   fmaxf(-kAlphaMax, -ex2_approx(e.y))), ok);
+          // -alpha = -min(0.99, 2^e) where e >= log2(1/255), else -0 (the 0 that a 0/1 multiplier
+          // would give; a select keeps it off the FMA pipe, the busiest here)
+          const float2 na = make_float2(
+              e.x >= kLog2AlphaMin ? fmaxf(-kAlphaMax, -ex2_approx(e.x)) : -0.f,
+              e.y >= kLog2AlphaMin ? fmaxf(-kAlphaMax, -ex2_approx(e.y)) : -0.f);
           const float2 nw = __fmul2_rn(na, T2[q]);          // -alpha T
           const float2 nT = __fadd2_rn(T2[q], nw);          // T - alpha T
           // the entry that takes T below 1e-4 stops the pixel and blends nothing. T never
