@@ -524,7 +524,6 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
     for (int b = 0; cnt > 0 && !warp_done; ++b) {
       const int st = b & 1;
       const int cnt_next = issue_c(st ^ 1);
-      refill();                          // the entries of the stage after it
       cp_async_wait<1>();
       __syncwarp();
       run_hits(cnt, st, 0u, [&](int k, float4 &a, float4 &b4, float2 &c) {
@@ -533,6 +532,7 @@ __device__ __forceinline__ bool blend_tile(const BlendTile &bt, const K *__restr
         c = make_float2(sm.stage.g2[st][k].x, __int_as_float(k));
       });
       check_done();
+      if (!warp_done) refill();          // the entries of the stage after the next
       __syncwarp();                      // buffer st is staged into again by the next call
       cnt = cnt_next;
     }
