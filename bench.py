@@ -583,13 +583,18 @@ def run_ours(args):
     per = (B + E2E_COPY_STREAMS - 1) // E2E_COPY_STREAMS
     # the copies are spread over several streams so that several copy engines run at once
     copy_streams = [torch.cuda.Stream() for _ in range(E2E_COPY_STREAMS)]
+    serve_log = {"step_ms": [], "copy_wait_ms": []}
     def serve(step_list):
         copied = [None, None]
+        serve_log["step_ms"].clear()
+        serve_log["copy_wait_ms"].clear()
         for i, (c_, t_) in enumerate(step_list):
             j = i % 2
+            ts0 = time.perf_counter()
             if copied[j] is not None:
                 for ev in copied[j]:
                     ev.synchronize()              # the copy out of this image set finished
+            serve_log["copy_wait_ms"].append((time.perf_counter() - ts0) * 1e3)
             sc.render_batch(c_, t_, outs=outs2[j])  # returns with the batch rendered
             copied[j] = []
             for k, cs in enumerate(copy_streams):
@@ -600,6 +605,7 @@ def run_ours(args):
                     ev = torch.cuda.Event()
                     ev.record(cs)
                     copied[j].append(ev)
+            serve_log["step_ms"].append((time.perf_counter() - ts0) * 1e3)
         for cs in copy_streams:
             cs.synchronize()
 
@@ -624,7 +630,14 @@ def run_ours(args):
     for cs in copy_streams:
         cs.synchronize()
     d2h_gbs = B * 3 * H_FULL * W_FULL * 4 / (time.perf_counter() - tl) / 1e9
-    res["e2e"] = dict(value=e2e_fps, unit="FPS", d2h_copy_gbs=d2h_gbs,
+    # per timed step (host clock): the whole step and the wait for the copy out of the image
+    # set it renders into (issued two steps before); a copy that did not overlap the render
+    # shows up as a long wait
+    st_ms, cw_ms = serve_log["step_ms"], serve_log["copy_wait_ms"]
+    step_diag = {"step_ms_median": statistics.median(st_ms), "step_ms_max": max(st_ms),
+                 "copy_wait_ms_median": statistics.median(cw_ms),
+                 "copy_wait_ms_max": max(cw_ms)} if st_ms else {}
+    res["e2e"] = dict(value=e2e_fps, unit="FPS", d2h_copy_gbs=d2h_gbs, **step_diag,
                       h2d_bytes_per_step=B * (16 * 4 + 8 * 4 + 4),
                       d2h_bytes_per_step=B * 3 * H_FULL * W_FULL * 4,
                       overlap="device->host copy of step i (on %d streams) with the render "
